@@ -1,0 +1,236 @@
+"""The electrostatic global-placement iteration (Eq. 2 minimised by Nesterov's
+method with a Lipschitz step estimate), float64.
+
+Test infrastructure only (see ``oracle/__init__.py``).
+
+Algorithm 1 runs "DREAMPlace for global placement ... until it reaches
+convergence"; Eq. 2 is the objective sum_e WL_e + lambda D, with lambda small
+at the start (Section 3.1).  The optimiser, the schedules and the stop test are
+cited (ePlace, "... Nesterov's method") but not restated.  The reading below is
+the one the CUDA library implements; every constant is a field of ``Params``.
+
+Iteration k at reference point v_k (movable lower-left corners):
+
+    gamma_k = gamma_base * w_bin * 10^((20/9) tau_{k-1} - 11/9)
+    WL, gWL  = weighted-average wirelength and gradient at v_k (Eq. 3)
+    M_k, tau_k = density map and overflow at v_k; stop here if tau_k <= tau_stop
+    rho -> (psi, E); gD = field gather at v_k
+    k == 0:  lambda = eta * |gWL|_1 / |gD|_1
+    P_i = max(1, pins_i + lambda * area_i)
+    g_k = (gWL + lambda gD) / P
+    alpha_k = alpha0 * w_bin / rms(g_0)                       (k == 0)
+            = |v_k - v_{k-1}|_2 / |g_k - g_{k-1}|_2           (k >= 1)
+    u_{k+1} = clamp(v_k - alpha_k g_k)
+    a_{k+1} = (1 + sqrt(4 a_k^2 + 1)) / 2
+    v_{k+1} = clamp(u_{k+1} + (a_k - 1)/a_{k+1} (u_{k+1} - u_k))
+    k >= 1:  lambda *= clamp(mu_base^(1 - (HPWL_k - HPWL_{k-1}) / dref), mu_lo, mu_hi)
+
+with a_0 = 1, u_0 = v_0 = the start, tau_{-1} = tau(v_0),
+dref = hpwl_ref * n_nets * w_bin, w_bin = sqrt(bin_w * bin_h), and clamp
+keeping each cell inside the die (x in [xl, xh - w]).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from . import density as dens
+from . import poisson as pois
+from . import wirelength as wlm
+
+
+def lipschitz_step(v, v_prev, g, g_prev, alpha_prev):
+    """Inverse-Lipschitz step estimate |v - v_prev|_2 / |g - g_prev|_2 over
+    all coordinates; keeps the previous step when the gradients coincide."""
+    num = math.sqrt(sum(float(np.sum((a - b) ** 2)) for a, b in zip(v, v_prev)))
+    den = math.sqrt(sum(float(np.sum((a - b) ** 2)) for a, b in zip(g, g_prev)))
+    return num / den if den > 0 else alpha_prev
+
+
+def nesterov_update(v, u, g, a, alpha, clamp):
+    """One Nesterov step from reference point v with major point u:
+    u' = clamp(v - alpha g), a' = (1 + sqrt(4a^2 + 1))/2,
+    v' = clamp(u' + (a - 1)/a' (u' - u)).  v, u, g are tuples of arrays."""
+    u_new = clamp(*[vi - alpha * gi for vi, gi in zip(v, g)])
+    a_new = (1.0 + math.sqrt(4.0 * a * a + 1.0)) / 2.0
+    coef = (a - 1.0) / a_new
+    v_new = clamp(*[un + coef * (un - uo) for un, uo in zip(u_new, u)])
+    return u_new, v_new, a_new
+
+
+def lambda_multiplier(d_hpwl, dref, mu_base, mu_lo, mu_hi):
+    """Density-weight growth factor mu = clamp(mu_base^(1 - dHPWL/dref),
+    mu_lo, mu_hi): lambda grows fastest while the wirelength is flat and
+    shrinks when the wirelength rises faster than dref per iteration."""
+    mu = mu_base ** (1.0 - d_hpwl / dref)
+    return min(max(mu, mu_lo), mu_hi)
+
+
+@dataclasses.dataclass
+class Params:
+    gamma_base: float = 4.0
+    lambda_eta: float = 1e-3
+    alpha0: float = 0.05
+    hpwl_ref: float = 0.1
+    mu_base: float = 1.1
+    mu_lo: float = 0.95
+    mu_hi: float = 1.05
+    tau_stop: float = 0.07
+    max_iters: int = 1000
+    constant_gamma: float = 0.0  # > 0: use this gamma every iteration
+
+
+class Placer:
+    """FP64 placer state for one design."""
+
+    def __init__(self, design, params: Params | None = None):
+        self.d = design
+        self.p = params or Params()
+        d = design
+        self.n = d.n_movable
+        self.w = d.w.astype(np.float64)
+        self.h = d.h.astype(np.float64)
+        total_area = float(np.sum(self.w * self.h))
+        self.F = dens.frac_bits(d.die, total_area)
+        self.g = dens.Grid(d.die, d.nx, d.ny, self.F)
+        self.t = float(np.float32(d.target_density))
+        self.W = dens.quantize(d.w, self.F)
+        self.H = dens.quantize(d.h, self.F)
+        fx = dens.quantize(d.x[self.n:], self.F)
+        fy = dens.quantize(d.y[self.n:], self.F)
+        self.Fmap = dens.overlap_map(fx, fy, self.W[self.n:], self.H[self.n:], self.g)
+        self.mov_area_q = int(np.sum(self.W[:self.n] * self.H[:self.n]))
+        self.fixed_x = d.x[self.n:].astype(np.float64)
+        self.fixed_y = d.y[self.n:].astype(np.float64)
+        pc = d.pin_cell.astype(np.int64)
+        self.pins = np.bincount(pc[pc < self.n], minlength=self.n).astype(np.float64)
+        self.area = self.w[:self.n] * self.h[:self.n]
+        self.w_bin = math.sqrt(self.g.bin_w * self.g.bin_h)
+        self.dref = self.p.hpwl_ref * d.n_nets * self.w_bin
+        self.reset(d.x[:self.n], d.y[:self.n])
+
+    # -- helpers -----------------------------------------------------------
+    def clamp(self, x, y):
+        xl, yl, xh, yh = self.g.die
+        x = np.maximum(xl, np.minimum(x, xh - self.w[:self.n]))
+        y = np.maximum(yl, np.minimum(y, yh - self.h[:self.n]))
+        return x, y
+
+    def full(self, x, y):
+        return (np.concatenate([x, self.fixed_x]), np.concatenate([y, self.fixed_y]))
+
+    def density_map(self, x, y):
+        X = dens.quantize(x, self.F)
+        Y = dens.quantize(y, self.F)
+        return dens.overlap_map(X, Y, self.W[:self.n], self.H[:self.n], self.g)
+
+    def overflow(self, M):
+        return dens.overflow(M, self.Fmap, self.t, self.g, self.mov_area_q)
+
+    def hpwl(self, x, y):
+        fx, fy = self.full(x, y)
+        d = self.d
+        return wlm.hpwl(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, fx, fy)
+
+    def gamma(self, tau):
+        if self.p.constant_gamma > 0:
+            return self.p.constant_gamma
+        return self.p.gamma_base * self.w_bin * 10.0 ** ((20.0 / 9.0) * tau - 11.0 / 9.0)
+
+    def field(self, M):
+        rho = dens.bin_density(M, self.Fmap, self.t, self.g)
+        return pois.poisson(rho, self.g.bin_w, self.g.bin_h)
+
+    def wirelength(self, x, y, gamma):
+        fx, fy = self.full(x, y)
+        d = self.d
+        return wlm.wa_wirelength(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, fx, fy,
+                                 gamma, self.n)
+
+    def density_grad(self, x, y, ex, ey):
+        X = dens.quantize(x, self.F)
+        Y = dens.quantize(y, self.F)
+        return dens.field_gather(X, Y, self.W[:self.n], self.H[:self.n], self.g, ex, ey)
+
+    # -- optimiser ------------------------------------------------------------
+    def reset(self, x, y):
+        """Restart the optimiser from movable positions (x, y)."""
+        x = np.asarray(x, np.float64).copy()
+        y = np.asarray(y, np.float64).copy()
+        x, y = self.clamp(x, y)
+        self.ux, self.uy = x.copy(), y.copy()
+        self.vx, self.vy = x.copy(), y.copy()
+        self.a = 1.0
+        self.k = 0
+        self.lam = 0.0
+        self.alpha = 0.0
+        self.vpx = self.vpy = self.gpx = self.gpy = None
+        self.hpwl_prev = 0.0
+        self.tau_prev = self.overflow(self.density_map(x, y))
+        self.tau = self.tau_prev
+        self.converged = False
+        self.stopped = False
+        self.history = []
+
+    def step(self):
+        """One iteration at v_k.  Returns False once stopped."""
+        if self.stopped:
+            return False
+        if self.k >= self.p.max_iters:
+            self.stopped = True
+            return False
+        p = self.p
+        gamma = self.gamma(self.tau_prev)
+        vx, vy = self.vx, self.vy
+        wl, gwx, gwy = self.wirelength(vx, vy, gamma)
+        hp = self.hpwl(vx, vy)
+        M = self.density_map(vx, vy)
+        tau = self.overflow(M)
+        self.tau = tau
+        self.history.append((self.k, hp, tau, gamma, self.lam))
+        if tau <= p.tau_stop:
+            self.converged = self.stopped = True
+            return False
+        _, ex, ey = self.field(M)
+        gdx, gdy = self.density_grad(vx, vy, ex, ey)
+        if self.k == 0:
+            n1 = np.sum(np.abs(gwx)) + np.sum(np.abs(gwy))
+            d1 = np.sum(np.abs(gdx)) + np.sum(np.abs(gdy))
+            self.lam = p.lambda_eta * n1 / d1 if d1 > 0 else p.lambda_eta
+        lam = self.lam
+        prec = np.maximum(1.0, self.pins + lam * self.area)
+        gx = (gwx + lam * gdx) / prec
+        gy = (gwy + lam * gdy) / prec
+        if self.k == 0:
+            gn = math.sqrt((np.sum(gx * gx) + np.sum(gy * gy)) / (2 * self.n))
+            alpha = p.alpha0 * self.w_bin / gn if gn > 0 else 0.0
+        else:
+            alpha = lipschitz_step((vx, vy), (self.vpx, self.vpy), (gx, gy),
+                                   (self.gpx, self.gpy), self.alpha)
+        self.alpha = alpha
+        (nux, nuy), (nvx, nvy), a_new = nesterov_update(
+            (vx, vy), (self.ux, self.uy), (gx, gy), self.a, alpha, self.clamp)
+        if self.k >= 1:
+            self.lam = lam * lambda_multiplier(hp - self.hpwl_prev, self.dref,
+                                               p.mu_base, p.mu_lo, p.mu_hi)
+        self.hpwl_prev = hp
+        self.tau_prev = tau
+        self.vpx, self.vpy, self.gpx, self.gpy = vx, vy, gx, gy
+        self.ux, self.uy = nux, nuy
+        self.vx, self.vy = nvx, nvy
+        self.a = a_new
+        self.k += 1
+        return True
+
+    def run(self, n_iters=None):
+        n = self.p.max_iters if n_iters is None else n_iters
+        for _ in range(n):
+            if not self.step():
+                break
+        return self
+
+    def positions(self):
+        """Current solution (the reference point v) for all cells."""
+        return self.full(self.vx, self.vy)
