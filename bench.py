@@ -1,0 +1,351 @@
+"""Benchmark of the electrostatic global-placement inner loop on GB300.
+
+One step = one Nesterov iteration of Eq. 2 over the whole hot path: density
+scatter and overflow, the spectral Poisson solve, WA wirelength and
+gradients (Eq. 3), per-cell gradient assembly, preconditioned
+Nesterov/Lipschitz update, all copies of the design (Algorithm 1 line 3).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload large_2m|medium_210k|tiny_1k]
+
+Prints one JSON line (rank 0).  For N > 1 (torchrun) every rank places its own
+replica of the design: the design does not shard (the density map and the
+Poisson solve are global per iteration), so the ranks are independent and
+``value`` is the sum of their iterations/s (weak scaling, no collective on
+the data path).
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload (host cores of this machine).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2402_18311_gb300 import synth  # noqa: E402
+
+METRIC = "Nesterov iters/s @2M cells"
+WORKLOADS = {
+    "large_2m": (synth.large_2m, "2.1M movable cells, 60 fixed macros (30% area), 2.2M nets "
+                 "(12.0M pins, max degree 5000), 4096x4096 die, 1024x1024 bins, t=0.7"),
+    "medium_210k": (synth.medium_210k, "210k movable cells, 10 fixed macros (20% area), 220k "
+                    "nets (1.18M pins), 2000x2000 die, 512x512 bins, t=0.9"),
+    "tiny_1k": (synth.tiny_1k, "1k movable cells, 16 pads, 1.1k nets, 256x256 die, 64x64 bins, t=1.0"),
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def algorithmic(d, info):
+    """Algorithmic bytes / flops of one iteration per stage (one copy)."""
+    C, P, E, G = d.n_movable, d.n_pins, d.n_nets, d.nx * d.ny
+    n_all = d.n_cells
+    mov_pins = int(np.sum(d.pin_cell < d.n_movable))
+    return {
+        # scatter: x, y, W, H per cell (16 B), map clear + atomics 8 B/bin written,
+        # finish: map + fixed map read 16 B/bin, rho written 4 B/bin
+        "density": {"bytes": 16 * C + 8 * G + 16 * G + 4 * G},
+        # six M^3-type GEMMs (two per 2D transform: forward, Ex, Ey)
+        "spectral": {"flops": 2.0 * (2 * d.ny * d.ny * d.nx + 2 * d.nx * d.nx * d.ny) * 1.5},
+        # pin_cell 4 + offsets 8 + gradient write 8 per pin, net_ptr 4 per net,
+        # positions 8 per cell (gathered once)
+        "wirelength": {"bytes": 20 * P + 4 * E + 8 * n_all},
+        # cell->pin index 4 + pin gradient 8 per movable pin, 4 + 8 B/cell of
+        # index and size, positions 8, four gradients written 16, field 8 per cell
+        "cellgrad": {"bytes": 12 * mov_pins + 44 * C},
+        # read v, u, g 24, npins/area 8, gwl, gd 16, v_prev 8, g_prev 8; write u, v, v_prev, g 32
+        "update": {"bytes": 96 * C},
+    }
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2402_18311_gb300 import build, place
+    if not os.path.exists(place.LIB_PATH):
+        if rank == 0:
+            build.build()
+        if world > 1:
+            torch.distributed.barrier()
+    maker, desc = WORKLOADS[args.workload]
+    d = maker(0)
+    prm = place.place_default_params(tau_stop=-1.0, max_iters=1 << 30, dct_mode=args.dct)
+    stream = torch.cuda.current_stream()
+    h = place.place_create(d, prm, stream=stream.cuda_stream)
+    info = place.place_get_info(h)
+
+    # warm-up (also captures the iteration graph)
+    place.place_step(h, args.warmup)
+    torch.cuda.synchronize()
+
+    # device-timed steps: inputs resident in HBM
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    place.place_step(h, args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = clk.stop()
+
+    # per-stage device time (same kernels, launched stage by stage with events)
+    stage_ms = np.zeros(5, np.float32)
+    nprof = max(3, min(args.steps, 20))
+    place.place_step_timed(h, nprof, stage_ms)
+    stage_ms /= nprof
+
+    # end to end through the C ABI with pinned host buffers: every step uploads
+    # the movable positions (place_set_positions, which restarts the optimiser
+    # from them), runs one iteration and reads back all positions
+    xs = torch.empty(d.n_cells, dtype=torch.float32).pin_memory()
+    ys = torch.empty(d.n_cells, dtype=torch.float32).pin_memory()
+    place.place_get_positions(h, 0, xs, ys)
+    n_e2e = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        place.place_set_positions(h, 0, xs, ys)
+        place.place_step(h, 1)
+        place.place_get_positions(h, 0, xs, ys)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    hp = np.empty(prm.n_copies)
+    tv = np.empty(prm.n_copies)
+    place.place_eval_hpwl_overflow(h, hp, tv)
+    place.place_destroy(h)
+
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * args.steps / (ms_max / 1e3)
+    e2e_v = world * n_e2e / e2e_s
+
+    alg = algorithmic(d, info)
+    pk, pk_kind = peaks()
+    names = ["density", "spectral", "wirelength", "cellgrad", "update"]
+    dom = int(np.argmax(stage_ms))
+    per = {}
+    for i, n in enumerate(names):
+        a = alg[n]
+        sec = float(stage_ms[i]) / 1e3
+        if "flops" in a:
+            per[n] = {"ms": float(stage_ms[i]), "TFLOP/s": a["flops"] / sec / 1e12 if sec > 0 else None}
+        else:
+            per[n] = {"ms": float(stage_ms[i]), "GB/s": a["bytes"] / sec / 1e9 if sec > 0 else None}
+    dn = names[dom]
+    sec = float(stage_ms[dom]) / 1e3
+    if dn == "spectral":
+        if args.dct == 1:
+            peak = pk["bf16_tflops"] / 2.0
+            unit, bound = "TFLOP/s", "tensor"
+            achieved = alg[dn]["flops"] * 3 / sec / 1e12
+            peak_note = f"TF32 = bf16 {pk_kind} x 1/2 (nominal ratio); 3 TF32 products per GEMM"
+        else:
+            # FP32 FMA on CUDA cores: 152 SMs x 128 lanes x 2 flop x max clock
+            peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            unit, bound = "TFLOP/s", "alu"
+            achieved = alg[dn]["flops"] / sec / 1e12
+            peak_note = "FP32 CUDA-core peak from 152 SMs x 128 FMA lanes x max SM clock"
+    else:
+        peak = pk["hbm_gbs"]
+        unit, bound = "GB/s", "hbm"
+        achieved = alg[dn]["bytes"] / sec / 1e9
+        peak_note = f"HBM copy bandwidth ({pk_kind})"
+    roofline = {"kernel": dn, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
+                "stages": per}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(d, args)
+    out = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.dct == 0 else "f32+tf32x3", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": desc, "copies_per_gpu": prm.n_copies,
+                   "parallelism": f"replicas{world}", "l2": "inputs larger than L2 "
+                   "(per-iteration working set > 129 MB)" if args.workload == "large_2m"
+                   else "working set fits L2 (no flush)",
+                   "dct_mode": ["fp32", "tf32x3"][args.dct]},
+        "e2e": {"value": e2e_v, "unit": "iters/s",
+                "h2d_bytes_per_step": 8 * d.n_movable, "d2h_bytes_per_step": 8 * d.n_cells,
+                "note": "per step: set_positions (h2d, restarts the optimiser) + 1 iteration "
+                        "+ get_positions (d2h), pinned host buffers"},
+        "gpu_launches": int(info.kernels_per_iter) * args.steps,
+        "roofline": roofline,
+        "clocks": clocks,
+        "final_hpwl": float(hp[0]), "final_overflow": float(tv[0]),
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(d, args, n_iters=1):
+    """The FP64 oracle as it stands, on the same workload: n_iters full
+    iterations after its set-up."""
+    from oracle import placer as opl
+    t0 = time.perf_counter()
+    o = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=1 << 30))
+    setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.run(n_iters)
+    el = time.perf_counter() - t0
+    return {"value": n_iters / el, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n_iters} full iteration(s) of the {args.workload} workload after "
+                      f"{setup:.1f} s of oracle set-up; numpy float64 (elementwise work single-"
+                      f"threaded, BLAS matmuls multi-threaded)"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    maker, desc = WORKLOADS[args.workload]
+    d = maker(0)
+    from oracle import placer as opl
+    o = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=1 << 30))
+    o.run(args.warmup)
+    t0 = time.perf_counter()
+    o.run(args.steps)
+    el = time.perf_counter() - t0
+    v = args.steps / el
+    out = {"metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": args.workload, "desc": desc, "parallelism": "cpu"},
+           "cpu_baseline": {"value": v, "unit": "iters/s", "cores": os.cpu_count(),
+                            "kind": "oracle",
+                            "sample": f"{args.steps} timed oracle iterations after {args.warmup} "
+                                      f"warm-up iterations of the {args.workload} workload"},
+           "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large_2m", choices=sorted(WORKLOADS))
+    ap.add_argument("--dct", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        # bounded sample: one oracle iteration takes about ten seconds at 2M
+        # cells, so at most 3 warm-up and 3 timed iterations are run
+        args.steps = min(args.steps, 3)
+        args.warmup = min(args.warmup, 3)
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

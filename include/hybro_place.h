@@ -1,0 +1,223 @@
+/*
+ * hybro_place.h -- C ABI of the GB300 (sm_103a) electrostatic global-placement
+ * library: the inner loop that every perturb-and-reoptimise round of Hybro
+ * (Algorithm 1, "Execute DREAMPlace for global placement ... until it reaches
+ * convergence") re-runs, plus the Shuffle perturbations and best-result
+ * selection of Algorithm 1.
+ *
+ * Conventions
+ *  - Every function returns PLACE_OK (0) or a negative PLACE_E* code; the
+ *    message of the last failure on the calling host thread is returned by
+ *    place_last_error() (borrowed, valid until the next failing call on that
+ *    thread).
+ *  - A handle owns a private device copy of the netlist and all device state.
+ *    Handles are not thread-safe: use one handle per host thread.
+ *  - All device work is issued on the stream given at creation (a
+ *    cudaStream_t passed as void*; NULL = legacy default stream).  Functions
+ *    that return results to host memory synchronise that stream.
+ *  - "host or device" pointers are copied with cudaMemcpyDefault (unified
+ *    addressing); the caller keeps ownership of every pointer it passes.
+ *  - A handle holds K independent copies of the design ("copies", Algorithm 1
+ *    restarts run as a batch); copy c is 0..K-1.  Copies share the netlist and
+ *    the fixed cells; each has its own positions, optimiser state, density map
+ *    and spectral buffers.
+ *  - Layouts: cell arrays are [n_cells] with movable cells first; bin maps
+ *    are x-major, element (ix, iy) at ix * ny + iy.
+ */
+#ifndef HYBRO_PLACE_H
+#define HYBRO_PLACE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PLACE_OK 0
+#define PLACE_EINVAL (-1)    /* malformed argument or netlist */
+#define PLACE_ENOMEM (-2)    /* device or host allocation failed */
+#define PLACE_ECUDA (-3)     /* a CUDA call failed */
+#define PLACE_ERANGE (-4)    /* design does not fit the fixed-point range */
+#define PLACE_ETIMEOUT (-5)  /* a bounded device wait gave up */
+#define PLACE_EINTERNAL (-6) /* a device-side check failed */
+
+/* Perturbation operators of Algorithm 1 (Section 4.2). */
+#define PLACE_SHUFFLE_MACRO 0 /* Shuffle: p% of the movable macros */
+#define PLACE_SHUFFLE_ALL 1   /* Shuffle (all): p% of all movable cells */
+
+/* Spectral-solve arithmetic. */
+#define PLACE_DCT_FP32 0   /* FP32 CUDA-core GEMMs */
+#define PLACE_DCT_TF32X3 1 /* split-TF32 (3 products) on the tcgen05 tensor cores */
+
+typedef struct place_t place_t;
+
+/* Netlist N = (V, E) of Section 3 (Preliminaries).  Host pointers.
+ * Cells [0, n_movable) move; the rest are fixed.  x0/y0 are lower-left
+ * corners (initial positions for movable cells, final for fixed ones).
+ * Net e owns pins net_ptr[e] .. net_ptr[e+1]-1; pin j sits on cell
+ * pin_cell[j] at offset (pin_dx[j], pin_dy[j]) from the cell's lower-left.
+ * net_w (nullable: all 1) weights a net in HPWL (Eq. 1) and WL (Eq. 2).
+ * is_macro (nullable: none) marks cells that Shuffle may pick. */
+typedef struct place_netlist {
+  int32_t n_cells, n_movable, n_nets, n_pins;
+  const float *w, *h, *x0, *y0;
+  const int32_t *net_ptr;
+  const int32_t *pin_cell;
+  const float *pin_dx, *pin_dy;
+  const float *net_w;
+  const uint8_t *is_macro;
+} place_netlist;
+
+/* Placement region [xl, xh) x [yl, yh).  xl, yl and the bin size must be
+ * exact multiples of 2^-F for the fixed-point resolution F chosen at create
+ * (any die with integer or dyadic-rational bounds qualifies). */
+typedef struct place_die { double xl, yl, xh, yh; } place_die;
+
+/* nx x ny density bins and the target density t of the overflow test
+ * (D(s) <= epsilon in Eq. 1). */
+typedef struct place_bins { int32_t nx, ny; float target_density; } place_bins;
+
+/* Optimiser constants.  The paper cites, but does not restate, the
+ * Nesterov optimiser and the lambda/gamma schedules of DREAMPlace/ePlace; the
+ * defaults from place_default_params() are this library's reading:
+ *   gamma_k = gamma_base * w_bin * 10^((20/9) tau_{k-1} - 11/9)  (Eq. 3's gamma)
+ *   lambda_0 = lambda_eta * |grad WL|_1 / |grad D|_1            (Eq. 2's lambda)
+ *   lambda_{k+1} = lambda_k * clamp(mu_base^(1 - dHPWL/dref), mu_lo, mu_hi),
+ *     dref = hpwl_ref * n_nets * w_bin
+ *   alpha_0 = alpha0 * w_bin / rms(g_0); then |dv| / |dg|
+ *   stop when overflow <= tau_stop (tau_stop < 0: never) or after max_iters. */
+typedef struct place_params {
+  int32_t n_copies;       /* K >= 1 */
+  float gamma_base;       /* 4 */
+  float lambda_eta;       /* 1e-3 */
+  float alpha0;           /* 0.05 */
+  float hpwl_ref;         /* 0.1 */
+  float mu_base, mu_lo, mu_hi; /* 1.1, 0.95, 1.05 */
+  float tau_stop;         /* 0.07 */
+  int32_t max_iters;      /* 1000 */
+  float constant_gamma;   /* > 0: fixed gamma (tests) */
+  int32_t dct_mode;       /* PLACE_DCT_* */
+} place_params;
+
+/* Read-only facts about a handle. */
+typedef struct place_info {
+  int32_t n_cells, n_movable, n_nets, n_pins, nx, ny, n_copies;
+  int32_t frac_bits;      /* F: coordinates are quantised to multiples of 2^-F */
+  int64_t bin_w_q, bin_h_q; /* bin size in units of 2^-F */
+  double bin_w, bin_h;
+  int64_t device_bytes;   /* device memory the handle holds */
+  int32_t kernels_per_iter; /* this library's kernel launches in one iteration */
+  int32_t pad;
+} place_info;
+
+/* Optimiser scalars of one copy after its last iteration. */
+typedef struct place_state {
+  int32_t iter;        /* iterations done since the last reset */
+  int32_t converged;   /* 1: stopped by the overflow test */
+  int32_t stopped;     /* 1: converged or reached max_iters */
+  int32_t pad;
+  double lambda, gamma, alpha, a;
+  double overflow;     /* tau at the current reference point */
+  double hpwl_wa;      /* HPWL measured in the last iteration's WA pass */
+} place_state;
+
+void place_default_params(place_params *p);
+
+/* Create a handle: validates and copies the netlist (host pointers), chooses
+ * the fixed-point resolution F, builds the device state for K copies (all
+ * starting at x0/y0) and resets their optimisers.  Section 3 (problem
+ * statement), Algorithm 1 line 1.  *out receives the handle; on failure it is
+ * set to NULL and nothing is leaked. */
+int place_create(const place_netlist *nl, const place_die *die, const place_bins *bins,
+                 const place_params *params, void *stream, place_t **out);
+
+/* Release every resource of the handle (NULL is ignored). */
+int place_destroy(place_t *h);
+
+int place_get_info(const place_t *h, place_info *out);
+
+/* Run up to n_iters Nesterov iterations of Eq. 2 on every active copy
+ * (Algorithm 1 line 3).  A copy stops updating once converged or at
+ * max_iters; the others continue.  converged (nullable, host [K]) receives
+ * the stopped flags, which synchronises the stream; with NULL the call is
+ * asynchronous. */
+int place_step(place_t *h, int32_t n_iters, int32_t *converged);
+
+/* Perturb (Algorithm 1 line 4; Section 4.2): Shuffle or Shuffle (all) with
+ * strength p in [0, 1] applied to copy `copy` (-1: every copy, copy c using
+ * seed + c), followed by a full optimiser reset of the perturbed copies.
+ * Selection draws SplitMix64 keys from `seed`. */
+int place_perturb(place_t *h, int32_t op, float p, uint64_t seed, int32_t copy);
+
+/* Exact FP64 HPWL (Eq. 1) and overflow of every copy at its current
+ * positions: hpwl, overflow are host [K] (either may be NULL).  Synchronises. */
+int place_eval_hpwl_overflow(place_t *h, double *hpwl, double *overflow);
+
+/* Positions of copy `copy`: x, y are [n_cells] host or device buffers. */
+int place_get_positions(place_t *h, int32_t copy, float *x, float *y);
+
+/* Set the movable positions of copy `copy` (-1: all copies) from [n_cells]
+ * host or device arrays (entries >= n_movable are ignored), clamp them into
+ * the die and reset that copy's optimiser. */
+int place_set_positions(place_t *h, int32_t copy, const float *x, const float *y);
+
+int place_get_state(place_t *h, int32_t copy, place_state *out);
+
+/* ---- stage-level evaluation at the current positions of one copy --------
+ * These run the same kernels as place_step on the copy's reference point
+ * v and leave the optimiser state untouched (the stage buffers they use are
+ * overwritten). */
+
+/* Eq. 3 summed over nets in x and y with the given gamma: *wl (host,
+ * nullable) and grad_x/grad_y ([n_movable] host or device, nullable), the
+ * gradient with respect to the movable lower-left corners. */
+int place_eval_wirelength(place_t *h, int32_t copy, float gamma, double *wl,
+                          float *grad_x, float *grad_y);
+
+/* Movable-cell density map M (int64, units of 2^-2F, [nx*ny] x-major,
+ * host or device, nullable) and the overflow tau (host, nullable). */
+int place_eval_density(place_t *h, int32_t copy, int64_t *map, double *overflow);
+
+/* Fixed-cell map F (int64, [nx*ny], host or device). */
+int place_get_fixed_map(place_t *h, int64_t *map);
+
+/* Spectral Poisson solve of rho = (M + t F) / A_bin at the current positions:
+ * psi, ex, ey are [nx*ny] host or device float buffers (nullable). */
+int place_eval_field(place_t *h, int32_t copy, float *psi, float *ex, float *ey);
+
+/* Density gradient -sum_b a_ib E_b for the movable cells using the field of
+ * the current positions: grad_x/grad_y [n_movable] host or device. */
+int place_eval_density_grad(place_t *h, int32_t copy, float *grad_x, float *grad_y);
+
+/* Hybro (Algorithm 1) on every copy: rounds 0..n_rounds place each copy until
+ * convergence, record (HPWL, overflow), and perturb the current solution with
+ * `op`, `p` and seed + round * K + copy before the next round.  The best
+ * solution of each copy by (overflow <= tau_target, HPWL, overflow, round)
+ * is kept on the device.  best_hpwl, best_overflow, best_round: host [K],
+ * nullable.  Synchronises. */
+int place_hybro(place_t *h, int32_t n_rounds, int32_t op, float p, uint64_t seed,
+                float tau_target, double *best_hpwl, double *best_overflow,
+                int32_t *best_round);
+
+/* Best positions kept by place_hybro for copy `copy` ([n_cells], host or device). */
+int place_get_best_positions(place_t *h, int32_t copy, float *x, float *y);
+
+/* Measurement helper: run n_iters iterations like place_step, but launched
+ * stage by stage (no graph) with CUDA events between the stages, and add the
+ * device time of each stage in milliseconds to stage_ms (host
+ * [PLACE_N_STAGES]).  Synchronises.  Stages: */
+#define PLACE_STAGE_DENSITY 0  /* clear map, scatter, overflow/rho, stop test */
+#define PLACE_STAGE_SPECTRAL 1 /* the four transform GEMMs of the Poisson solve */
+#define PLACE_STAGE_WIRELENGTH 2 /* WA value and per-pin gradients (Eq. 3) */
+#define PLACE_STAGE_CELLGRAD 3 /* pin-gradient sums and field gather per cell */
+#define PLACE_STAGE_UPDATE 4   /* preconditioner, step size, Nesterov update */
+#define PLACE_N_STAGES 5
+int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms);
+
+const char *place_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYBRO_PLACE_H */

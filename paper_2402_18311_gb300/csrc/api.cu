@@ -1,0 +1,796 @@
+// Host side of the C ABI declared in include/hybro_place.h: validation,
+// netlist preprocessing, device-state layout, CUDA-graph iteration, stage
+// evaluation and the Hybro driver (Algorithm 1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace hp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(PLACE_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));       \
+  } while (0)
+
+#define CKL()                                                                         \
+  do {                                                                                \
+    cudaError_t e_ = cudaGetLastError();                                              \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(PLACE_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e_));   \
+  } while (0)
+
+// Bump allocator over one device allocation (256-byte aligned sub-arrays).
+struct Arena {
+  char *base = nullptr;
+  size_t off = 0;
+  template <typename T>
+  T *take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+int degree_class(int deg) {
+  if (deg <= 4) return 0;
+  if (deg <= 8) return 1;
+  if (deg <= 16) return 2;
+  if (deg <= 256) return 3;
+  return 4;
+}
+constexpr int kGroupWidth[4] = {4, 8, 16, 32};
+
+bool is_integer(double v) { return std::floor(v) == v && std::isfinite(v); }
+
+}  // namespace
+
+struct place_t {
+  Dev d{};
+  cudaStream_t stream = nullptr;     // caller's stream
+  cudaStream_t cap = nullptr;        // private stream used for graph capture
+  void *mem = nullptr;
+  size_t mem_bytes = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int n_cand_all = 0, n_cand_macro = 0;
+  // Hybro bookkeeping (host)
+  std::vector<double> best_hpwl, best_tau;
+  std::vector<int> best_round;
+};
+
+extern "C" {
+
+const char *place_last_error(void) { return g_err.c_str(); }
+
+void place_default_params(place_params *p) {
+  if (!p) return;
+  p->n_copies = 1;
+  p->gamma_base = 4.0f;
+  p->lambda_eta = 1e-3f;
+  p->alpha0 = 0.05f;
+  p->hpwl_ref = 0.1f;
+  p->mu_base = 1.1f;
+  p->mu_lo = 0.95f;
+  p->mu_hi = 1.05f;
+  p->tau_stop = 0.07f;
+  p->max_iters = 1000;
+  p->constant_gamma = 0.0f;
+  p->dct_mode = PLACE_DCT_FP32;
+}
+
+int place_destroy(place_t *h) {
+  if (!h) return PLACE_OK;
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->mem) cudaFree(h->mem);
+  delete h;
+  return PLACE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Device layout of every array the handle owns.
+void layout(Dev &d, Arena &a, int n_copies) {
+  const size_t K = n_copies, C = d.n_cells, Mv = d.n_mov, P = d.n_pins, G = d.G;
+  d.net_ptr = a.take<int>(d.n_nets + 1);
+  d.net_w = d.has_net_w ? a.take<float>(std::max(d.n_nets, 1)) : nullptr;
+  d.pin_cell = a.take<int>(P);
+  d.pin_off = a.take<float2>(P);
+  d.cell_pin_ptr = a.take<int>(Mv + 1);
+  d.cell_pins = a.take<int>(std::max<size_t>(d.n_mov_pins, 1));
+  d.w = a.take<float>(C);
+  d.h = a.take<float>(C);
+  d.Wq = a.take<int>(C);
+  d.Hq = a.take<int>(C);
+  d.npins = a.take<float>(Mv);
+  d.area = a.take<float>(Mv);
+  d.is_macro = a.take<unsigned char>(C);
+  d.x = a.take<float>(K * C);
+  d.y = a.take<float>(K * C);
+  d.ux = a.take<float>(K * Mv);
+  d.uy = a.take<float>(K * Mv);
+  d.vpx = a.take<float>(K * Mv);
+  d.vpy = a.take<float>(K * Mv);
+  for (int q = 0; q < 2; ++q) {
+    d.gx[q] = a.take<float>(K * Mv);
+    d.gy[q] = a.take<float>(K * Mv);
+  }
+  d.gwx = a.take<float>(K * Mv);
+  d.gwy = a.take<float>(K * Mv);
+  d.gdx = a.take<float>(K * Mv);
+  d.gdy = a.take<float>(K * Mv);
+  d.pin_grad = a.take<float2>(K * P);
+  d.M = a.take<unsigned long long>(K * G);
+  d.Fmap = a.take<long long>(G);
+  d.rho = a.take<float>(K * G);
+  d.T = a.take<float>(K * 3 * G);
+  d.SB = a.take<float>(K * 3 * G);
+  d.E = a.take<float>(K * 3 * G);
+  d.cs = a.take<CopyState>(K);
+  d.part = a.take<double>(K * S_COUNT * (size_t)d.nb_red);
+  d.scal = a.take<double>(K * S_COUNT);
+  d.Cn = a.take<float>((size_t)d.ny * d.ny);
+  d.CTn = a.take<float>((size_t)d.ny * d.ny);
+  d.STn = a.take<float>((size_t)d.ny * d.ny);
+  d.Cm = a.take<float>((size_t)d.nx * d.nx);
+  d.CTm = a.take<float>((size_t)d.nx * d.nx);
+  d.STm = a.take<float>((size_t)d.nx * d.nx);
+  d.wu = a.take<float>(d.nx);
+  d.wv = a.take<float>(d.ny);
+  d.cu = a.take<float>(d.nx);
+  d.cv = a.take<float>(d.ny);
+  d.bx = a.take<float>(K * C);
+  d.by = a.take<float>(K * C);
+  d.sort_key = a.take<unsigned long long>(d.sort_n);
+  d.sort_idx = a.take<unsigned int>(d.sort_n);
+  d.sel_idx = a.take<unsigned int>(d.sort_n);
+  d.px_tmp = a.take<float>(C);
+  d.py_tmp = a.take<float>(C);
+}
+
+// Optimiser reset of copies [c0, c0+n): clamp, u = v, scalars, tau_{-1}.
+int enqueue_reset(place_t *h, int c0, int n) {
+  Dev &d = h->d;
+  cudaStream_t st = h->stream;
+  launch_reset(d, c0, n, st);
+  CK(cudaMemsetAsync(d.M + (size_t)c0 * d.G, 0, sizeof(unsigned long long) * d.G * n, st));
+  launch_scatter(d, c0, n, 1, st);
+  launch_density_finish(d, c0, n, 1, st);
+  launch_iteration_scalars(d, PH_TAU_RESET, c0, n, st);
+  CKL();
+  return PLACE_OK;
+}
+
+// One Nesterov iteration of every copy (the graph body).
+void enqueue_iteration(const Dev &d, cudaStream_t st) {
+  const int K = d.K;
+  launch_iteration_scalars(d, PH_BEGIN, 0, K, st);
+  cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.G * K, st);
+  launch_scatter(d, 0, K, 0, st);
+  launch_density_finish(d, 0, K, 0, st);
+  launch_iteration_scalars(d, PH_TAU, 0, K, st);
+  launch_spectral(d, 0, K, 0, 0, st);
+  launch_wa(d, 0, K, 0, nullptr, st);
+  launch_cell_grad(d, 0, K, 0, st);
+  launch_iteration_scalars(d, PH_MID, 0, K, st);
+  launch_precond0(d, 0, K, st);
+  launch_iteration_scalars(d, PH_ALPHA, 0, K, st);
+  launch_update(d, 0, K, st);
+  launch_iteration_scalars(d, PH_END, 0, K, st);
+}
+
+int ensure_graph(place_t *h) {
+  if (h->exec) return PLACE_OK;
+  CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  enqueue_iteration(h->d, h->cap);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+  if (e != cudaSuccess) return fail(PLACE_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  h->graph = g;
+  CK(cudaGraphInstantiate(&h->exec, g, 0));
+  return PLACE_OK;
+}
+
+int check_copy(const place_t *h, int copy, bool allow_all) {
+  if (!h) return fail(PLACE_EINVAL, "null handle");
+  if (copy == -1 && allow_all) return PLACE_OK;
+  if (copy < 0 || copy >= h->d.K) return fail(PLACE_EINVAL, "copy %d out of range [0,%d)", copy, h->d.K);
+  return PLACE_OK;
+}
+
+void host_dct_tables(int n, double h, std::vector<float> &C, std::vector<float> &CT,
+                     std::vector<float> &S, std::vector<float> &ST, std::vector<float> &w,
+                     std::vector<float> &c) {
+  // C[k][i] = cos(pi k (i + 1/2) / n); CT = C^T; ST[i][k] = sin(pi k (i + 1/2) / n); S = ST^T
+  C.assign((size_t)n * n, 0.f); CT = C; S = C; ST = C;
+  w.assign(n, 0.f); c.assign(n, 0.f);
+  for (int k = 0; k < n; ++k) {
+    w[k] = (float)(M_PI * k / (n * h));
+    c[k] = (float)((k == 0 ? 1.0 : 2.0) / n);
+    for (int i = 0; i < n; ++i) {
+      double arg = M_PI * k * (i + 0.5) / n;
+      float cv = (float)std::cos(arg), sv = (float)std::sin(arg);
+      C[(size_t)k * n + i] = cv;
+      CT[(size_t)i * n + k] = cv;
+      S[(size_t)k * n + i] = sv;
+      ST[(size_t)i * n + k] = sv;
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int place_create(const place_netlist *nl, const place_die *die, const place_bins *bins,
+                 const place_params *params, void *stream, place_t **out) {
+  if (out) *out = nullptr;
+  if (!nl || !die || !bins || !out) return fail(PLACE_EINVAL, "null argument");
+  place_params prm;
+  if (params) prm = *params; else place_default_params(&prm);
+  const int C = nl->n_cells, Mv = nl->n_movable, E = nl->n_nets, P = nl->n_pins;
+  if (C <= 0 || Mv < 0 || Mv > C || E < 0 || P < 0)
+    return fail(PLACE_EINVAL, "bad sizes: n_cells=%d n_movable=%d n_nets=%d n_pins=%d", C, Mv, E, P);
+  if (C >= (1 << 30)) return fail(PLACE_EINVAL, "too many cells");
+  if (!nl->w || !nl->h || !nl->x0 || !nl->y0 || !nl->net_ptr || (P > 0 && (!nl->pin_cell || !nl->pin_dx || !nl->pin_dy)))
+    return fail(PLACE_EINVAL, "null netlist array");
+  if (prm.n_copies < 1 || prm.n_copies > 4096) return fail(PLACE_EINVAL, "n_copies must be in [1, 4096]");
+  if (prm.max_iters < 0) return fail(PLACE_EINVAL, "max_iters < 0");
+  if (prm.dct_mode != PLACE_DCT_FP32 && prm.dct_mode != PLACE_DCT_TF32X3)
+    return fail(PLACE_EINVAL, "unknown dct_mode %d", prm.dct_mode);
+  const int nx = bins->nx, ny = bins->ny;
+  if (nx < 16 || ny < 16 || nx % 16 || ny % 16 || nx > 8192 || ny > 8192)
+    return fail(PLACE_EINVAL, "bins must be multiples of 16 in [16, 8192], got %dx%d", nx, ny);
+  if (!(die->xh > die->xl) || !(die->yh > die->yl)) return fail(PLACE_EINVAL, "empty die");
+  if (!(bins->target_density > 0.f)) return fail(PLACE_EINVAL, "target density must be > 0");
+
+  // netlist checks
+  if (nl->net_ptr[0] != 0 || nl->net_ptr[E] != P) return fail(PLACE_EINVAL, "net_ptr must start at 0 and end at n_pins");
+  for (int e = 0; e < E; ++e)
+    if (nl->net_ptr[e + 1] < nl->net_ptr[e]) return fail(PLACE_EINVAL, "net_ptr not monotone at net %d", e);
+  for (int j = 0; j < P; ++j)
+    if (nl->pin_cell[j] < 0 || nl->pin_cell[j] >= C) return fail(PLACE_EINVAL, "pin %d on cell %d out of range", j, nl->pin_cell[j]);
+  double total_area = 0.0;
+  for (int i = 0; i < C; ++i) {
+    if (!(nl->w[i] > 0.f) || !(nl->h[i] > 0.f)) return fail(PLACE_EINVAL, "cell %d has non-positive size", i);
+    if (!std::isfinite(nl->x0[i]) || !std::isfinite(nl->y0[i])) return fail(PLACE_EINVAL, "cell %d has a non-finite position", i);
+    total_area += (double)nl->w[i] * (double)nl->h[i];
+  }
+
+  // fixed-point resolution: the largest F <= 24 with |coordinate| 2^F < 2^30
+  // and total area 2^2F < 2^62
+  const double ext = std::max(std::max(std::fabs(die->xl), std::fabs(die->xh)),
+                              std::max(std::fabs(die->yl), std::fabs(die->yh)));
+  int F = -1;
+  for (int f = 24; f >= 0; --f) {
+    if (ext * std::ldexp(1.0, f) < std::ldexp(1.0, 30) && total_area * std::ldexp(1.0, 2 * f) < std::ldexp(1.0, 62)) {
+      F = f;
+      break;
+    }
+  }
+  if (F < 0) return fail(PLACE_ERANGE, "design does not fit the 64-bit fixed-point density range");
+  const double s = std::ldexp(1.0, F);
+  const double bw = (die->xh - die->xl) / nx, bh = (die->yh - die->yl) / ny;
+  if (!is_integer(die->xl * s) || !is_integer(die->yl * s) || !is_integer(bw * s) || !is_integer(bh * s))
+    return fail(PLACE_EINVAL, "die origin and bin size must be multiples of 2^-%d", F);
+
+  place_t *h = new place_t();
+  Dev &d = h->d;
+  d.K = prm.n_copies;
+  d.n_cells = C; d.n_mov = Mv; d.n_nets = E; d.n_pins = P;
+  d.nx = nx; d.ny = ny; d.G = nx * ny;
+  d.F = F;
+  d.scale = (float)s;
+  d.inv_area_q = (float)std::ldexp(1.0, -2 * F);
+  d.XL = (long long)(die->xl * s); d.YL = (long long)(die->yl * s);
+  d.BW = (long long)(bw * s); d.BH = (long long)(bh * s);
+  d.t = (double)bins->target_density;
+  d.abin_q = (double)d.BW * (double)d.BH;
+  d.die_xl = die->xl; d.die_yl = die->yl; d.die_xh = die->xh; d.die_yh = die->yh;
+  d.fxl = (float)die->xl; d.fyl = (float)die->yl; d.fxh = (float)die->xh; d.fyh = (float)die->yh;
+  d.w_bin = std::sqrt(bw * bh);
+  d.dref = (double)prm.hpwl_ref * (double)E * d.w_bin;
+  d.prm = prm;
+  d.has_net_w = nl->net_w ? 1 : 0;
+  h->stream = (cudaStream_t)stream;
+
+  // quantised sizes and movable area
+  std::vector<int> Wq(C), Hq(C);
+  double mov_area_q = 0.0;
+  for (int i = 0; i < C; ++i) {
+    double wq = std::nearbyint((double)nl->w[i] * s), hq = std::nearbyint((double)nl->h[i] * s);
+    if (wq < 1 || hq < 1 || wq >= 2147483647.0 || hq >= 2147483647.0) {
+      delete h;
+      return fail(PLACE_ERANGE, "cell %d size out of the fixed-point range", i);
+    }
+    Wq[i] = (int)wq; Hq[i] = (int)hq;
+    if (i < Mv) mov_area_q += wq * hq;
+  }
+  d.mov_area_q = mov_area_q > 0 ? mov_area_q : 1.0;
+
+  // nets grouped by degree class (stable), pins in the new net order
+  std::vector<int> order(E);
+  {
+    std::vector<int> cnt(6, 0);
+    for (int e = 0; e < E; ++e) cnt[degree_class(nl->net_ptr[e + 1] - nl->net_ptr[e]) + 1]++;
+    for (int c = 0; c < 5; ++c) cnt[c + 1] += cnt[c];
+    d.n_cls = 5;
+    for (int c = 0; c <= 5; ++c) d.cls_begin[c] = cnt[c];
+    std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+    for (int e = 0; e < E; ++e) order[pos[degree_class(nl->net_ptr[e + 1] - nl->net_ptr[e])]++] = e;
+  }
+  std::vector<int> net_ptr(E + 1), pin_cell(P);
+  std::vector<float2> pin_off(P);
+  std::vector<float> net_w;
+  if (nl->net_w) net_w.resize(E);
+  net_ptr[0] = 0;
+  for (int ne = 0; ne < E; ++ne) {
+    int e = order[ne];
+    int p0 = nl->net_ptr[e], p1 = nl->net_ptr[e + 1];
+    int q = net_ptr[ne];
+    for (int j = p0; j < p1; ++j, ++q) {
+      pin_cell[q] = nl->pin_cell[j];
+      pin_off[q] = make_float2(nl->pin_dx[j], nl->pin_dy[j]);
+    }
+    net_ptr[ne + 1] = q;
+    if (nl->net_w) net_w[ne] = nl->net_w[e];
+  }
+  // movable cell -> pins (library pin ids), counting sort by cell
+  std::vector<int> cpp(Mv + 1, 0);
+  for (int j = 0; j < P; ++j)
+    if (pin_cell[j] < Mv) cpp[pin_cell[j] + 1]++;
+  for (int i = 0; i < Mv; ++i) cpp[i + 1] += cpp[i];
+  d.n_mov_pins = cpp[Mv];
+  std::vector<int> cpins(std::max(d.n_mov_pins, 1));
+  {
+    std::vector<int> fill(cpp.begin(), cpp.end() - 1);
+    for (int j = 0; j < P; ++j)
+      if (pin_cell[j] < Mv) cpins[fill[pin_cell[j]]++] = j;
+  }
+  std::vector<float> npins(std::max(Mv, 1)), area(std::max(Mv, 1));
+  for (int i = 0; i < Mv; ++i) {
+    npins[i] = (float)(cpp[i + 1] - cpp[i]);
+    area[i] = nl->w[i] * nl->h[i];
+  }
+  std::vector<unsigned char> macro(C, 0);
+  if (nl->is_macro)
+    for (int i = 0; i < C; ++i) macro[i] = nl->is_macro[i] ? 1 : 0;
+  h->n_cand_all = Mv;
+  h->n_cand_macro = 0;
+  for (int i = 0; i < Mv; ++i) h->n_cand_macro += macro[i];
+
+  // launch plan
+  d.cell_blocks = std::max(1, std::min((Mv + kThreads - 1) / kThreads, kMaxCellBlocks));
+  d.bin_blocks = std::max(1, std::min((d.G + kThreads - 1) / kThreads, kMaxCellBlocks));
+  d.wa_blocks_total = 0;
+  for (int c = 0; c < 5; ++c) {
+    int n = d.cls_begin[c + 1] - d.cls_begin[c];
+    int nb = c < 4 ? (n + (kThreads / kGroupWidth[c]) - 1) / (kThreads / kGroupWidth[c]) : n;
+    d.wa_blocks[c] = nb;
+    d.wa_block_base[c] = d.wa_blocks_total;
+    d.wa_blocks_total += nb;
+  }
+  d.nb_red = std::max(std::max(d.cell_blocks, d.bin_blocks), std::max(d.wa_blocks_total, 1));
+  int sn = 2;
+  while (sn < C) sn <<= 1;
+  d.sort_n = sn;
+
+  // device memory: one allocation carved into arrays
+  Arena a;
+  layout(d, a, d.K);
+  h->mem_bytes = a.off + 256;
+  cudaError_t e = cudaMalloc(&h->mem, h->mem_bytes);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(PLACE_ENOMEM, "cudaMalloc(%zu) failed: %s", (size_t)a.off, cudaGetErrorString(e));
+  }
+  a = Arena();
+  a.base = (char *)h->mem;
+  layout(d, a, d.K);
+
+  int rc = PLACE_OK;
+  auto up = [&](void *dst, const void *src, size_t bytes) {
+    if (rc != PLACE_OK || bytes == 0) return;
+    cudaError_t ce = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) rc = fail(PLACE_ECUDA, "upload failed: %s", cudaGetErrorString(ce));
+  };
+  up(d.net_ptr, net_ptr.data(), sizeof(int) * (E + 1));
+  up(d.pin_cell, pin_cell.data(), sizeof(int) * P);
+  up(d.pin_off, pin_off.data(), sizeof(float2) * P);
+  up(d.cell_pin_ptr, cpp.data(), sizeof(int) * (Mv + 1));
+  up(d.cell_pins, cpins.data(), sizeof(int) * cpins.size());
+  up(d.w, nl->w, sizeof(float) * C);
+  up(d.h, nl->h, sizeof(float) * C);
+  up(d.Wq, Wq.data(), sizeof(int) * C);
+  up(d.Hq, Hq.data(), sizeof(int) * C);
+  up(d.npins, npins.data(), sizeof(float) * Mv);
+  up(d.area, area.data(), sizeof(float) * Mv);
+  up(d.is_macro, macro.data(), C);
+  if (d.net_w) up(d.net_w, net_w.data(), sizeof(float) * E);
+  {
+    std::vector<float> Cn, CTn, Sn, STn, Cm, CTm, Sm, STm, wu, wv, cu, cv;
+    host_dct_tables(ny, bh, Cn, CTn, Sn, STn, wv, cv);
+    host_dct_tables(nx, bw, Cm, CTm, Sm, STm, wu, cu);
+    up(d.Cn, Cn.data(), sizeof(float) * Cn.size());
+    up(d.CTn, CTn.data(), sizeof(float) * CTn.size());
+    // G3 for Ey uses S_N[y][v] = sin(pi v (y+1/2)/N): the "ST" layout [i][k]
+    up(d.STn, STn.data(), sizeof(float) * STn.size());
+    up(d.Cm, Cm.data(), sizeof(float) * Cm.size());
+    up(d.CTm, CTm.data(), sizeof(float) * CTm.size());
+    up(d.STm, STm.data(), sizeof(float) * STm.size());
+    up(d.wu, wu.data(), sizeof(float) * nx);
+    up(d.wv, wv.data(), sizeof(float) * ny);
+    up(d.cu, cu.data(), sizeof(float) * nx);
+    up(d.cv, cv.data(), sizeof(float) * ny);
+  }
+  for (int c = 0; c < d.K && rc == PLACE_OK; ++c) {
+    up(d.x + (size_t)c * C, nl->x0, sizeof(float) * C);
+    up(d.y + (size_t)c * C, nl->y0, sizeof(float) * C);
+  }
+  if (rc != PLACE_OK) {
+    place_destroy(h);
+    return rc;
+  }
+  cudaError_t ce = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) {
+    place_destroy(h);
+    return fail(PLACE_ECUDA, "stream create: %s", cudaGetErrorString(ce));
+  }
+  ce = cudaMemsetAsync(d.E, 0, sizeof(float) * (size_t)d.K * 3 * d.G, h->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(d.Fmap, 0, sizeof(long long) * d.G, h->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(d.pin_grad, 0, sizeof(float2) * (size_t)d.K * P, h->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(d.cs, 0, sizeof(CopyState) * d.K, h->stream);
+  if (ce != cudaSuccess) {
+    place_destroy(h);
+    return fail(PLACE_ECUDA, "memset: %s", cudaGetErrorString(ce));
+  }
+  launch_scatter_fixed(d, d.x, d.y, Mv, C, reinterpret_cast<unsigned long long *>(d.Fmap), h->stream);
+  rc = enqueue_reset(h, 0, d.K);
+  if (rc == PLACE_OK) {
+    ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) rc = fail(PLACE_ECUDA, "create: %s", cudaGetErrorString(ce));
+  }
+  if (rc != PLACE_OK) {
+    place_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return PLACE_OK;
+}
+
+int place_get_info(const place_t *h, place_info *o) {
+  if (!h || !o) return fail(PLACE_EINVAL, "null argument");
+  const Dev &d = h->d;
+  o->n_cells = d.n_cells; o->n_movable = d.n_mov; o->n_nets = d.n_nets; o->n_pins = d.n_pins;
+  o->nx = d.nx; o->ny = d.ny; o->n_copies = d.K;
+  o->frac_bits = d.F;
+  o->bin_w_q = d.BW; o->bin_h_q = d.BH;
+  o->bin_w = (d.die_xh - d.die_xl) / d.nx;
+  o->bin_h = (d.die_yh - d.die_yl) / d.ny;
+  o->device_bytes = (int64_t)h->mem_bytes;
+  int wa = 0;
+  for (int c = 0; c < d.n_cls; ++c) wa += d.wa_blocks[c] > 0;
+  // scalars x6, scatter, finish, 4 GEMMs, WA classes, cell grad, precond0, update
+  o->kernels_per_iter = 6 + 2 + 4 + wa + 3;
+  o->pad = 0;
+  return PLACE_OK;
+}
+
+int place_step(place_t *h, int32_t n_iters, int32_t *converged) {
+  if (!h) return fail(PLACE_EINVAL, "null handle");
+  if (n_iters < 0) return fail(PLACE_EINVAL, "n_iters < 0");
+  if (n_iters > 0) {
+    int rc = ensure_graph(h);
+    if (rc) return rc;
+    for (int i = 0; i < n_iters; ++i) CK(cudaGraphLaunch(h->exec, h->stream));
+  }
+  if (converged) {
+    std::vector<CopyState> cs(h->d.K);
+    CK(cudaMemcpyAsync(cs.data(), h->d.cs, sizeof(CopyState) * h->d.K, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int c = 0; c < h->d.K; ++c) converged[c] = cs[c].stopped;
+  }
+  return PLACE_OK;
+}
+
+int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms) {
+  if (!h || !stage_ms) return fail(PLACE_EINVAL, "null argument");
+  const Dev &d = h->d;
+  const int K = d.K;
+  cudaStream_t st = h->stream;
+  cudaEvent_t ev[PLACE_N_STAGES + 1];
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  std::vector<double> acc(PLACE_N_STAGES, 0.0);
+  int rc = PLACE_OK;
+  for (int it = 0; it < n_iters && rc == PLACE_OK; ++it) {
+    cudaEventRecord(ev[0], st);
+    launch_iteration_scalars(d, PH_BEGIN, 0, K, st);
+    cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.G * K, st);
+    launch_scatter(d, 0, K, 0, st);
+    launch_density_finish(d, 0, K, 0, st);
+    launch_iteration_scalars(d, PH_TAU, 0, K, st);
+    cudaEventRecord(ev[1], st);
+    launch_spectral(d, 0, K, 0, 0, st);
+    cudaEventRecord(ev[2], st);
+    launch_wa(d, 0, K, 0, nullptr, st);
+    cudaEventRecord(ev[3], st);
+    launch_cell_grad(d, 0, K, 0, st);
+    cudaEventRecord(ev[4], st);
+    launch_iteration_scalars(d, PH_MID, 0, K, st);
+    launch_precond0(d, 0, K, st);
+    launch_iteration_scalars(d, PH_ALPHA, 0, K, st);
+    launch_update(d, 0, K, st);
+    launch_iteration_scalars(d, PH_END, 0, K, st);
+    cudaEventRecord(ev[5], st);
+    cudaError_t e = cudaEventSynchronize(ev[5]);
+    if (e != cudaSuccess) { rc = fail(PLACE_ECUDA, "timed step: %s", cudaGetErrorString(e)); break; }
+    for (int s = 0; s < PLACE_N_STAGES; ++s) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[s], ev[s + 1]);
+      acc[s] += ms;
+    }
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (rc) return rc;
+  CKL();
+  for (int s = 0; s < PLACE_N_STAGES; ++s) stage_ms[s] += (float)acc[s];
+  return PLACE_OK;
+}
+
+int place_get_state(place_t *h, int32_t copy, place_state *o) {
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  if (!o) return fail(PLACE_EINVAL, "null output");
+  CopyState cs;
+  CK(cudaMemcpyAsync(&cs, h->d.cs + copy, sizeof cs, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  o->iter = cs.k; o->converged = cs.converged; o->stopped = cs.stopped; o->pad = 0;
+  o->lambda = cs.lam; o->gamma = cs.gamma; o->alpha = cs.alpha; o->a = cs.a;
+  o->overflow = cs.tau; o->hpwl_wa = cs.hpwl;
+  return PLACE_OK;
+}
+
+int place_get_positions(place_t *h, int32_t copy, float *x, float *y) {
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  const size_t C = h->d.n_cells;
+  if (x) CK(cudaMemcpyAsync(x, h->d.x + copy * C, sizeof(float) * C, cudaMemcpyDefault, h->stream));
+  if (y) CK(cudaMemcpyAsync(y, h->d.y + copy * C, sizeof(float) * C, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PLACE_OK;
+}
+
+int place_set_positions(place_t *h, int32_t copy, const float *x, const float *y) {
+  int rc = check_copy(h, copy, true);
+  if (rc) return rc;
+  if (!x || !y) return fail(PLACE_EINVAL, "null positions");
+  const size_t C = h->d.n_cells, Mv = h->d.n_mov;
+  int c0 = copy < 0 ? 0 : copy, n = copy < 0 ? h->d.K : 1;
+  for (int c = c0; c < c0 + n; ++c) {
+    CK(cudaMemcpyAsync(h->d.x + c * C, x, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
+    CK(cudaMemcpyAsync(h->d.y + c * C, y, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
+  }
+  return enqueue_reset(h, c0, n);
+}
+
+int place_eval_wirelength(place_t *h, int32_t copy, float gamma, double *wl, float *gx, float *gy) {
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  if (!(gamma > 0.f)) return fail(PLACE_EINVAL, "gamma must be > 0");
+  Dev &d = h->d;
+  float *gdev = reinterpret_cast<float *>(d.scal + (size_t)copy * S_COUNT + S_G2);
+  CK(cudaMemcpyAsync(gdev, &gamma, sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  launch_wa(d, copy, 1, 1, gdev, h->stream);
+  launch_cell_grad(d, copy, 1, 1, h->stream);
+  launch_reduce_slot(d, S_WL, d.wa_blocks_total, copy, 1, h->stream);
+  CKL();
+  const size_t Mv = d.n_mov;
+  if (gx) CK(cudaMemcpyAsync(gx, d.gwx + copy * Mv, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
+  if (gy) CK(cudaMemcpyAsync(gy, d.gwy + copy * Mv, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
+  double v = 0;
+  CK(cudaMemcpyAsync(&v, d.scal + (size_t)copy * S_COUNT + S_WL, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (wl) *wl = v;
+  return PLACE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int density_at(place_t *h, int copy) {
+  Dev &d = h->d;
+  CK(cudaMemsetAsync(d.M + (size_t)copy * d.G, 0, sizeof(unsigned long long) * d.G, h->stream));
+  launch_scatter(d, copy, 1, 1, h->stream);
+  launch_density_finish(d, copy, 1, 1, h->stream);
+  launch_reduce_slot(d, S_TAU, d.bin_blocks, copy, 1, h->stream);
+  CKL();
+  return PLACE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int place_eval_density(place_t *h, int32_t copy, int64_t *map, double *overflow) {
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  Dev &d = h->d;
+  if ((rc = density_at(h, copy))) return rc;
+  if (map) CK(cudaMemcpyAsync(map, d.M + (size_t)copy * d.G, sizeof(int64_t) * d.G, cudaMemcpyDefault, h->stream));
+  double s = 0;
+  CK(cudaMemcpyAsync(&s, d.scal + (size_t)copy * S_COUNT + S_TAU, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (overflow) *overflow = s / d.mov_area_q;
+  return PLACE_OK;
+}
+
+int place_get_fixed_map(place_t *h, int64_t *map) {
+  if (!h || !map) return fail(PLACE_EINVAL, "null argument");
+  CK(cudaMemcpyAsync(map, h->d.Fmap, sizeof(int64_t) * h->d.G, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PLACE_OK;
+}
+
+int place_eval_field(place_t *h, int32_t copy, float *psi, float *ex, float *ey) {
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  Dev &d = h->d;
+  if ((rc = density_at(h, copy))) return rc;
+  launch_spectral(d, copy, 1, 1, 1, h->stream);
+  CKL();
+  const size_t G = d.G;
+  const float *E = d.E + (size_t)copy * 3 * G;
+  if (ex) CK(cudaMemcpyAsync(ex, E, sizeof(float) * G, cudaMemcpyDefault, h->stream));
+  if (ey) CK(cudaMemcpyAsync(ey, E + G, sizeof(float) * G, cudaMemcpyDefault, h->stream));
+  if (psi) CK(cudaMemcpyAsync(psi, E + 2 * G, sizeof(float) * G, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PLACE_OK;
+}
+
+int place_eval_density_grad(place_t *h, int32_t copy, float *gx, float *gy) {
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  Dev &d = h->d;
+  if ((rc = density_at(h, copy))) return rc;
+  launch_spectral(d, copy, 1, 0, 1, h->stream);
+  launch_cell_grad(d, copy, 1, 1, h->stream);
+  CKL();
+  const size_t Mv = d.n_mov;
+  if (gx) CK(cudaMemcpyAsync(gx, d.gdx + copy * Mv, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
+  if (gy) CK(cudaMemcpyAsync(gy, d.gdy + copy * Mv, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PLACE_OK;
+}
+
+int place_eval_hpwl_overflow(place_t *h, double *hpwl, double *overflow) {
+  if (!h) return fail(PLACE_EINVAL, "null handle");
+  Dev &d = h->d;
+  const int K = d.K;
+  launch_hpwl64(d, 0, K, h->stream);
+  launch_reduce_slot(d, S_HP64, d.cell_blocks, 0, K, h->stream);
+  CK(cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.G * K, h->stream));
+  launch_scatter(d, 0, K, 1, h->stream);
+  launch_density_finish(d, 0, K, 1, h->stream);
+  launch_reduce_slot(d, S_TAU, d.bin_blocks, 0, K, h->stream);
+  CKL();
+  std::vector<double> sc((size_t)K * S_COUNT);
+  CK(cudaMemcpyAsync(sc.data(), d.scal, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < K; ++c) {
+    if (hpwl) hpwl[c] = sc[(size_t)c * S_COUNT + S_HP64];
+    if (overflow) overflow[c] = sc[(size_t)c * S_COUNT + S_TAU] / d.mov_area_q;
+  }
+  return PLACE_OK;
+}
+
+int place_perturb(place_t *h, int32_t op, float p, uint64_t seed, int32_t copy) {
+  int rc = check_copy(h, copy, true);
+  if (rc) return rc;
+  if (op != PLACE_SHUFFLE_MACRO && op != PLACE_SHUFFLE_ALL) return fail(PLACE_EINVAL, "unknown perturbation op %d", op);
+  if (!(p >= 0.f && p <= 1.f)) return fail(PLACE_EINVAL, "p must be in [0, 1]");
+  Dev &d = h->d;
+  const int ncand = op == PLACE_SHUFFLE_ALL ? h->n_cand_all : h->n_cand_macro;
+  int k = (int)std::floor((double)p * ncand + 0.5);
+  k = std::max(0, std::min(k, ncand));
+  int c0 = copy < 0 ? 0 : copy, n = copy < 0 ? d.K : 1;
+  for (int c = c0; c < c0 + n; ++c) {
+    uint64_t sd = copy < 0 ? seed + (uint64_t)c : seed;
+    if (k > 0) {
+      launch_shuffle(d, c, op, p, sd, h->stream);
+      launch_shuffle_finish(d, c, k, h->stream);
+      CKL();
+    }
+  }
+  return enqueue_reset(h, c0, n);
+}
+
+int place_hybro(place_t *h, int32_t n_rounds, int32_t op, float p, uint64_t seed, float tau_target,
+                double *best_hpwl, double *best_overflow, int32_t *best_round) {
+  if (!h) return fail(PLACE_EINVAL, "null handle");
+  if (n_rounds < 0) return fail(PLACE_EINVAL, "n_rounds < 0");
+  Dev &d = h->d;
+  const int K = d.K;
+  const size_t C = d.n_cells;
+  std::vector<double> bh(K, 0.0), bt(K, 0.0), hp(K), tau(K);
+  std::vector<int> br(K, -1), conv(K);
+  for (int r = 0; r <= n_rounds; ++r) {
+    // place every copy until it stops (converged or max_iters)
+    for (;;) {
+      int rc = place_step(h, 32, conv.data());
+      if (rc) return rc;
+      bool all = true;
+      for (int c = 0; c < K; ++c) all = all && conv[c];
+      if (all) break;
+    }
+    int rc = place_eval_hpwl_overflow(h, hp.data(), tau.data());
+    if (rc) return rc;
+    for (int c = 0; c < K; ++c) {
+      bool better = br[c] < 0;
+      if (!better) {
+        int fa = tau[c] <= tau_target ? 0 : 1, fb = bt[c] <= tau_target ? 0 : 1;
+        better = fa != fb ? fa < fb : (hp[c] != bh[c] ? hp[c] < bh[c] : tau[c] < bt[c]);
+      }
+      if (better) {
+        bh[c] = hp[c]; bt[c] = tau[c]; br[c] = r;
+        CK(cudaMemcpyAsync(d.bx + c * C, d.x + c * C, sizeof(float) * C, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(d.by + c * C, d.y + c * C, sizeof(float) * C, cudaMemcpyDeviceToDevice, h->stream));
+      }
+    }
+    if (r < n_rounds) {
+      for (int c = 0; c < K; ++c) {
+        int rc2 = place_perturb(h, op, p, seed + (uint64_t)r * K + c, c);
+        if (rc2) return rc2;
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < K; ++c) {
+    if (best_hpwl) best_hpwl[c] = bh[c];
+    if (best_overflow) best_overflow[c] = bt[c];
+    if (best_round) best_round[c] = br[c];
+  }
+  h->best_hpwl = bh; h->best_tau = bt; h->best_round = br;
+  return PLACE_OK;
+}
+
+int place_get_best_positions(place_t *h, int32_t copy, float *x, float *y) {
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  if (h->best_round.empty()) return fail(PLACE_EINVAL, "place_hybro has not run on this handle");
+  const size_t C = h->d.n_cells;
+  if (x) CK(cudaMemcpyAsync(x, h->d.bx + copy * C, sizeof(float) * C, cudaMemcpyDefault, h->stream));
+  if (y) CK(cudaMemcpyAsync(y, h->d.by + copy * C, sizeof(float) * C, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PLACE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// Device helpers shared by the library's kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hp {
+
+__device__ __forceinline__ long long floordiv_ll(long long a, long long b) {
+  long long q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+  return q;
+}
+
+// Deterministic block sum of one double per thread (fixed shuffle/smem tree);
+// the result is valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *sm) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sm[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = (l < NT / 32) ? sm[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;
+}
+
+// Quantised rectangle of a cell and the clipped bin range it touches.
+struct QRect {
+  long long X, Y, W, H;
+  int ix0, ix1, iy0, iy1;
+};
+
+__device__ __forceinline__ QRect qrect(float x, float y, int W, int H, float scale, long long XL,
+                                       long long YL, long long BW, long long BH, int nx, int ny) {
+  QRect r;
+  // x * 2^F is exact in FP32; rounding to the nearest integer, ties to even
+  // non-finite or huge coordinates saturate far outside the die (empty range)
+  const float lim = 4.0e18f;
+  float xs = x * scale, ys = y * scale;
+  xs = (xs == xs) ? fminf(fmaxf(xs, -lim), lim) : -lim;
+  ys = (ys == ys) ? fminf(fmaxf(ys, -lim), lim) : -lim;
+  r.X = __float2ll_rn(xs);
+  r.Y = __float2ll_rn(ys);
+  r.W = W;
+  r.H = H;
+  long long a0 = floordiv_ll(r.X - XL, BW), a1 = floordiv_ll(r.X + r.W - 1 - XL, BW);
+  long long b0 = floordiv_ll(r.Y - YL, BH), b1 = floordiv_ll(r.Y + r.H - 1 - YL, BH);
+  // clip to the grid in 64 bits before narrowing; an empty range (lo > hi)
+  // results for rectangles outside the die or non-finite coordinates
+  a0 = a0 < 0 ? 0 : (a0 > nx ? nx : a0);
+  a1 = a1 >= nx ? nx - 1 : (a1 < -1 ? -1 : a1);
+  b0 = b0 < 0 ? 0 : (b0 > ny ? ny : b0);
+  b1 = b1 >= ny ? ny - 1 : (b1 < -1 ? -1 : b1);
+  r.ix0 = (int)a0;
+  r.ix1 = (int)a1;
+  r.iy0 = (int)b0;
+  r.iy1 = (int)b1;
+  return r;
+}
+
+__device__ __forceinline__ long long overlap1(long long lo, long long size, long long b0,
+                                              long long step) {
+  long long hi = lo + size, bh = b0 + step;
+  long long o = (hi < bh ? hi : bh) - (lo > b0 ? lo : b0);
+  return o > 0 ? o : 0;
+}
+
+}  // namespace hp

@@ -1,0 +1,135 @@
+// Internal declarations of the sm_103a placement library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hybro_place.h"
+
+namespace hp {
+
+constexpr int kThreads = 256;       // block size of the per-cell / per-bin kernels
+constexpr int kRedThreads = 1024;   // block size of the per-copy reducers
+constexpr int kMaxCellBlocks = 1216;  // per copy: 8 blocks per SM on 152 SMs
+
+// Optimiser scalars of one copy, resident on the device.  Kernels of one
+// iteration read and write these; the host only reads them back on demand.
+struct CopyState {
+  double lam;        // density weight lambda (Eq. 2)
+  double alpha;      // step length of the current iteration
+  double a;          // Nesterov momentum sequence a_k
+  double a_next;
+  double coef;       // (a_k - 1) / a_{k+1}
+  double tau;        // overflow at the current reference point
+  double tau_prev;   // overflow of the previous reference point (drives gamma)
+  double hpwl;       // HPWL of the last WA pass (pin max - min, FP32 pins)
+  double hpwl_prev;
+  double wl;         // WA wirelength of the last pass (Eq. 2 first term)
+  double gamma;      // gamma of the current iteration (Eq. 3)
+  int k;             // iterations done since reset
+  int converged;
+  int stopped;
+  int parity;        // selects the current / previous gradient buffer
+  int err;
+  int pad[3];
+};
+
+// Reduction slots (FP64) per copy: each kernel that reduces writes one value
+// per block into its slot range; a reducer sums them in a fixed order.
+enum Slot { S_TAU = 0, S_HPWL, S_WL, S_GW1, S_GD1, S_DG2, S_DV2, S_G2, S_HP64, S_COUNT };
+
+struct Dev {
+  // sizes
+  int K, n_cells, n_mov, n_nets, n_pins, n_mov_pins, nx, ny, G;
+  int F;
+  long long XL, YL, BW, BH;   // fixed point
+  float scale;                // 2^F
+  float inv_area_q;           // 2^-2F as float
+  double t;                   // target density (float widened)
+  double abin_q;              // BW * BH
+  double mov_area_q;
+  double die_xl, die_yl, die_xh, die_yh;
+  float fxl, fyl, fxh, fyh;
+  double w_bin, dref;
+  int nb_red;                 // partial slots per reduction per copy
+  int cell_blocks;            // blocks per copy for per-cell kernels
+  int bin_blocks;             // blocks per copy for per-bin kernels
+  place_params prm;
+
+  // netlist (library order: nets grouped by degree class)
+  int *net_ptr;      // [n_nets+1]
+  int *pin_cell;     // [n_pins]
+  float2 *pin_off;   // [n_pins]
+  float *net_w;      // [n_nets] or nullptr
+  int has_net_w;
+  int *cell_pin_ptr; // [n_mov+1]
+  int *cell_pins;    // [n_mov_pins] pin ids of each movable cell
+  float *w, *h;      // [n_cells]
+  int *Wq, *Hq;      // [n_cells] quantised sizes
+  float *npins;      // [n_mov] pin count per movable cell
+  float *area;       // [n_mov]
+  unsigned char *is_macro;  // [n_cells]
+
+  // per-copy state
+  float *x, *y;              // [K][n_cells] reference positions v (fixed part replicated)
+  float *ux, *uy;            // [K][n_mov]
+  float *vpx, *vpy;          // [K][n_mov]
+  float *gx[2], *gy[2];      // [K][n_mov] preconditioned gradient, by parity
+  float *gwx, *gwy, *gdx, *gdy;  // [K][n_mov] raw gradients
+  float2 *pin_grad;          // [K][n_pins]
+  unsigned long long *M;     // [K][G]
+  long long *Fmap;           // [G]
+  float *rho;                // [K][G]
+  float *T;                  // [K][3][G] transform intermediates
+  float *SB;                 // [K][3][G] spectral coefficients (x, y, psi)
+  float *E;                  // [K][3][G] Ex, Ey, psi
+  CopyState *cs;             // [K]
+  double *part;              // [K][S_COUNT][nb_red]
+  double *scal;              // [K][S_COUNT] reduced values (eval reductions)
+
+  // spectral tables
+  float *Cn, *Cm, *CTn, *STn, *STm, *CTm;  // transform matrices
+  float *wu, *wv;                          // wavenumbers
+  float *cu, *cv;                          // c_k / n factors
+
+  // Hybro best solutions
+  float *bx, *by;            // [K][n_cells]
+
+  // perturbation scratch
+  unsigned long long *sort_key;  // [2^ceil(log2 n_cells)]
+  unsigned int *sort_idx;
+  unsigned int *sel_idx;          // [pow2]
+  float *px_tmp, *py_tmp;         // [n_cells]
+  int sort_n;                      // padded length
+
+  // WA launch plan: nets [cls_begin[c], cls_begin[c+1]) belong to class c
+  int cls_begin[8];
+  int n_cls;
+  int wa_blocks[8];           // blocks per class per copy
+  int wa_block_base[8];       // slot offset of the class's blocks
+  int wa_blocks_total;
+};
+
+// ---- launchers (all enqueue on `st`) ------------------------------------
+// eval != 0 ignores the stopped flag of the copy (stage-level evaluation).
+void launch_scatter(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
+void launch_scatter_fixed(const Dev &d, const float *x, const float *y, int n0, int n1,
+                          unsigned long long *out, cudaStream_t st);
+void launch_density_finish(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
+void launch_spectral(const Dev &d, int copy0, int ncopy, int with_psi, int eval, cudaStream_t st);
+void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_override,
+               cudaStream_t st);
+void launch_hpwl64(const Dev &d, int copy0, int ncopy, cudaStream_t st);
+void launch_cell_grad(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
+void launch_iteration_scalars(const Dev &d, int phase, int copy0, int ncopy, cudaStream_t st);
+void launch_precond0(const Dev &d, int copy0, int ncopy, cudaStream_t st);
+void launch_update(const Dev &d, int copy0, int ncopy, cudaStream_t st);
+void launch_reset(const Dev &d, int copy0, int ncopy, cudaStream_t st);
+void launch_reduce_slot(const Dev &d, int slot, int nvals, int copy0, int ncopy, cudaStream_t st);
+int launch_shuffle(const Dev &d, int copy, int op, float p, uint64_t seed, cudaStream_t st);
+void launch_shuffle_finish(const Dev &d, int copy, int kcount, cudaStream_t st);
+
+// iteration phases of launch_iteration_scalars
+enum Phase { PH_BEGIN = 0, PH_TAU, PH_TAU_RESET, PH_MID, PH_ALPHA, PH_END };
+
+}  // namespace hp

@@ -1,0 +1,146 @@
+// Spectral Poisson solve as chains of dense transforms (the ePlace
+// electrostatic system the paper cites): with C[u][x] = cos(pi u (x+1/2)/M),
+// S[x][u] = sin(pi u (x+1/2)/M) and continuous wavenumbers
+// w_u = pi u / (M h_x):
+//   a_uv  = c_u c_v / (M N) sum_x sum_y rho_xy C_M[u][x] C_N[v][y]
+//   Ex_xy = sum_uv a_uv w_u / (w_u^2 + w_v^2) S_M[x][u] C_N[y][v]
+//   Ey_xy = sum_uv a_uv w_v / (w_u^2 + w_v^2) C_M[x][u] S_N[y][v]
+//   psi_xy = sum_uv a_uv / (w_u^2 + w_v^2) C_M[x][u] C_N[y][v]    ((u,v) != 0)
+// Every step is one GEMM D = A B^T with both operands K-major (row-major,
+// K contiguous):
+//   G1  T1[v][x]  = sum_y Cn[v][y]  rho[x][y]
+//   G2  A^[u][v]  = sum_x Cm[u][x]  T1[v][x]    epilogue: spectral weights -> Bx, By (, Bpsi)
+//   G3  T[w][y][u] = sum_v An_w[y][v] B_w[u][v]  An = (C_N^T, S_N, C_N^T) for (x, y, psi)
+//   G4  E[w][x][y] = sum_u Am_w[x][u] T[w][y][u] Am = (S_M, C_M^T, C_M^T)
+// so no transpose pass is needed between steps.
+//
+// This file holds the FP32 CUDA-core GEMM (64x64x16 tiles, 4x4 register
+// micro-tiles); the tensor-core split-TF32 path lives in spectral_tc.cu.
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace hp {
+
+struct GemmArgs {
+  const float *A[3];
+  const float *B;
+  long long sBw, sBc;  // stride between 'which' and between copies
+  float *D;
+  long long sDw, sDc;
+  int M, N, K;         // D is M x N, contraction K
+  int nwhich, copy0;
+  int spectral;        // G2 epilogue
+  int with_psi;
+  const float *wu, *wv, *cu, *cv;
+  const CopyState *cs;
+  int eval;
+};
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm_nt(GemmArgs g) {
+  __shared__ float As[BK][BM + 4];
+  __shared__ float Bs[BK][BN + 4];
+  const int z = blockIdx.z;
+  const int which = z % g.nwhich;
+  const int c = g.copy0 + z / g.nwhich;
+  if (!g.eval && g.cs[c].stopped) return;
+  const float *A = g.A[which];
+  const float *B = g.B + which * g.sBw + c * g.sBc;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int tid = threadIdx.x;
+  const int lr = tid >> 2, lk = (tid & 3) * 4;  // loader: row, k offset
+  const int tx = tid & 15, ty = tid >> 4;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < g.K; k0 += BK) {
+    float4 av = make_float4(0.f, 0.f, 0.f, 0.f), bv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m0 + lr < g.M) av = *reinterpret_cast<const float4 *>(A + (size_t)(m0 + lr) * g.K + k0 + lk);
+    if (n0 + lr < g.N) bv = *reinterpret_cast<const float4 *>(B + (size_t)(n0 + lr) * g.K + k0 + lk);
+    As[lk + 0][lr] = av.x; As[lk + 1][lr] = av.y; As[lk + 2][lr] = av.z; As[lk + 3][lr] = av.w;
+    Bs[lk + 0][lr] = bv.x; Bs[lk + 1][lr] = bv.y; Bs[lk + 2][lr] = bv.z; Bs[lk + 3][lr] = bv.w;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float4 a4 = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+      float4 b4 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+      float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float *D = g.D + which * g.sDw + c * g.sDc;
+  const size_t GN = (size_t)g.M * g.N;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty * 4 + i;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx * 4 + j;
+      if (n >= g.N) continue;
+      const size_t o = (size_t)m * g.N + n;
+      if (!g.spectral) {
+        D[o] = acc[i][j];
+      } else {
+        const float a = acc[i][j] * g.cu[m] * g.cv[n];
+        const float wu = g.wu[m], wv = g.wv[n];
+        const float den = wu * wu + wv * wv;
+        const bool dc = (m == 0 && n == 0);
+        const float inv = dc ? 0.f : 1.f / den;
+        D[o] = a * wu * inv;
+        D[GN + o] = a * wv * inv;
+        if (g.with_psi) D[2 * GN + o] = a * inv;
+      }
+    }
+  }
+}
+
+static void gemm(const GemmArgs &g, int ncopy, cudaStream_t st) {
+  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.nwhich * ncopy);
+  k_gemm_nt<<<grid, 256, 0, st>>>(g);
+}
+
+void launch_spectral_fp32(const Dev &d, int copy0, int ncopy, int with_psi, int eval,
+                          cudaStream_t st) {
+  const int M = d.nx, N = d.ny;
+  const long long G = d.G;
+  GemmArgs g = {};
+  g.copy0 = copy0;
+  g.cs = d.cs;
+  g.eval = eval;
+  g.wu = d.wu; g.wv = d.wv; g.cu = d.cu; g.cv = d.cv;
+  // G1: T1 = Cn * rho^T   (N x M, K = N)
+  g.A[0] = d.Cn;
+  g.B = d.rho; g.sBw = 0; g.sBc = G;
+  g.D = d.T; g.sDw = 0; g.sDc = 3 * G;
+  g.M = N; g.N = M; g.K = N; g.nwhich = 1; g.spectral = 0;
+  gemm(g, ncopy, st);
+  // G2: A^ = Cm * T1^T   (M x N, K = M), spectral epilogue into SB
+  g.A[0] = d.Cm;
+  g.B = d.T; g.sBw = 0; g.sBc = 3 * G;
+  g.D = d.SB; g.sDw = 0; g.sDc = 3 * G;
+  g.M = M; g.N = N; g.K = M; g.spectral = 1; g.with_psi = with_psi;
+  gemm(g, ncopy, st);
+  // G3: T[w] = An_w * B_w^T   (N x M, K = N)
+  g.A[0] = d.CTn; g.A[1] = d.STn; g.A[2] = d.CTn;
+  g.B = d.SB; g.sBw = G; g.sBc = 3 * G;
+  g.D = d.T; g.sDw = G; g.sDc = 3 * G;
+  g.M = N; g.N = M; g.K = N; g.spectral = 0; g.nwhich = with_psi ? 3 : 2;
+  gemm(g, ncopy, st);
+  // G4: E[w] = Am_w * T[w]^T   (M x N, K = M)
+  g.A[0] = d.STm; g.A[1] = d.CTm; g.A[2] = d.CTm;
+  g.B = d.T; g.sBw = G; g.sBc = 3 * G;
+  g.D = d.E; g.sDw = G; g.sDc = 3 * G;
+  g.M = M; g.N = N; g.K = M;
+  gemm(g, ncopy, st);
+}
+
+void launch_spectral(const Dev &d, int copy0, int ncopy, int with_psi, int eval,
+                     cudaStream_t st) {
+  launch_spectral_fp32(d, copy0, ncopy, with_psi, eval, st);
+}
+
+}  // namespace hp

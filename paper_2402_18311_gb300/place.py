@@ -1,0 +1,265 @@
+"""ctypes binding of the C ABI in ``include/hybro_place.h``.
+
+Argument marshalling only: every computation runs in ``libhybro_place.so``.
+Functions keep the C names.  Array arguments accept numpy arrays (host
+memory) or torch tensors (host or CUDA); results are written into the
+caller's buffers, as in C.  The library must have been built
+(``paper_2402_18311_gb300.build.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhybro_place.so")
+
+PLACE_OK = 0
+PLACE_EINVAL = -1
+PLACE_ENOMEM = -2
+PLACE_ECUDA = -3
+PLACE_ERANGE = -4
+PLACE_ETIMEOUT = -5
+PLACE_EINTERNAL = -6
+PLACE_SHUFFLE_MACRO = 0
+PLACE_SHUFFLE_ALL = 1
+PLACE_DCT_FP32 = 0
+PLACE_DCT_TF32X3 = 1
+PLACE_STAGES = ("density", "spectral", "wirelength", "cellgrad", "update")
+
+
+class PlaceError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"place error {code}: {msg}")
+        self.code = code
+
+
+class place_netlist(ct.Structure):
+    _fields_ = [("n_cells", ct.c_int32), ("n_movable", ct.c_int32), ("n_nets", ct.c_int32),
+                ("n_pins", ct.c_int32),
+                ("w", ct.c_void_p), ("h", ct.c_void_p), ("x0", ct.c_void_p), ("y0", ct.c_void_p),
+                ("net_ptr", ct.c_void_p), ("pin_cell", ct.c_void_p),
+                ("pin_dx", ct.c_void_p), ("pin_dy", ct.c_void_p),
+                ("net_w", ct.c_void_p), ("is_macro", ct.c_void_p)]
+
+
+class place_die(ct.Structure):
+    _fields_ = [("xl", ct.c_double), ("yl", ct.c_double), ("xh", ct.c_double), ("yh", ct.c_double)]
+
+
+class place_bins(ct.Structure):
+    _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("target_density", ct.c_float)]
+
+
+class place_params(ct.Structure):
+    _fields_ = [("n_copies", ct.c_int32), ("gamma_base", ct.c_float), ("lambda_eta", ct.c_float),
+                ("alpha0", ct.c_float), ("hpwl_ref", ct.c_float), ("mu_base", ct.c_float),
+                ("mu_lo", ct.c_float), ("mu_hi", ct.c_float), ("tau_stop", ct.c_float),
+                ("max_iters", ct.c_int32), ("constant_gamma", ct.c_float), ("dct_mode", ct.c_int32)]
+
+
+class place_info(ct.Structure):
+    _fields_ = [("n_cells", ct.c_int32), ("n_movable", ct.c_int32), ("n_nets", ct.c_int32),
+                ("n_pins", ct.c_int32), ("nx", ct.c_int32), ("ny", ct.c_int32),
+                ("n_copies", ct.c_int32), ("frac_bits", ct.c_int32),
+                ("bin_w_q", ct.c_int64), ("bin_h_q", ct.c_int64),
+                ("bin_w", ct.c_double), ("bin_h", ct.c_double), ("device_bytes", ct.c_int64),
+                ("kernels_per_iter", ct.c_int32), ("pad", ct.c_int32)]
+
+
+class place_state(ct.Structure):
+    _fields_ = [("iter", ct.c_int32), ("converged", ct.c_int32), ("stopped", ct.c_int32),
+                ("pad", ct.c_int32), ("lambda_", ct.c_double), ("gamma", ct.c_double),
+                ("alpha", ct.c_double), ("a", ct.c_double), ("overflow", ct.c_double),
+                ("hpwl_wa", ct.c_double)]
+
+
+_VP = ct.c_void_p
+_SIGS = {
+    "place_default_params": (None, [ct.POINTER(place_params)]),
+    "place_create": (ct.c_int, [ct.POINTER(place_netlist), ct.POINTER(place_die),
+                                ct.POINTER(place_bins), ct.POINTER(place_params), _VP,
+                                ct.POINTER(_VP)]),
+    "place_destroy": (ct.c_int, [_VP]),
+    "place_get_info": (ct.c_int, [_VP, ct.POINTER(place_info)]),
+    "place_step": (ct.c_int, [_VP, ct.c_int32, _VP]),
+    "place_perturb": (ct.c_int, [_VP, ct.c_int32, ct.c_float, ct.c_uint64, ct.c_int32]),
+    "place_eval_hpwl_overflow": (ct.c_int, [_VP, _VP, _VP]),
+    "place_get_positions": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
+    "place_set_positions": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
+    "place_get_state": (ct.c_int, [_VP, ct.c_int32, ct.POINTER(place_state)]),
+    "place_eval_wirelength": (ct.c_int, [_VP, ct.c_int32, ct.c_float, _VP, _VP, _VP]),
+    "place_eval_density": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
+    "place_get_fixed_map": (ct.c_int, [_VP, _VP]),
+    "place_eval_field": (ct.c_int, [_VP, ct.c_int32, _VP, _VP, _VP]),
+    "place_eval_density_grad": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
+    "place_hybro": (ct.c_int, [_VP, ct.c_int32, ct.c_int32, ct.c_float, ct.c_uint64, ct.c_float,
+                               _VP, _VP, _VP]),
+    "place_get_best_positions": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
+    "place_step_timed": (ct.c_int, [_VP, ct.c_int32, _VP]),
+    "place_last_error": (ct.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load the library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2402_18311_gb300.build.build()")
+        L = ct.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc):
+    if rc != PLACE_OK:
+        raise PlaceError(rc, lib().place_last_error().decode(errors="replace"))
+    return rc
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+# ---- C entry points with their C names ------------------------------------
+
+def place_default_params(**overrides):
+    p = place_params()
+    lib().place_default_params(ct.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def place_create(design, params=None, stream=None):
+    """Create a handle for a ``synth.Design`` (host arrays are copied)."""
+    keep = dict(w=np.ascontiguousarray(design.w, np.float32),
+                h=np.ascontiguousarray(design.h, np.float32),
+                x0=np.ascontiguousarray(design.x, np.float32),
+                y0=np.ascontiguousarray(design.y, np.float32),
+                net_ptr=np.ascontiguousarray(design.net_ptr, np.int32),
+                pin_cell=np.ascontiguousarray(design.pin_cell, np.int32),
+                pin_dx=np.ascontiguousarray(design.pin_dx, np.float32),
+                pin_dy=np.ascontiguousarray(design.pin_dy, np.float32))
+    net_w = getattr(design, "net_w", None)
+    if net_w is not None:
+        keep["net_w"] = np.ascontiguousarray(net_w, np.float32)
+    if design.is_macro is not None:
+        keep["is_macro"] = np.ascontiguousarray(design.is_macro, np.uint8)
+    nl = place_netlist(design.n_cells, design.n_movable, design.n_nets, design.n_pins,
+                       *(_ptr(keep[k]) for k in ("w", "h", "x0", "y0", "net_ptr", "pin_cell",
+                                                 "pin_dx", "pin_dy")),
+                       _ptr(keep.get("net_w")), _ptr(keep.get("is_macro")))
+    die = place_die(*design.die)
+    bins = place_bins(design.nx, design.ny, design.target_density)
+    prm = params if params is not None else place_default_params()
+    h = _VP()
+    _check(lib().place_create(ct.byref(nl), ct.byref(die), ct.byref(bins), ct.byref(prm),
+                              _VP(stream or 0), ct.byref(h)))
+    return h
+
+
+def place_destroy(h):
+    return _check(lib().place_destroy(h))
+
+
+def place_get_info(h):
+    o = place_info()
+    _check(lib().place_get_info(h, ct.byref(o)))
+    return o
+
+
+def place_step(h, n_iters, converged=None):
+    return _check(lib().place_step(h, int(n_iters), _ptr(converged)))
+
+
+def place_perturb(h, op, p, seed, copy=-1):
+    return _check(lib().place_perturb(h, int(op), float(p), int(seed), int(copy)))
+
+
+def place_eval_hpwl_overflow(h, hpwl=None, overflow=None):
+    return _check(lib().place_eval_hpwl_overflow(h, _ptr(hpwl), _ptr(overflow)))
+
+
+def place_get_positions(h, copy, x, y):
+    return _check(lib().place_get_positions(h, int(copy), _ptr(x), _ptr(y)))
+
+
+def place_set_positions(h, copy, x, y):
+    return _check(lib().place_set_positions(h, int(copy), _ptr(x), _ptr(y)))
+
+
+def place_get_state(h, copy):
+    o = place_state()
+    _check(lib().place_get_state(h, int(copy), ct.byref(o)))
+    return o
+
+
+def place_eval_wirelength(h, copy, gamma, grad_x=None, grad_y=None):
+    wl = ct.c_double()
+    _check(lib().place_eval_wirelength(h, int(copy), float(gamma), ct.byref(wl),
+                                       _ptr(grad_x), _ptr(grad_y)))
+    return wl.value
+
+
+def place_eval_density(h, copy, out_map=None):
+    tau = ct.c_double()
+    _check(lib().place_eval_density(h, int(copy), _ptr(out_map), ct.byref(tau)))
+    return tau.value
+
+
+def place_get_fixed_map(h, out_map):
+    return _check(lib().place_get_fixed_map(h, _ptr(out_map)))
+
+
+def place_eval_field(h, copy, psi=None, ex=None, ey=None):
+    return _check(lib().place_eval_field(h, int(copy), _ptr(psi), _ptr(ex), _ptr(ey)))
+
+
+def place_eval_density_grad(h, copy, grad_x=None, grad_y=None):
+    return _check(lib().place_eval_density_grad(h, int(copy), _ptr(grad_x), _ptr(grad_y)))
+
+
+def place_hybro(h, n_rounds, op, p, seed, tau_target, best_hpwl=None, best_overflow=None,
+                best_round=None):
+    return _check(lib().place_hybro(h, int(n_rounds), int(op), float(p), int(seed),
+                                    float(tau_target), _ptr(best_hpwl), _ptr(best_overflow),
+                                    _ptr(best_round)))
+
+
+def place_get_best_positions(h, copy, x, y):
+    return _check(lib().place_get_best_positions(h, int(copy), _ptr(x), _ptr(y)))
+
+
+def place_step_timed(h, n_iters, stage_ms):
+    """stage_ms: float32 numpy array [5]; per-stage milliseconds are added."""
+    return _check(lib().place_step_timed(h, int(n_iters), _ptr(stage_ms)))
+
+
+def place_last_error():
+    return lib().place_last_error().decode(errors="replace")

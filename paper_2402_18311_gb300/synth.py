@@ -98,7 +98,10 @@ def _distinct_pins(rng, deg, n_cells):
     n_pins = int(ptr[-1])
     net_of_pin = np.repeat(np.arange(deg.shape[0], dtype=np.int64), deg)
     cells = rng.integers(0, n_cells, n_pins)
-    for _ in range(64):
+    # nets that take a large share of the cells: draw without replacement
+    for e in np.nonzero(2 * deg > n_cells)[0]:
+        cells[ptr[e]:ptr[e + 1]] = rng.choice(n_cells, int(deg[e]), replace=False)
+    for _ in range(200):
         key = net_of_pin * n_cells + cells
         order = np.argsort(key, kind="stable")
         sk = key[order]

@@ -1,0 +1,89 @@
+"""The C-ABI library loads, exports every entry point its header declares, and
+rejects malformed input on the host before touching the GPU."""
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import placer as opl
+from paper_2402_18311_gb300 import place, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hybro_place.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not os.path.exists(place.LIB_PATH):
+        from paper_2402_18311_gb300 import build
+        build.build()
+    return place.lib()
+
+
+def declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(place_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(place.exported_symbols()) == names
+
+
+def test_default_params_match_the_oracle_reading(L):
+    p = place.place_default_params()
+    o = opl.Params()
+    assert p.n_copies == 1
+    for f in ("gamma_base", "lambda_eta", "alpha0", "hpwl_ref", "mu_base", "mu_lo", "mu_hi",
+              "tau_stop"):
+        assert getattr(p, f) == pytest.approx(getattr(o, f), rel=1e-7), f
+    assert p.max_iters == o.max_iters
+
+
+def test_struct_sizes_match_header_layout():
+    assert ct.sizeof(place.place_netlist) == 4 * 4 + 10 * 8
+    assert ct.sizeof(place.place_params) == 12 * 4
+    assert ct.sizeof(place.place_state) == 4 * 4 + 6 * 8
+    assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 2 * 4
+
+
+def _design():
+    return synth.make_design(n_movable=20, die=(0, 0, 64, 64), nx=16, ny=16, n_nets=15,
+                             n_pads=4, seed=3)
+
+
+@pytest.mark.parametrize("mut,msg", [
+    (lambda d: setattr(d, "nx", 12), "multiples of 16"),
+    (lambda d: d.pin_cell.__setitem__(0, 10 ** 6), "out of range"),
+    (lambda d: d.w.__setitem__(3, 0.0), "non-positive size"),
+    (lambda d: d.net_ptr.__setitem__(1, d.net_ptr[2] + 1), "monotone"),
+    (lambda d: setattr(d, "die", (0.1, 0, 64, 64)), "multiples of 2^-"),
+])
+def test_create_rejects_malformed_input_on_host(L, mut, msg):
+    d = _design()
+    mut(d)
+    with pytest.raises(place.PlaceError) as ei:
+        place.place_create(d)
+    assert ei.value.code == place.PLACE_EINVAL
+    assert msg in str(ei.value)
+
+
+def test_create_rejects_bad_params(L):
+    d = _design()
+    with pytest.raises(place.PlaceError) as ei:
+        place.place_create(d, place.place_default_params(n_copies=0))
+    assert ei.value.code == place.PLACE_EINVAL
+    with pytest.raises(place.PlaceError):
+        place.place_create(d, place.place_default_params(dct_mode=7))
+
+
+def test_null_handle_calls_fail_cleanly(L):
+    assert L.place_step(None, 1, None) == place.PLACE_EINVAL
+    assert L.place_destroy(None) == place.PLACE_OK
+    assert b"null" in L.place_last_error()

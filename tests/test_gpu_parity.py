@@ -1,0 +1,307 @@
+"""Parity of the sm_103a library (through its C ABI) with the FP64 oracle.
+
+Tolerances: density maps, fixed maps and perturbation results bit-exact;
+WA wirelength relative 1e-5; gradients and fields relative L2 1e-4; FP64
+HPWL relative 1e-12; final HPWL after 300 identical-seed iterations relative
+1e-3.
+"""
+import numpy as np
+import pytest
+
+from oracle import density as odens
+from oracle import hybro as ohy
+from oracle import perturb as opt
+from oracle import placer as opl
+from oracle import poisson as opois
+from oracle import wirelength as owl
+from paper_2402_18311_gb300 import place, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    if not os.path.exists(place.LIB_PATH):
+        from paper_2402_18311_gb300 import build
+        build.build()
+    place.lib()
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64); b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+class Handle:
+    def __init__(self, design, **params):
+        self.d = design
+        self.prm = place.place_default_params(**params)
+        self.h = place.place_create(design, self.prm)
+        self.info = place.place_get_info(self.h)
+
+    def pos(self, copy=0):
+        x = np.empty(self.d.n_cells, np.float32); y = np.empty(self.d.n_cells, np.float32)
+        place.place_get_positions(self.h, copy, x, y)
+        return x, y
+
+    def close(self):
+        place.place_destroy(self.h)
+
+
+def oracle_grid(d, info):
+    return odens.Grid(d.die, d.nx, d.ny, info.frac_bits)
+
+
+def oracle_maps(d, info, x, y):
+    g = oracle_grid(d, info)
+    n = d.n_movable
+    W, H = odens.quantize(d.w, g.F), odens.quantize(d.h, g.F)
+    M = odens.overlap_map(odens.quantize(x[:n], g.F), odens.quantize(y[:n], g.F), W[:n], H[:n], g)
+    Fm = odens.overlap_map(odens.quantize(d.x[n:], g.F), odens.quantize(d.y[n:], g.F), W[n:], H[n:], g)
+    return g, M, Fm, int(np.sum(W[:n] * H[:n]))
+
+
+def spread(handle, iters):
+    place.place_step(handle.h, iters)
+    return handle.pos()
+
+
+def check_stages(handle, x, y, gamma):
+    d, info = handle.d, handle.info
+    n = d.n_movable
+    # WA wirelength and gradient (Eq. 3)
+    gx = np.empty(n, np.float32); gy = np.empty(n, np.float32)
+    wl = place.place_eval_wirelength(handle.h, 0, gamma, gx, gy)
+    owl_v, ogx, ogy = owl.wa_wirelength(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, x, y, gamma, n)
+    assert wl == pytest.approx(owl_v, rel=1e-5)
+    assert rel_l2(np.concatenate([gx, gy]), np.concatenate([ogx, ogy])) < 1e-4
+    # density map: bit-exact
+    g, M, Fm, amov = oracle_maps(d, info, x, y)
+    gm = np.empty(d.nx * d.ny, np.int64)
+    tau = place.place_eval_density(handle.h, 0, gm)
+    np.testing.assert_array_equal(gm.reshape(d.nx, d.ny), M)
+    fm = np.empty(d.nx * d.ny, np.int64)
+    place.place_get_fixed_map(handle.h, fm)
+    np.testing.assert_array_equal(fm.reshape(d.nx, d.ny), Fm)
+    otau = odens.overflow(M, Fm, np.float32(d.target_density), g, amov)
+    assert tau == pytest.approx(otau, rel=1e-12, abs=1e-15)
+    # field
+    rho = odens.bin_density(M, Fm, np.float32(d.target_density), g)
+    opsi, oex, oey = opois.poisson(rho, g.bin_w, g.bin_h)
+    G = d.nx * d.ny
+    psi = np.empty(G, np.float32); ex = np.empty(G, np.float32); ey = np.empty(G, np.float32)
+    place.place_eval_field(handle.h, 0, psi, ex, ey)
+    assert rel_l2(ex, oex.ravel()) < 1e-4
+    assert rel_l2(ey, oey.ravel()) < 1e-4
+    assert rel_l2(psi, opsi.ravel()) < 1e-4
+    # density gradient (field gather)
+    dgx = np.empty(n, np.float32); dgy = np.empty(n, np.float32)
+    place.place_eval_density_grad(handle.h, 0, dgx, dgy)
+    ogdx, ogdy = odens.field_gather(odens.quantize(x[:n], g.F), odens.quantize(y[:n], g.F),
+                                    odens.quantize(d.w[:n], g.F), odens.quantize(d.h[:n], g.F),
+                                    g, oex, oey)
+    assert rel_l2(np.concatenate([dgx, dgy]), np.concatenate([ogdx, ogdy])) < 1e-4
+    # FP64 HPWL (Eq. 1)
+    hp = np.empty(1); tv = np.empty(1)
+    place.place_eval_hpwl_overflow(handle.h, hp, tv)
+    assert hp[0] == pytest.approx(owl.hpwl(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, x, y), rel=1e-12)
+    assert tv[0] == pytest.approx(otau, rel=1e-12, abs=1e-15)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    h = Handle(synth.tiny_1k(0), tau_stop=-1.0, max_iters=300)
+    yield h
+    h.close()
+
+
+def test_stages_tiny_at_start(tiny):
+    x, y = tiny.pos()
+    d = tiny.d
+    np.testing.assert_array_equal(x[d.n_movable:], d.x[d.n_movable:])
+    for gamma in (16.0, 2.5):
+        check_stages(tiny, x, y, gamma)
+
+
+def test_stages_tiny_after_spreading(tiny):
+    x, y = spread(tiny, 150)
+    check_stages(tiny, x, y, 3.0)
+
+
+def test_first_step_matches_oracle():
+    d = synth.tiny_1k(0)
+    h = Handle(d, tau_stop=-1.0, max_iters=300)
+    try:
+        x0, y0 = h.pos()
+        place.place_step(h.h, 1)
+        x1, y1 = h.pos()
+        st = place.place_get_state(h.h, 0)
+        o = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=300))
+        o.step()
+        n = d.n_movable
+        dx = np.concatenate([x1[:n] - x0[:n], y1[:n] - y0[:n]])
+        odx = np.concatenate([o.vx - x0[:n], o.vy - y0[:n]])
+        assert rel_l2(dx, odx) < 1e-4
+        assert st.iter == 1
+        assert st.alpha == pytest.approx(o.alpha, rel=1e-4)
+        assert st.gamma == pytest.approx(o.history[0][3], rel=1e-6)
+        # lambda_0 is set in iteration 0; its first update comes in iteration 1
+        assert st.lambda_ == pytest.approx(o.lam, rel=1e-4)
+    finally:
+        h.close()
+
+
+def test_trajectory_300_iterations():
+    d = synth.tiny_1k(0)
+    h = Handle(d, tau_stop=-1.0, max_iters=300)
+    try:
+        o = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=300))
+        first_bad = None
+        hp = np.empty(1); tv = np.empty(1)
+        for k in range(0, 300, 20):
+            place.place_step(h.h, 20)
+            o.run(20)
+            place.place_eval_hpwl_overflow(h.h, hp, tv)
+            ohp = o.hpwl(o.vx, o.vy)
+            if first_bad is None and abs(hp[0] - ohp) > 1e-3 * ohp:
+                first_bad = (k + 20, hp[0], ohp)
+        st = place.place_get_state(h.h, 0)
+        assert st.iter == 300 and o.k == 300
+        ohp = o.hpwl(o.vx, o.vy)
+        assert hp[0] == pytest.approx(ohp, rel=1e-3), f"first divergence beyond 1e-3: {first_bad}"
+        assert tv[0] == pytest.approx(o.tau, abs=5e-3)
+    finally:
+        h.close()
+
+
+def test_shuffle_bit_exact():
+    d = synth.tiny_1k(0)
+    h = Handle(d, tau_stop=-1.0, max_iters=300)
+    try:
+        x, y = spread(h, 120)
+        for seed in (0, 5, 2 ** 63 + 17):
+            place.place_set_positions(h.h, 0, x, y)
+            place.place_perturb(h.h, place.PLACE_SHUFFLE_ALL, 0.5, seed, 0)
+            gx, gy = h.pos()
+            cand = ohy.candidates(d, ohy.SHUFFLE_ALL)
+            ox, oy = opt.shuffle(x, y, d.w, d.h, cand, 0.5, seed, d.die)
+            np.testing.assert_array_equal(gx, ox)
+            np.testing.assert_array_equal(gy, oy)
+        # Shuffle (macros) has no candidates here: positions unchanged
+        place.place_set_positions(h.h, 0, x, y)
+        place.place_perturb(h.h, place.PLACE_SHUFFLE_MACRO, 0.5, 3, 0)
+        gx, gy = h.pos()
+        np.testing.assert_array_equal(gx, x)
+    finally:
+        h.close()
+
+
+def test_batched_copies_equal_solo_runs():
+    d = synth.tiny_1k(1)
+    K = 3
+    hb = Handle(d, tau_stop=-1.0, max_iters=300, n_copies=K)
+    try:
+        place.place_step(hb.h, 80)
+        base_x, base_y = hb.pos(0)
+        place.place_set_positions(hb.h, -1, base_x, base_y)
+        place.place_perturb(hb.h, place.PLACE_SHUFFLE_ALL, 0.5, 100, -1)
+        place.place_step(hb.h, 60)
+        for c in range(K):
+            hs = Handle(d, tau_stop=-1.0, max_iters=300)
+            try:
+                place.place_set_positions(hs.h, 0, base_x, base_y)
+                place.place_perturb(hs.h, place.PLACE_SHUFFLE_ALL, 0.5, 100 + c, 0)
+                place.place_step(hs.h, 60)
+                sx, sy = hs.pos()
+                bx, by = hb.pos(c)
+                np.testing.assert_array_equal(bx, sx)
+                np.testing.assert_array_equal(by, sy)
+            finally:
+                hs.close()
+    finally:
+        hb.close()
+
+
+def test_convergence_stops_copy():
+    d = synth.tiny_1k(0)
+    h = Handle(d, tau_stop=0.3, max_iters=1000)
+    try:
+        conv = np.zeros(1, np.int32)
+        for _ in range(30):
+            place.place_step(h.h, 20, conv)
+            if conv[0]:
+                break
+        st = place.place_get_state(h.h, 0)
+        assert conv[0] == 1 and st.converged == 1 and st.overflow <= 0.3
+        x, y = h.pos()
+        place.place_step(h.h, 5)
+        x2, _ = h.pos()
+        np.testing.assert_array_equal(x, x2)
+        o = opl.Placer(d, opl.Params(tau_stop=0.3, max_iters=1000))
+        o.run()
+        assert abs(st.iter - o.k) <= 3
+    finally:
+        h.close()
+
+
+def test_hybro_two_rounds_matches_oracle():
+    d = synth.tiny_1k(0)
+    h = Handle(d, tau_stop=-1.0, max_iters=100)
+    try:
+        bh = np.empty(1); bt = np.empty(1); br = np.empty(1, np.int32)
+        place.place_hybro(h.h, 1, place.PLACE_SHUFFLE_ALL, 0.5, 7, 0.1, bh, bt, br)
+        best, rounds = ohy.run(d, opl.Params(tau_stop=-1.0, max_iters=100), n_rounds=1,
+                               op=ohy.SHUFFLE_ALL, p=0.5, seed=7, tau_target=0.1)
+        assert bh[0] == pytest.approx(rounds[best][0], rel=2e-3)
+        bx = np.empty(d.n_cells, np.float32); by = np.empty(d.n_cells, np.float32)
+        place.place_get_best_positions(h.h, 0, bx, by)
+        hp = owl.hpwl(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, bx, by)
+        assert hp == pytest.approx(bh[0], rel=1e-12)
+    finally:
+        h.close()
+
+
+def test_stages_scaled_20k_with_big_nets():
+    d = synth.scaled(20000, 128, seed=2)
+    assert np.max(np.diff(d.net_ptr)) > 256
+    h = Handle(d, tau_stop=-1.0, max_iters=1000)
+    try:
+        x, y = spread(h, 250)
+        check_stages(h, x, y, 1.7)
+    finally:
+        h.close()
+
+
+def test_edge_cases_small_design():
+    # empty and single-pin nets, one-cell design, cells at the die corners
+    d = synth.make_design(n_movable=3, die=(0, 0, 32, 32), nx=16, ny=16, n_nets=4,
+                          n_pads=4, seed=1)
+    d.net_ptr = np.array([0, 0, 1, 1, 3, 5], np.int32)
+    d.pin_cell = np.array([0, 1, 2, 3, 4], np.int32)
+    d.pin_dx = np.full(5, 0.25, np.float32); d.pin_dy = np.full(5, 0.5, np.float32)
+    d.x[:3] = [0.0, 31.0 - d.w[1], 16.5]
+    d.y[:3] = [0.0, 31.0, 7.25]
+    h = Handle(d, tau_stop=-1.0)
+    try:
+        x, y = h.pos()
+        check_stages(h, x, y, 2.0)
+        place.place_step(h.h, 10)
+        x, y = h.pos()
+        assert np.all(np.isfinite(x)) and np.all(x[:3] >= 0) and np.all(x[:3] + d.w[:3] <= 32)
+    finally:
+        h.close()
+
+
+@pytest.mark.slow
+def test_full_size_2m_stages():
+    d = synth.large_2m(0)
+    h = Handle(d, tau_stop=-1.0, max_iters=1000)
+    try:
+        x, y = spread(h, 30)
+        check_stages(h, x, y, 12.0)
+    finally:
+        h.close()
