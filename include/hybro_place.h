@@ -46,8 +46,9 @@ extern "C" {
 #define PLACE_SHUFFLE_ALL 1   /* Shuffle (all): p% of all movable cells */
 
 /* Spectral-solve arithmetic. */
-#define PLACE_DCT_FP32 0   /* FP32 CUDA-core GEMMs */
-#define PLACE_DCT_TF32X3 1 /* split-TF32 (3 products) on the tcgen05 tensor cores */
+#define PLACE_DCT_FP32 0   /* FP32 CUDA-core GEMMs (any grid, multiples of 16) */
+#define PLACE_DCT_BF16X3 1 /* split-BF16 (3 products, FP32 accumulation) on the
+                              tcgen05 tensor cores; grids must be multiples of 128 */
 
 typedef struct place_t place_t;
 

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "spectral_tc.cuh"
 
 using namespace hp;
 
@@ -77,6 +78,7 @@ struct place_t {
   size_t mem_bytes = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  CUtensorMap maps[16];              // tensor maps of the tcgen05 spectral path
   int n_cand_all = 0, n_cand_macro = 0;
   // Hybro bookkeeping (host)
   std::vector<double> best_hpwl, best_tau;
@@ -157,6 +159,8 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.cs = a.take<CopyState>(K);
   d.part = a.take<double>(K * S_COUNT * (size_t)d.nb_red);
   d.scal = a.take<double>(K * S_COUNT);
+  d.tau_part = a.take<unsigned long long>(K * 2 * (size_t)d.nb_red);
+  d.ctr = a.take<unsigned int>(K * C_COUNT);
   d.Cn = a.take<float>((size_t)d.ny * d.ny);
   d.CTn = a.take<float>((size_t)d.ny * d.ny);
   d.STn = a.take<float>((size_t)d.ny * d.ny);
@@ -174,6 +178,66 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.sel_idx = a.take<unsigned int>(d.sort_n);
   d.px_tmp = a.take<float>(C);
   d.py_tmp = a.take<float>(C);
+  d.err = a.take<int>(1);
+  if (d.tc) {
+    const size_t nx2 = (size_t)d.nx * d.nx, ny2 = (size_t)d.ny * d.ny;
+    d.rho_h = a.take<__nv_bfloat16>(K * G);
+    d.rho_l = a.take<__nv_bfloat16>(K * G);
+    d.T_h = a.take<__nv_bfloat16>(K * 3 * G);
+    d.T_l = a.take<__nv_bfloat16>(K * 3 * G);
+    d.SB_h = a.take<__nv_bfloat16>(K * 3 * G);
+    d.SB_l = a.take<__nv_bfloat16>(K * 3 * G);
+    d.A1h = a.take<__nv_bfloat16>(ny2);
+    d.A1l = a.take<__nv_bfloat16>(ny2);
+    d.A2h = a.take<__nv_bfloat16>(nx2);
+    d.A2l = a.take<__nv_bfloat16>(nx2);
+    d.A3h = a.take<__nv_bfloat16>(3 * ny2);
+    d.A3l = a.take<__nv_bfloat16>(3 * ny2);
+    d.A4h = a.take<__nv_bfloat16>(3 * nx2);
+    d.A4l = a.take<__nv_bfloat16>(3 * nx2);
+  }
+}
+
+// Split the FP32 transform matrices into bf16 pairs and encode the tensor
+// maps of the four GEMM stages.
+int setup_tc(place_t *h) {
+  Dev &d = h->d;
+  cudaStream_t st = h->stream;
+  const size_t nx2 = (size_t)d.nx * d.nx, ny2 = (size_t)d.ny * d.ny;
+  launch_split_bf16(d.Cn, d.A1h, d.A1l, ny2, st);
+  launch_split_bf16(d.Cm, d.A2h, d.A2l, nx2, st);
+  launch_split_bf16(d.CTn, d.A3h, d.A3l, ny2, st);
+  launch_split_bf16(d.STn, d.A3h + ny2, d.A3l + ny2, ny2, st);
+  launch_split_bf16(d.CTn, d.A3h + 2 * ny2, d.A3l + 2 * ny2, ny2, st);
+  launch_split_bf16(d.STm, d.A4h, d.A4l, nx2, st);
+  launch_split_bf16(d.CTm, d.A4h + nx2, d.A4l + nx2, nx2, st);
+  launch_split_bf16(d.CTm, d.A4h + 2 * nx2, d.A4l + 2 * nx2, nx2, st);
+  CKL();
+  const int nx = d.nx, ny = d.ny, K = d.K;
+  struct M { const void *p; int k, rows, batch, box; } spec[16] = {
+      {d.A1h, ny, ny, 1, 128}, {d.A1l, ny, ny, 1, 128},
+      {d.rho_h, ny, nx, K, 128}, {d.rho_l, ny, nx, K, 128},
+      {d.A2h, nx, nx, 1, 128}, {d.A2l, nx, nx, 1, 128},
+      {d.T_h, nx, ny, 3 * K, 128}, {d.T_l, nx, ny, 3 * K, 128},
+      {d.A3h, ny, ny, 3, 128}, {d.A3l, ny, ny, 3, 128},
+      {d.SB_h, ny, nx, 3 * K, 128}, {d.SB_l, ny, nx, 3 * K, 128},
+      {d.A4h, nx, nx, 3, 128}, {d.A4l, nx, nx, 3, 128},
+      {d.T_h, nx, ny, 3 * K, 128}, {d.T_l, nx, ny, 3 * K, 128}};
+  for (int i = 0; i < 16; ++i) {
+    int r = make_map_bf16_3d(&h->maps[i], spec[i].p, spec[i].k, spec[i].rows, spec[i].batch, spec[i].box);
+    if (r) return fail(PLACE_ECUDA, "tensor map %d could not be encoded (%d)", i, r);
+  }
+  d.tcm = h->maps;
+  if (tc_prepare()) return fail(PLACE_ECUDA, "cannot reserve %d bytes of shared memory", tc_smem_bytes());
+  return PLACE_OK;
+}
+
+// Device-side error flag (bounded waits that gave up); call after a sync.
+int check_dev_err(place_t *h) {
+  int e = 0;
+  CK(cudaMemcpy(&e, h->d.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) return fail(PLACE_ETIMEOUT, "a device wait gave up (tensor-core pipeline)");
+  return PLACE_OK;
 }
 
 // Optimiser reset of copies [c0, c0+n): clamp, u = v, scalars, tau_{-1}.
@@ -183,8 +247,7 @@ int enqueue_reset(place_t *h, int c0, int n) {
   launch_reset(d, c0, n, st);
   CK(cudaMemsetAsync(d.M + (size_t)c0 * d.G, 0, sizeof(unsigned long long) * d.G * n, st));
   launch_scatter(d, c0, n, 1, st);
-  launch_density_finish(d, c0, n, 1, st);
-  launch_iteration_scalars(d, PH_TAU_RESET, c0, n, st);
+  launch_density_finish(d, c0, n, FIN_RESET, st);
   CKL();
   return PLACE_OK;
 }
@@ -192,19 +255,14 @@ int enqueue_reset(place_t *h, int c0, int n) {
 // One Nesterov iteration of every copy (the graph body).
 void enqueue_iteration(const Dev &d, cudaStream_t st) {
   const int K = d.K;
-  launch_iteration_scalars(d, PH_BEGIN, 0, K, st);
   cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.G * K, st);
   launch_scatter(d, 0, K, 0, st);
-  launch_density_finish(d, 0, K, 0, st);
-  launch_iteration_scalars(d, PH_TAU, 0, K, st);
+  launch_density_finish(d, 0, K, FIN_ITER, st);
   launch_spectral(d, 0, K, 0, 0, st);
   launch_wa(d, 0, K, 0, nullptr, st);
   launch_cell_grad(d, 0, K, 0, st);
-  launch_iteration_scalars(d, PH_MID, 0, K, st);
   launch_precond0(d, 0, K, st);
-  launch_iteration_scalars(d, PH_ALPHA, 0, K, st);
   launch_update(d, 0, K, st);
-  launch_iteration_scalars(d, PH_END, 0, K, st);
 }
 
 int ensure_graph(place_t *h) {
@@ -264,8 +322,10 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     return fail(PLACE_EINVAL, "null netlist array");
   if (prm.n_copies < 1 || prm.n_copies > 4096) return fail(PLACE_EINVAL, "n_copies must be in [1, 4096]");
   if (prm.max_iters < 0) return fail(PLACE_EINVAL, "max_iters < 0");
-  if (prm.dct_mode != PLACE_DCT_FP32 && prm.dct_mode != PLACE_DCT_TF32X3)
+  if (prm.dct_mode != PLACE_DCT_FP32 && prm.dct_mode != PLACE_DCT_BF16X3)
     return fail(PLACE_EINVAL, "unknown dct_mode %d", prm.dct_mode);
+  if (prm.dct_mode == PLACE_DCT_BF16X3 && (bins->nx % 128 || bins->ny % 128))
+    return fail(PLACE_EINVAL, "the tensor-core spectral path needs bins in multiples of 128");
   const int nx = bins->nx, ny = bins->ny;
   if (nx < 16 || ny < 16 || nx % 16 || ny % 16 || nx > 8192 || ny > 8192)
     return fail(PLACE_EINVAL, "bins must be multiples of 16 in [16, 8192], got %dx%d", nx, ny);
@@ -313,6 +373,17 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   d.XL = (long long)(die->xl * s); d.YL = (long long)(die->yl * s);
   d.BW = (long long)(bw * s); d.BH = (long long)(bh * s);
   d.t = (double)bins->target_density;
+  {
+    // t = mant * 2^-shift exactly (24-bit mantissa of the float)
+    int e = 0;
+    double f = std::frexp((double)bins->target_density, &e);
+    d.t_mant = (long long)std::ldexp(f, 24);
+    d.t_shift = 24 - e;
+    if (d.t_shift < 0 || d.t_shift > 60) {
+      delete h;
+      return fail(PLACE_EINVAL, "target density out of range");
+    }
+  }
   d.abin_q = (double)d.BW * (double)d.BH;
   d.die_xl = die->xl; d.die_yl = die->yl; d.die_xh = die->xh; d.die_yh = die->yh;
   d.fxl = (float)die->xl; d.fyl = (float)die->yl; d.fxh = (float)die->xh; d.fyh = (float)die->yh;
@@ -320,6 +391,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   d.dref = (double)prm.hpwl_ref * (double)E * d.w_bin;
   d.prm = prm;
   d.has_net_w = nl->net_w ? 1 : 0;
+  d.tc = prm.dct_mode == PLACE_DCT_BF16X3 ? 1 : 0;
   h->stream = (cudaStream_t)stream;
 
   // quantised sizes and movable area
@@ -394,11 +466,12 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   for (int c = 0; c < 5; ++c) {
     int n = d.cls_begin[c + 1] - d.cls_begin[c];
     int nb = c < 4 ? (n + (kThreads / kGroupWidth[c]) - 1) / (kThreads / kGroupWidth[c]) : n;
+    nb = std::min(nb, kMaxCellBlocks);
     d.wa_blocks[c] = nb;
     d.wa_block_base[c] = d.wa_blocks_total;
     d.wa_blocks_total += nb;
   }
-  d.nb_red = std::max(std::max(d.cell_blocks, d.bin_blocks), std::max(d.wa_blocks_total, 1));
+  d.nb_red = std::max(std::max(2 * d.cell_blocks, d.bin_blocks), std::max(d.wa_blocks_total, 1));
   int sn = 2;
   while (sn < C) sn <<= 1;
   d.sort_n = sn;
@@ -468,9 +541,15 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.Fmap, 0, sizeof(long long) * d.G, h->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.pin_grad, 0, sizeof(float2) * (size_t)d.K * P, h->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.cs, 0, sizeof(CopyState) * d.K, h->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(d.ctr, 0, sizeof(unsigned int) * d.K * C_COUNT, h->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(d.err, 0, sizeof(int), h->stream);
   if (ce != cudaSuccess) {
     place_destroy(h);
     return fail(PLACE_ECUDA, "memset: %s", cudaGetErrorString(ce));
+  }
+  if (d.tc && (rc = setup_tc(h)) != PLACE_OK) {
+    place_destroy(h);
+    return rc;
   }
   launch_scatter_fixed(d, d.x, d.y, Mv, C, reinterpret_cast<unsigned long long *>(d.Fmap), h->stream);
   rc = enqueue_reset(h, 0, d.K);
@@ -498,8 +577,8 @@ int place_get_info(const place_t *h, place_info *o) {
   o->device_bytes = (int64_t)h->mem_bytes;
   int wa = 0;
   for (int c = 0; c < d.n_cls; ++c) wa += d.wa_blocks[c] > 0;
-  // scalars x6, scatter, finish, 4 GEMMs, WA classes, cell grad, precond0, update
-  o->kernels_per_iter = 6 + 2 + 4 + wa + 3;
+  // scatter, finish, 4 GEMMs, WA classes, cell grad, precond0, update
+  o->kernels_per_iter = 2 + 4 + wa + 3;
   o->pad = 0;
   return PLACE_OK;
 }
@@ -517,6 +596,7 @@ int place_step(place_t *h, int32_t n_iters, int32_t *converged) {
     CK(cudaMemcpyAsync(cs.data(), h->d.cs, sizeof(CopyState) * h->d.K, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     for (int c = 0; c < h->d.K; ++c) converged[c] = cs[c].stopped;
+    return check_dev_err(h);
   }
   return PLACE_OK;
 }
@@ -532,11 +612,9 @@ int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms) {
   int rc = PLACE_OK;
   for (int it = 0; it < n_iters && rc == PLACE_OK; ++it) {
     cudaEventRecord(ev[0], st);
-    launch_iteration_scalars(d, PH_BEGIN, 0, K, st);
     cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.G * K, st);
     launch_scatter(d, 0, K, 0, st);
-    launch_density_finish(d, 0, K, 0, st);
-    launch_iteration_scalars(d, PH_TAU, 0, K, st);
+    launch_density_finish(d, 0, K, FIN_ITER, st);
     cudaEventRecord(ev[1], st);
     launch_spectral(d, 0, K, 0, 0, st);
     cudaEventRecord(ev[2], st);
@@ -544,11 +622,8 @@ int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms) {
     cudaEventRecord(ev[3], st);
     launch_cell_grad(d, 0, K, 0, st);
     cudaEventRecord(ev[4], st);
-    launch_iteration_scalars(d, PH_MID, 0, K, st);
     launch_precond0(d, 0, K, st);
-    launch_iteration_scalars(d, PH_ALPHA, 0, K, st);
     launch_update(d, 0, K, st);
-    launch_iteration_scalars(d, PH_END, 0, K, st);
     cudaEventRecord(ev[5], st);
     cudaError_t e = cudaEventSynchronize(ev[5]);
     if (e != cudaSuccess) { rc = fail(PLACE_ECUDA, "timed step: %s", cudaGetErrorString(e)); break; }
@@ -561,6 +636,7 @@ int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms) {
   for (auto &e : ev) cudaEventDestroy(e);
   if (rc) return rc;
   CKL();
+  if ((rc = check_dev_err(h))) return rc;
   for (int s = 0; s < PLACE_N_STAGES; ++s) stage_ms[s] += (float)acc[s];
   return PLACE_OK;
 }
@@ -572,6 +648,7 @@ int place_get_state(place_t *h, int32_t copy, place_state *o) {
   CopyState cs;
   CK(cudaMemcpyAsync(&cs, h->d.cs + copy, sizeof cs, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if ((rc = check_dev_err(h))) return rc;
   o->iter = cs.k; o->converged = cs.converged; o->stopped = cs.stopped; o->pad = 0;
   o->lambda = cs.lam; o->gamma = cs.gamma; o->alpha = cs.alpha; o->a = cs.a;
   o->overflow = cs.tau; o->hpwl_wa = cs.hpwl;
@@ -630,8 +707,7 @@ int density_at(place_t *h, int copy) {
   Dev &d = h->d;
   CK(cudaMemsetAsync(d.M + (size_t)copy * d.G, 0, sizeof(unsigned long long) * d.G, h->stream));
   launch_scatter(d, copy, 1, 1, h->stream);
-  launch_density_finish(d, copy, 1, 1, h->stream);
-  launch_reduce_slot(d, S_TAU, d.bin_blocks, copy, 1, h->stream);
+  launch_density_finish(d, copy, 1, FIN_EVAL, h->stream);
   CKL();
   return PLACE_OK;
 }
@@ -649,7 +725,7 @@ int place_eval_density(place_t *h, int32_t copy, int64_t *map, double *overflow)
   double s = 0;
   CK(cudaMemcpyAsync(&s, d.scal + (size_t)copy * S_COUNT + S_TAU, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  if (overflow) *overflow = s / d.mov_area_q;
+  if (overflow) *overflow = s;
   return PLACE_OK;
 }
 
@@ -673,7 +749,7 @@ int place_eval_field(place_t *h, int32_t copy, float *psi, float *ex, float *ey)
   if (ey) CK(cudaMemcpyAsync(ey, E + G, sizeof(float) * G, cudaMemcpyDefault, h->stream));
   if (psi) CK(cudaMemcpyAsync(psi, E + 2 * G, sizeof(float) * G, cudaMemcpyDefault, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  return PLACE_OK;
+  return check_dev_err(h);
 }
 
 int place_eval_density_grad(place_t *h, int32_t copy, float *gx, float *gy) {
@@ -688,7 +764,7 @@ int place_eval_density_grad(place_t *h, int32_t copy, float *gx, float *gy) {
   if (gx) CK(cudaMemcpyAsync(gx, d.gdx + copy * Mv, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
   if (gy) CK(cudaMemcpyAsync(gy, d.gdy + copy * Mv, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  return PLACE_OK;
+  return check_dev_err(h);
 }
 
 int place_eval_hpwl_overflow(place_t *h, double *hpwl, double *overflow) {
@@ -696,18 +772,17 @@ int place_eval_hpwl_overflow(place_t *h, double *hpwl, double *overflow) {
   Dev &d = h->d;
   const int K = d.K;
   launch_hpwl64(d, 0, K, h->stream);
-  launch_reduce_slot(d, S_HP64, d.cell_blocks, 0, K, h->stream);
+  launch_reduce_slot(d, S_HP64, 2 * d.cell_blocks, 0, K, h->stream);
   CK(cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.G * K, h->stream));
   launch_scatter(d, 0, K, 1, h->stream);
-  launch_density_finish(d, 0, K, 1, h->stream);
-  launch_reduce_slot(d, S_TAU, d.bin_blocks, 0, K, h->stream);
+  launch_density_finish(d, 0, K, FIN_EVAL, h->stream);
   CKL();
   std::vector<double> sc((size_t)K * S_COUNT);
   CK(cudaMemcpyAsync(sc.data(), d.scal, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   for (int c = 0; c < K; ++c) {
     if (hpwl) hpwl[c] = sc[(size_t)c * S_COUNT + S_HP64];
-    if (overflow) overflow[c] = sc[(size_t)c * S_COUNT + S_TAU] / d.mov_area_q;
+    if (overflow) overflow[c] = sc[(size_t)c * S_COUNT + S_TAU];
   }
   return PLACE_OK;
 }

@@ -31,6 +31,72 @@ __device__ __forceinline__ double block_sum(double v, double *sm) {
   return r;
 }
 
+// Deterministic block sum of floats (fixed tree); valid in thread 0.
+template <int NT>
+__device__ __forceinline__ float block_sum_f(float v, float *sm) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sm[w] = v;
+  __syncthreads();
+  float r = 0.f;
+  if (threadIdx.x < 32) {
+    r = (l < NT / 32) ? sm[l] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  }
+  return r;
+}
+
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 shfl_xor_u128(u128 v, int o) {
+  unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+  lo = __shfl_xor_sync(0xffffffffu, lo, o);
+  hi = __shfl_xor_sync(0xffffffffu, hi, o);
+  return ((u128)hi << 64) | lo;
+}
+
+// Exact block sum of unsigned 128-bit integers; valid in thread 0.
+template <int NT>
+__device__ __forceinline__ u128 block_sum_u128(u128 v, u128 *sm) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor_u128(v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sm[w] = v;
+  __syncthreads();
+  u128 r = 0;
+  if (threadIdx.x < 32) {
+    r = (l < NT / 32) ? sm[l] : (u128)0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += shfl_xor_u128(r, o);
+  }
+  return r;
+}
+
+__device__ __forceinline__ double u128_to_double(u128 v) {
+  return (double)(unsigned long long)(v >> 64) * 18446744073709551616.0 +
+         (double)(unsigned long long)v;
+}
+
+// Last-block pattern: every block has published its partials; returns true
+// (in all threads) for the block that arrives last, which then reduces the
+// partials in a fixed order and resets the counter.
+__device__ __forceinline__ bool arrive_last(unsigned int *ctr, int *sm_flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int prev = atomicAdd(ctr, 1u);
+    *sm_flag = (prev == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  const bool last = *sm_flag != 0;
+  if (last) __threadfence();
+  return last;
+}
+
 // Quantised rectangle of a cell and the clipped bin range it touches.
 struct QRect {
   long long X, Y, W, H;

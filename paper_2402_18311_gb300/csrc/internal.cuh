@@ -1,6 +1,7 @@
 // Internal declarations of the sm_103a placement library (not part of the ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -38,6 +39,12 @@ struct CopyState {
 // per block into its slot range; a reducer sums them in a fixed order.
 enum Slot { S_TAU = 0, S_HPWL, S_WL, S_GW1, S_GD1, S_DG2, S_DV2, S_G2, S_HP64, S_COUNT };
 
+// Last-block counters per copy.
+enum Counter { C_FINISH = 0, C_CELL, C_PRE0, C_UPDATE, C_COUNT };
+
+// What the density-finish kernel does with the overflow it reduces.
+enum FinishMode { FIN_ITER = 0, FIN_EVAL = 1, FIN_RESET = 2 };
+
 struct Dev {
   // sizes
   int K, n_cells, n_mov, n_nets, n_pins, n_mov_pins, nx, ny, G;
@@ -46,6 +53,8 @@ struct Dev {
   float scale;                // 2^F
   float inv_area_q;           // 2^-2F as float
   double t;                   // target density (float widened)
+  long long t_mant;           // t = t_mant * 2^-t_shift exactly
+  int t_shift;
   double abin_q;              // BW * BH
   double mov_area_q;
   double die_xl, die_yl, die_xh, die_yh;
@@ -86,11 +95,22 @@ struct Dev {
   CopyState *cs;             // [K]
   double *part;              // [K][S_COUNT][nb_red]
   double *scal;              // [K][S_COUNT] reduced values (eval reductions)
+  unsigned long long *tau_part;  // [K][nb_red][2] exact 128-bit overflow partials
+  unsigned int *ctr;         // [K][C_COUNT] last-block counters
 
   // spectral tables
   float *Cn, *Cm, *CTn, *STn, *STm, *CTm;  // transform matrices
   float *wu, *wv;                          // wavenumbers
   float *cu, *cv;                          // c_k / n factors
+
+  // tensor-core spectral path (BF16x3): split operands, host tensor maps
+  int tc;
+  __nv_bfloat16 *rho_h, *rho_l;     // [K][G]
+  __nv_bfloat16 *T_h, *T_l;         // [K][3][G]
+  __nv_bfloat16 *SB_h, *SB_l;       // [K][3][G]
+  __nv_bfloat16 *A1h, *A1l, *A2h, *A2l, *A3h, *A3l, *A4h, *A4l;
+  const void *tcm;                  // host array of 16 CUtensorMap (4 per GEMM stage)
+  int *err;                         // device error flag (bounded waits)
 
   // Hybro best solutions
   float *bx, *by;            // [K][n_cells]
@@ -115,13 +135,12 @@ struct Dev {
 void launch_scatter(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
 void launch_scatter_fixed(const Dev &d, const float *x, const float *y, int n0, int n1,
                           unsigned long long *out, cudaStream_t st);
-void launch_density_finish(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
+void launch_density_finish(const Dev &d, int copy0, int ncopy, int mode, cudaStream_t st);
 void launch_spectral(const Dev &d, int copy0, int ncopy, int with_psi, int eval, cudaStream_t st);
 void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_override,
                cudaStream_t st);
 void launch_hpwl64(const Dev &d, int copy0, int ncopy, cudaStream_t st);
 void launch_cell_grad(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
-void launch_iteration_scalars(const Dev &d, int phase, int copy0, int ncopy, cudaStream_t st);
 void launch_precond0(const Dev &d, int copy0, int ncopy, cudaStream_t st);
 void launch_update(const Dev &d, int copy0, int ncopy, cudaStream_t st);
 void launch_reset(const Dev &d, int copy0, int ncopy, cudaStream_t st);
@@ -129,7 +148,10 @@ void launch_reduce_slot(const Dev &d, int slot, int nvals, int copy0, int ncopy,
 int launch_shuffle(const Dev &d, int copy, int op, float p, uint64_t seed, cudaStream_t st);
 void launch_shuffle_finish(const Dev &d, int copy, int kcount, cudaStream_t st);
 
-// iteration phases of launch_iteration_scalars
-enum Phase { PH_BEGIN = 0, PH_TAU, PH_TAU_RESET, PH_MID, PH_ALPHA, PH_END };
+// gamma of the weighted-average model from the previous overflow (Eq. 3)
+__device__ __forceinline__ double gamma_of(const Dev &d, double tau_prev) {
+  if (d.prm.constant_gamma > 0.f) return (double)d.prm.constant_gamma;
+  return (double)d.prm.gamma_base * d.w_bin * pow(10.0, (20.0 / 9.0) * tau_prev - 11.0 / 9.0);
+}
 
 }  // namespace hp

@@ -11,8 +11,11 @@
 //   a_{k+1} = (1 + sqrt(4 a_k^2 + 1)) / 2
 //   v_{k+1} = clamp(u_{k+1} + (a_k - 1)/a_{k+1} (u_{k+1} - u_k))
 //   lambda_0 = eta |gWL|_1 / |gD|_1;  lambda_{k+1} = lambda_k clamp(mu^(1 - dHPWL/dref))
-// Per-cell work is FP32; norms and scalars are FP64, reduced in a fixed
-// order so that every run of the same input gives the same bits.
+// Per-cell work is FP32 (GB300's FP64 rate is tiny); each block sums its
+// cells in FP32 and publishes one FP64 partial; the last block of each copy
+// reduces the partials in a fixed order and advances the copy's scalars, so
+// every run of the same input gives the same bits and no separate scalar
+// kernels are launched.
 #include <math.h>
 
 #include "common.cuh"
@@ -24,27 +27,63 @@ __device__ __forceinline__ double *part_ptr(const Dev &d, int c, int slot) {
   return d.part + ((size_t)c * S_COUNT + slot) * d.nb_red;
 }
 
+// Fixed-order sum of one slot's partials by a whole block; valid in thread 0.
+template <int NT>
+__device__ double sum_slot(const Dev &d, int c, int slot, int n, double *sm) {
+  const double *p = part_ptr(d, c, slot);
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += NT) v += p[i];
+  return block_sum<NT>(v, sm);
+}
+
+// Step length, momentum and lambda schedule of iteration k (thread 0 only).
+__device__ void advance_scalars(const Dev &d, CopyState *cs, bool first, double g2, double dv2,
+                                double dg2) {
+  const place_params &P = d.prm;
+  double alpha;
+  if (first) {
+    double rms = sqrt(g2 / (2.0 * d.n_mov));
+    alpha = rms > 0 ? (double)P.alpha0 * d.w_bin / rms : 0.0;
+  } else {
+    alpha = dg2 > 0 ? sqrt(dv2) / sqrt(dg2) : cs->alpha;
+  }
+  cs->alpha = alpha;
+  cs->a_next = (1.0 + sqrt(4.0 * cs->a * cs->a + 1.0)) / 2.0;
+  cs->coef = (cs->a - 1.0) / cs->a_next;
+  if (!first) {
+    double mu = pow((double)P.mu_base, 1.0 - (cs->hpwl - cs->hpwl_prev) / d.dref);
+    mu = fmin(fmax(mu, (double)P.mu_lo), (double)P.mu_hi);
+    cs->lam *= mu;
+  }
+  cs->hpwl_prev = cs->hpwl;
+  cs->tau_prev = cs->tau;
+  cs->gamma = gamma_of(d, cs->tau);
+}
+
 // Gradient of the wirelength (sum of the cell's pin gradients) and of the
 // density (field gather -sum_b a_ib E_b) for every movable cell.  For k >= 1
 // (lambda known) the preconditioned gradient and the step-size norms are
-// formed here too.
+// formed here too, and the last block advances the scalars.
 __global__ void __launch_bounds__(kThreads) k_cell_grad(Dev d, int copy0, int eval) {
-  __shared__ double sm[32];
+  __shared__ float smf[32];
+  __shared__ double smd[32];
+  __shared__ int flag;
   const int c = copy0 + blockIdx.y;
-  const CopyState &cs = d.cs[c];
-  if (!eval && cs.stopped) return;
-  const int k = cs.k;
+  CopyState *cs = d.cs + c;
+  if (!eval && cs->stopped) return;
+  const int k = cs->k;
   const bool full = !eval && k >= 1;
-  const float lam = (float)cs.lam;
-  const int par = cs.parity;
+  const float lam = (float)cs->lam;
+  const int par = cs->parity;
   const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
   const float *x = d.x + cn, *y = d.y + cn;
   const float2 *pg = d.pin_grad + (size_t)c * d.n_pins;
   const float *ex = d.E + (size_t)c * 3 * d.G, *ey = ex + d.G;
-  double n1 = 0, d1 = 0, dg2 = 0, dv2 = 0;
+  float n1 = 0.f, d1 = 0.f, dg2 = 0.f, dv2 = 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
     float sx = 0.f, sy = 0.f;
-    for (int q = d.cell_pin_ptr[i]; q < d.cell_pin_ptr[i + 1]; ++q) {
+    const int q1 = d.cell_pin_ptr[i + 1];
+    for (int q = d.cell_pin_ptr[i]; q < q1; ++q) {
       float2 g = pg[d.cell_pins[q]];
       sx += g.x;
       sy += g.y;
@@ -66,62 +105,89 @@ __global__ void __launch_bounds__(kThreads) k_cell_grad(Dev d, int copy0, int ev
     }
     d.gwx[cm + i] = sx; d.gwy[cm + i] = sy;
     d.gdx[cm + i] = dx; d.gdy[cm + i] = dy;
-    n1 += fabs((double)sx) + fabs((double)sy);
-    d1 += fabs((double)dx) + fabs((double)dy);
+    n1 += fabsf(sx) + fabsf(sy);
+    d1 += fabsf(dx) + fabsf(dy);
     if (full) {
       float P = fmaxf(1.f, d.npins[i] + lam * d.area[i]);
       float gx = (sx + lam * dx) / P, gy = (sy + lam * dy) / P;
       d.gx[par][cm + i] = gx;
       d.gy[par][cm + i] = gy;
-      double ax = (double)gx - (double)d.gx[par ^ 1][cm + i];
-      double ay = (double)gy - (double)d.gy[par ^ 1][cm + i];
+      float ax = gx - d.gx[par ^ 1][cm + i], ay = gy - d.gy[par ^ 1][cm + i];
       dg2 += ax * ax + ay * ay;
-      double bx = (double)xi - (double)d.vpx[cm + i];
-      double by = (double)yi - (double)d.vpy[cm + i];
+      float bx = xi - d.vpx[cm + i], by = yi - d.vpy[cm + i];
       dv2 += bx * bx + by * by;
     }
   }
-  double r0 = block_sum<kThreads>(n1, sm);
-  double r1 = block_sum<kThreads>(d1, sm);
-  double r2 = block_sum<kThreads>(dg2, sm);
-  double r3 = block_sum<kThreads>(dv2, sm);
+  float r0 = block_sum_f<kThreads>(n1, smf);
+  float r1 = block_sum_f<kThreads>(d1, smf);
+  float r2 = block_sum_f<kThreads>(dg2, smf);
+  float r3 = block_sum_f<kThreads>(dv2, smf);
   if (threadIdx.x == 0) {
     part_ptr(d, c, S_GW1)[blockIdx.x] = r0;
     part_ptr(d, c, S_GD1)[blockIdx.x] = r1;
     part_ptr(d, c, S_DG2)[blockIdx.x] = r2;
     part_ptr(d, c, S_DV2)[blockIdx.x] = r3;
   }
+  if (eval) return;
+  if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_CELL, &flag)) return;
+  const double hp = sum_slot<kThreads>(d, c, S_HPWL, d.wa_blocks_total, smd);
+  const double wl = sum_slot<kThreads>(d, c, S_WL, d.wa_blocks_total, smd);
+  const double s1 = sum_slot<kThreads>(d, c, S_GW1, gridDim.x, smd);
+  const double s2 = sum_slot<kThreads>(d, c, S_GD1, gridDim.x, smd);
+  const double s3 = sum_slot<kThreads>(d, c, S_DG2, gridDim.x, smd);
+  const double s4 = sum_slot<kThreads>(d, c, S_DV2, gridDim.x, smd);
+  if (threadIdx.x == 0) {
+    cs->hpwl = hp;
+    cs->wl = wl;
+    if (k == 0) {
+      cs->lam = s2 > 0 ? (double)d.prm.lambda_eta * s1 / s2 : (double)d.prm.lambda_eta;
+    } else {
+      advance_scalars(d, cs, false, 0.0, s4, s3);
+    }
+    d.ctr[(size_t)c * C_COUNT + C_CELL] = 0u;
+  }
 }
 
-// k == 0 only: preconditioned gradient once lambda_0 is known, and |g|^2.
+// k == 0 only: preconditioned gradient once lambda_0 is known, |g|^2, and the
+// first step length.
 __global__ void __launch_bounds__(kThreads) k_precond0(Dev d, int copy0) {
-  __shared__ double sm[32];
+  __shared__ float smf[32];
+  __shared__ double smd[32];
+  __shared__ int flag;
   const int c = copy0 + blockIdx.y;
-  const CopyState &cs = d.cs[c];
-  if (cs.stopped || cs.k != 0) return;
-  const float lam = (float)cs.lam;
-  const int par = cs.parity;
+  CopyState *cs = d.cs + c;
+  if (cs->stopped || cs->k != 0) return;
+  const float lam = (float)cs->lam;
+  const int par = cs->parity;
   const size_t cm = (size_t)c * d.n_mov;
-  double g2 = 0;
+  float g2 = 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
     float P = fmaxf(1.f, d.npins[i] + lam * d.area[i]);
     float gx = (d.gwx[cm + i] + lam * d.gdx[cm + i]) / P;
     float gy = (d.gwy[cm + i] + lam * d.gdy[cm + i]) / P;
     d.gx[par][cm + i] = gx;
     d.gy[par][cm + i] = gy;
-    g2 += (double)gx * gx + (double)gy * gy;
+    g2 += gx * gx + gy * gy;
   }
-  double r = block_sum<kThreads>(g2, sm);
+  float r = block_sum_f<kThreads>(g2, smf);
   if (threadIdx.x == 0) part_ptr(d, c, S_G2)[blockIdx.x] = r;
+  if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_PRE0, &flag)) return;
+  const double s = sum_slot<kThreads>(d, c, S_G2, gridDim.x, smd);
+  if (threadIdx.x == 0) {
+    advance_scalars(d, cs, true, s, 0.0, 0.0);
+    d.ctr[(size_t)c * C_COUNT + C_PRE0] = 0u;
+  }
 }
 
-// Nesterov step with clamping into the die.
+// Nesterov step with clamping into the die; the last block closes the
+// iteration (k, a_k, buffer parity, max_iters stop).
 __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
+  __shared__ int flag;
   const int c = copy0 + blockIdx.y;
-  const CopyState &cs = d.cs[c];
-  if (cs.stopped) return;
-  const float alpha = (float)cs.alpha, coef = (float)cs.coef;
-  const int par = cs.parity;
+  CopyState *cs = d.cs + c;
+  if (cs->stopped) return;
+  const float alpha = (float)cs->alpha, coef = (float)cs->coef;
+  const int par = cs->parity;
   const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
     const float xh = d.fxh - d.w[i], yh = d.fyh - d.h[i];
@@ -135,10 +201,18 @@ __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
     d.ux[cm + i] = nux; d.uy[cm + i] = nuy;
     d.x[cn + i] = nvx; d.y[cn + i] = nvy;
   }
+  if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_UPDATE, &flag)) return;
+  if (threadIdx.x == 0) {
+    cs->k += 1;
+    cs->a = cs->a_next;
+    cs->parity ^= 1;
+    if (cs->k >= d.prm.max_iters) cs->stopped = 1;
+    d.ctr[(size_t)c * C_COUNT + C_UPDATE] = 0u;
+  }
 }
 
 // Optimiser reset: clamp the movable positions into the die, u = v, and
-// initial scalars.
+// initial scalars (tau_{-1} and gamma_0 follow from the density pass).
 __global__ void __launch_bounds__(kThreads) k_reset(Dev d, int copy0) {
   const int c = copy0 + blockIdx.y;
   const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
@@ -155,117 +229,12 @@ __global__ void __launch_bounds__(kThreads) k_reset(Dev d, int copy0) {
   }
 }
 
-// Deterministic sum of one slot's block partials: strided per-thread sums,
-// then a fixed tree.
-__device__ double reduce_slot(const Dev &d, int c, int slot, int nvals, double *sm) {
-  const double *p = part_ptr(d, c, slot);
-  double v = 0.0;
-  for (int i = threadIdx.x; i < nvals; i += blockDim.x) v += p[i];
-  double r = block_sum<kRedThreads>(v, sm);
-  __syncthreads();
-  if (threadIdx.x == 0) sm[32] = r;
-  __syncthreads();
-  r = sm[32];
-  __syncthreads();
-  return r;
-}
-
-__global__ void __launch_bounds__(kRedThreads) k_scalars(Dev d, int phase, int copy0) {
-  __shared__ double sm[40];
-  const int c = copy0 + blockIdx.x;
-  CopyState *cs = d.cs + c;
-  const place_params &P = d.prm;
-  if (phase == PH_TAU_RESET) {
-    double s = reduce_slot(d, c, S_TAU, d.bin_blocks, sm);
-    if (threadIdx.x == 0) cs->tau = cs->tau_prev = s / d.mov_area_q;
-    return;
-  }
-  if (cs->stopped) return;
-  switch (phase) {
-    case PH_BEGIN:
-      if (threadIdx.x == 0) {
-        if (cs->k >= P.max_iters) {
-          cs->stopped = 1;
-        } else if (P.constant_gamma > 0.f) {
-          cs->gamma = (double)P.constant_gamma;
-        } else {
-          cs->gamma = (double)P.gamma_base * d.w_bin *
-                      pow(10.0, (20.0 / 9.0) * cs->tau_prev - 11.0 / 9.0);
-        }
-      }
-      break;
-    case PH_TAU: {
-      double s = reduce_slot(d, c, S_TAU, d.bin_blocks, sm);
-      if (threadIdx.x == 0) {
-        double tau = s / d.mov_area_q;
-        cs->tau = tau;
-        if (tau <= (double)P.tau_stop) cs->converged = cs->stopped = 1;
-      }
-      break;
-    }
-    case PH_MID: {
-      double hp = reduce_slot(d, c, S_HPWL, d.wa_blocks_total, sm);
-      double wl = reduce_slot(d, c, S_WL, d.wa_blocks_total, sm);
-      double n1 = 0, d1 = 0;
-      const bool first = cs->k == 0;
-      if (first) {
-        n1 = reduce_slot(d, c, S_GW1, d.cell_blocks, sm);
-        d1 = reduce_slot(d, c, S_GD1, d.cell_blocks, sm);
-      }
-      if (threadIdx.x == 0) {
-        cs->hpwl = hp;
-        cs->wl = wl;
-        if (first) cs->lam = d1 > 0 ? (double)P.lambda_eta * n1 / d1 : (double)P.lambda_eta;
-      }
-      break;
-    }
-    case PH_ALPHA: {
-      const bool first = cs->k == 0;
-      double g2 = 0, dv2 = 0, dg2 = 0;
-      if (first) {
-        g2 = reduce_slot(d, c, S_G2, d.cell_blocks, sm);
-      } else {
-        dv2 = reduce_slot(d, c, S_DV2, d.cell_blocks, sm);
-        dg2 = reduce_slot(d, c, S_DG2, d.cell_blocks, sm);
-      }
-      if (threadIdx.x == 0) {
-        double alpha;
-        if (first) {
-          double rms = sqrt(g2 / (2.0 * d.n_mov));
-          alpha = rms > 0 ? (double)P.alpha0 * d.w_bin / rms : 0.0;
-        } else {
-          alpha = dg2 > 0 ? sqrt(dv2) / sqrt(dg2) : cs->alpha;
-        }
-        cs->alpha = alpha;
-        cs->a_next = (1.0 + sqrt(4.0 * cs->a * cs->a + 1.0)) / 2.0;
-        cs->coef = (cs->a - 1.0) / cs->a_next;
-        if (!first) {
-          double mu = pow((double)P.mu_base, 1.0 - (cs->hpwl - cs->hpwl_prev) / d.dref);
-          mu = fmin(fmax(mu, (double)P.mu_lo), (double)P.mu_hi);
-          cs->lam *= mu;
-        }
-        cs->hpwl_prev = cs->hpwl;
-        cs->tau_prev = cs->tau;
-      }
-      break;
-    }
-    case PH_END:
-      if (threadIdx.x == 0) {
-        cs->k += 1;
-        cs->a = cs->a_next;
-        cs->parity ^= 1;
-        if (cs->k >= P.max_iters) cs->stopped = 1;
-      }
-      break;
-  }
-}
-
 // Reduce one slot for evaluation calls: d.scal[c * S_COUNT + slot].
 __global__ void __launch_bounds__(kRedThreads) k_reduce_slot(Dev d, int slot, int nvals,
                                                              int copy0) {
-  __shared__ double sm[40];
+  __shared__ double sm[32];
   const int c = copy0 + blockIdx.x;
-  double s = reduce_slot(d, c, slot, nvals, sm);
+  double s = sum_slot<kRedThreads>(d, c, slot, nvals, sm);
   if (threadIdx.x == 0) d.scal[(size_t)c * S_COUNT + slot] = s;
 }
 
@@ -280,9 +249,6 @@ void launch_update(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
 }
 void launch_reset(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
   k_reset<<<dim3(d.cell_blocks, ncopy), kThreads, 0, st>>>(d, copy0);
-}
-void launch_iteration_scalars(const Dev &d, int phase, int copy0, int ncopy, cudaStream_t st) {
-  k_scalars<<<ncopy, kRedThreads, 0, st>>>(d, phase, copy0);
 }
 void launch_reduce_slot(const Dev &d, int slot, int nvals, int copy0, int ncopy,
                         cudaStream_t st) {

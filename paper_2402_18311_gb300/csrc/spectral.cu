@@ -18,6 +18,7 @@
 // micro-tiles); the tensor-core split-TF32 path lives in spectral_tc.cu.
 #include "common.cuh"
 #include "internal.cuh"
+#include "spectral_tc.cuh"
 
 namespace hp {
 
@@ -138,9 +139,42 @@ void launch_spectral_fp32(const Dev &d, int copy0, int ncopy, int with_psi, int 
   gemm(g, ncopy, st);
 }
 
+// Tensor-core chain (BF16x3): rho_hl -> T_hl[0] -> SB_hl -> T_hl[w] -> E[w].
+void launch_spectral_tc(const Dev &d, int copy0, int ncopy, int with_psi, int eval,
+                        cudaStream_t st) {
+  const CUtensorMap *mp = static_cast<const CUtensorMap *>(d.tcm);
+  TcArgs g = {};
+  g.copy0 = copy0;
+  g.cs = d.cs;
+  g.eval = eval;
+  g.err = d.err;
+  g.wu = d.wu; g.wv = d.wv; g.cu = d.cu; g.cv = d.cv;
+  g.with_psi = with_psi;
+  const int nw = with_psi ? 3 : 2;
+  // G1: T[0] = Cn rho^T   (ny x nx, K = ny)
+  g.M = d.ny; g.N = d.nx; g.K = d.ny; g.nwhich = 1; g.b_per_copy = 1; g.d_per_copy = 3;
+  g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
+  launch_tc_gemm(mp + 0, g, ncopy, st);
+  // G2: SB = spectral(Cm T[0]^T)   (nx x ny, K = nx)
+  g.M = d.nx; g.N = d.ny; g.K = d.nx; g.b_per_copy = 3; g.d_per_copy = 3;
+  g.epi = TC_EPI_SPECTRAL; g.Dh = d.SB_h; g.Dl = d.SB_l;
+  launch_tc_gemm(mp + 4, g, ncopy, st);
+  // G3: T[w] = An_w SB[w]^T   (ny x nx, K = ny)
+  g.M = d.ny; g.N = d.nx; g.K = d.ny; g.nwhich = nw;
+  g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
+  launch_tc_gemm(mp + 8, g, ncopy, st);
+  // G4: E[w] = Am_w T[w]^T   (nx x ny, K = nx)
+  g.M = d.nx; g.N = d.ny; g.K = d.nx;
+  g.epi = TC_EPI_F32; g.Df = d.E; g.Dh = g.Dl = nullptr;
+  launch_tc_gemm(mp + 12, g, ncopy, st);
+}
+
 void launch_spectral(const Dev &d, int copy0, int ncopy, int with_psi, int eval,
                      cudaStream_t st) {
-  launch_spectral_fp32(d, copy0, ncopy, with_psi, eval, st);
+  if (d.tc)
+    launch_spectral_tc(d, copy0, ncopy, with_psi, eval, st);
+  else
+    launch_spectral_fp32(d, copy0, ncopy, with_psi, eval, st);
 }
 
 }  // namespace hp

@@ -1,0 +1,358 @@
+// Spectral Poisson solve on the 5th-generation tensor cores (tcgen05).
+//
+// Same chain of four GEMM stages as spectral.cu (D = A B^T, both operands
+// K-major), computed as BF16x3: every FP32 operand is split into
+// hi = bf16(x) and lo = bf16(x - hi), and
+//     D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
+// accumulates in FP32 in tensor memory.  The transform matrices are split
+// once at create; every data operand is split by the kernel that produces it
+// (density finish for rho, the GEMM epilogues for the intermediates), so the
+// GEMMs read bf16 pairs straight from global memory.
+//
+// Kernel layout: one 128 x BN output tile per CTA of 4 warps.  Warp 0 (one
+// lane) streams K-blocks of 64 elements of A_hi, A_lo, B_hi, B_lo into a
+// 3-stage shared-memory ring with TMA (128-byte swizzle); warp 1 (one lane)
+// issues tcgen05.mma (M=128, N=BN, K=16) into a TMEM accumulator and frees
+// each stage with tcgen05.commit; then all four warps read the accumulator
+// with tcgen05.ld and run the fused epilogue (plain FP32 store, bf16 split,
+// or the spectral weights of the Poisson solve).  Every wait on an mbarrier
+// gives up after about a second of clock cycles and raises an error flag
+// instead of hanging.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "internal.cuh"
+#include "spectral_tc.cuh"
+
+namespace hp {
+
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BKE = 64;   // tile (bf16 K elements per stage)
+constexpr int STAGES = 3;
+constexpr int TILE_A = BM * BKE * 2;           // bytes of one A_hi or A_lo stage tile
+constexpr int TILE_B = BN * BKE * 2;
+constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr long long kWaitCycles = 2000000000ll;  // about one second
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false after about kWaitCycles without completion.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart, SM100 descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = BN.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void split_store(__nv_bfloat16 *hi, __nv_bfloat16 *lo, const float *v) {
+  // 32 consecutive values -> 32 bf16 hi and 32 bf16 lo (64 bytes each)
+  __align__(16) __nv_bfloat16 h[32];
+  __align__(16) __nv_bfloat16 l[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    h[i] = __float2bfloat16_rn(v[i]);
+    l[i] = __float2bfloat16_rn(v[i] - __bfloat162float(h[i]));
+  }
+  uint4 *dh = reinterpret_cast<uint4 *>(hi), *dl = reinterpret_cast<uint4 *>(lo);
+  const uint4 *sh = reinterpret_cast<const uint4 *>(h), *sl = reinterpret_cast<const uint4 *>(l);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    dh[i] = sh[i];
+    dl[i] = sl[i];
+  }
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+// D[z] = A[which] x B[z]^T over one 128 x BN tile; z = copy * nwhich + which.
+__global__ void __launch_bounds__(128, 1)
+    k_umma_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+                const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+                TcArgs g) {
+  extern __shared__ unsigned char smem_raw[];
+  const int z = blockIdx.z;
+  const int which = z % g.nwhich;
+  const int c = g.copy0 + z / g.nwhich;
+  if (!g.eval && g.cs[c].stopped) return;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int bz = c * g.b_per_copy + which;  // batch index of B
+  const int dz = c * g.d_per_copy + which;  // batch index of D
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023);
+  unsigned char *tiles = reinterpret_cast<unsigned char *>(base);
+  uint64_t *full = reinterpret_cast<uint64_t *>(tiles + STAGES * STAGE_BYTES);
+  uint64_t *empty = full + STAGES;
+  uint64_t *done = empty + STAGES;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int nk = g.K / BKE;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const int round = kb / STAGES;
+      if (kb >= STAGES && !mbar_wait(&empty[s], (round - 1) & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*(volatile int *)abort_flag) break;
+      unsigned char *st = tiles + s * STAGE_BYTES;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_3d(st, &mAh, &full[s], kb * BKE, m0, which);
+      tma_load_3d(st + TILE_A, &mAl, &full[s], kb * BKE, m0, which);
+      tma_load_3d(st + 2 * TILE_A, &mBh, &full[s], kb * BKE, n0, bz);
+      tma_load_3d(st + 2 * TILE_A + TILE_B, &mBl, &full[s], kb * BKE, n0, bz);
+      issued = kb + 1;
+    }
+    // make sure no copy is still landing in shared memory when the CTA ends
+    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb) {
+      if (!mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
+        ok = false;
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = smem_u32(tiles + s * STAGE_BYTES);
+      const uint32_t ah = st, al = st + TILE_A, bh = st + 2 * TILE_A, bl = st + 2 * TILE_A + TILE_B;
+#pragma unroll
+      for (int k = 0; k < BKE / 16; ++k) {
+        const uint32_t off = k * 32;  // 16 bf16 = 32 bytes along K inside the swizzle atom
+        const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
+        umma_bf16(tmem, sw128_desc(ah + off), sw128_desc(bh + off), acc0);
+        umma_bf16(tmem, sw128_desc(ah + off), sw128_desc(bl + off), 1u);
+        umma_bf16(tmem, sw128_desc(al + off), sw128_desc(bh + off), 1u);
+      }
+      umma_commit(&empty[s]);
+    }
+    if (ok) umma_commit(done);
+  }
+  __syncwarp();
+
+  // epilogue: TMEM lanes 32*warp .. +31 hold rows m0 + 32*warp + lane
+  // the tcgen05.ld below is warp-collective: decide per warp
+  const bool have = __all_sync(0xffffffffu, mbar_wait(done, 0)) != 0;
+  if (!have) *abort_flag = 1;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncwarp();
+  const int m = m0 + warp * 32 + lane;
+  if (have) {
+#pragma unroll 1
+    for (int cc = 0; cc < BN; cc += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, r);
+      float v[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+      const int n = n0 + cc;
+      const size_t o = (size_t)dz * g.M * g.N + (size_t)m * g.N + n;
+      if (g.epi == TC_EPI_F32) {
+        float4 *dst = reinterpret_cast<float4 *>(g.Df + o);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+      } else if (g.epi == TC_EPI_SPLIT) {
+        split_store(g.Dh + o, g.Dl + o, v);
+      } else {
+        // spectral weights: a_uv = acc c_u c_v/(M N); (Bx, By, Bpsi) = a (w_u, w_v, 1)/(w_u^2 + w_v^2)
+        const size_t G = (size_t)g.M * g.N;
+        const size_t ob = (size_t)c * g.d_per_copy * G + (size_t)m * g.N + n;
+        const float cu = g.cu[m], wu = g.wu[m];
+        float bx[32], by[32], bp[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float wv = g.wv[n + i];
+          const float den = wu * wu + wv * wv;
+          const float inv = (m == 0 && n + i == 0) ? 0.f : 1.f / den;
+          const float a = v[i] * cu * g.cv[n + i] * inv;
+          bx[i] = a * wu;
+          by[i] = a * wv;
+          bp[i] = a;
+        }
+        split_store(g.Dh + ob, g.Dl + ob, bx);
+        split_store(g.Dh + ob + G, g.Dl + ob + G, by);
+        if (g.with_psi) split_store(g.Dh + ob + 2 * G, g.Dl + ob + 2 * G, bp);
+      }
+    }
+  }
+  if (threadIdx.x == 0 && *(volatile int *)abort_flag) atomicExch(g.err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+  }
+}
+
+int tc_smem_bytes() { return SMEM_BYTES; }
+
+void launch_tc_gemm(const CUtensorMap *maps4, const TcArgs &g, int ncopy, cudaStream_t st) {
+  dim3 grid(g.N / BN, g.M / BM, g.nwhich * ncopy);
+  k_umma_gemm<<<grid, 128, SMEM_BYTES, st>>>(maps4[0], maps4[1], maps4[2], maps4[3], g);
+}
+
+int tc_prepare() {
+  cudaError_t e = cudaFuncSetAttribute(k_umma_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       SMEM_BYTES);
+  return e == cudaSuccess ? 0 : -1;
+}
+
+// FP32 -> (bf16 hi, bf16 lo) for the static transform matrices.
+__global__ void k_split_bf16(const float *src, __nv_bfloat16 *hi, __nv_bfloat16 *lo, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float v = src[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+void launch_split_bf16(const float *src, __nv_bfloat16 *hi, __nv_bfloat16 *lo, size_t n,
+                       cudaStream_t st) {
+  size_t b = (n + 255) / 256;
+  int blocks = (int)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
+  k_split_bf16<<<blocks, 256, 0, st>>>(src, hi, lo, n);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int make_map_bf16_3d(CUtensorMap *map, const void *base, int K, int rows, int batch, int box_rows) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return -1;
+    fn = (EncodeTiledFn)p;
+  }
+  if (((uintptr_t)base & 15) || K % BKE || rows % box_rows) return -2;
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)K * 2, (cuuint64_t)K * 2 * rows};
+  cuuint32_t box[3] = {(cuuint32_t)BKE, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -3;
+}
+
+}  // namespace hp

@@ -305,3 +305,45 @@ def test_full_size_2m_stages():
         check_stages(h, x, y, 12.0)
     finally:
         h.close()
+
+
+def test_tensor_core_spectral_path_scaled():
+    # BF16x3 on tcgen05: field within the same 1e-4 L2 tolerance
+    d = synth.scaled(20000, 128, seed=2)
+    h = Handle(d, tau_stop=-1.0, max_iters=1000, dct_mode=place.PLACE_DCT_BF16X3)
+    try:
+        x, y = h.pos()
+        check_stages(h, x, y, 1.7)
+        x, y = spread(h, 250)
+        check_stages(h, x, y, 1.7)
+    finally:
+        h.close()
+
+
+def test_tensor_core_matches_fp32_path_trajectory():
+    # the two spectral paths drive the same 200-iteration trajectory to HPWL
+    # and overflow within 1e-3 (the BF16x3 field differs by ~1e-5 L2)
+    d = synth.scaled(20000, 128, seed=3)
+    out = []
+    for mode in (place.PLACE_DCT_FP32, place.PLACE_DCT_BF16X3):
+        h = Handle(d, tau_stop=-1.0, max_iters=1000, dct_mode=mode)
+        try:
+            place.place_step(h.h, 200)
+            hp = np.empty(1); tv = np.empty(1)
+            place.place_eval_hpwl_overflow(h.h, hp, tv)
+            out.append((hp[0], tv[0]))
+        finally:
+            h.close()
+    assert out[1][0] == pytest.approx(out[0][0], rel=1e-3)
+    assert out[1][1] == pytest.approx(out[0][1], abs=1e-3)
+
+
+@pytest.mark.slow
+def test_full_size_2m_stages_tensor_core():
+    d = synth.large_2m(0)
+    h = Handle(d, tau_stop=-1.0, max_iters=1000, dct_mode=place.PLACE_DCT_BF16X3)
+    try:
+        x, y = spread(h, 30)
+        check_stages(h, x, y, 12.0)
+    finally:
+        h.close()
