@@ -215,6 +215,41 @@ int place_get_best_positions(place_t *h, int32_t copy, float *x, float *y);
 #define PLACE_N_STAGES 5
 int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms);
 
+/* Density map and overflow of a placement without any device allocation.
+ *
+ * The paper has no counterpart to this function: it serves callers that
+ * cannot allocate device memory when they need the overflow, such as a host
+ * framework whose memory pool owns all device memory during a step, a
+ * real-time service that forbids allocation after start-up, or a callback
+ * that must not trigger the device-wide synchronisation an allocation can
+ * cause.  Its scratch (64-bit density map and reduction partials) is one
+ * fixed-size array inside the library's module; every GPU that loads the
+ * library holds it (about 8 MB) until the process exits.
+ *
+ * Computes exactly what place_eval_density() computes for a handle: the
+ * movable-cell map M in units of 2^-2F and tau = sum_b max(0, M_b -
+ * t (A_b - F_b)) / A_mov, for n_movable cells with lower-left corners x, y
+ * and sizes w, h (device float arrays), the die and bins, the fixed-point
+ * resolution frac_bits (place_info.frac_bits of a handle of the same
+ * design), the total movable area mov_area (sum of w*h, layout units) and
+ * the fixed-cell map fixed_map (device int64 [nx*ny], x-major; NULL: no
+ * fixed cells).  Outputs: *overflow (device double) and, if map_out is not
+ * NULL, the map (device int64 [nx*ny]).  Work runs asynchronously on
+ * `stream`.
+ *
+ * Limits: nx * ny <= PLACE_NOALLOC_MAX_BINS, else PLACE_EINVAL.  All calls
+ * share the one scratch array and each call clears it first; calls whose
+ * work overlaps on the GPU (different streams or host threads) race on it
+ * and must be serialised.  The first call with a given device current looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Calls no cudaMalloc, cudaFree or allocating
+ * library routine. */
+#define PLACE_NOALLOC_MAX_BINS (1024 * 1024)
+int place_overflow_noalloc(const float *x, const float *y, const float *w, const float *h,
+                           int32_t n_movable, double mov_area, const place_die *die,
+                           const place_bins *bins, int32_t frac_bits, const int64_t *fixed_map,
+                           double *overflow, int64_t *map_out, void *stream);
+
 const char *place_last_error(void);
 
 #ifdef __cplusplus

@@ -70,6 +70,11 @@ bool is_integer(double v) { return std::floor(v) == v && std::isfinite(v); }
 
 }  // namespace
 
+namespace hp {
+// Lets other translation units report through place_last_error().
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace hp
+
 struct place_t {
   Dev d{};
   cudaStream_t stream = nullptr;     // caller's stream

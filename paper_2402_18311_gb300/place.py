@@ -99,6 +99,9 @@ _SIGS = {
                                _VP, _VP, _VP]),
     "place_get_best_positions": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
     "place_step_timed": (ct.c_int, [_VP, ct.c_int32, _VP]),
+    "place_overflow_noalloc": (ct.c_int, [_VP, _VP, _VP, _VP, ct.c_int32, ct.c_double,
+                                          ct.POINTER(place_die), ct.POINTER(place_bins),
+                                          ct.c_int32, _VP, _VP, _VP, _VP]),
     "place_last_error": (ct.c_char_p, []),
 }
 
@@ -259,6 +262,19 @@ def place_get_best_positions(h, copy, x, y):
 def place_step_timed(h, n_iters, stage_ms):
     """stage_ms: float32 numpy array [5]; per-stage milliseconds are added."""
     return _check(lib().place_step_timed(h, int(n_iters), _ptr(stage_ms)))
+
+
+def place_overflow_noalloc(x, y, w, h, n_movable, mov_area, die, bins, frac_bits, fixed_map,
+                           overflow, map_out=None, stream=None):
+    """Overflow (and optionally the density map) into caller-owned device
+    buffers, using only the library's static scratch (no allocation).
+    ``die``: (xl, yl, xh, yh); ``bins``: (nx, ny, target_density)."""
+    d = place_die(*die)
+    b = place_bins(*bins)
+    return _check(lib().place_overflow_noalloc(_ptr(x), _ptr(y), _ptr(w), _ptr(h),
+                                               int(n_movable), float(mov_area), ct.byref(d),
+                                               ct.byref(b), int(frac_bits), _ptr(fixed_map),
+                                               _ptr(overflow), _ptr(map_out), _VP(stream or 0)))
 
 
 def place_last_error():
