@@ -57,14 +57,18 @@ struct Arena {
   }
 };
 
+// WA launch classes: thread per net (<= 4 pins), 4-lane groups (<= 16),
+// 16-lane groups (<= 64), warps (<= 256), a block per net (> 256); chunk
+// sizes keep a chunk's pins within the staging buffers.
 int degree_class(int deg) {
   if (deg <= 4) return 0;
-  if (deg <= 8) return 1;
-  if (deg <= 16) return 2;
+  if (deg <= 16) return 1;
+  if (deg <= 64) return 2;
   if (deg <= 256) return 3;
   return 4;
 }
-constexpr int kGroupWidth[4] = {4, 8, 16, 32};
+constexpr int kNetsPerBlock[4] = {256, 64, 16, 8};
+constexpr int kBigCapMax = 12288;  // pins of a big net kept in shared memory (96 KB)
 
 bool is_integer(double v) { return std::floor(v) == v && std::isfinite(v); }
 
@@ -79,6 +83,8 @@ struct place_t {
   Dev d{};
   cudaStream_t stream = nullptr;     // caller's stream
   cudaStream_t cap = nullptr;        // private stream used for graph capture
+  cudaStream_t cap2 = nullptr;       // second captured stream: wirelength branch
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   void *mem = nullptr;
   size_t mem_bytes = 0;
   cudaGraph_t graph = nullptr;
@@ -115,6 +121,9 @@ int place_destroy(place_t *h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->cap2) cudaStreamDestroy(h->cap2);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->mem) cudaFree(h->mem);
   delete h;
   return PLACE_OK;
@@ -140,8 +149,7 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.npins = a.take<float>(Mv);
   d.area = a.take<float>(Mv);
   d.is_macro = a.take<unsigned char>(C);
-  d.x = a.take<float>(K * C);
-  d.y = a.take<float>(K * C);
+  d.xy = a.take<float2>(K * C);
   d.ux = a.take<float>(K * Mv);
   d.uy = a.take<float>(K * Mv);
   d.vpx = a.take<float>(K * Mv);
@@ -154,7 +162,7 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.gwy = a.take<float>(K * Mv);
   d.gdx = a.take<float>(K * Mv);
   d.gdy = a.take<float>(K * Mv);
-  d.pin_grad = a.take<float2>(K * P);
+  d.pin_grad = a.take<float2>(K * std::max<size_t>(P, 1));
   d.M = a.take<unsigned long long>(K * G);
   d.Fmap = a.take<long long>(G);
   d.rho = a.take<float>(K * G);
@@ -176,8 +184,7 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.wv = a.take<float>(d.ny);
   d.cu = a.take<float>(d.nx);
   d.cv = a.take<float>(d.ny);
-  d.bx = a.take<float>(K * C);
-  d.by = a.take<float>(K * C);
+  d.bxy = a.take<float2>(K * C);
   d.sort_key = a.take<unsigned long long>(d.sort_n);
   d.sort_idx = a.take<unsigned int>(d.sort_n);
   d.sel_idx = a.take<unsigned int>(d.sort_n);
@@ -257,14 +264,23 @@ int enqueue_reset(place_t *h, int c0, int n) {
   return PLACE_OK;
 }
 
-// One Nesterov iteration of every copy (the graph body).
-void enqueue_iteration(const Dev &d, cudaStream_t st) {
+// One Nesterov iteration of every copy (the graph body).  The wirelength
+// kernels depend only on the positions and on gamma_k (from the previous
+// iteration's overflow), so they run on a second stream beside the density
+// scatter and the tensor-core Poisson solve and join before the per-cell
+// gradient.
+void enqueue_iteration(const Dev &d, cudaStream_t st, cudaStream_t st2, cudaEvent_t fork,
+                       cudaEvent_t join) {
   const int K = d.K;
+  cudaEventRecord(fork, st);
+  cudaStreamWaitEvent(st2, fork, 0);
+  launch_wa(d, 0, K, 0, nullptr, st2);
+  cudaEventRecord(join, st2);
   cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.G * K, st);
   launch_scatter(d, 0, K, 0, st);
   launch_density_finish(d, 0, K, FIN_ITER, st);
   launch_spectral(d, 0, K, 0, 0, st);
-  launch_wa(d, 0, K, 0, nullptr, st);
+  cudaStreamWaitEvent(st, join, 0);
   launch_cell_grad(d, 0, K, 0, st);
   launch_precond0(d, 0, K, st);
   launch_update(d, 0, K, st);
@@ -273,12 +289,24 @@ void enqueue_iteration(const Dev &d, cudaStream_t st) {
 int ensure_graph(place_t *h) {
   if (h->exec) return PLACE_OK;
   CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-  enqueue_iteration(h->d, h->cap);
+  enqueue_iteration(h->d, h->cap, h->cap2, h->ev_fork, h->ev_join);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap, &g);
   if (e != cudaSuccess) return fail(PLACE_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
   h->graph = g;
   CK(cudaGraphInstantiate(&h->exec, g, 0));
+  return PLACE_OK;
+}
+
+// Interleaved device positions -> caller's x, y (host or device) through the
+// handle's scratch; synchronises.
+int copy_out_xy(place_t *h, const float2 *src, float *x, float *y) {
+  const int C = h->d.n_cells;
+  launch_unpack_xy(h->d.px_tmp, h->d.py_tmp, src, C, h->stream);
+  CKL();
+  if (x) CK(cudaMemcpyAsync(x, h->d.px_tmp, sizeof(float) * C, cudaMemcpyDefault, h->stream));
+  if (y) CK(cudaMemcpyAsync(y, h->d.py_tmp, sizeof(float) * C, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   return PLACE_OK;
 }
 
@@ -452,6 +480,9 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     for (int j = 0; j < P; ++j)
       if (pin_cell[j] < Mv) cpins[fill[pin_cell[j]]++] = j;
   }
+  int max_deg = 0;
+  for (int e = 0; e < E; ++e) max_deg = std::max(max_deg, net_ptr[e + 1] - net_ptr[e]);
+  d.wa_big_cap = std::min(std::max(max_deg, 1), kBigCapMax);
   std::vector<float> npins(std::max(Mv, 1)), area(std::max(Mv, 1));
   for (int i = 0; i < Mv; ++i) {
     npins[i] = (float)(cpp[i + 1] - cpp[i]);
@@ -470,7 +501,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   d.wa_blocks_total = 0;
   for (int c = 0; c < 5; ++c) {
     int n = d.cls_begin[c + 1] - d.cls_begin[c];
-    int nb = c < 4 ? (n + (kThreads / kGroupWidth[c]) - 1) / (kThreads / kGroupWidth[c]) : n;
+    int nb = c < 4 ? (n + kNetsPerBlock[c] - 1) / kNetsPerBlock[c] : n;
     nb = std::min(nb, kMaxCellBlocks);
     d.wa_blocks[c] = nb;
     d.wa_block_base[c] = d.wa_blocks_total;
@@ -529,22 +560,28 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     up(d.cu, cu.data(), sizeof(float) * nx);
     up(d.cv, cv.data(), sizeof(float) * ny);
   }
-  for (int c = 0; c < d.K && rc == PLACE_OK; ++c) {
-    up(d.x + (size_t)c * C, nl->x0, sizeof(float) * C);
-    up(d.y + (size_t)c * C, nl->y0, sizeof(float) * C);
+  {
+    std::vector<float2> xy0(C);
+    for (int i = 0; i < C; ++i) xy0[i] = make_float2(nl->x0[i], nl->y0[i]);
+    for (int c = 0; c < d.K && rc == PLACE_OK; ++c) up(d.xy + (size_t)c * C, xy0.data(), sizeof(float2) * C);
   }
   if (rc != PLACE_OK) {
     place_destroy(h);
     return rc;
   }
   cudaError_t ce = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
   if (ce != cudaSuccess) {
     place_destroy(h);
     return fail(PLACE_ECUDA, "stream create: %s", cudaGetErrorString(ce));
   }
   ce = cudaMemsetAsync(d.E, 0, sizeof(float) * (size_t)d.K * 3 * d.G, h->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.Fmap, 0, sizeof(long long) * d.G, h->stream);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(d.pin_grad, 0, sizeof(float2) * (size_t)d.K * P, h->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemsetAsync(d.pin_grad, 0, sizeof(float2) * (size_t)d.K * std::max(P, 1), h->stream);
+  if (ce == cudaSuccess && wa_prepare(d.wa_big_cap)) ce = cudaErrorInvalidValue;
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.cs, 0, sizeof(CopyState) * d.K, h->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.ctr, 0, sizeof(unsigned int) * d.K * C_COUNT, h->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.err, 0, sizeof(int), h->stream);
@@ -556,7 +593,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     place_destroy(h);
     return rc;
   }
-  launch_scatter_fixed(d, d.x, d.y, Mv, C, reinterpret_cast<unsigned long long *>(d.Fmap), h->stream);
+  launch_scatter_fixed(d, d.xy, Mv, C, reinterpret_cast<unsigned long long *>(d.Fmap), h->stream);
   rc = enqueue_reset(h, 0, d.K);
   if (rc == PLACE_OK) {
     ce = cudaStreamSynchronize(h->stream);
@@ -664,10 +701,7 @@ int place_get_positions(place_t *h, int32_t copy, float *x, float *y) {
   int rc = check_copy(h, copy, false);
   if (rc) return rc;
   const size_t C = h->d.n_cells;
-  if (x) CK(cudaMemcpyAsync(x, h->d.x + copy * C, sizeof(float) * C, cudaMemcpyDefault, h->stream));
-  if (y) CK(cudaMemcpyAsync(y, h->d.y + copy * C, sizeof(float) * C, cudaMemcpyDefault, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  return PLACE_OK;
+  return copy_out_xy(h, h->d.xy + copy * C, x, y);
 }
 
 int place_set_positions(place_t *h, int32_t copy, const float *x, const float *y) {
@@ -676,10 +710,10 @@ int place_set_positions(place_t *h, int32_t copy, const float *x, const float *y
   if (!x || !y) return fail(PLACE_EINVAL, "null positions");
   const size_t C = h->d.n_cells, Mv = h->d.n_mov;
   int c0 = copy < 0 ? 0 : copy, n = copy < 0 ? h->d.K : 1;
-  for (int c = c0; c < c0 + n; ++c) {
-    CK(cudaMemcpyAsync(h->d.x + c * C, x, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
-    CK(cudaMemcpyAsync(h->d.y + c * C, y, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
-  }
+  (void)C;
+  CK(cudaMemcpyAsync(h->d.px_tmp, x, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
+  CK(cudaMemcpyAsync(h->d.py_tmp, y, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
+  for (int c = c0; c < c0 + n; ++c) launch_pack_xy(h->d.xy + c * C, h->d.px_tmp, h->d.py_tmp, (int)Mv, h->stream);
   return enqueue_reset(h, c0, n);
 }
 
@@ -841,8 +875,7 @@ int place_hybro(place_t *h, int32_t n_rounds, int32_t op, float p, uint64_t seed
       }
       if (better) {
         bh[c] = hp[c]; bt[c] = tau[c]; br[c] = r;
-        CK(cudaMemcpyAsync(d.bx + c * C, d.x + c * C, sizeof(float) * C, cudaMemcpyDeviceToDevice, h->stream));
-        CK(cudaMemcpyAsync(d.by + c * C, d.y + c * C, sizeof(float) * C, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(d.bxy + c * C, d.xy + c * C, sizeof(float2) * C, cudaMemcpyDeviceToDevice, h->stream));
       }
     }
     if (r < n_rounds) {
@@ -867,10 +900,7 @@ int place_get_best_positions(place_t *h, int32_t copy, float *x, float *y) {
   if (rc) return rc;
   if (h->best_round.empty()) return fail(PLACE_EINVAL, "place_hybro has not run on this handle");
   const size_t C = h->d.n_cells;
-  if (x) CK(cudaMemcpyAsync(x, h->d.bx + copy * C, sizeof(float) * C, cudaMemcpyDefault, h->stream));
-  if (y) CK(cudaMemcpyAsync(y, h->d.by + copy * C, sizeof(float) * C, cudaMemcpyDefault, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  return PLACE_OK;
+  return copy_out_xy(h, h->d.bxy + copy * C, x, y);
 }
 
 }  // extern "C"

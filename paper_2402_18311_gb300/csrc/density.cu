@@ -17,12 +17,47 @@ namespace hp {
 
 constexpr int kHash = 2048;  // shared-memory aggregation table entries
 
-// Cells are processed grid-stride; each block first aggregates its overlap
-// areas per bin in a shared-memory hash table (bounded linear probing) and
-// flushes the table with one 64-bit atomic per distinct bin.  Contributions
-// that find no slot go straight to global memory.  When many cells share
-// few bins (the centred start of a placement) this removes almost all
-// contention on the global map.
+// Adds one (bin, area) contribution to the block's shared-memory table, or to
+// the global map when its slot is taken (bounded linear probing).
+__device__ __forceinline__ void hash_add(int *keys, unsigned long long *vals,
+                                         unsigned long long *M, int b,
+                                         unsigned long long a) {
+  unsigned int hsh = ((unsigned int)b * 2654435761u) >> (32 - 11);
+#pragma unroll 1
+  for (int probe = 0; probe < 2; ++probe) {
+    int k = keys[hsh];  // plain read first: no atomic when the bin is already there
+    if (k == -1) k = atomicCAS(&keys[hsh], -1, b);
+    if (k == -1 || k == b) {
+      atomicAdd(&vals[hsh], a);
+      return;
+    }
+    hsh = (hsh + 1) & (kHash - 1);
+  }
+  atomicAdd(&M[b], a);
+}
+
+// Exact sum of 64-bit values over the lanes in `mask` (all of which call
+// this with the same mask): three 21-bit limbs are summed with the 32-bit
+// warp reduction, which cannot overflow for 32 lanes.
+__device__ __forceinline__ unsigned long long group_sum_u64(unsigned int mask,
+                                                            unsigned long long a) {
+  const unsigned int l0 = (unsigned int)(a & 0x1FFFFF);
+  const unsigned int l1 = (unsigned int)((a >> 21) & 0x1FFFFF);
+  const unsigned int l2 = (unsigned int)(a >> 42);
+  const unsigned long long s0 = __reduce_add_sync(mask, l0);
+  const unsigned long long s1 = __reduce_add_sync(mask, l1);
+  const unsigned long long s2 = __reduce_add_sync(mask, l2);
+  return s0 + (s1 << 21) + (s2 << 42);
+}
+
+// Cells are processed grid-stride, a warp at a time.  Each cell touches at
+// most 2 x 2 bins when it is no larger than a bin (standard cells); those
+// four slots are visited in lock-step by the warp, lanes that hit the same
+// bin are merged with a match/reduce (exact integer sums), and one lane per
+// distinct bin adds the total to a shared-memory hash table.  Larger cells
+// add their remaining bins directly.  The table is flushed with one 64-bit
+// atomic per distinct bin.  When many cells share few bins (the centred
+// start of a placement) this removes almost all contention on the map.
 __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval) {
   __shared__ int keys[kHash];
   __shared__ unsigned long long vals[kHash];
@@ -33,33 +68,55 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
     vals[i] = 0ull;
   }
   __syncthreads();
-  const float *x = d.x + (size_t)c * d.n_cells;
-  const float *y = d.y + (size_t)c * d.n_cells;
+  const float2 *xy = d.xy + (size_t)c * d.n_cells;
   unsigned long long *M = d.M + (size_t)c * d.G;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
-    QRect r = qrect(x[i], y[i], d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW, d.BH, d.nx, d.ny);
-    for (int ix = r.ix0; ix <= r.ix1; ++ix) {
-      long long ox = overlap1(r.X, r.W, d.XL + (long long)ix * d.BW, d.BW);
-      if (ox == 0) continue;
-      for (int iy = r.iy0; iy <= r.iy1; ++iy) {
-        long long oy = overlap1(r.Y, r.H, d.YL + (long long)iy * d.BH, d.BH);
-        if (oy == 0) continue;
-        const int b = ix * d.ny + iy;
-        const unsigned long long a = (unsigned long long)(ox * oy);
-        unsigned int hsh = ((unsigned int)b * 2654435761u) >> (32 - 11);
-        bool done = false;
-#pragma unroll 1
-        for (int probe = 0; probe < 2; ++probe) {
-          int k = keys[hsh];  // plain read first: no atomic when the bin is already there
-          if (k == -1) k = atomicCAS(&keys[hsh], -1, b);
-          if (k == -1 || k == b) {
-            atomicAdd(&vals[hsh], a);
-            done = true;
-            break;
-          }
-          hsh = (hsh + 1) & (kHash - 1);
+  const int stride = gridDim.x * blockDim.x;
+  // warp-uniform trip count
+  for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < d.n_mov; i0 += stride) {
+    const int i = i0 + (threadIdx.x & 31);
+    const bool valid = i < d.n_mov;
+    QRect r;
+    if (valid) {
+      const float2 v = xy[i];
+      r = qrect(v.x, v.y, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW, d.BH, d.nx, d.ny);
+    } else {
+      r.X = r.Y = r.W = r.H = 0;
+      r.ix0 = r.iy0 = 0;
+      r.ix1 = r.iy1 = -1;
+    }
+#pragma unroll
+    for (int sl = 0; sl < 4; ++sl) {
+      const int ix = r.ix0 + (sl & 1), iy = r.iy0 + (sl >> 1);
+      int b = -1;
+      unsigned long long a = 0ull;
+      if (ix <= r.ix1 && iy <= r.iy1) {
+        const long long ox = overlap1(r.X, r.W, d.XL + (long long)ix * d.BW, d.BW);
+        const long long oy = overlap1(r.Y, r.H, d.YL + (long long)iy * d.BH, d.BH);
+        a = (unsigned long long)(ox * oy);
+        if (a != 0ull) b = ix * d.ny + iy;
+      }
+      const unsigned int mask = __match_any_sync(0xffffffffu, b);
+      const unsigned long long tot = group_sum_u64(mask, a);
+      if (b >= 0 && (threadIdx.x & 31) == __ffs(mask) - 1) {
+        // lanes alone on their bin (spread placements) go straight to the map;
+        // shared bins (clustered placements) go through the block table
+        if (__popc(mask) == 1)
+          atomicAdd(&M[b], tot);
+        else
+          hash_add(keys, vals, M, b, tot);
+      }
+    }
+    // bins beyond the first 2 x 2 (cells larger than a bin)
+    if (valid && (r.ix1 - r.ix0 > 1 || r.iy1 - r.iy0 > 1)) {
+      for (int ix = r.ix0; ix <= r.ix1; ++ix) {
+        const long long ox = overlap1(r.X, r.W, d.XL + (long long)ix * d.BW, d.BW);
+        if (ox == 0) continue;
+        for (int iy = r.iy0; iy <= r.iy1; ++iy) {
+          if (ix - r.ix0 <= 1 && iy - r.iy0 <= 1) continue;  // done above
+          const long long oy = overlap1(r.Y, r.H, d.YL + (long long)iy * d.BH, d.BH);
+          if (oy == 0) continue;
+          hash_add(keys, vals, M, ix * d.ny + iy, (unsigned long long)(ox * oy));
         }
-        if (!done) atomicAdd(&M[b], a);
       }
     }
   }
@@ -72,10 +129,10 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
 
 // Same map for an arbitrary cell range (the fixed cells, once at create).
 __global__ void __launch_bounds__(kThreads)
-    k_scatter_range(Dev d, const float *x, const float *y, int n0, int n1,
-                    unsigned long long *out) {
+    k_scatter_range(Dev d, const float2 *xy, int n0, int n1, unsigned long long *out) {
   for (int i = n0 + blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += gridDim.x * blockDim.x) {
-    QRect r = qrect(x[i], y[i], d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW, d.BH, d.nx, d.ny);
+    const float2 v = xy[i];
+    QRect r = qrect(v.x, v.y, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW, d.BH, d.nx, d.ny);
     for (int ix = r.ix0; ix <= r.ix1; ++ix) {
       long long ox = overlap1(r.X, r.W, d.XL + (long long)ix * d.BW, d.BW);
       if (ox == 0) continue;
@@ -153,12 +210,12 @@ void launch_scatter(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t s
   k_scatter<<<grid, kThreads, 0, st>>>(d, copy0, eval);
 }
 
-void launch_scatter_fixed(const Dev &d, const float *x, const float *y, int n0, int n1,
+void launch_scatter_fixed(const Dev &d, const float2 *xy, int n0, int n1,
                           unsigned long long *out, cudaStream_t st) {
   if (n1 <= n0) return;
   int blocks = (n1 - n0 + kThreads - 1) / kThreads;
   if (blocks > 4096) blocks = 4096;
-  k_scatter_range<<<blocks, kThreads, 0, st>>>(d, x, y, n0, n1, out);
+  k_scatter_range<<<blocks, kThreads, 0, st>>>(d, xy, n0, n1, out);
 }
 
 void launch_density_finish(const Dev &d, int copy0, int ncopy, int mode, cudaStream_t st) {

@@ -80,12 +80,12 @@ struct Dev {
   unsigned char *is_macro;  // [n_cells]
 
   // per-copy state
-  float *x, *y;              // [K][n_cells] reference positions v (fixed part replicated)
+  float2 *xy;                // [K][n_cells] reference positions v, interleaved (fixed part replicated)
   float *ux, *uy;            // [K][n_mov]
   float *vpx, *vpy;          // [K][n_mov]
   float *gx[2], *gy[2];      // [K][n_mov] preconditioned gradient, by parity
   float *gwx, *gwy, *gdx, *gdy;  // [K][n_mov] raw gradients
-  float2 *pin_grad;          // [K][n_pins]
+  float2 *pin_grad;          // [K][n_pins] per-pin WA gradients (pin order)
   unsigned long long *M;     // [K][G]
   long long *Fmap;           // [G]
   float *rho;                // [K][G]
@@ -113,7 +113,7 @@ struct Dev {
   int *err;                         // device error flag (bounded waits)
 
   // Hybro best solutions
-  float *bx, *by;            // [K][n_cells]
+  float2 *bxy;               // [K][n_cells]
 
   // perturbation scratch
   unsigned long long *sort_key;  // [2^ceil(log2 n_cells)]
@@ -128,18 +128,22 @@ struct Dev {
   int wa_blocks[8];           // blocks per class per copy
   int wa_block_base[8];       // slot offset of the class's blocks
   int wa_blocks_total;
+  int wa_big_cap;             // pins of a > 256-pin net kept in shared memory
 };
 
 // ---- launchers (all enqueue on `st`) ------------------------------------
 // eval != 0 ignores the stopped flag of the copy (stage-level evaluation).
 void launch_scatter(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
-void launch_scatter_fixed(const Dev &d, const float *x, const float *y, int n0, int n1,
+void launch_scatter_fixed(const Dev &d, const float2 *xy, int n0, int n1,
                           unsigned long long *out, cudaStream_t st);
+void launch_pack_xy(float2 *dst, const float *x, const float *y, int n, cudaStream_t st);
+void launch_unpack_xy(float *x, float *y, const float2 *src, int n, cudaStream_t st);
 void launch_density_finish(const Dev &d, int copy0, int ncopy, int mode, cudaStream_t st);
 void launch_spectral(const Dev &d, int copy0, int ncopy, int with_psi, int eval, cudaStream_t st);
 void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_override,
                cudaStream_t st);
 void launch_hpwl64(const Dev &d, int copy0, int ncopy, cudaStream_t st);
+int wa_prepare(int cap);
 void launch_cell_grad(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
 void launch_precond0(const Dev &d, int copy0, int ncopy, cudaStream_t st);
 void launch_update(const Dev &d, int copy0, int ncopy, cudaStream_t st);

@@ -76,19 +76,29 @@ __global__ void __launch_bounds__(kThreads) k_cell_grad(Dev d, int copy0, int ev
   const float lam = (float)cs->lam;
   const int par = cs->parity;
   const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
-  const float *x = d.x + cn, *y = d.y + cn;
+  const float2 *xy = d.xy + cn;
   const float2 *pg = d.pin_grad + (size_t)c * d.n_pins;
   const float *ex = d.E + (size_t)c * 3 * d.G, *ey = ex + d.G;
   float n1 = 0.f, d1 = 0.f, dg2 = 0.f, dv2 = 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
     float sx = 0.f, sy = 0.f;
-    const int q1 = d.cell_pin_ptr[i + 1];
-    for (int q = d.cell_pin_ptr[i]; q < q1; ++q) {
-      float2 g = pg[d.cell_pins[q]];
-      sx += g.x;
-      sy += g.y;
+    const int q0 = d.cell_pin_ptr[i], q1 = d.cell_pin_ptr[i + 1];
+    // four pins at a time: the index loads, then the gathers, all in flight
+    for (int q = q0; q < q1; q += 4) {
+      int j[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) j[u] = (q + u < q1) ? d.cell_pins[q + u] : -1;
+      float2 g[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) g[u] = j[u] >= 0 ? pg[j[u]] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        sx += g[u].x;
+        sy += g[u].y;
+      }
     }
-    const float xi = x[i], yi = y[i];
+    const float2 vi = xy[i];
+    const float xi = vi.x, yi = vi.y;
     QRect r = qrect(xi, yi, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW, d.BH, d.nx, d.ny);
     float dx = 0.f, dy = 0.f;
     for (int ix = r.ix0; ix <= r.ix1; ++ix) {
@@ -191,7 +201,8 @@ __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
   const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
     const float xh = d.fxh - d.w[i], yh = d.fyh - d.h[i];
-    const float vx = d.x[cn + i], vy = d.y[cn + i];
+    const float2 v = d.xy[cn + i];
+    const float vx = v.x, vy = v.y;
     const float ux = d.ux[cm + i], uy = d.uy[cm + i];
     float nux = fmaxf(d.fxl, fminf(vx - alpha * d.gx[par][cm + i], xh));
     float nuy = fmaxf(d.fyl, fminf(vy - alpha * d.gy[par][cm + i], yh));
@@ -199,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
     float nvy = fmaxf(d.fyl, fminf(nuy + coef * (nuy - uy), yh));
     d.vpx[cm + i] = vx; d.vpy[cm + i] = vy;
     d.ux[cm + i] = nux; d.uy[cm + i] = nuy;
-    d.x[cn + i] = nvx; d.y[cn + i] = nvy;
+    d.xy[cn + i] = make_float2(nvx, nvy);
   }
   if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_UPDATE, &flag)) return;
   if (threadIdx.x == 0) {
@@ -217,9 +228,10 @@ __global__ void __launch_bounds__(kThreads) k_reset(Dev d, int copy0) {
   const int c = copy0 + blockIdx.y;
   const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
-    float vx = fmaxf(d.fxl, fminf(d.x[cn + i], d.fxh - d.w[i]));
-    float vy = fmaxf(d.fyl, fminf(d.y[cn + i], d.fyh - d.h[i]));
-    d.x[cn + i] = vx; d.y[cn + i] = vy;
+    const float2 v = d.xy[cn + i];
+    float vx = fmaxf(d.fxl, fminf(v.x, d.fxh - d.w[i]));
+    float vy = fmaxf(d.fyl, fminf(v.y, d.fyh - d.h[i]));
+    d.xy[cn + i] = make_float2(vx, vy);
     d.ux[cm + i] = vx; d.uy[cm + i] = vy;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -236,6 +248,31 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_slot(Dev d, int slot, in
   const int c = copy0 + blockIdx.x;
   double s = sum_slot<kRedThreads>(d, c, slot, nvals, sm);
   if (threadIdx.x == 0) d.scal[(size_t)c * S_COUNT + slot] = s;
+}
+
+__global__ void k_pack_xy(float2 *dst, const float *x, const float *y, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = make_float2(x[i], y[i]);
+}
+
+__global__ void k_unpack_xy(float *x, float *y, const float2 *src, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float2 v = src[i];
+    x[i] = v.x;
+    y[i] = v.y;
+  }
+}
+
+void launch_pack_xy(float2 *dst, const float *x, const float *y, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  int b = (n + kThreads - 1) / kThreads;
+  k_pack_xy<<<b < 4096 ? b : 4096, kThreads, 0, st>>>(dst, x, y, n);
+}
+
+void launch_unpack_xy(float *x, float *y, const float2 *src, int n, cudaStream_t st) {
+  if (n <= 0) return;
+  int b = (n + kThreads - 1) / kThreads;
+  k_unpack_xy<<<b < 4096 ? b : 4096, kThreads, 0, st>>>(x, y, src, n);
 }
 
 void launch_cell_grad(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st) {

@@ -78,12 +78,13 @@ __global__ void k_bitonic_u32(unsigned int *v, int n, int j, int k) {
 }
 
 __global__ void k_shuffle_compute(Dev d, int copy, int k) {
-  const float *x = d.x + (size_t)copy * d.n_cells, *y = d.y + (size_t)copy * d.n_cells;
+  const float2 *xy = d.xy + (size_t)copy * d.n_cells;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
     const int r = (int)d.sort_idx[j];  // receiver (key order)
     const int s = (int)d.sel_idx[j];   // donor (index order)
-    double cx = (double)x[s] + 0.5 * (double)d.w[s];
-    double cy = (double)y[s] + 0.5 * (double)d.h[s];
+    const float2 ps = xy[s];
+    double cx = (double)ps.x + 0.5 * (double)d.w[s];
+    double cy = (double)ps.y + 0.5 * (double)d.h[s];
     double nx = cx - 0.5 * (double)d.w[r];
     double ny = cy - 0.5 * (double)d.h[r];
     nx = fmax(d.die_xl, fmin(nx, d.die_xh - (double)d.w[r]));
@@ -94,11 +95,10 @@ __global__ void k_shuffle_compute(Dev d, int copy, int k) {
 }
 
 __global__ void k_shuffle_apply(Dev d, int copy, int k) {
-  float *x = d.x + (size_t)copy * d.n_cells, *y = d.y + (size_t)copy * d.n_cells;
+  float2 *xy = d.xy + (size_t)copy * d.n_cells;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
     const int r = (int)d.sort_idx[j];
-    x[r] = d.px_tmp[j];
-    y[r] = d.py_tmp[j];
+    xy[r] = make_float2(d.px_tmp[j], d.py_tmp[j]);
   }
 }
 

@@ -7,13 +7,18 @@
 //   WL_e = (m+ - m-) + R+ - R-                     (Eq. 3, exactly)
 //   dWL_e/dp_j = (a_j/S+)(1 + (p_j - m+ - R+)/g) - (b_j/S-)(1 - (p_j - m- - R-)/g)
 // Pin coordinates are taken relative to the net's first pin (WA is
-// shift-invariant), and exponents relative to m+ / m-, so that FP32 keeps the
-// digits that matter even where the cells of a net sit close together far
-// from the origin.  Nets are grouped by degree at create: groups of G lanes
-// (G = 4, 8, 16, 32) handle one net each, looping for degree > G; nets with
-// more than 256 pins get a whole block.  Per-pin gradients are written to a
-// pin-ordered array; the per-cell sum runs in the cell-gradient kernel in a
-// fixed order (no floating-point atomics, so results are deterministic).
+// shift-invariant), (x_j - x_0) + (dx_j - dx_0), and exponents relative to
+// m+ / m-, so FP32 keeps the digits that matter even where the cells of a
+// net sit close together far from the origin.
+//
+// Nets are grouped by degree at create: one thread per net up to 4 pins
+// (pins in registers), groups of 4 lanes up to 16 pins, 16 lanes up to 64, a
+// warp up to 256, and a block of 512 threads beyond, which keeps the net's
+// coordinates in shared memory between its three passes.  Positions are
+// interleaved (x, y), so every pin costs one gather.  Per-pin gradients are
+// written in pin order (coalesced); the cell-gradient kernel sums each
+// cell's pins in a fixed order: no floating-point atomics, deterministic
+// results.
 #include <cfloat>
 
 #include "common.cuh"
@@ -44,6 +49,91 @@ __device__ __forceinline__ float copy_gamma(const Dev &d, int c, const float *ov
   return ovr ? *ovr : (float)d.cs[c].gamma;
 }
 
+// Nets of at most D pins: one thread per net, pins held in registers, no
+// shuffles (most nets of a netlist have 2 or 3 pins).
+template <int D>
+__global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int cls, int eval,
+                                                            const float *gamma_ovr) {
+  __shared__ float sm[32];
+  const int c = copy0 + blockIdx.y;
+  if (!eval && d.cs[c].stopped) return;
+  const float g = copy_gamma(d, c, gamma_ovr);
+  const float ig = 1.0f / g;
+  const float2 *xy = d.xy + (size_t)c * d.n_cells;
+  float2 *pg = d.pin_grad + (size_t)c * d.n_pins;
+  const int e_end = d.cls_begin[cls + 1];
+  float hp_acc = 0.f, wl_acc = 0.f;
+  for (int e = d.cls_begin[cls] + blockIdx.x * blockDim.x + threadIdx.x; e < e_end;
+       e += gridDim.x * blockDim.x) {
+    const int p0 = d.net_ptr[e], p1 = d.net_ptr[e + 1];
+    const int deg = p1 - p0;
+    if (deg <= 0) continue;
+    int cell[D];
+    float2 off[D], pos[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      if (k < deg) {
+        cell[k] = d.pin_cell[p0 + k];
+        off[k] = d.pin_off[p0 + k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+      if (k < deg) pos[k] = xy[cell[k]];
+    float px[D], py[D];
+    px[0] = 0.f;
+    py[0] = 0.f;
+#pragma unroll
+    for (int k = 1; k < D; ++k) {
+      if (k < deg) {
+        px[k] = (pos[k].x - pos[0].x) + (off[k].x - off[0].x);
+        py[k] = (pos[k].y - pos[0].y) + (off[k].y - off[0].y);
+      }
+    }
+    float mxx = 0.f, mnx = 0.f, mxy = 0.f, mny = 0.f;
+#pragma unroll
+    for (int k = 1; k < D; ++k) {
+      if (k < deg) {
+        mxx = fmaxf(mxx, px[k]); mnx = fminf(mnx, px[k]);
+        mxy = fmaxf(mxy, py[k]); mny = fminf(mny, py[k]);
+      }
+    }
+    float ax[D], bx[D], ay[D], by[D];
+    float sxp = 0.f, txp = 0.f, sxm = 0.f, txm = 0.f, syp = 0.f, typ = 0.f, sym = 0.f, tym = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      if (k < deg) {
+        ax[k] = expf((px[k] - mxx) * ig); bx[k] = expf((mnx - px[k]) * ig);
+        ay[k] = expf((py[k] - mxy) * ig); by[k] = expf((mny - py[k]) * ig);
+        sxp += ax[k]; txp += (px[k] - mxx) * ax[k]; sxm += bx[k]; txm += (px[k] - mnx) * bx[k];
+        syp += ay[k]; typ += (py[k] - mxy) * ay[k]; sym += by[k]; tym += (py[k] - mny) * by[k];
+      }
+    }
+    const float wn = d.net_w ? d.net_w[e] : 1.0f;
+    const float rxp = txp / sxp, rxm = txm / sxm, ryp = typ / syp, rym = tym / sym;
+    const float isxp = 1.f / sxp, isxm = 1.f / sxm, isyp = 1.f / syp, isym = 1.f / sym;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      if (k < deg) {
+        const float gx = ax[k] * isxp * (1.f + (px[k] - mxx - rxp) * ig) -
+                         bx[k] * isxm * (1.f - (px[k] - mnx - rxm) * ig);
+        const float gy = ay[k] * isyp * (1.f + (py[k] - mxy - ryp) * ig) -
+                         by[k] * isym * (1.f - (py[k] - mny - rym) * ig);
+        pg[p0 + k] = make_float2(gx * wn, gy * wn);
+      }
+    }
+    hp_acc += wn * ((mxx - mnx) + (mxy - mny));
+    wl_acc += wn * (((mxx - mnx) + (rxp - rxm)) + ((mxy - mny) + (ryp - rym)));
+  }
+  float rh = block_sum_f<kThreads>(hp_acc, sm);
+  float rw = block_sum_f<kThreads>(wl_acc, sm);
+  if (threadIdx.x == 0) {
+    size_t base = (size_t)c * S_COUNT * d.nb_red + d.wa_block_base[cls] + blockIdx.x;
+    d.part[base + (size_t)S_HPWL * d.nb_red] = rh;
+    d.part[base + (size_t)S_WL * d.nb_red] = rw;
+  }
+}
+
 template <int G>
 __global__ void __launch_bounds__(kThreads) k_wa_group(Dev d, int copy0, int cls, int eval,
                                                         const float *gamma_ovr) {
@@ -52,8 +142,7 @@ __global__ void __launch_bounds__(kThreads) k_wa_group(Dev d, int copy0, int cls
   if (!eval && d.cs[c].stopped) return;
   const float g = copy_gamma(d, c, gamma_ovr);
   const float ig = 1.0f / g;
-  const float *x = d.x + (size_t)c * d.n_cells;
-  const float *y = d.y + (size_t)c * d.n_cells;
+  const float2 *xy = d.xy + (size_t)c * d.n_cells;
   float2 *pg = d.pin_grad + (size_t)c * d.n_pins;
   constexpr int NPB = kThreads / G;
   const int lane = threadIdx.x % G;
@@ -72,26 +161,26 @@ __global__ void __launch_bounds__(kThreads) k_wa_group(Dev d, int copy0, int cls
     // rounds relative to the pin spacing, not to the absolute position
     float rx = 0.f, ry = 0.f, rdx = 0.f, rdy = 0.f;
     if (p1 > p0) {
-      int cell = d.pin_cell[p0];
-      float2 o = d.pin_off[p0];
-      rx = x[cell]; ry = y[cell]; rdx = o.x; rdy = o.y;
+      const float2 o = d.pin_off[p0];
+      const float2 v = xy[d.pin_cell[p0]];
+      rx = v.x; ry = v.y; rdx = o.x; rdy = o.y;
     }
     // first pin of each lane stays in registers; higher degrees reload
     const int j0 = p0 + lane;
     const bool has0 = j0 < p1;
     float px0 = 0.f, py0 = 0.f;
     if (has0) {
-      int cell = d.pin_cell[j0];
-      float2 o = d.pin_off[j0];
-      px0 = (x[cell] - rx) + (o.x - rdx);
-      py0 = (y[cell] - ry) + (o.y - rdy);
+      const float2 o = d.pin_off[j0];
+      const float2 v = xy[d.pin_cell[j0]];
+      px0 = (v.x - rx) + (o.x - rdx);
+      py0 = (v.y - ry) + (o.y - rdy);
     }
     float mxx = has0 ? px0 : -FLT_MAX, mnx = has0 ? px0 : FLT_MAX;
     float mxy = has0 ? py0 : -FLT_MAX, mny = has0 ? py0 : FLT_MAX;
     for (int j = j0 + G; j < p1; j += G) {
-      int cell = d.pin_cell[j];
-      float2 o = d.pin_off[j];
-      float px = (x[cell] - rx) + (o.x - rdx), py = (y[cell] - ry) + (o.y - rdy);
+      const float2 o = d.pin_off[j];
+      const float2 v = xy[d.pin_cell[j]];
+      float px = (v.x - rx) + (o.x - rdx), py = (v.y - ry) + (o.y - rdy);
       mxx = fmaxf(mxx, px); mnx = fminf(mnx, px);
       mxy = fmaxf(mxy, py); mny = fminf(mny, py);
     }
@@ -107,9 +196,9 @@ __global__ void __launch_bounds__(kThreads) k_wa_group(Dev d, int copy0, int cls
       syp += a0y; typ += (py0 - mxy) * a0y; sym += b0y; tym += (py0 - mny) * b0y;
     }
     for (int j = j0 + G; j < p1; j += G) {
-      int cell = d.pin_cell[j];
-      float2 o = d.pin_off[j];
-      float px = (x[cell] - rx) + (o.x - rdx), py = (y[cell] - ry) + (o.y - rdy);
+      const float2 o = d.pin_off[j];
+      const float2 v = xy[d.pin_cell[j]];
+      float px = (v.x - rx) + (o.x - rdx), py = (v.y - ry) + (o.y - rdy);
       float a = expf((px - mxx) * ig), b = expf((mnx - px) * ig);
       sxp += a; txp += (px - mxx) * a; sxm += b; txm += (px - mnx) * b;
       a = expf((py - mxy) * ig); b = expf((mny - py) * ig);
@@ -126,9 +215,9 @@ __global__ void __launch_bounds__(kThreads) k_wa_group(Dev d, int copy0, int cls
         pg[j0] = make_float2(gx * wn, gy * wn);
       }
       for (int j = j0 + G; j < p1; j += G) {
-        int cell = d.pin_cell[j];
-        float2 o = d.pin_off[j];
-        float px = (x[cell] - rx) + (o.x - rdx), py = (y[cell] - ry) + (o.y - rdy);
+        const float2 o = d.pin_off[j];
+        const float2 v = xy[d.pin_cell[j]];
+        float px = (v.x - rx) + (o.x - rdx), py = (v.y - ry) + (o.y - rdy);
         float a = expf((px - mxx) * ig), b = expf((mnx - px) * ig);
         float gx = a * isxp * (1.f + (px - mxx - rxp) * ig) - b * isxm * (1.f - (px - mnx - rxm) * ig);
         a = expf((py - mxy) * ig); b = expf((mny - py) * ig);
@@ -151,82 +240,86 @@ __global__ void __launch_bounds__(kThreads) k_wa_group(Dev d, int copy0, int cls
 }
 
 // Block-wide reductions for the one-block-per-net kernel.
-__device__ __forceinline__ float bred_max(float v, float *sm) {
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+constexpr int kBigNet = 512;
+__device__ __forceinline__ float bred(float v, float *sm, int op) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = op == 0 ? fmaxf(v, w) : (op == 1 ? fminf(v, w) : v + w);
+  }
   __syncthreads();
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
   __syncthreads();
   float r = sm[0];
-  for (int i = 1; i < kThreads / 32; ++i) r = fmaxf(r, sm[i]);
-  return r;
-}
-__device__ __forceinline__ float bred_min(float v, float *sm) {
-  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float r = sm[0];
-  for (int i = 1; i < kThreads / 32; ++i) r = fminf(r, sm[i]);
-  return r;
-}
-__device__ __forceinline__ float bred_sum(float v, float *sm) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float r = sm[0];
-  for (int i = 1; i < kThreads / 32; ++i) r += sm[i];
+#pragma unroll
+  for (int i = 1; i < kBigNet / 32; ++i) r = op == 0 ? fmaxf(r, sm[i]) : (op == 1 ? fminf(r, sm[i]) : r + sm[i]);
   return r;
 }
 
-__global__ void __launch_bounds__(kThreads) k_wa_block(Dev d, int copy0, int cls, int eval,
-                                                        const float *gamma_ovr) {
+// One block per net (degree > 256).  Net-relative pin coordinates are kept
+// in dynamic shared memory when the net fits `cap` pins; longer nets reload
+// pins from global memory in every pass.
+__global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, int eval,
+                                                    const float *gamma_ovr, int cap) {
+  extern __shared__ float dyn[];
+  float *spx = dyn, *spy = dyn + cap;
   __shared__ float sm[32];
   const int c = copy0 + blockIdx.y;
   if (!eval && d.cs[c].stopped) return;
   const float g = copy_gamma(d, c, gamma_ovr);
   const float ig = 1.0f / g;
-  const float *x = d.x + (size_t)c * d.n_cells;
-  const float *y = d.y + (size_t)c * d.n_cells;
+  const float2 *xy = d.xy + (size_t)c * d.n_cells;
   float2 *pg = d.pin_grad + (size_t)c * d.n_pins;
   float hp_acc = 0.f, wl_acc = 0.f;
   for (int e = d.cls_begin[cls] + blockIdx.x; e < d.cls_begin[cls + 1]; e += gridDim.x) {
     const int p0 = d.net_ptr[e], p1 = d.net_ptr[e + 1];
+    const bool cached = (p1 - p0) <= cap;
     const float wn = d.net_w ? d.net_w[e] : 1.0f;
-    const int cell0 = d.pin_cell[p0];
     const float2 o0 = d.pin_off[p0];
-    const float rx = x[cell0], ry = y[cell0], rdx = o0.x, rdy = o0.y;
+    const float2 v0 = xy[d.pin_cell[p0]];
+    const float rx = v0.x, ry = v0.y, rdx = o0.x, rdy = o0.y;
     float mxx = -FLT_MAX, mnx = FLT_MAX, mxy = -FLT_MAX, mny = FLT_MAX;
-    for (int j = p0 + threadIdx.x; j < p1; j += kThreads) {
-      int cell = d.pin_cell[j];
-      float2 o = d.pin_off[j];
-      float px = (x[cell] - rx) + (o.x - rdx), py = (y[cell] - ry) + (o.y - rdy);
+    for (int j = p0 + threadIdx.x; j < p1; j += kBigNet) {
+      const float2 o = d.pin_off[j];
+      const float2 v = xy[d.pin_cell[j]];
+      const float px = (v.x - rx) + (o.x - rdx), py = (v.y - ry) + (o.y - rdy);
+      if (cached) { spx[j - p0] = px; spy[j - p0] = py; }
       mxx = fmaxf(mxx, px); mnx = fminf(mnx, px);
       mxy = fmaxf(mxy, py); mny = fminf(mny, py);
     }
-    mxx = bred_max(mxx, sm); mnx = bred_min(mnx, sm);
-    mxy = bred_max(mxy, sm); mny = bred_min(mny, sm);
+    mxx = bred(mxx, sm, 0); mnx = bred(mnx, sm, 1);
+    mxy = bred(mxy, sm, 0); mny = bred(mny, sm, 1);
     float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int j = p0 + threadIdx.x; j < p1; j += kThreads) {
-      int cell = d.pin_cell[j];
-      float2 o = d.pin_off[j];
-      float px = (x[cell] - rx) + (o.x - rdx), py = (y[cell] - ry) + (o.y - rdy);
+    for (int j = p0 + threadIdx.x; j < p1; j += kBigNet) {
+      float px, py;
+      if (cached) {
+        px = spx[j - p0]; py = spy[j - p0];
+      } else {
+        const float2 o = d.pin_off[j];
+        const float2 v = xy[d.pin_cell[j]];
+        px = (v.x - rx) + (o.x - rdx); py = (v.y - ry) + (o.y - rdy);
+      }
       float a = expf((px - mxx) * ig), b = expf((mnx - px) * ig);
       s[0] += a; s[1] += (px - mxx) * a; s[2] += b; s[3] += (px - mnx) * b;
       a = expf((py - mxy) * ig); b = expf((mny - py) * ig);
       s[4] += a; s[5] += (py - mxy) * a; s[6] += b; s[7] += (py - mny) * b;
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) s[q] = bred_sum(s[q], sm);
+    for (int q = 0; q < 8; ++q) s[q] = bred(s[q], sm, 2);
     const float rxp = s[1] / s[0], rxm = s[3] / s[2], ryp = s[5] / s[4], rym = s[7] / s[6];
-    for (int j = p0 + threadIdx.x; j < p1; j += kThreads) {
-      int cell = d.pin_cell[j];
-      float2 o = d.pin_off[j];
-      float px = (x[cell] - rx) + (o.x - rdx), py = (y[cell] - ry) + (o.y - rdy);
+    for (int j = p0 + threadIdx.x; j < p1; j += kBigNet) {
+      float px, py;
+      if (cached) {
+        px = spx[j - p0]; py = spy[j - p0];
+      } else {
+        const float2 o = d.pin_off[j];
+        const float2 v = xy[d.pin_cell[j]];
+        px = (v.x - rx) + (o.x - rdx); py = (v.y - ry) + (o.y - rdy);
+      }
       float a = expf((px - mxx) * ig), b = expf((mnx - px) * ig);
-      float gx = a / s[0] * (1.f + (px - mxx - rxp) * ig) - b / s[2] * (1.f - (px - mnx - rxm) * ig);
+      const float gx = a / s[0] * (1.f + (px - mxx - rxp) * ig) - b / s[2] * (1.f - (px - mnx - rxm) * ig);
       a = expf((py - mxy) * ig); b = expf((mny - py) * ig);
-      float gy = a / s[4] * (1.f + (py - mxy - ryp) * ig) - b / s[6] * (1.f - (py - mny - rym) * ig);
+      const float gy = a / s[4] * (1.f + (py - mxy - ryp) * ig) - b / s[6] * (1.f - (py - mny - rym) * ig);
       pg[j] = make_float2(gx * wn, gy * wn);
     }
     hp_acc += wn * ((mxx - mnx) + (mxy - mny));
@@ -249,8 +342,7 @@ __global__ void __launch_bounds__(kThreads) k_hpwl64(Dev d, int copy0, int e_beg
                                                       int slot_base) {
   __shared__ double sm[32];
   const int c = copy0 + blockIdx.y;
-  const float *x = d.x + (size_t)c * d.n_cells;
-  const float *y = d.y + (size_t)c * d.n_cells;
+  const float2 *xy = d.xy + (size_t)c * d.n_cells;
   constexpr int NPB = kThreads / G;
   const int lane = threadIdx.x % G;
   double acc = 0.0;
@@ -263,9 +355,9 @@ __global__ void __launch_bounds__(kThreads) k_hpwl64(Dev d, int copy0, int e_beg
     }
     double mxx = -1e300, mnx = 1e300, mxy = -1e300, mny = 1e300;
     for (int j = p0 + lane; j < p1; j += G) {
-      int cell = d.pin_cell[j];
-      float2 o = d.pin_off[j];
-      double px = (double)x[cell] + (double)o.x, py = (double)y[cell] + (double)o.y;
+      const float2 o = d.pin_off[j];
+      const float2 v = xy[d.pin_cell[j]];
+      double px = (double)v.x + (double)o.x, py = (double)v.y + (double)o.y;
       mxx = fmax(mxx, px); mnx = fmin(mnx, px);
       mxy = fmax(mxy, py); mny = fmin(mny, py);
     }
@@ -293,13 +385,22 @@ void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_
     if (nb == 0) continue;
     dim3 grid(nb, ncopy);
     switch (cls) {
-      case 0: k_wa_group<4><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
-      case 1: k_wa_group<8><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
+      case 0: k_wa_thread<4><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
+      case 1: k_wa_group<4><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
       case 2: k_wa_group<16><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
       case 3: k_wa_group<32><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
-      default: k_wa_block<<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
+      default:
+        k_wa_big<<<grid, kBigNet, 2 * sizeof(float) * d.wa_big_cap, st>>>(d, copy0, cls, eval,
+                                                                          gamma_ovr, d.wa_big_cap);
+        break;
     }
   }
+}
+
+int wa_prepare(int cap) {
+  cudaError_t e = cudaFuncSetAttribute(k_wa_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(2 * sizeof(float) * cap));
+  return e == cudaSuccess ? 0 : -1;
 }
 
 int hpwl64_blocks(const Dev &d) { return 2 * d.cell_blocks; }
