@@ -131,9 +131,11 @@ def algorithmic(d, info):
         # pin_cell 4 + offsets 8 + gradient write 8 per pin, net_ptr 4 per net,
         # positions 8 per cell (gathered once)
         "wirelength": {"bytes": 20 * P + 4 * E + 8 * n_all},
-        # cell->pin index 4 + pin gradient 8 per movable pin, 4 + 8 B/cell of
-        # index and size, positions 8, four gradients written 16, field 8 per cell
-        "cellgrad": {"bytes": 12 * mov_pins + 44 * C},
+        # pin sums: cell->pin index 4 + pin gradient 8 per movable pin, CSR 4 per
+        # cell; gather: position 8, sizes 8, field 8, pins/area 8, previous
+        # gradient 8, previous position 8; writes: four raw gradients 16 and the
+        # gradient 8 per cell
+        "cellgrad": {"bytes": 12 * mov_pins + 76 * C},
         # read v, u, g 24, npins/area 8, gwl, gd 16, v_prev 8, g_prev 8; write u, v, v_prev, g 32
         "update": {"bytes": 96 * C},
     }

@@ -226,21 +226,29 @@ int setup_tc(place_t *h) {
   launch_split_bf16(d.CTm, d.A4h + 2 * nx2, d.A4l + 2 * nx2, nx2, st);
   CKL();
   const int nx = d.nx, ny = d.ny, K = d.K;
+  // tile width per stage: 128; 64 only for grids so small that 128-wide
+  // tiles would occupy under a quarter of the SMs
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  if (sms <= 0) sms = 152;
+  const int tiles128[4] = {(nx / 128) * (ny / 128) * K, (ny / 128) * (nx / 128) * K,
+                           (nx / 128) * (ny / 128) * 2 * K, (ny / 128) * (nx / 128) * 2 * K};
+  for (int s = 0; s < 4; ++s) d.tc_bn[s] = tiles128[s] * 4 <= sms ? 64 : 128;
   struct M { const void *p; int k, rows, batch, box; } spec[16] = {
       {d.A1h, ny, ny, 1, 128}, {d.A1l, ny, ny, 1, 128},
-      {d.rho_h, ny, nx, K, 128}, {d.rho_l, ny, nx, K, 128},
+      {d.rho_h, ny, nx, K, d.tc_bn[0]}, {d.rho_l, ny, nx, K, d.tc_bn[0]},
       {d.A2h, nx, nx, 1, 128}, {d.A2l, nx, nx, 1, 128},
-      {d.T_h, nx, ny, 3 * K, 128}, {d.T_l, nx, ny, 3 * K, 128},
+      {d.T_h, nx, ny, 3 * K, d.tc_bn[1]}, {d.T_l, nx, ny, 3 * K, d.tc_bn[1]},
       {d.A3h, ny, ny, 3, 128}, {d.A3l, ny, ny, 3, 128},
-      {d.SB_h, ny, nx, 3 * K, 128}, {d.SB_l, ny, nx, 3 * K, 128},
+      {d.SB_h, ny, nx, 3 * K, d.tc_bn[2]}, {d.SB_l, ny, nx, 3 * K, d.tc_bn[2]},
       {d.A4h, nx, nx, 3, 128}, {d.A4l, nx, nx, 3, 128},
-      {d.T_h, nx, ny, 3 * K, 128}, {d.T_l, nx, ny, 3 * K, 128}};
+      {d.T_h, nx, ny, 3 * K, d.tc_bn[3]}, {d.T_l, nx, ny, 3 * K, d.tc_bn[3]}};
   for (int i = 0; i < 16; ++i) {
     int r = make_map_bf16_3d(&h->maps[i], spec[i].p, spec[i].k, spec[i].rows, spec[i].batch, spec[i].box);
     if (r) return fail(PLACE_ECUDA, "tensor map %d could not be encoded (%d)", i, r);
   }
   d.tcm = h->maps;
-  if (tc_prepare()) return fail(PLACE_ECUDA, "cannot reserve %d bytes of shared memory", tc_smem_bytes());
+  if (tc_prepare()) return fail(PLACE_ECUDA, "cannot reserve %d bytes of shared memory", tc_smem_bytes(128));
   return PLACE_OK;
 }
 
@@ -507,7 +515,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     d.wa_block_base[c] = d.wa_blocks_total;
     d.wa_blocks_total += nb;
   }
-  d.nb_red = std::max(std::max(2 * d.cell_blocks, d.bin_blocks), std::max(d.wa_blocks_total, 1));
+  d.nb_red = std::max(std::max(2 * d.cell_blocks + 2, d.bin_blocks), std::max(d.wa_blocks_total, 1));
   int sn = 2;
   while (sn < C) sn <<= 1;
   d.sort_n = sn;
@@ -811,7 +819,7 @@ int place_eval_hpwl_overflow(place_t *h, double *hpwl, double *overflow) {
   Dev &d = h->d;
   const int K = d.K;
   launch_hpwl64(d, 0, K, h->stream);
-  launch_reduce_slot(d, S_HP64, 2 * d.cell_blocks, 0, K, h->stream);
+  launch_reduce_slot(d, S_HP64, d.cell_blocks + 2 * std::max(d.cell_blocks / 2, 1), 0, K, h->stream);
   CK(cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.G * K, h->stream));
   launch_scatter(d, 0, K, 1, h->stream);
   launch_density_finish(d, 0, K, FIN_EVAL, h->stream);

@@ -110,6 +110,7 @@ struct Dev {
   __nv_bfloat16 *SB_h, *SB_l;       // [K][3][G]
   __nv_bfloat16 *A1h, *A1l, *A2h, *A2l, *A3h, *A3l, *A4h, *A4l;
   const void *tcm;                  // host array of 16 CUtensorMap (4 per GEMM stage)
+  int tc_bn[4];                     // tile width N (64 or 128) of each GEMM stage
   int *err;                         // device error flag (bounded waits)
 
   // Hybro best solutions

@@ -60,10 +60,10 @@ __device__ void advance_scalars(const Dev &d, CopyState *cs, bool first, double 
   cs->gamma = gamma_of(d, cs->tau);
 }
 
-// Gradient of the wirelength (sum of the cell's pin gradients) and of the
-// density (field gather -sum_b a_ib E_b) for every movable cell.  For k >= 1
-// (lambda known) the preconditioned gradient and the step-size norms are
-// formed here too, and the last block advances the scalars.
+// Gradient of the wirelength (sum of the cell's pin gradients, fixed order)
+// and of the density (field gather -sum_b a_ib E_b) for every movable cell.
+// For k >= 1 (lambda known) the preconditioned gradient and the step-size
+// norms are formed here too, and the last block advances the scalars.
 __global__ void __launch_bounds__(kThreads) k_cell_grad(Dev d, int copy0, int eval) {
   __shared__ float smf[32];
   __shared__ double smd[32];

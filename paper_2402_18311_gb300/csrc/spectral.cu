@@ -154,19 +154,19 @@ void launch_spectral_tc(const Dev &d, int copy0, int ncopy, int with_psi, int ev
   // G1: T[0] = Cn rho^T   (ny x nx, K = ny)
   g.M = d.ny; g.N = d.nx; g.K = d.ny; g.nwhich = 1; g.b_per_copy = 1; g.d_per_copy = 3;
   g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
-  launch_tc_gemm(mp + 0, g, ncopy, st);
+  launch_tc_gemm(mp + 0, g, ncopy, d.tc_bn[0], st);
   // G2: SB = spectral(Cm T[0]^T)   (nx x ny, K = nx)
   g.M = d.nx; g.N = d.ny; g.K = d.nx; g.b_per_copy = 3; g.d_per_copy = 3;
   g.epi = TC_EPI_SPECTRAL; g.Dh = d.SB_h; g.Dl = d.SB_l;
-  launch_tc_gemm(mp + 4, g, ncopy, st);
+  launch_tc_gemm(mp + 4, g, ncopy, d.tc_bn[1], st);
   // G3: T[w] = An_w SB[w]^T   (ny x nx, K = ny)
   g.M = d.ny; g.N = d.nx; g.K = d.ny; g.nwhich = nw;
   g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
-  launch_tc_gemm(mp + 8, g, ncopy, st);
+  launch_tc_gemm(mp + 8, g, ncopy, d.tc_bn[2], st);
   // G4: E[w] = Am_w T[w]^T   (nx x ny, K = nx)
   g.M = d.nx; g.N = d.ny; g.K = d.nx;
   g.epi = TC_EPI_F32; g.Df = d.E; g.Dh = g.Dl = nullptr;
-  launch_tc_gemm(mp + 12, g, ncopy, st);
+  launch_tc_gemm(mp + 12, g, ncopy, d.tc_bn[3], st);
 }
 
 void launch_spectral(const Dev &d, int copy0, int ncopy, int with_psi, int eval,

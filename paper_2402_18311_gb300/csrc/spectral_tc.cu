@@ -29,13 +29,19 @@ namespace hp {
 
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BKE = 64;   // tile (bf16 K elements per stage)
-constexpr int STAGES = 3;
-constexpr int TILE_A = BM * BKE * 2;           // bytes of one A_hi or A_lo stage tile
-constexpr int TILE_B = BN * BKE * 2;
-constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int BM = 128, BKE = 64;   // tile rows, bf16 K elements per stage
+constexpr int TILE_A = BM * BKE * 2;  // bytes of one A_hi or A_lo stage tile
 constexpr long long kWaitCycles = 2000000000ll;  // about one second
+
+template <int BN, int STAGES>
+struct Cfg {
+  static constexpr int TILE_B = BN * BKE * 2;
+  static constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  // Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = BN.
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -93,16 +99,13 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = BN.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
@@ -148,6 +151,7 @@ __device__ __forceinline__ void split_store(__nv_bfloat16 *hi, __nv_bfloat16 *lo
 using namespace tc;
 
 // D[z] = A[which] x B[z]^T over one 128 x BN tile; z = copy * nwhich + which.
+template <int BN, int STAGES>
 __global__ void __launch_bounds__(128, 1)
     k_umma_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                 const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
@@ -162,6 +166,8 @@ __global__ void __launch_bounds__(128, 1)
   const int dz = c * g.d_per_copy + which;  // batch index of D
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+  using C = Cfg<BN, STAGES>;
+  constexpr int TILE_B = C::TILE_B, STAGE_BYTES = C::STAGE_BYTES;
   uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023);
   unsigned char *tiles = reinterpret_cast<unsigned char *>(base);
   uint64_t *full = reinterpret_cast<uint64_t *>(tiles + STAGES * STAGE_BYTES);
@@ -234,9 +240,9 @@ __global__ void __launch_bounds__(128, 1)
       for (int k = 0; k < BKE / 16; ++k) {
         const uint32_t off = k * 32;  // 16 bf16 = 32 bytes along K inside the swizzle atom
         const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
-        umma_bf16(tmem, sw128_desc(ah + off), sw128_desc(bh + off), acc0);
-        umma_bf16(tmem, sw128_desc(ah + off), sw128_desc(bl + off), 1u);
-        umma_bf16(tmem, sw128_desc(al + off), sw128_desc(bh + off), 1u);
+        umma_bf16(tmem, sw128_desc(ah + off), sw128_desc(bh + off), C::IDESC, acc0);
+        umma_bf16(tmem, sw128_desc(ah + off), sw128_desc(bl + off), C::IDESC, 1u);
+        umma_bf16(tmem, sw128_desc(al + off), sw128_desc(bh + off), C::IDESC, 1u);
       }
       umma_commit(&empty[s]);
     }
@@ -297,16 +303,30 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
-int tc_smem_bytes() { return SMEM_BYTES; }
+int tc_smem_bytes(int bn) {
+  return bn == 64 ? Cfg<64, 2>::SMEM_BYTES : Cfg<128, 3>::SMEM_BYTES;
+}
 
-void launch_tc_gemm(const CUtensorMap *maps4, const TcArgs &g, int ncopy, cudaStream_t st) {
-  dim3 grid(g.N / BN, g.M / BM, g.nwhich * ncopy);
-  k_umma_gemm<<<grid, 128, SMEM_BYTES, st>>>(maps4[0], maps4[1], maps4[2], maps4[3], g);
+// bn = 128: 3-stage ring, one CTA per SM; bn = 64: 2-stage ring, two CTAs
+// per SM (twice the tiles for grids that would leave SMs idle).
+void launch_tc_gemm(const CUtensorMap *maps4, const TcArgs &g, int ncopy, int bn,
+                    cudaStream_t st) {
+  dim3 grid(g.N / bn, g.M / BM, g.nwhich * ncopy);
+  if (bn == 64)
+    k_umma_gemm<64, 2><<<grid, 128, Cfg<64, 2>::SMEM_BYTES, st>>>(maps4[0], maps4[1], maps4[2],
+                                                                 maps4[3], g);
+  else
+    k_umma_gemm<128, 3><<<grid, 128, Cfg<128, 3>::SMEM_BYTES, st>>>(maps4[0], maps4[1], maps4[2],
+                                                                   maps4[3], g);
 }
 
 int tc_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_umma_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       SMEM_BYTES);
+  cudaError_t e = cudaFuncSetAttribute(k_umma_gemm<128, 3>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Cfg<128, 3>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_umma_gemm<64, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Cfg<64, 2>::SMEM_BYTES);
   return e == cudaSuccess ? 0 : -1;
 }
 

@@ -25,9 +25,9 @@ struct TcArgs {
   int *err;                    // set to 1 when a bounded wait gives up
 };
 
-int tc_smem_bytes();
+int tc_smem_bytes(int bn);
 int tc_prepare();
-void launch_tc_gemm(const CUtensorMap *maps4, const TcArgs &g, int ncopy, cudaStream_t st);
+void launch_tc_gemm(const CUtensorMap *maps4, const TcArgs &g, int ncopy, int bn, cudaStream_t st);
 void launch_split_bf16(const float *src, __nv_bfloat16 *hi, __nv_bfloat16 *lo, size_t n,
                        cudaStream_t st);
 // 3D bf16 tensor map {K, rows, batch} with a {64, box_rows, 1} box and

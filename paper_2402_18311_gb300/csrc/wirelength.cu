@@ -403,14 +403,56 @@ int wa_prepare(int cap) {
   return e == cudaSuccess ? 0 : -1;
 }
 
+// Nets above 256 pins: one block per net, FP64 block reductions.
+__global__ void __launch_bounds__(kThreads) k_hpwl64_big(Dev d, int copy0, int e_begin, int e_end,
+                                                          int slot_base) {
+  __shared__ double sm[4][32];
+  const int c = copy0 + blockIdx.y;
+  const float2 *xy = d.xy + (size_t)c * d.n_cells;
+  double acc = 0.0;
+  for (int e = e_begin + blockIdx.x; e < e_end; e += gridDim.x) {
+    const int p0 = d.net_ptr[e], p1 = d.net_ptr[e + 1];
+    double v[4] = {-1e300, -1e300, -1e300, -1e300};  // max x, -min x, max y, -min y
+    for (int j = p0 + threadIdx.x; j < p1; j += kThreads) {
+      const float2 o = d.pin_off[j];
+      const float2 q = xy[d.pin_cell[j]];
+      const double px = (double)q.x + (double)o.x, py = (double)q.y + (double)o.y;
+      v[0] = fmax(v[0], px); v[1] = fmax(v[1], -px);
+      v[2] = fmax(v[2], py); v[3] = fmax(v[3], -py);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v[k] = fmax(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0)
+      for (int k = 0; k < 4; ++k) sm[k][threadIdx.x >> 5] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double r[4];
+      for (int k = 0; k < 4; ++k) {
+        r[k] = sm[k][0];
+        for (int w = 1; w < kThreads / 32; ++w) r[k] = fmax(r[k], sm[k][w]);
+      }
+      const double wn = d.net_w ? (double)d.net_w[e] : 1.0;
+      acc += wn * ((r[0] + r[1]) + (r[2] + r[3]));
+    }
+  }
+  if (threadIdx.x == 0)
+    d.part[((size_t)c * S_COUNT + S_HP64) * d.nb_red + slot_base + blockIdx.x] = acc;
+}
+
 int hpwl64_blocks(const Dev &d) { return 2 * d.cell_blocks; }
 
 void launch_hpwl64(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
-  // small nets: 4 lanes each; nets with more than 4 pins: a warp each
-  const int split = d.cls_begin[1];
-  dim3 grid(d.cell_blocks, ncopy);
+  // nets up to 4 pins: 4 lanes each; up to 256 pins: a warp each; longer: a block each
+  const int split = d.cls_begin[1], big = d.cls_begin[4];
+  const int half = d.cell_blocks / 2 > 0 ? d.cell_blocks / 2 : 1;
+  dim3 grid(d.cell_blocks, ncopy), grid2(half, ncopy);
   k_hpwl64<4><<<grid, kThreads, 0, st>>>(d, copy0, 0, split, 0);
-  k_hpwl64<32><<<grid, kThreads, 0, st>>>(d, copy0, split, d.n_nets, d.cell_blocks);
+  k_hpwl64<32><<<grid2, kThreads, 0, st>>>(d, copy0, split, big, d.cell_blocks);
+  k_hpwl64_big<<<grid2, kThreads, 0, st>>>(d, copy0, big, d.n_nets, d.cell_blocks + half);
 }
 
 }  // namespace hp
