@@ -110,6 +110,29 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def stage_traffic(stage, workload):
+    """DRAM bytes of one pass of `stage` from the committed ncu capture
+    (profiles/traffic_<workload>.txt), or None when there is none or the
+    stage's kernel source changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    total, found, sha_ok = 0, False, True
+    for line in open(path):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "sha" and f[1] == stage:
+            src = os.path.join(ROOT, "paper_2402_18311_gb300", "csrc", f[2])
+            cur = hashlib.sha1(open(src, "rb").read()).hexdigest() if os.path.exists(src) else ""
+            sha_ok = sha_ok and cur == f[3]
+        elif f[0] == stage and len(f) == 3:
+            total += int(f[2])
+            found = True
+    return total if (found and sha_ok) else None
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -252,8 +275,10 @@ def run_ours(args):
         achieved = alg[dn]["bytes"] / sec / 1e9
         peak_note = f"HBM copy bandwidth ({pk_kind})"
     roofline = {"kernel": dn, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_note,
-                "stages": per}
+                "frac": achieved / peak, "traffic": stage_traffic(dn, args.workload),
+                "algorithmic": alg[dn], "peak_source": peak_note, "stages": per,
+                "traffic_note": "DRAM bytes of one pass of the stage from the committed ncu "
+                                "capture (cold L2), null if the kernel source changed since"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(d, args)
