@@ -97,6 +97,16 @@ __device__ __forceinline__ bool arrive_last(unsigned int *ctr, int *sm_flag) {
   return last;
 }
 
+// floor(a / b) for b > 0 and |a| below 2^40: a float estimate of the
+// quotient, then one exact integer correction in each direction (the
+// estimate is off by at most one for these magnitudes).
+__device__ __forceinline__ long long floordiv_est(long long a, long long b, float inv_b) {
+  long long q = (long long)floorf((float)a * inv_b);
+  if (q * b > a) --q;
+  if ((q + 1) * b <= a) ++q;
+  return q;
+}
+
 // Quantised rectangle of a cell and the clipped bin range it touches.
 struct QRect {
   long long X, Y, W, H;
@@ -116,8 +126,18 @@ __device__ __forceinline__ QRect qrect(float x, float y, int W, int H, float sca
   r.Y = __float2ll_rn(ys);
   r.W = W;
   r.H = H;
-  long long a0 = floordiv_ll(r.X - XL, BW), a1 = floordiv_ll(r.X + r.W - 1 - XL, BW);
-  long long b0 = floordiv_ll(r.Y - YL, BH), b1 = floordiv_ll(r.Y + r.H - 1 - YL, BH);
+  // offsets far outside the die are clipped to one bin beyond it first, which
+  // leaves the clipped range unchanged and keeps the quotients small
+  const long long lox = -BW, hix = (long long)(nx + 1) * BW;
+  const long long loy = -BH, hiy = (long long)(ny + 1) * BH;
+  long long ax0 = r.X - XL, ax1 = r.X + r.W - 1 - XL, ay0 = r.Y - YL, ay1 = r.Y + r.H - 1 - YL;
+  ax0 = ax0 < lox ? lox : (ax0 > hix ? hix : ax0);
+  ax1 = ax1 < lox ? lox : (ax1 > hix ? hix : ax1);
+  ay0 = ay0 < loy ? loy : (ay0 > hiy ? hiy : ay0);
+  ay1 = ay1 < loy ? loy : (ay1 > hiy ? hiy : ay1);
+  const float ibw = 1.0f / (float)BW, ibh = 1.0f / (float)BH;
+  long long a0 = floordiv_est(ax0, BW, ibw), a1 = floordiv_est(ax1, BW, ibw);
+  long long b0 = floordiv_est(ay0, BH, ibh), b1 = floordiv_est(ay1, BH, ibh);
   // clip to the grid in 64 bits before narrowing; an empty range (lo > hi)
   // results for rectangles outside the die or non-finite coordinates
   a0 = a0 < 0 ? 0 : (a0 > nx ? nx : a0);
