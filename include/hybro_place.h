@@ -250,6 +250,73 @@ int place_overflow_noalloc(const float *x, const float *y, const float *w, const
                            const place_bins *bins, int32_t frac_bits, const int64_t *fixed_map,
                            double *overflow, int64_t *map_out, void *stream);
 
+/* Device memory place_create would take for this netlist, bins and
+ * parameters (an upper bound; no device work).  Used for admission control. */
+int place_estimate_device_bytes(const place_netlist *nl, const place_bins *bins,
+                                const place_params *params, int64_t *bytes);
+
+/* ---- job server: continuous batching of placement and restart jobs -------
+ * Algorithm 1 runs a placement, then perturbed re-placements ("restarts") of
+ * its result.  The server runs many such jobs of different designs on one GPU
+ * at once.  Jobs are admitted once they have arrived, their parent (for a
+ * restart) has finished, a slot is free and their device footprint
+ * (place_estimate_device_bytes) fits the budget; later jobs that fit may pass
+ * a head job that does not.  Each active job keeps its state on the device
+ * and runs on its own stream, iters_per_tick iterations per scheduling step,
+ * so the work of all active jobs overlaps on the GPU.  A finished job's
+ * handle stays resident while restarts depend on it; the last restart to be
+ * admitted adopts it.  Results are those of the same job run alone (the
+ * kernels are deterministic). */
+#define PLACE_JOB_PLACE 0   /* place from the netlist's x0/y0 until the stop test */
+#define PLACE_JOB_RESTART 1 /* perturb the parent's result (op, p, seed), re-place */
+
+typedef struct place_server place_server;
+
+typedef struct place_job {
+  int32_t kind;      /* PLACE_JOB_* */
+  int32_t op;        /* restart: PLACE_SHUFFLE_* */
+  float p;           /* restart: strength */
+  int32_t pad;
+  uint64_t seed;     /* restart: SplitMix64 seed */
+  int64_t parent;    /* restart: id of an earlier job of the same design */
+  double arrival_s;  /* not admitted before this many seconds into place_server_run */
+} place_job;
+
+typedef struct place_job_result {
+  int64_t id;
+  int32_t kind, iterations, converged, pad;
+  double arrival_s, admit_s, done_s; /* seconds since place_server_run started */
+  double hpwl, overflow;             /* exact FP64 HPWL (Eq. 1) and overflow at the end */
+  int64_t device_bytes;
+  uint64_t position_hash;            /* FNV-1a of the final x then y arrays */
+} place_job_result;
+
+/* hbm_budget: bytes of device memory the jobs may hold at once; max_active:
+ * concurrent jobs (1 = one job at a time, in arrival order). */
+int place_server_create(int64_t hbm_budget, int32_t max_active, int32_t iters_per_tick,
+                        place_server **out);
+
+/* Queue a job.  The netlist arrays are borrowed until the job has finished
+ * (the server does not copy them); params->n_copies is forced to 1.  *id
+ * receives the job id (submission order from 0).  PLACE_ENOMEM if the job
+ * alone exceeds the budget. */
+int place_server_submit(place_server *s, const place_netlist *nl, const place_die *die,
+                        const place_bins *bins, const place_params *params, const place_job *job,
+                        int64_t *id);
+
+/* Run until every queued job has finished (or timeout_s > 0 elapses:
+ * PLACE_ETIMEOUT).  *makespan_s (nullable) receives the wall time. */
+int place_server_run(place_server *s, double timeout_s, double *makespan_s);
+
+/* Results of the finished jobs in submission order; *n receives their count
+ * (out may be NULL to query it). */
+int place_server_results(place_server *s, place_job_result *out, int32_t cap, int32_t *n);
+
+/* Peak device bytes held by jobs and peak number of active jobs. */
+int place_server_stats(place_server *s, int64_t *peak_bytes, int32_t *peak_active);
+
+int place_server_destroy(place_server *s);
+
 const char *place_last_error(void);
 
 #ifdef __cplusplus

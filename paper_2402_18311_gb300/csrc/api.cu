@@ -118,13 +118,14 @@ void place_default_params(place_params *p) {
 
 int place_destroy(place_t *h) {
   if (!h) return PLACE_OK;
+  cudaStreamSynchronize(h->stream);  // no work of this handle may still run
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->cap2) cudaStreamDestroy(h->cap2);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
-  if (h->mem) cudaFree(h->mem);
+  if (h->mem) cudaFreeAsync(h->mem, h->stream);  // stream-ordered: no device-wide sync
   delete h;
   return PLACE_OK;
 }
@@ -524,10 +525,13 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   Arena a;
   layout(d, a, d.K);
   h->mem_bytes = a.off + 256;
-  cudaError_t e = cudaMalloc(&h->mem, h->mem_bytes);
+  // stream-ordered allocation: creating and destroying handles (as the
+  // job server does while other jobs run) never synchronises the device
+  cudaError_t e = cudaMallocAsync(&h->mem, h->mem_bytes, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // usable by the uploads below
   if (e != cudaSuccess) {
     delete h;
-    return fail(PLACE_ENOMEM, "cudaMalloc(%zu) failed: %s", (size_t)a.off, cudaGetErrorString(e));
+    return fail(PLACE_ENOMEM, "device allocation of %zu bytes failed: %s", (size_t)a.off, cudaGetErrorString(e));
   }
   a = Arena();
   a.base = (char *)h->mem;
@@ -912,3 +916,66 @@ int place_get_best_positions(place_t *h, int32_t copy, float *x, float *y) {
 }
 
 }  // extern "C"
+
+extern "C" int place_estimate_device_bytes(const place_netlist *nl, const place_bins *bins,
+                                           const place_params *params, int64_t *bytes) {
+  if (!nl || !bins || !bytes) return fail(PLACE_EINVAL, "null argument");
+  place_params prm;
+  if (params) prm = *params; else place_default_params(&prm);
+  if (nl->n_cells <= 0 || nl->n_pins < 0 || nl->n_nets < 0 || bins->nx <= 0 || bins->ny <= 0 ||
+      prm.n_copies < 1)
+    return fail(PLACE_EINVAL, "bad sizes");
+  // the layout of place_create with upper bounds for the sizes that depend on
+  // the netlist's contents (pins on movable cells, reduction slots)
+  Dev d{};
+  d.K = prm.n_copies;
+  d.n_cells = nl->n_cells; d.n_mov = nl->n_movable; d.n_nets = nl->n_nets; d.n_pins = nl->n_pins;
+  d.n_mov_pins = nl->n_pins;
+  d.nx = bins->nx; d.ny = bins->ny; d.G = bins->nx * bins->ny;
+  d.has_net_w = nl->net_w ? 1 : 0;
+  d.tc = prm.dct_mode == PLACE_DCT_BF16X3 ? 1 : 0;
+  const int cb = std::max(1, std::min((d.n_mov + kThreads - 1) / kThreads, kMaxCellBlocks));
+  const int bb = std::max(1, std::min((d.G + kThreads - 1) / kThreads, kMaxCellBlocks));
+  d.nb_red = std::max(std::max(2 * cb + 2, bb), 5 * kMaxCellBlocks);
+  int sn = 2;
+  while (sn < d.n_cells) sn <<= 1;
+  d.sort_n = sn;
+  Arena a;
+  layout(d, a, d.K);
+  *bytes = (int64_t)(a.off + 256);
+  return PLACE_OK;
+}
+
+namespace hp {
+
+// Launch n iterations on the handle's stream, then copy the copies' stopped
+// flags into host memory (pinned, [K]) and record `ev`; never blocks.
+int step_async(place_t *h, int n, int *stopped_host, cudaEvent_t ev) {
+  if (n > 0) {
+    int rc = ensure_graph(h);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(h->exec, h->stream));
+  }
+  for (int c = 0; c < h->d.K; ++c)
+    CK(cudaMemcpyAsync(stopped_host + c, &h->d.cs[c].stopped, sizeof(int), cudaMemcpyDeviceToHost,
+                       h->stream));
+  CK(cudaEventRecord(ev, h->stream));
+  return PLACE_OK;
+}
+
+// Positions of copy 0 of `src` into every copy of `dst` (same design),
+// device to device on dst's stream after src's work; resets dst's optimiser.
+int copy_positions(place_t *dst, place_t *src, cudaEvent_t src_done) {
+  if (dst->d.n_cells != src->d.n_cells) return fail(PLACE_EINVAL, "designs differ");
+  CK(cudaEventRecord(src_done, src->stream));
+  CK(cudaStreamWaitEvent(dst->stream, src_done, 0));
+  const size_t C = dst->d.n_cells;
+  for (int c = 0; c < dst->d.K; ++c)
+    CK(cudaMemcpyAsync(dst->d.xy + c * C, src->d.xy, sizeof(float2) * C, cudaMemcpyDeviceToDevice,
+                       dst->stream));
+  return enqueue_reset(dst, 0, dst->d.K);
+}
+
+cudaStream_t handle_stream(place_t *h) { return h->stream; }
+
+}  // namespace hp

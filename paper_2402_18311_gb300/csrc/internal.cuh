@@ -153,6 +153,11 @@ void launch_reduce_slot(const Dev &d, int slot, int nvals, int copy0, int ncopy,
 int launch_shuffle(const Dev &d, int copy, int op, float p, uint64_t seed, cudaStream_t st);
 void launch_shuffle_finish(const Dev &d, int copy, int kcount, cudaStream_t st);
 
+// hooks for the job server (api.cu)
+int step_async(place_t *h, int n, int *stopped_host, cudaEvent_t ev);
+int copy_positions(place_t *dst, place_t *src, cudaEvent_t src_done);
+cudaStream_t handle_stream(place_t *h);
+
 // gamma of the weighted-average model from the previous overflow (Eq. 3)
 __device__ __forceinline__ double gamma_of(const Dev &d, double tau_prev) {
   if (d.prm.constant_gamma > 0.f) return (double)d.prm.constant_gamma;

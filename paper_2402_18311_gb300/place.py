@@ -76,6 +76,22 @@ class place_state(ct.Structure):
                 ("hpwl_wa", ct.c_double)]
 
 
+class place_job(ct.Structure):
+    _fields_ = [("kind", ct.c_int32), ("op", ct.c_int32), ("p", ct.c_float), ("pad", ct.c_int32),
+                ("seed", ct.c_uint64), ("parent", ct.c_int64), ("arrival_s", ct.c_double)]
+
+
+class place_job_result(ct.Structure):
+    _fields_ = [("id", ct.c_int64), ("kind", ct.c_int32), ("iterations", ct.c_int32),
+                ("converged", ct.c_int32), ("pad", ct.c_int32), ("arrival_s", ct.c_double),
+                ("admit_s", ct.c_double), ("done_s", ct.c_double), ("hpwl", ct.c_double),
+                ("overflow", ct.c_double), ("device_bytes", ct.c_int64),
+                ("position_hash", ct.c_uint64)]
+
+
+PLACE_JOB_PLACE = 0
+PLACE_JOB_RESTART = 1
+
 _VP = ct.c_void_p
 _SIGS = {
     "place_default_params": (None, [ct.POINTER(place_params)]),
@@ -102,6 +118,16 @@ _SIGS = {
     "place_overflow_noalloc": (ct.c_int, [_VP, _VP, _VP, _VP, ct.c_int32, ct.c_double,
                                           ct.POINTER(place_die), ct.POINTER(place_bins),
                                           ct.c_int32, _VP, _VP, _VP, _VP]),
+    "place_estimate_device_bytes": (ct.c_int, [ct.POINTER(place_netlist), ct.POINTER(place_bins),
+                                                ct.POINTER(place_params), ct.POINTER(ct.c_int64)]),
+    "place_server_create": (ct.c_int, [ct.c_int64, ct.c_int32, ct.c_int32, ct.POINTER(_VP)]),
+    "place_server_submit": (ct.c_int, [_VP, ct.POINTER(place_netlist), ct.POINTER(place_die),
+                                       ct.POINTER(place_bins), ct.POINTER(place_params),
+                                       ct.POINTER(place_job), ct.POINTER(ct.c_int64)]),
+    "place_server_run": (ct.c_int, [_VP, ct.c_double, ct.POINTER(ct.c_double)]),
+    "place_server_results": (ct.c_int, [_VP, _VP, ct.c_int32, ct.POINTER(ct.c_int32)]),
+    "place_server_stats": (ct.c_int, [_VP, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int32)]),
+    "place_server_destroy": (ct.c_int, [_VP]),
     "place_last_error": (ct.c_char_p, []),
 }
 
@@ -159,8 +185,9 @@ def place_default_params(**overrides):
     return p
 
 
-def place_create(design, params=None, stream=None):
-    """Create a handle for a ``synth.Design`` (host arrays are copied)."""
+def _netlist(design):
+    """place_netlist of a ``synth.Design`` plus the arrays it points into
+    (which must stay alive while the netlist is in use)."""
     keep = dict(w=np.ascontiguousarray(design.w, np.float32),
                 h=np.ascontiguousarray(design.h, np.float32),
                 x0=np.ascontiguousarray(design.x, np.float32),
@@ -178,6 +205,12 @@ def place_create(design, params=None, stream=None):
                        *(_ptr(keep[k]) for k in ("w", "h", "x0", "y0", "net_ptr", "pin_cell",
                                                  "pin_dx", "pin_dy")),
                        _ptr(keep.get("net_w")), _ptr(keep.get("is_macro")))
+    return nl, keep
+
+
+def place_create(design, params=None, stream=None):
+    """Create a handle for a ``synth.Design`` (host arrays are copied)."""
+    nl, keep = _netlist(design)
     die = place_die(*design.die)
     bins = place_bins(design.nx, design.ny, design.target_density)
     prm = params if params is not None else place_default_params()
@@ -275,6 +308,61 @@ def place_overflow_noalloc(x, y, w, h, n_movable, mov_area, die, bins, frac_bits
                                                int(n_movable), float(mov_area), ct.byref(d),
                                                ct.byref(b), int(frac_bits), _ptr(fixed_map),
                                                _ptr(overflow), _ptr(map_out), _VP(stream or 0)))
+
+
+def place_estimate_device_bytes(design, params=None):
+    nl, keep = _netlist(design)
+    b = ct.c_int64()
+    bins = place_bins(design.nx, design.ny, design.target_density)
+    prm = params if params is not None else place_default_params()
+    _check(lib().place_estimate_device_bytes(ct.byref(nl), ct.byref(bins), ct.byref(prm), ct.byref(b)))
+    return b.value
+
+
+class Server:
+    """Job server (continuous batching).  Keeps every submitted design's host
+    arrays alive until the server is destroyed, as the C ABI requires."""
+
+    def __init__(self, hbm_budget, max_active, iters_per_tick=32):
+        self.h = _VP()
+        _check(lib().place_server_create(int(hbm_budget), int(max_active), int(iters_per_tick),
+                                         ct.byref(self.h)))
+        self._keep = []
+
+    def submit(self, design, params=None, kind=PLACE_JOB_PLACE, arrival_s=0.0, parent=-1,
+               op=PLACE_SHUFFLE_ALL, p=0.5, seed=0):
+        nl, keep = _netlist(design)
+        die = place_die(*design.die)
+        bins = place_bins(design.nx, design.ny, design.target_density)
+        prm = params if params is not None else place_default_params()
+        job = place_job(kind, op, p, 0, seed, parent, arrival_s)
+        jid = ct.c_int64()
+        _check(lib().place_server_submit(self.h, ct.byref(nl), ct.byref(die), ct.byref(bins),
+                                         ct.byref(prm), ct.byref(job), ct.byref(jid)))
+        self._keep.append((nl, keep, die, bins, prm))
+        return jid.value
+
+    def run(self, timeout_s=0.0):
+        m = ct.c_double()
+        _check(lib().place_server_run(self.h, float(timeout_s), ct.byref(m)))
+        return m.value
+
+    def results(self):
+        n = ct.c_int32()
+        _check(lib().place_server_results(self.h, None, 0, ct.byref(n)))
+        arr = (place_job_result * max(n.value, 1))()
+        _check(lib().place_server_results(self.h, ct.cast(arr, _VP), n.value, ct.byref(n)))
+        return [arr[i] for i in range(n.value)]
+
+    def stats(self):
+        b = ct.c_int64(); a = ct.c_int32()
+        _check(lib().place_server_stats(self.h, ct.byref(b), ct.byref(a)))
+        return b.value, a.value
+
+    def close(self):
+        if self.h:
+            lib().place_server_destroy(self.h)
+            self.h = None
 
 
 def place_last_error():

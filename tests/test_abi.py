@@ -51,6 +51,8 @@ def test_struct_sizes_match_header_layout():
     assert ct.sizeof(place.place_params) == 12 * 4
     assert ct.sizeof(place.place_state) == 4 * 4 + 6 * 8
     assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 2 * 4
+    assert ct.sizeof(place.place_job) == 4 * 4 + 8 + 8 + 8
+    assert ct.sizeof(place.place_job_result) == 8 + 4 * 4 + 5 * 8 + 8 + 8
 
 
 def _design():
@@ -87,3 +89,26 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.place_step(None, 1, None) == place.PLACE_EINVAL
     assert L.place_destroy(None) == place.PLACE_OK
     assert b"null" in L.place_last_error()
+
+
+def test_server_rejects_bad_arguments_on_host(L):
+    with pytest.raises(place.PlaceError):
+        place.Server(0, 1)
+    s = place.Server(1 << 30, 2)
+    try:
+        d = _design()
+        with pytest.raises(place.PlaceError) as ei:
+            s.submit(d, kind=place.PLACE_JOB_RESTART, parent=5)
+        assert ei.value.code == place.PLACE_EINVAL
+    finally:
+        s.close()
+
+
+def test_footprint_estimate_grows_with_the_design(L):
+    small = synth.scaled(2000, 128, seed=1)
+    big = synth.scaled(20000, 256, seed=1)
+    a = place.place_estimate_device_bytes(small)
+    b = place.place_estimate_device_bytes(big)
+    assert 0 < a < b
+    b4 = place.place_estimate_device_bytes(big, place.place_default_params(n_copies=4))
+    assert b < b4 < 4 * b  # the netlist and transform tables are shared by the copies

@@ -1,0 +1,98 @@
+"""Job server (continuous batching): every job's result is the same alone and
+in the mix, restarts start from their parent's converged result, and the
+device-memory budget bounds admission."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2402_18311_gb300 import place, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not os.path.exists(place.LIB_PATH):
+        from paper_2402_18311_gb300 import build
+        build.build()
+    place.lib()
+
+
+def designs():
+    return [synth.scaled(4000, 128, seed=11, name="a"), synth.scaled(9000, 128, seed=12, name="b"),
+            synth.scaled(6000, 128, seed=13, name="c")]
+
+
+def params():
+    return place.place_default_params(tau_stop=0.15, max_iters=1500,
+                                      dct_mode=place.PLACE_DCT_BF16X3)
+
+
+def run_trace(max_active, budget=8 << 30, arrivals=(0.0, 0.0, 0.05, 0.0, 0.0, 0.1, 0.0)):
+    ds = designs()
+    s = place.Server(budget, max_active, iters_per_tick=16)
+    try:
+        ids = [s.submit(ds[0], params(), arrival_s=arrivals[0]),
+               s.submit(ds[1], params(), arrival_s=arrivals[1]),
+               s.submit(ds[2], params(), arrival_s=arrivals[2])]
+        ids.append(s.submit(ds[0], params(), kind=place.PLACE_JOB_RESTART, parent=ids[0], seed=3,
+                            arrival_s=arrivals[3]))
+        ids.append(s.submit(ds[0], params(), kind=place.PLACE_JOB_RESTART, parent=ids[0], seed=4,
+                            arrival_s=arrivals[4]))
+        ids.append(s.submit(ds[1], params(), kind=place.PLACE_JOB_RESTART, parent=ids[1], seed=5,
+                            arrival_s=arrivals[5]))
+        ids.append(s.submit(ds[2], params(), kind=place.PLACE_JOB_RESTART, parent=ids[2], seed=6,
+                            arrival_s=arrivals[6]))
+        s.run(timeout_s=300)
+        res = {r.id: r for r in s.results()}
+        return res, s.stats()
+    finally:
+        s.close()
+
+
+def test_results_identical_alone_and_in_the_mix():
+    fifo, (peak_b1, peak_a1) = run_trace(1)
+    mix, (peak_b, peak_a) = run_trace(8)
+    assert peak_a1 == 1 and peak_a >= 2
+    assert sorted(fifo) == sorted(mix) == list(range(7))
+    for i in range(7):
+        a, b = fifo[i], mix[i]
+        assert a.hpwl == b.hpwl and a.overflow == b.overflow, i
+        assert a.position_hash == b.position_hash, i
+        assert a.iterations == b.iterations
+        assert b.admit_s >= b.arrival_s - 1e-9 and b.done_s > b.admit_s
+    # restarts begin after their parent finished
+    for child, parent in ((3, 0), (4, 0), (5, 1), (6, 2)):
+        assert mix[child].admit_s >= mix[parent].done_s - 1e-9
+        assert fifo[child].converged == 1 or fifo[child].iterations == 1500
+
+
+def test_placement_job_equals_plain_handle_run():
+    res, _ = run_trace(4)
+    d = designs()[1]
+    h = place.place_create(d, params())
+    try:
+        conv = np.zeros(1, np.int32)
+        while True:
+            place.place_step(h, 16, conv)
+            if conv[0]:
+                break
+        hp = np.empty(1); tv = np.empty(1)
+        place.place_eval_hpwl_overflow(h, hp, tv)
+        assert res[1].hpwl == hp[0] and res[1].overflow == tv[0]
+    finally:
+        place.place_destroy(h)
+
+
+def test_budget_bounds_admission():
+    ds = designs()
+    need = max(place.place_estimate_device_bytes(d, params()) for d in ds)
+    budget = 2 * need + need // 2  # room for two jobs at a time
+    res, (peak_bytes, peak_active) = run_trace(8, budget=budget)
+    assert len(res) == 7
+    assert peak_bytes <= budget
+    assert peak_active <= 2
