@@ -239,6 +239,9 @@ def run_ours(args):
     restarts = None
     if not args.no_restarts:
         restarts = run_restarts(args, place, torch)
+    serving = None
+    if args.serving_jobs > 0:
+        serving = run_serving(args, place, args.serving_jobs, 10_000, args.serving_max_cells)
 
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -309,6 +312,8 @@ def run_ours(args):
         out["cpu_baseline"] = cpu
     if restarts is not None:
         out["restarts"] = restarts
+    if serving is not None:
+        out["serving"] = serving
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -376,6 +381,70 @@ def run_restarts(args, place, torch, K=32, p=0.5):
             "start_hpwl": float(base_hp[0]), "start_overflow": float(base_tau[0])}
 
 
+def serving_trace(n_jobs, min_cells, max_cells, seed=0):
+    """Jobs of the serving workload: designs of log-uniform size, grid
+    clamp(2^round(log2 sqrt(C)), 128, 1024), target density U[0.7, 1.0];
+    half placement jobs and half restarts of an earlier placement job."""
+    import math
+    rng = np.random.default_rng(seed)
+    jobs, designs = [], []
+    for i in range(n_jobs):
+        if i > 0 and rng.random() < 0.5 and any(j[0] == "place" for j in jobs):
+            parents = [k for k, j in enumerate(jobs) if j[0] == "place"]
+            par = int(rng.choice(parents))
+            jobs.append(("restart", jobs[par][1], par, int(rng.integers(0, 2 ** 31))))
+        else:
+            c = int(round(math.exp(rng.uniform(math.log(min_cells), math.log(max_cells)))))
+            g = int(min(1024, max(128, 2 ** round(math.log2(math.sqrt(c))))))
+            t = float(rng.uniform(0.7, 1.0))
+            designs.append(synth.scaled(c, g, seed=int(rng.integers(0, 2 ** 31)),
+                                        target_density=t, name=f"job{i}"))
+            jobs.append(("place", len(designs) - 1, -1, 0))
+    return jobs, designs
+
+
+def run_serving(args, place, n_jobs, min_cells, max_cells, max_active=16):
+    """Continuous batching against one job at a time on the same Poisson
+    arrival trace (rate 0.8 x the measured one-at-a-time service rate)."""
+    jobs, designs = serving_trace(n_jobs, min_cells, max_cells)
+    prm = place.place_default_params(tau_stop=0.1, max_iters=2000, dct_mode=args.dct)
+    budget = 64 << 30
+
+    def run(slots, arrivals):
+        srv = place.Server(budget, slots, iters_per_tick=32)
+        try:
+            for (kind, di, par, seed), a in zip(jobs, arrivals):
+                if kind == "place":
+                    srv.submit(designs[di], prm, arrival_s=a)
+                else:
+                    srv.submit(designs[di], prm, kind=place.PLACE_JOB_RESTART, parent=par,
+                               seed=seed, arrival_s=a)
+            span = srv.run(timeout_s=600)
+            res = srv.results()
+            return span, res, srv.stats()
+        finally:
+            srv.close()
+
+    span0, _, _ = run(1, [0.0] * n_jobs)
+    rate = 0.8 * n_jobs / span0
+    gaps = np.random.default_rng(1).exponential(1.0 / rate, n_jobs)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    out = {"jobs": n_jobs, "cells": [min_cells, max_cells], "arrival_rate_per_s": rate,
+           "fifo_service_rate_per_s": n_jobs / span0, "tau_stop": 0.1}
+    for name, slots in (("fifo", 1), ("batched", max_active)):
+        span, res, (peak_b, peak_a) = run(slots, arrivals)
+        lat = np.array([r.done_s - r.arrival_s for r in res]) * 1e3
+        iters = sum(r.iterations for r in res)
+        out[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "mean_ms": float(lat.mean()), "makespan_s": span,
+                     "agg_iters_per_s": iters / span, "peak_active": peak_a,
+                     "peak_device_bytes": peak_b, "max_active": slots}
+        out.setdefault("_hash", {})[name] = [int(r.position_hash) for r in res]
+    h = out.pop("_hash")
+    out["results_identical"] = h["fifo"] == h["batched"]
+    return out
+
+
 def cpu_baseline(d, args, n_iters=1):
     """The FP64 oracle as it stands, on the same workload: n_iters full
     iterations after its set-up."""
@@ -431,6 +500,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-restarts", action="store_true",
                     help="skip the batched-vs-serial restarts measurement")
+    ap.add_argument("--serving-jobs", type=int, default=24,
+                    help="jobs in the serving trace (0: skip; 200 for the full workload)")
+    ap.add_argument("--serving-max-cells", type=int, default=200_000,
+                    help="largest design of the serving trace (1000000 for the full workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
