@@ -133,6 +133,17 @@ def stage_traffic(stage, workload):
     return total if (found and sha_ok) else None
 
 
+def aggregate_ranks(ms, steps, world, device="cpu"):
+    """Whole-job throughput of replicas: every rank ran `steps` iterations of
+    its own copy of the design; the job took the slowest rank's time."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * steps / (ms_max / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -243,11 +254,7 @@ def run_ours(args):
     if args.serving_jobs > 0:
         serving = run_serving(args, place, args.serving_jobs, 10_000, args.serving_max_cells)
 
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    ms_max, value = aggregate_ranks(ms, args.steps, world, device="cuda")
     e2e_v = world * n_e2e / e2e_s
 
     alg = algorithmic(d, info)
