@@ -12,10 +12,12 @@
 // polls the chunk's event.
 //
 // A restart job (Algorithm 1 line 4) perturbs the converged result of its
-// parent and re-optimises it.  The parent's handle stays resident while
-// restarts depend on it; the last restart to be admitted adopts it (no new
-// allocation, no netlist upload), earlier ones copy its positions device to
-// device into a handle of their own.
+// parent and re-optimises it.  When a job with pending restarts finishes, its
+// converged positions are saved in a device buffer and its handle stays
+// resident; the first restart admitted adopts the handle (no new allocation,
+// no netlist upload), later ones create a handle and start from the saved
+// positions.  Every job fits the budget alone, and the handles of active jobs
+// are freed when they finish, so admission always makes progress.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -64,6 +66,8 @@ struct Job {
   bool in_flight = false;
   int pending_children = 0;  // restart jobs that still need this job's result
   bool keep = false;         // handle kept resident for children
+  float2 *result_xy = nullptr;  // converged positions while restarts are pending
+  int64_t result_bytes = 0;
   double admit_s = 0, done_s = 0;
   place_job_result res{};
 };
@@ -97,6 +101,10 @@ Job *find(place_server *s, int64_t id) {
 }
 
 void release(place_server *s, Job *j) {
+  if (j->result_xy) {
+    cudaFreeAsync(j->result_xy, j->st);
+    j->result_xy = nullptr;
+  }
   if (j->h) {
     place_destroy(j->h);
     j->h = nullptr;
@@ -136,6 +144,13 @@ int finish(place_server *s, Job *j) {
   j->state = J_DONE;
   if (j->pending_children > 0) {
     j->keep = true;  // stays resident for its restarts
+    j->result_bytes = (int64_t)sizeof(float2) * j->nl.n_cells;
+    // 8 bytes per cell, outside the budget (so that a saved result can never
+    // keep a restart from fitting)
+    cudaError_t e = cudaMallocAsync(&j->result_xy, j->result_bytes, j->st);
+    if (e != cudaSuccess) return sfail(PLACE_ENOMEM, "result buffer: %s", cudaGetErrorString(e));
+    if ((rc = save_xy(j->h, j->result_xy))) return rc;
+    if (cudaStreamSynchronize(j->st) != cudaSuccess) return sfail(PLACE_ECUDA, "saving a result");
     if (j->ev) cudaEventDestroy(j->ev);
     j->ev = nullptr;
   } else {
@@ -144,13 +159,25 @@ int finish(place_server *s, Job *j) {
   return PLACE_OK;
 }
 
-// Admit a job: handle (new or adopted from the parent), stream, first chunk.
+// A restart no longer needs its parent's saved positions.
+void drop_child(place_server *s, Job *parent, cudaStream_t after) {
+  if (--parent->pending_children > 0) return;
+  if (parent->result_xy) {
+    cudaFreeAsync(parent->result_xy, after);  // after the child's copy
+    parent->result_xy = nullptr;
+  }
+  if (parent->keep) {
+    parent->keep = false;
+    release(s, parent);
+  }
+}
+
+// Admit a job: handle (new, or the parent's resident one), stream, first chunk.
 int admit(place_server *s, Job *j) {
   Job *parent = j->spec.kind == PLACE_JOB_RESTART ? find(s, j->spec.parent) : nullptr;
   cudaError_t e;
-  bool adopt = parent && parent->keep && parent->pending_children == 1 &&
-               parent->nl.n_cells == j->nl.n_cells;
-  if (adopt) {
+  int rc;
+  if (parent && parent->keep) {
     // take over the parent's resident handle and stream
     j->h = parent->h;
     j->st = parent->st;
@@ -162,37 +189,26 @@ int admit(place_server *s, Job *j) {
     parent->flags = nullptr;
     parent->ev_src = nullptr;
     parent->keep = false;
-    parent->pending_children = 0;
     e = cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return sfail(PLACE_ECUDA, "event: %s", cudaGetErrorString(e));
-    int rc = place_perturb(j->h, j->spec.op, j->spec.p, j->spec.seed, 0);
-    if (rc) return rc;
   } else {
     e = cudaStreamCreateWithFlags(&j->st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->ev_src, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost(&j->flags, sizeof(int));
     if (e != cudaSuccess) return sfail(PLACE_ECUDA, "job resources: %s", cudaGetErrorString(e));
-    int rc = place_create(&j->nl, &j->die, &j->bins, &j->prm, j->st, &j->h);
-    if (rc) return rc;
+    if ((rc = place_create(&j->nl, &j->die, &j->bins, &j->prm, j->st, &j->h))) return rc;
     s->used += j->footprint;
-    if (parent) {
-      if ((rc = copy_positions(j->h, parent->h, j->ev_src))) return rc;
-      if ((rc = place_perturb(j->h, j->spec.op, j->spec.p, j->spec.seed, 0))) return rc;
-      if (--parent->pending_children == 0 && parent->keep) {
-        parent->keep = false;
-        // the child's stream has queued the copy; wait for it before freeing
-        cudaStreamSynchronize(j->st);
-        release(s, parent);
-      }
-    }
+    if (parent && (rc = load_xy(j->h, parent->result_xy))) return rc;
   }
-  if (adopt) parent = nullptr;
+  if (parent) {
+    if ((rc = place_perturb(j->h, j->spec.op, j->spec.p, j->spec.seed, 0))) return rc;
+    drop_child(s, parent, j->st);
+  }
   j->admit_s = now_s(s);
   j->state = J_ACTIVE;
   s->peak_used = std::max(s->peak_used, s->used);
-  int rc = step_async(j->h, s->iters_per_tick, j->flags, j->ev);
-  if (rc) return rc;
+  if ((rc = step_async(j->h, s->iters_per_tick, j->flags, j->ev))) return rc;
   j->in_flight = true;
   return PLACE_OK;
 }
@@ -289,8 +305,7 @@ int place_server_run(place_server *s, double timeout_s, double *makespan_s) {
       if (j->spec.kind == PLACE_JOB_RESTART) {
         Job *p = find(s, j->spec.parent);
         if (!p || p->state != J_DONE) continue;
-        const bool adopts = p->keep && p->pending_children == 1;
-        if (!adopts && s->used + j->footprint > s->budget) continue;
+        if (!p->keep && s->used + j->footprint > s->budget) continue;  // adopting needs no memory
       } else if (s->used + j->footprint > s->budget) {
         continue;
       }

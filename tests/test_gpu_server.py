@@ -91,8 +91,17 @@ def test_placement_job_equals_plain_handle_run():
 def test_budget_bounds_admission():
     ds = designs()
     need = max(place.place_estimate_device_bytes(d, params()) for d in ds)
-    budget = 2 * need + need // 2  # room for two jobs at a time
+    free, _ = run_trace(8)
+    # room for one handle at a time: jobs run one after another, restarts adopt
+    # their parent's resident handle, and nothing deadlocks
+    budget = need + need // 5
     res, (peak_bytes, peak_active) = run_trace(8, budget=budget)
     assert len(res) == 7
     assert peak_bytes <= budget
-    assert peak_active <= 2
+    assert peak_active == 1
+    for i in range(7):
+        assert res[i].position_hash == free[i].position_hash
+    # two handles at a time
+    budget2 = 2 * need + need // 5
+    res2, (peak_bytes2, peak_active2) = run_trace(8, budget=budget2)
+    assert len(res2) == 7 and peak_bytes2 <= budget2 and 1 <= peak_active2 <= 2
