@@ -113,8 +113,10 @@ __global__ void __launch_bounds__(kThreads) k_cell_grad(Dev d, int copy0, int ev
         dy -= a * ey[b];
       }
     }
-    d.gwx[cm + i] = sx; d.gwy[cm + i] = sy;
-    d.gdx[cm + i] = dx; d.gdy[cm + i] = dy;
+    if (!full) {  // raw gradients are read only by k = 0 (lambda_0) and evaluations
+      d.gwx[cm + i] = sx; d.gwy[cm + i] = sy;
+      d.gdx[cm + i] = dx; d.gdy[cm + i] = dy;
+    }
     n1 += fabsf(sx) + fabsf(sy);
     d1 += fabsf(dx) + fabsf(dy);
     if (full) {

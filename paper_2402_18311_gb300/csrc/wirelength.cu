@@ -11,6 +11,11 @@
 // m+ / m-, so FP32 keeps the digits that matter even where the cells of a
 // net sit close together far from the origin.
 //
+// Exponentials use the fast intrinsic __expf.  Its documented error grows
+// with |argument| (2 + floor(|1.16 x|) ulp); every argument here is <= 0 after
+// the max/min shift, and the terms with large |x| are the ones that vanish in
+// the sums, so the WA value and gradient stay well inside their tolerance.
+//
 // Nets are grouped by degree at create: one thread per net up to 4 pins
 // (pins in registers), groups of 4 lanes up to 16 pins, 16 lanes up to 64, a
 // warp up to 256, and a block of 512 threads beyond, which keeps the net's
@@ -103,15 +108,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       if (k < deg) {
-        ax[k] = expf((px[k] - mxx) * ig); bx[k] = expf((mnx - px[k]) * ig);
-        ay[k] = expf((py[k] - mxy) * ig); by[k] = expf((mny - py[k]) * ig);
+        ax[k] = __expf((px[k] - mxx) * ig); bx[k] = __expf((mnx - px[k]) * ig);
+        ay[k] = __expf((py[k] - mxy) * ig); by[k] = __expf((mny - py[k]) * ig);
         sxp += ax[k]; txp += (px[k] - mxx) * ax[k]; sxm += bx[k]; txm += (px[k] - mnx) * bx[k];
         syp += ay[k]; typ += (py[k] - mxy) * ay[k]; sym += by[k]; tym += (py[k] - mny) * by[k];
       }
     }
     const float wn = d.net_w ? d.net_w[e] : 1.0f;
-    const float rxp = txp / sxp, rxm = txm / sxm, ryp = typ / syp, rym = tym / sym;
     const float isxp = 1.f / sxp, isxm = 1.f / sxm, isyp = 1.f / syp, isym = 1.f / sym;
+    const float rxp = txp * isxp, rxm = txm * isxm, ryp = typ * isyp, rym = tym * isym;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       if (k < deg) {
@@ -190,25 +195,25 @@ __global__ void __launch_bounds__(kThreads) k_wa_group(Dev d, int copy0, int cls
     float syp = 0.f, typ = 0.f, sym = 0.f, tym = 0.f;
     float a0x = 0.f, b0x = 0.f, a0y = 0.f, b0y = 0.f;
     if (has0) {
-      a0x = expf((px0 - mxx) * ig); b0x = expf((mnx - px0) * ig);
+      a0x = __expf((px0 - mxx) * ig); b0x = __expf((mnx - px0) * ig);
       sxp += a0x; txp += (px0 - mxx) * a0x; sxm += b0x; txm += (px0 - mnx) * b0x;
-      a0y = expf((py0 - mxy) * ig); b0y = expf((mny - py0) * ig);
+      a0y = __expf((py0 - mxy) * ig); b0y = __expf((mny - py0) * ig);
       syp += a0y; typ += (py0 - mxy) * a0y; sym += b0y; tym += (py0 - mny) * b0y;
     }
     for (int j = j0 + G; j < p1; j += G) {
       const float2 o = d.pin_off[j];
       const float2 v = xy[d.pin_cell[j]];
       float px = (v.x - rx) + (o.x - rdx), py = (v.y - ry) + (o.y - rdy);
-      float a = expf((px - mxx) * ig), b = expf((mnx - px) * ig);
+      float a = __expf((px - mxx) * ig), b = __expf((mnx - px) * ig);
       sxp += a; txp += (px - mxx) * a; sxm += b; txm += (px - mnx) * b;
-      a = expf((py - mxy) * ig); b = expf((mny - py) * ig);
+      a = __expf((py - mxy) * ig); b = __expf((mny - py) * ig);
       syp += a; typ += (py - mxy) * a; sym += b; tym += (py - mny) * b;
     }
     sxp = gsum<G>(sxp); txp = gsum<G>(txp); sxm = gsum<G>(sxm); txm = gsum<G>(txm);
     syp = gsum<G>(syp); typ = gsum<G>(typ); sym = gsum<G>(sym); tym = gsum<G>(tym);
     if (p1 > p0) {
-      const float rxp = txp / sxp, rxm = txm / sxm, ryp = typ / syp, rym = tym / sym;
       const float isxp = 1.f / sxp, isxm = 1.f / sxm, isyp = 1.f / syp, isym = 1.f / sym;
+      const float rxp = txp * isxp, rxm = txm * isxm, ryp = typ * isyp, rym = tym * isym;
       if (has0) {
         float gx = a0x * isxp * (1.f + (px0 - mxx - rxp) * ig) - b0x * isxm * (1.f - (px0 - mnx - rxm) * ig);
         float gy = a0y * isyp * (1.f + (py0 - mxy - ryp) * ig) - b0y * isym * (1.f - (py0 - mny - rym) * ig);
@@ -218,9 +223,9 @@ __global__ void __launch_bounds__(kThreads) k_wa_group(Dev d, int copy0, int cls
         const float2 o = d.pin_off[j];
         const float2 v = xy[d.pin_cell[j]];
         float px = (v.x - rx) + (o.x - rdx), py = (v.y - ry) + (o.y - rdy);
-        float a = expf((px - mxx) * ig), b = expf((mnx - px) * ig);
+        float a = __expf((px - mxx) * ig), b = __expf((mnx - px) * ig);
         float gx = a * isxp * (1.f + (px - mxx - rxp) * ig) - b * isxm * (1.f - (px - mnx - rxm) * ig);
-        a = expf((py - mxy) * ig); b = expf((mny - py) * ig);
+        a = __expf((py - mxy) * ig); b = __expf((mny - py) * ig);
         float gy = a * isyp * (1.f + (py - mxy - ryp) * ig) - b * isym * (1.f - (py - mny - rym) * ig);
         pg[j] = make_float2(gx * wn, gy * wn);
       }
@@ -299,9 +304,9 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
         const float2 v = xy[d.pin_cell[j]];
         px = (v.x - rx) + (o.x - rdx); py = (v.y - ry) + (o.y - rdy);
       }
-      float a = expf((px - mxx) * ig), b = expf((mnx - px) * ig);
+      float a = __expf((px - mxx) * ig), b = __expf((mnx - px) * ig);
       s[0] += a; s[1] += (px - mxx) * a; s[2] += b; s[3] += (px - mnx) * b;
-      a = expf((py - mxy) * ig); b = expf((mny - py) * ig);
+      a = __expf((py - mxy) * ig); b = __expf((mny - py) * ig);
       s[4] += a; s[5] += (py - mxy) * a; s[6] += b; s[7] += (py - mny) * b;
     }
 #pragma unroll
@@ -316,9 +321,9 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
         const float2 v = xy[d.pin_cell[j]];
         px = (v.x - rx) + (o.x - rdx); py = (v.y - ry) + (o.y - rdy);
       }
-      float a = expf((px - mxx) * ig), b = expf((mnx - px) * ig);
+      float a = __expf((px - mxx) * ig), b = __expf((mnx - px) * ig);
       const float gx = a / s[0] * (1.f + (px - mxx - rxp) * ig) - b / s[2] * (1.f - (px - mnx - rxm) * ig);
-      a = expf((py - mxy) * ig); b = expf((mny - py) * ig);
+      a = __expf((py - mxy) * ig); b = __expf((mny - py) * ig);
       const float gy = a / s[4] * (1.f + (py - mxy - ryp) * ig) - b / s[6] * (1.f - (py - mny - rym) * ig);
       pg[j] = make_float2(gx * wn, gy * wn);
     }
