@@ -75,7 +75,8 @@ typedef struct place_netlist {
 typedef struct place_die { double xl, yl, xh, yh; } place_die;
 
 /* nx x ny density bins and the target density t of the overflow test
- * (D(s) <= epsilon in Eq. 1). */
+ * (D(s) <= epsilon in Eq. 1).  nx and ny are multiples of 16 up to 8192; the
+ * tensor-core spectral path needs multiples of 128. */
 typedef struct place_bins { int32_t nx, ny; float target_density; } place_bins;
 
 /* Optimiser constants.  The paper cites, but does not restate, the
@@ -291,8 +292,10 @@ typedef struct place_job_result {
   uint64_t position_hash;            /* FNV-1a of the final x then y arrays */
 } place_job_result;
 
-/* hbm_budget: bytes of device memory the jobs may hold at once; max_active:
- * concurrent jobs (1 = one job at a time, in arrival order). */
+/* hbm_budget: bytes of device memory the jobs' handles may hold at once (a
+ * finished job's saved positions, 8 bytes per cell while restarts of it are
+ * pending, are not counted); max_active: concurrent jobs (1 = one job at a
+ * time, in arrival order). */
 int place_server_create(int64_t hbm_budget, int32_t max_active, int32_t iters_per_tick,
                         place_server **out);
 

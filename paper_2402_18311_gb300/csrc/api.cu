@@ -175,6 +175,7 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.scal = a.take<double>(K * S_COUNT);
   d.tau_part = a.take<unsigned long long>(K * 2 * (size_t)d.nb_red);
   d.ctr = a.take<unsigned int>(K * C_COUNT);
+  d.conc_part = a.take<float>(K * (size_t)d.nb_red);
   d.Cn = a.take<float>((size_t)d.ny * d.ny);
   d.CTn = a.take<float>((size_t)d.ny * d.ny);
   d.STn = a.take<float>((size_t)d.ny * d.ny);
@@ -977,5 +978,21 @@ int copy_positions(place_t *dst, place_t *src, cudaEvent_t src_done) {
 }
 
 cudaStream_t handle_stream(place_t *h) { return h->stream; }
+
+// Copy 0's positions into a device buffer (stream-ordered on h's stream).
+int save_xy(place_t *h, float2 *dst) {
+  CK(cudaMemcpyAsync(dst, h->d.xy, sizeof(float2) * h->d.n_cells, cudaMemcpyDeviceToDevice,
+                     h->stream));
+  return PLACE_OK;
+}
+
+// Every copy of h takes the positions in `src` (device); resets the optimiser.
+int load_xy(place_t *h, const float2 *src) {
+  const size_t C = h->d.n_cells;
+  for (int c = 0; c < h->d.K; ++c)
+    CK(cudaMemcpyAsync(h->d.xy + c * C, src, sizeof(float2) * C, cudaMemcpyDeviceToDevice,
+                       h->stream));
+  return enqueue_reset(h, 0, h->d.K);
+}
 
 }  // namespace hp

@@ -33,6 +33,8 @@ struct CopyState {
   int parity;        // selects the current / previous gradient buffer
   int err;
   int pad[3];
+  double n_eff;      // effective number of occupied bins of the last density
+                     // pass, (sum M)^2 / sum M^2; 0 before the first pass
 };
 
 // Reduction slots (FP64) per copy: each kernel that reduces writes one value
@@ -97,6 +99,7 @@ struct Dev {
   double *scal;              // [K][S_COUNT] reduced values (eval reductions)
   unsigned long long *tau_part;  // [K][nb_red][2] exact 128-bit overflow partials
   unsigned int *ctr;         // [K][C_COUNT] last-block counters
+  float *conc_part;          // [K][nb_red] per-block sums of (M / A_bin)^2
 
   // spectral tables
   float *Cn, *Cm, *CTn, *STn, *STm, *CTm;  // transform matrices
@@ -157,6 +160,8 @@ void launch_shuffle_finish(const Dev &d, int copy, int kcount, cudaStream_t st);
 int step_async(place_t *h, int n, int *stopped_host, cudaEvent_t ev);
 int copy_positions(place_t *dst, place_t *src, cudaEvent_t src_done);
 cudaStream_t handle_stream(place_t *h);
+int save_xy(place_t *h, float2 *dst);
+int load_xy(place_t *h, const float2 *src);
 
 // gamma of the weighted-average model from the previous overflow (Eq. 3)
 __device__ __forceinline__ double gamma_of(const Dev &d, double tau_prev) {
