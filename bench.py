@@ -3,7 +3,8 @@
 One step = one Nesterov iteration of Eq. 2 over the whole hot path: density
 scatter and overflow, the spectral Poisson solve, WA wirelength and
 gradients (Eq. 3), per-cell gradient assembly, preconditioned
-Nesterov/Lipschitz update, all copies of the design (Algorithm 1 line 3).
+Nesterov/Lipschitz update, all copies of the design (the global-placement
+step of Algorithm 1).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload large_2m|medium_210k|tiny_1k]
@@ -155,21 +156,20 @@ def algorithmic(d, info):
     """Algorithmic bytes / flops of one iteration per stage (one copy)."""
     C, P, E, G = d.n_movable, d.n_pins, d.n_nets, d.nx * d.ny
     n_all = d.n_cells
-    mov_pins = int(np.sum(d.pin_cell < d.n_movable))
     return {
         # scatter: x, y, W, H per cell (16 B), map clear + atomics 8 B/bin written,
         # finish: map + fixed map read 16 B/bin, rho written 4 B/bin
         "density": {"bytes": 16 * C + 8 * G + 16 * G + 4 * G},
         # six M^3-type GEMMs (two per 2D transform: forward, Ex, Ey)
         "spectral": {"flops": 2.0 * (2 * d.ny * d.ny * d.nx + 2 * d.nx * d.nx * d.ny) * 1.5},
-        # pin_cell 4 + offsets 8 + gradient write 8 per pin, net_ptr 4 per net,
-        # positions 8 per cell (gathered once)
-        "wirelength": {"bytes": 20 * P + 4 * E + 8 * n_all},
-        # pin sums: cell->pin index 4 + pin gradient 8 per movable pin, CSR 4 per
-        # cell; gather: position 8, sizes 8, field 8, pins/area 8, previous
-        # gradient 8, previous position 8; writes: four raw gradients 16 and the
-        # gradient 8 per cell
-        "cellgrad": {"bytes": 12 * mov_pins + 76 * C},
+        # pin_cell 4 + offsets 8 per pin, net_ptr 4 per net, positions 8 per
+        # cell (gathered once), the packed gradient sum 8 per movable cell
+        # (accumulated in L2 by 64-bit reductions, written once)
+        "wirelength": {"bytes": 12 * P + 4 * E + 8 * n_all + 8 * C},
+        # per cell: gradient sum read 8 + cleared 8, position 8, sizes 8,
+        # field 8, pins/area 8, previous gradient 8, previous position 8,
+        # gradient written 8 (the raw gradients are written only at k = 0)
+        "cellgrad": {"bytes": 72 * C},
         # read v, u, g 24, npins/area 8, gwl, gd 16, v_prev 8, g_prev 8; write u, v, v_prev, g 32
         "update": {"bytes": 96 * C},
     }

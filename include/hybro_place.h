@@ -121,6 +121,11 @@ typedef struct place_state {
   double lambda, gamma, alpha, a;
   double overflow;     /* tau at the current reference point */
   double hpwl_wa;      /* HPWL measured in the last iteration's WA pass */
+  double bins_effective; /* (sum M)^2 / sum M^2 over the movable-area map of the
+                          * last density pass: the effective number of occupied
+                          * bins (0 before the first pass).  Below 32 the
+                          * density scatter merges the lanes of a warp that hit
+                          * the same bin; the map is the same either way. */
 } place_state;
 
 void place_default_params(place_params *p);
@@ -128,8 +133,13 @@ void place_default_params(place_params *p);
 /* Create a handle: validates and copies the netlist (host pointers), chooses
  * the fixed-point resolution F, builds the device state for K copies (all
  * starting at x0/y0) and resets their optimisers.  Section 3 (problem
- * statement), Algorithm 1 line 1.  *out receives the handle; on failure it is
- * set to NULL and nothing is leaked. */
+ * statement), the initial placement of Algorithm 1.  *out receives the
+ * handle; on failure it is set to NULL and nothing is leaked.
+ * PLACE_ERANGE: the die, a cell or the total area does not fit the 64-bit
+ * density fixed point, or a movable cell carries so many pins that its
+ * wirelength-gradient sum (accumulated as 32-bit fixed point with a scale
+ * 2^Fg, Fg >= 10, from the bound 3 + 2 ln(degree) per pin and unit net
+ * weight) would not fit. */
 int place_create(const place_netlist *nl, const place_die *die, const place_bins *bins,
                  const place_params *params, void *stream, place_t **out);
 
@@ -138,15 +148,15 @@ int place_destroy(place_t *h);
 
 int place_get_info(const place_t *h, place_info *out);
 
-/* Run up to n_iters Nesterov iterations of Eq. 2 on every active copy
- * (Algorithm 1 line 3).  A copy stops updating once converged or at
- * max_iters; the others continue.  converged (nullable, host [K]) receives
+/* Run up to n_iters Nesterov iterations of Eq. 2 on every active copy (the
+ * global-placement step of Algorithm 1).  A copy stops updating once
+ * converged or at max_iters; the others continue.  converged (nullable, host [K]) receives
  * the stopped flags, which synchronises the stream; with NULL the call is
  * asynchronous. */
 int place_step(place_t *h, int32_t n_iters, int32_t *converged);
 
-/* Perturb (Algorithm 1 line 4; Section 4.2): Shuffle or Shuffle (all) with
- * strength p in [0, 1] applied to copy `copy` (-1: every copy, copy c using
+/* Perturb (the perturbation step of Algorithm 1; Section 4.2): Shuffle or
+ * Shuffle (all) with strength p in [0, 1] applied to copy `copy` (-1: every copy, copy c using
  * seed + c), followed by a full optimiser reset of the perturbed copies.
  * Selection draws SplitMix64 keys from `seed`. */
 int place_perturb(place_t *h, int32_t op, float p, uint64_t seed, int32_t copy);
@@ -210,8 +220,8 @@ int place_get_best_positions(place_t *h, int32_t copy, float *x, float *y);
  * [PLACE_N_STAGES]).  Synchronises.  Stages: */
 #define PLACE_STAGE_DENSITY 0  /* clear map, scatter, overflow/rho, stop test */
 #define PLACE_STAGE_SPECTRAL 1 /* the four transform GEMMs of the Poisson solve */
-#define PLACE_STAGE_WIRELENGTH 2 /* WA value and per-pin gradients (Eq. 3) */
-#define PLACE_STAGE_CELLGRAD 3 /* pin-gradient sums and field gather per cell */
+#define PLACE_STAGE_WIRELENGTH 2 /* WA value and gradients summed per cell (Eq. 3) */
+#define PLACE_STAGE_CELLGRAD 3 /* per-cell gradient, field gather, preconditioning */
 #define PLACE_STAGE_UPDATE 4   /* preconditioner, step size, Nesterov update */
 #define PLACE_N_STAGES 5
 int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms);

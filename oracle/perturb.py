@@ -3,8 +3,9 @@ SplitMix64 as the random source.
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-The paper: "randomly select p% of all the macros [all the cells] and shuffle
-their locations", p = 50%.  It does not fix the count rounding, what a
+Section 4.2: Shuffle picks a fraction p of the macros at random (Shuffle
+(all): of all the cells) and permutes their locations among themselves;
+the experiments use p = 50%.  It does not fix the count rounding, what a
 location is for cells of different sizes, or the random source.  Reading:
 
 * Candidates: movable macros (Shuffle) or all movable cells (Shuffle (all)).

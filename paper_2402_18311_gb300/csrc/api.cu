@@ -141,8 +141,6 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.net_w = d.has_net_w ? a.take<float>(std::max(d.n_nets, 1)) : nullptr;
   d.pin_cell = a.take<int>(P);
   d.pin_off = a.take<float2>(P);
-  d.cell_pin_ptr = a.take<int>(Mv + 1);
-  d.cell_pins = a.take<int>(std::max<size_t>(d.n_mov_pins, 1));
   d.w = a.take<float>(C);
   d.h = a.take<float>(C);
   d.Wq = a.take<int>(C);
@@ -163,7 +161,7 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.gwy = a.take<float>(K * Mv);
   d.gdx = a.take<float>(K * Mv);
   d.gdy = a.take<float>(K * Mv);
-  d.pin_grad = a.take<float2>(K * std::max<size_t>(P, 1));
+  d.gacc = a.take<unsigned long long>(K * std::max<size_t>(Mv, 1));
   d.M = a.take<unsigned long long>(K * G);
   d.Fmap = a.take<long long>(G);
   d.rho = a.take<float>(K * G);
@@ -230,9 +228,7 @@ int setup_tc(place_t *h) {
   const int nx = d.nx, ny = d.ny, K = d.K;
   // tile width per stage: 128; 64 only for grids so small that 128-wide
   // tiles would occupy under a quarter of the SMs
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  if (sms <= 0) sms = 152;
+  const int sms = d.sms;
   const int tiles128[4] = {(nx / 128) * (ny / 128) * K, (ny / 128) * (nx / 128) * K,
                            (nx / 128) * (ny / 128) * 2 * K, (ny / 128) * (nx / 128) * 2 * K};
   for (int s = 0; s < 4; ++s) d.tc_bn[s] = tiles128[s] * 4 <= sms ? 64 : 128;
@@ -430,6 +426,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   d.abin_q = (double)d.BW * (double)d.BH;
   d.die_xl = die->xl; d.die_yl = die->yl; d.die_xh = die->xh; d.die_yh = die->yh;
   d.fxl = (float)die->xl; d.fyl = (float)die->yl; d.fxh = (float)die->xh; d.fyh = (float)die->yh;
+  d.fbw = (float)bw; d.fbh = (float)bh; d.fibw = (float)(1.0 / bw); d.fibh = (float)(1.0 / bh);
   d.w_bin = std::sqrt(bw * bh);
   d.dref = (double)prm.hpwl_ref * (double)E * d.w_bin;
   d.prm = prm;
@@ -478,24 +475,41 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     net_ptr[ne + 1] = q;
     if (nl->net_w) net_w[ne] = nl->net_w[e];
   }
-  // movable cell -> pins (library pin ids), counting sort by cell
-  std::vector<int> cpp(Mv + 1, 0);
-  for (int j = 0; j < P; ++j)
-    if (pin_cell[j] < Mv) cpp[pin_cell[j] + 1]++;
-  for (int i = 0; i < Mv; ++i) cpp[i + 1] += cpp[i];
-  d.n_mov_pins = cpp[Mv];
-  std::vector<int> cpins(std::max(d.n_mov_pins, 1));
-  {
-    std::vector<int> fill(cpp.begin(), cpp.end() - 1);
-    for (int j = 0; j < P; ++j)
-      if (pin_cell[j] < Mv) cpins[fill[pin_cell[j]]++] = j;
+  // pins per movable cell, and the fixed-point scale 2^Fg of the packed WA
+  // gradient sums.  One pin's gradient on a net of n pins is the difference
+  // of two softmax-weighted terms w_j (1 - t_j + r), with t_j >= 0 and
+  // r = sum w t = H(w) - ln S <= ln n (S >= 1, entropy H <= ln n), so
+  // |gradient| <= 2 (1 + 1/e + ln n) < 3 + 2 ln n per unit net weight.
+  // Fg keeps every cell's sum of those bounds below 0.9 * 2^31.
+  std::vector<int> cell_npins(std::max(Mv, 1), 0);
+  std::vector<double> gbound(std::max(Mv, 1), 0.0);
+  for (int e = 0; e < E; ++e) {
+    const int deg = net_ptr[e + 1] - net_ptr[e];
+    const double b = (3.0 + 2.0 * std::log((double)std::max(deg, 1))) *
+                     (nl->net_w ? std::fabs((double)net_w[e]) : 1.0);
+    for (int j = net_ptr[e]; j < net_ptr[e + 1]; ++j)
+      if (pin_cell[j] < Mv) {
+        cell_npins[pin_cell[j]]++;
+        gbound[pin_cell[j]] += b;
+      }
   }
+  double gmax = 0.0;
+  for (int i = 0; i < Mv; ++i) gmax = std::max(gmax, gbound[i]);
+  int Fg = 24;
+  while (Fg > 0 && gmax * std::ldexp(1.0, Fg) >= 0.9 * 2147483648.0) --Fg;
+  if (Fg < 10) {
+    delete h;
+    return fail(PLACE_ERANGE, "a movable cell carries too many pins (gradient bound %.3g) for "
+                "the 32-bit fixed-point wirelength-gradient sums", gmax);
+  }
+  d.gq = (float)std::ldexp(1.0, Fg);
+  d.giq = (float)std::ldexp(1.0, -Fg);
   int max_deg = 0;
   for (int e = 0; e < E; ++e) max_deg = std::max(max_deg, net_ptr[e + 1] - net_ptr[e]);
   d.wa_big_cap = std::min(std::max(max_deg, 1), kBigCapMax);
   std::vector<float> npins(std::max(Mv, 1)), area(std::max(Mv, 1));
   for (int i = 0; i < Mv; ++i) {
-    npins[i] = (float)(cpp[i + 1] - cpp[i]);
+    npins[i] = (float)cell_npins[i];
     area[i] = nl->w[i] * nl->h[i];
   }
   std::vector<unsigned char> macro(C, 0);
@@ -518,6 +532,14 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     d.wa_blocks_total += nb;
   }
   d.nb_red = std::max(std::max(2 * d.cell_blocks + 2, d.bin_blocks), std::max(d.wa_blocks_total, 1));
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || d.sms <= 0)
+      d.sms = 152;
+    // the cell-gradient kernel runs as one resident wave (grid-stride)
+    d.cg_blocks = std::max(1, std::min(d.cell_blocks, d.sms * cell_grad_blocks_per_sm()));
+  }
   int sn = 2;
   while (sn < C) sn <<= 1;
   d.sort_n = sn;
@@ -547,8 +569,6 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   up(d.net_ptr, net_ptr.data(), sizeof(int) * (E + 1));
   up(d.pin_cell, pin_cell.data(), sizeof(int) * P);
   up(d.pin_off, pin_off.data(), sizeof(float2) * P);
-  up(d.cell_pin_ptr, cpp.data(), sizeof(int) * (Mv + 1));
-  up(d.cell_pins, cpins.data(), sizeof(int) * cpins.size());
   up(d.w, nl->w, sizeof(float) * C);
   up(d.h, nl->h, sizeof(float) * C);
   up(d.Wq, Wq.data(), sizeof(int) * C);
@@ -593,7 +613,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   ce = cudaMemsetAsync(d.E, 0, sizeof(float) * (size_t)d.K * 3 * d.G, h->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.Fmap, 0, sizeof(long long) * d.G, h->stream);
   if (ce == cudaSuccess)
-    ce = cudaMemsetAsync(d.pin_grad, 0, sizeof(float2) * (size_t)d.K * std::max(P, 1), h->stream);
+    ce = cudaMemsetAsync(d.gacc, 0, sizeof(unsigned long long) * (size_t)d.K * std::max(Mv, 1), h->stream);
   if (ce == cudaSuccess && wa_prepare(d.wa_big_cap)) ce = cudaErrorInvalidValue;
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.cs, 0, sizeof(CopyState) * d.K, h->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.ctr, 0, sizeof(unsigned int) * d.K * C_COUNT, h->stream);
@@ -706,7 +726,7 @@ int place_get_state(place_t *h, int32_t copy, place_state *o) {
   if ((rc = check_dev_err(h))) return rc;
   o->iter = cs.k; o->converged = cs.converged; o->stopped = cs.stopped; o->pad = 0;
   o->lambda = cs.lam; o->gamma = cs.gamma; o->alpha = cs.alpha; o->a = cs.a;
-  o->overflow = cs.tau; o->hpwl_wa = cs.hpwl;
+  o->overflow = cs.tau; o->hpwl_wa = cs.hpwl; o->bins_effective = cs.n_eff;
   return PLACE_OK;
 }
 
@@ -737,6 +757,8 @@ int place_eval_wirelength(place_t *h, int32_t copy, float gamma, double *wl, flo
   Dev &d = h->d;
   float *gdev = reinterpret_cast<float *>(d.scal + (size_t)copy * S_COUNT + S_G2);
   CK(cudaMemcpyAsync(gdev, &gamma, sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  // the sums of a stopped copy's last WA pass may not have been consumed
+  CK(cudaMemsetAsync(d.gacc + (size_t)copy * d.n_mov, 0, sizeof(unsigned long long) * d.n_mov, h->stream));
   launch_wa(d, copy, 1, 1, gdev, h->stream);
   launch_cell_grad(d, copy, 1, 1, h->stream);
   launch_reduce_slot(d, S_WL, d.wa_blocks_total, copy, 1, h->stream);
@@ -931,7 +953,6 @@ extern "C" int place_estimate_device_bytes(const place_netlist *nl, const place_
   Dev d{};
   d.K = prm.n_copies;
   d.n_cells = nl->n_cells; d.n_mov = nl->n_movable; d.n_nets = nl->n_nets; d.n_pins = nl->n_pins;
-  d.n_mov_pins = nl->n_pins;
   d.nx = bins->nx; d.ny = bins->ny; d.G = bins->nx * bins->ny;
   d.has_net_w = nl->net_w ? 1 : 0;
   d.tc = prm.dct_mode == PLACE_DCT_BF16X3 ? 1 : 0;

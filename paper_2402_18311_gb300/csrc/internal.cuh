@@ -49,8 +49,9 @@ enum FinishMode { FIN_ITER = 0, FIN_EVAL = 1, FIN_RESET = 2 };
 
 struct Dev {
   // sizes
-  int K, n_cells, n_mov, n_nets, n_pins, n_mov_pins, nx, ny, G;
+  int K, n_cells, n_mov, n_nets, n_pins, nx, ny, G;
   int F;
+  float gq, giq;              // 2^Fg, 2^-Fg: fixed-point scale of the WA gradient sums
   long long XL, YL, BW, BH;   // fixed point
   float scale;                // 2^F
   float inv_area_q;           // 2^-2F as float
@@ -61,9 +62,12 @@ struct Dev {
   double mov_area_q;
   double die_xl, die_yl, die_xh, die_yh;
   float fxl, fyl, fxh, fyh;
+  float fbw, fbh, fibw, fibh;  // bin width/height and their inverses (FP32)
   double w_bin, dref;
   int nb_red;                 // partial slots per reduction per copy
   int cell_blocks;            // blocks per copy for per-cell kernels
+  int cg_blocks;              // blocks per copy of the cell-gradient kernel (one wave)
+  int sms;                    // SMs of the device
   int bin_blocks;             // blocks per copy for per-bin kernels
   place_params prm;
 
@@ -73,8 +77,6 @@ struct Dev {
   float2 *pin_off;   // [n_pins]
   float *net_w;      // [n_nets] or nullptr
   int has_net_w;
-  int *cell_pin_ptr; // [n_mov+1]
-  int *cell_pins;    // [n_mov_pins] pin ids of each movable cell
   float *w, *h;      // [n_cells]
   int *Wq, *Hq;      // [n_cells] quantised sizes
   float *npins;      // [n_mov] pin count per movable cell
@@ -87,7 +89,8 @@ struct Dev {
   float *vpx, *vpy;          // [K][n_mov]
   float *gx[2], *gy[2];      // [K][n_mov] preconditioned gradient, by parity
   float *gwx, *gwy, *gdx, *gdy;  // [K][n_mov] raw gradients
-  float2 *pin_grad;          // [K][n_pins] per-pin WA gradients (pin order)
+  unsigned long long *gacc;  // [K][n_mov] WA gradient sums, two int32 fixed-point
+                             // values packed as y * 2^32 + x (see add_pin_grad)
   unsigned long long *M;     // [K][G]
   long long *Fmap;           // [G]
   float *rho;                // [K][G]
@@ -135,6 +138,25 @@ struct Dev {
   int wa_big_cap;             // pins of a > 256-pin net kept in shared memory
 };
 
+// WA gradient sums per movable cell.  Each pin adds its (gx, gy), rounded to
+// the fixed-point grid 2^-Fg, to its cell as the one 64-bit integer
+// qy * 2^32 + qx.  Integer addition is exact and independent of order, so the
+// sums are deterministic.  The create-time choice of Fg bounds every cell's
+// |sum qx| and |sum qy| below 2^31; then the 64-bit total S equals
+// (sum qy) 2^32 + sum qx exactly, its low 32 bits read as a signed integer
+// are sum qx, and (S - sum qx) / 2^32 is sum qy.
+__device__ __forceinline__ void add_pin_grad(const Dev &d, unsigned long long *acc, int cell,
+                                             float gx, float gy) {
+  if (cell >= d.n_mov) return;  // fixed cells take no gradient
+  const long long qx = __float2int_rn(gx * d.gq), qy = __float2int_rn(gy * d.gq);
+  atomicAdd(acc + cell, (unsigned long long)(qy * 4294967296LL + qx));
+}
+__device__ __forceinline__ float2 unpack_grad(const Dev &d, unsigned long long s) {
+  const long long lo = (long long)(int)(unsigned int)(s & 0xffffffffull);
+  const long long hi = ((long long)s - lo) / 4294967296LL;
+  return make_float2((float)lo * d.giq, (float)hi * d.giq);
+}
+
 // ---- launchers (all enqueue on `st`) ------------------------------------
 // eval != 0 ignores the stopped flag of the copy (stage-level evaluation).
 void launch_scatter(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
@@ -148,6 +170,7 @@ void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_
                cudaStream_t st);
 void launch_hpwl64(const Dev &d, int copy0, int ncopy, cudaStream_t st);
 int wa_prepare(int cap);
+int cell_grad_blocks_per_sm();
 void launch_cell_grad(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
 void launch_precond0(const Dev &d, int copy0, int ncopy, cudaStream_t st);
 void launch_update(const Dev &d, int copy0, int ncopy, cudaStream_t st);

@@ -1,6 +1,7 @@
 // Per-cell gradient assembly, preconditioning, the Nesterov/Lipschitz update
 // and the per-copy scalar schedule (Eq. 2 minimised by Nesterov's method, as
-// in the ePlace/DREAMPlace placers the paper runs in Algorithm 1 line 3).
+// in the ePlace/DREAMPlace placers that the paper runs as the
+// global-placement step of Algorithm 1).
 //
 // Iteration k at reference point v_k (this library's reading; the paper
 // cites the method without restating it):
@@ -60,11 +61,11 @@ __device__ void advance_scalars(const Dev &d, CopyState *cs, bool first, double 
   cs->gamma = gamma_of(d, cs->tau);
 }
 
-// Gradient of the wirelength (sum of the cell's pin gradients, fixed order)
-// and of the density (field gather -sum_b a_ib E_b) for every movable cell.
+// Gradient of the wirelength (the cell's packed fixed-point pin-gradient sum,
+// read and cleared for the next pass) and of the density (field gather -sum_b a_ib E_b) for every movable cell.
 // For k >= 1 (lambda known) the preconditioned gradient and the step-size
 // norms are formed here too, and the last block advances the scalars.
-__global__ void __launch_bounds__(kThreads) k_cell_grad(Dev d, int copy0, int eval) {
+__global__ void __launch_bounds__(kThreads, 6) k_cell_grad(Dev d, int copy0, int eval) {
   __shared__ float smf[32];
   __shared__ double smd[32];
   __shared__ int flag;
@@ -77,40 +78,43 @@ __global__ void __launch_bounds__(kThreads) k_cell_grad(Dev d, int copy0, int ev
   const int par = cs->parity;
   const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
   const float2 *xy = d.xy + cn;
-  const float2 *pg = d.pin_grad + (size_t)c * d.n_pins;
+  unsigned long long *ga = d.gacc + cm;
   const float *ex = d.E + (size_t)c * 3 * d.G, *ey = ex + d.G;
   float n1 = 0.f, d1 = 0.f, dg2 = 0.f, dv2 = 0.f;
+  const float *gxo = d.gx[par ^ 1] + cm, *gyo = d.gy[par ^ 1] + cm;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
-    float sx = 0.f, sy = 0.f;
-    const int q0 = d.cell_pin_ptr[i], q1 = d.cell_pin_ptr[i + 1];
-    // four pins at a time: the index loads, then the gathers, all in flight
-    for (int q = q0; q < q1; q += 4) {
-      int j[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) j[u] = (q + u < q1) ? d.cell_pins[q + u] : -1;
-      float2 g[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) g[u] = j[u] >= 0 ? pg[j[u]] : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        sx += g[u].x;
-        sy += g[u].y;
-      }
-    }
+    // every load that does not depend on the position first, so they overlap
+    const unsigned long long gs = ga[i];
     const float2 vi = xy[i];
+    const float wi = d.w[i], hi = d.h[i];
+    float np = 0.f, ar = 0.f, gxp = 0.f, gyp = 0.f, vpx = 0.f, vpy = 0.f;
+    if (full) {
+      np = d.npins[i]; ar = d.area[i];
+      gxp = gxo[i]; gyp = gyo[i];
+      vpx = d.vpx[cm + i]; vpy = d.vpy[cm + i];
+    }
+    ga[i] = 0ull;
+    const float2 sw = unpack_grad(d, gs);
+    const float sx = sw.x, sy = sw.y;
+    // density gradient: -sum_b |cell ∩ b| E_b over the bins the cell covers,
+    // in FP32 with coordinates relative to the first bin's corner (exact
+    // subtractions, so each overlap keeps FP32 relative precision)
     const float xi = vi.x, yi = vi.y;
-    QRect r = qrect(xi, yi, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW, d.BH, d.nx, d.ny);
+    const int ix0 = min(max((int)floorf((xi - d.fxl) * d.fibw), 0), d.nx - 1);
+    const int iy0 = min(max((int)floorf((yi - d.fyl) * d.fibh), 0), d.ny - 1);
+    const float rx = xi - (d.fxl + (float)ix0 * d.fbw), ry = yi - (d.fyl + (float)iy0 * d.fbh);
+    const float rx1 = rx + wi, ry1 = ry + hi;
     float dx = 0.f, dy = 0.f;
-    for (int ix = r.ix0; ix <= r.ix1; ++ix) {
-      long long ox = overlap1(r.X, r.W, d.XL + (long long)ix * d.BW, d.BW);
-      if (ox == 0) continue;
-      for (int iy = r.iy0; iy <= r.iy1; ++iy) {
-        long long oy = overlap1(r.Y, r.H, d.YL + (long long)iy * d.BH, d.BH);
-        if (oy == 0) continue;
-        float a = (float)(ox * oy) * d.inv_area_q;
-        size_t b = (size_t)ix * d.ny + iy;
-        dx -= a * ex[b];
-        dy -= a * ey[b];
+    for (int kx = 0, ix = ix0; ix < d.nx && (float)kx * d.fbw < rx1; ++kx, ++ix) {
+      const float ox = fminf(rx1, (float)(kx + 1) * d.fbw) - fmaxf(rx, (float)kx * d.fbw);
+      if (!(ox > 0.f)) continue;
+      const float *exr = ex + (size_t)ix * d.ny, *eyr = ey + (size_t)ix * d.ny;
+      for (int ky = 0, iy = iy0; iy < d.ny && (float)ky * d.fbh < ry1; ++ky, ++iy) {
+        const float oy = fminf(ry1, (float)(ky + 1) * d.fbh) - fmaxf(ry, (float)ky * d.fbh);
+        if (!(oy > 0.f)) continue;
+        const float a = ox * oy;
+        dx = fmaf(-a, exr[iy], dx);
+        dy = fmaf(-a, eyr[iy], dy);
       }
     }
     if (!full) {  // raw gradients are read only by k = 0 (lambda_0) and evaluations
@@ -120,13 +124,13 @@ __global__ void __launch_bounds__(kThreads) k_cell_grad(Dev d, int copy0, int ev
     n1 += fabsf(sx) + fabsf(sy);
     d1 += fabsf(dx) + fabsf(dy);
     if (full) {
-      float P = fmaxf(1.f, d.npins[i] + lam * d.area[i]);
-      float gx = (sx + lam * dx) / P, gy = (sy + lam * dy) / P;
+      const float rP = 1.f / fmaxf(1.f, np + lam * ar);
+      const float gx = (sx + lam * dx) * rP, gy = (sy + lam * dy) * rP;
       d.gx[par][cm + i] = gx;
       d.gy[par][cm + i] = gy;
-      float ax = gx - d.gx[par ^ 1][cm + i], ay = gy - d.gy[par ^ 1][cm + i];
+      const float ax = gx - gxp, ay = gy - gyp;
       dg2 += ax * ax + ay * ay;
-      float bx = xi - d.vpx[cm + i], by = yi - d.vpy[cm + i];
+      const float bx = xi - vpx, by = yi - vpy;
       dv2 += bx * bx + by * by;
     }
   }
@@ -235,6 +239,7 @@ __global__ void __launch_bounds__(kThreads) k_reset(Dev d, int copy0) {
     float vy = fmaxf(d.fyl, fminf(v.y, d.fyh - d.h[i]));
     d.xy[cn + i] = make_float2(vx, vy);
     d.ux[cm + i] = vx; d.uy[cm + i] = vy;
+    d.gacc[cm + i] = 0ull;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     CopyState s = {};
@@ -278,7 +283,13 @@ void launch_unpack_xy(float *x, float *y, const float2 *src, int n, cudaStream_t
 }
 
 void launch_cell_grad(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st) {
-  k_cell_grad<<<dim3(d.cell_blocks, ncopy), kThreads, 0, st>>>(d, copy0, eval);
+  k_cell_grad<<<dim3(d.cg_blocks, ncopy), kThreads, 0, st>>>(d, copy0, eval);
+}
+int cell_grad_blocks_per_sm() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cell_grad, kThreads, 0) != cudaSuccess || n < 1)
+    n = 1;
+  return n;
 }
 void launch_precond0(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
   k_precond0<<<dim3(d.cell_blocks, ncopy), kThreads, 0, st>>>(d, copy0);

@@ -1,6 +1,7 @@
-// Shuffle and Shuffle (all) perturbations (Algorithm 1 line 4; Section 4.2:
-// "randomly select p% of all the macros [cells] and shuffle their
-// locations").  Reading used by this library:
+// Shuffle and Shuffle (all) perturbations (the perturbation step of
+// Algorithm 1; Section 4.2: a random fraction p of the macros, or of all the
+// cells, exchange their locations among themselves).  Reading used by this
+// library:
 //   - every cell i draws r_i, the (i+1)-th output of SplitMix64 started from
 //     `seed` (Steele, Lea and Flood, OOPSLA 2014), evaluated directly from
 //     its counter: state = seed + (i+1) * 0x9E3779B97F4A7C15, then the mix;

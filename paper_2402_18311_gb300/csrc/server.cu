@@ -11,7 +11,7 @@
 // chunk of iterations per job, copies the stopped flags to pinned memory, and
 // polls the chunk's event.
 //
-// A restart job (Algorithm 1 line 4) perturbs the converged result of its
+// A restart job (the perturbation step of Algorithm 1) perturbs the converged result of its
 // parent and re-optimises it.  When a job with pending restarts finishes, its
 // converged positions are saved in a device buffer and its handle stays
 // resident; the first restart admitted adopts the handle (no new allocation,

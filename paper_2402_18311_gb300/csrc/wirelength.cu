@@ -20,10 +20,10 @@
 // (pins in registers), groups of 4 lanes up to 16 pins, 16 lanes up to 64, a
 // warp up to 256, and a block of 512 threads beyond, which keeps the net's
 // coordinates in shared memory between its three passes.  Positions are
-// interleaved (x, y), so every pin costs one gather.  Per-pin gradients are
-// written in pin order (coalesced); the cell-gradient kernel sums each
-// cell's pins in a fixed order: no floating-point atomics, deterministic
-// results.
+// interleaved (x, y), so every pin costs one gather.  Each pin's gradient is
+// added to its cell as a packed fixed-point integer (add_pin_grad): one
+// 64-bit reduction per pin into an array that stays in L2, no floating-point
+// atomics, deterministic results.
 #include <cfloat>
 
 #include "common.cuh"
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int
   const float g = copy_gamma(d, c, gamma_ovr);
   const float ig = 1.0f / g;
   const float2 *xy = d.xy + (size_t)c * d.n_cells;
-  float2 *pg = d.pin_grad + (size_t)c * d.n_pins;
+  unsigned long long *ga = d.gacc + (size_t)c * d.n_mov;
   const int e_end = d.cls_begin[cls + 1];
   float hp_acc = 0.f, wl_acc = 0.f;
   for (int e = d.cls_begin[cls] + blockIdx.x * blockDim.x + threadIdx.x; e < e_end;
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int
                          bx[k] * isxm * (1.f - (px[k] - mnx - rxm) * ig);
         const float gy = ay[k] * isyp * (1.f + (py[k] - mxy - ryp) * ig) -
                          by[k] * isym * (1.f - (py[k] - mny - rym) * ig);
-        pg[p0 + k] = make_float2(gx * wn, gy * wn);
+        add_pin_grad(d, ga, cell[k], gx * wn, gy * wn);
       }
     }
     hp_acc += wn * ((mxx - mnx) + (mxy - mny));
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) k_wa_group(Dev d, int copy0, int cls
   const float g = copy_gamma(d, c, gamma_ovr);
   const float ig = 1.0f / g;
   const float2 *xy = d.xy + (size_t)c * d.n_cells;
-  float2 *pg = d.pin_grad + (size_t)c * d.n_pins;
+  unsigned long long *ga = d.gacc + (size_t)c * d.n_mov;
   constexpr int NPB = kThreads / G;
   const int lane = threadIdx.x % G;
   const int e_end = d.cls_begin[cls + 1];
@@ -174,9 +174,11 @@ __global__ void __launch_bounds__(kThreads) k_wa_group(Dev d, int copy0, int cls
     const int j0 = p0 + lane;
     const bool has0 = j0 < p1;
     float px0 = 0.f, py0 = 0.f;
+    int cell0 = 0;
     if (has0) {
       const float2 o = d.pin_off[j0];
-      const float2 v = xy[d.pin_cell[j0]];
+      cell0 = d.pin_cell[j0];
+      const float2 v = xy[cell0];
       px0 = (v.x - rx) + (o.x - rdx);
       py0 = (v.y - ry) + (o.y - rdy);
     }
@@ -217,17 +219,18 @@ __global__ void __launch_bounds__(kThreads) k_wa_group(Dev d, int copy0, int cls
       if (has0) {
         float gx = a0x * isxp * (1.f + (px0 - mxx - rxp) * ig) - b0x * isxm * (1.f - (px0 - mnx - rxm) * ig);
         float gy = a0y * isyp * (1.f + (py0 - mxy - ryp) * ig) - b0y * isym * (1.f - (py0 - mny - rym) * ig);
-        pg[j0] = make_float2(gx * wn, gy * wn);
+        add_pin_grad(d, ga, cell0, gx * wn, gy * wn);
       }
       for (int j = j0 + G; j < p1; j += G) {
         const float2 o = d.pin_off[j];
-        const float2 v = xy[d.pin_cell[j]];
+        const int cj = d.pin_cell[j];
+        const float2 v = xy[cj];
         float px = (v.x - rx) + (o.x - rdx), py = (v.y - ry) + (o.y - rdy);
         float a = __expf((px - mxx) * ig), b = __expf((mnx - px) * ig);
         float gx = a * isxp * (1.f + (px - mxx - rxp) * ig) - b * isxm * (1.f - (px - mnx - rxm) * ig);
         a = __expf((py - mxy) * ig); b = __expf((mny - py) * ig);
         float gy = a * isyp * (1.f + (py - mxy - ryp) * ig) - b * isym * (1.f - (py - mny - rym) * ig);
-        pg[j] = make_float2(gx * wn, gy * wn);
+        add_pin_grad(d, ga, cj, gx * wn, gy * wn);
       }
       if (lane == 0) {
         hp_acc += wn * ((mxx - mnx) + (mxy - mny));
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
   const float g = copy_gamma(d, c, gamma_ovr);
   const float ig = 1.0f / g;
   const float2 *xy = d.xy + (size_t)c * d.n_cells;
-  float2 *pg = d.pin_grad + (size_t)c * d.n_pins;
+  unsigned long long *ga = d.gacc + (size_t)c * d.n_mov;
   float hp_acc = 0.f, wl_acc = 0.f;
   for (int e = d.cls_begin[cls] + blockIdx.x; e < d.cls_begin[cls + 1]; e += gridDim.x) {
     const int p0 = d.net_ptr[e], p1 = d.net_ptr[e + 1];
@@ -314,18 +317,19 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
     const float rxp = s[1] / s[0], rxm = s[3] / s[2], ryp = s[5] / s[4], rym = s[7] / s[6];
     for (int j = p0 + threadIdx.x; j < p1; j += kBigNet) {
       float px, py;
+      const int cj = d.pin_cell[j];
       if (cached) {
         px = spx[j - p0]; py = spy[j - p0];
       } else {
         const float2 o = d.pin_off[j];
-        const float2 v = xy[d.pin_cell[j]];
+        const float2 v = xy[cj];
         px = (v.x - rx) + (o.x - rdx); py = (v.y - ry) + (o.y - rdy);
       }
       float a = __expf((px - mxx) * ig), b = __expf((mnx - px) * ig);
       const float gx = a / s[0] * (1.f + (px - mxx - rxp) * ig) - b / s[2] * (1.f - (px - mnx - rxm) * ig);
       a = __expf((py - mxy) * ig); b = __expf((mny - py) * ig);
       const float gy = a / s[4] * (1.f + (py - mxy - ryp) * ig) - b / s[6] * (1.f - (py - mny - rym) * ig);
-      pg[j] = make_float2(gx * wn, gy * wn);
+      add_pin_grad(d, ga, cj, gx * wn, gy * wn);
     }
     hp_acc += wn * ((mxx - mnx) + (mxy - mny));
     wl_acc += wn * (((mxx - mnx) + (rxp - rxm)) + ((mxy - mny) + (ryp - rym)));

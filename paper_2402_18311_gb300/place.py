@@ -73,7 +73,7 @@ class place_state(ct.Structure):
     _fields_ = [("iter", ct.c_int32), ("converged", ct.c_int32), ("stopped", ct.c_int32),
                 ("pad", ct.c_int32), ("lambda_", ct.c_double), ("gamma", ct.c_double),
                 ("alpha", ct.c_double), ("a", ct.c_double), ("overflow", ct.c_double),
-                ("hpwl_wa", ct.c_double)]
+                ("hpwl_wa", ct.c_double), ("bins_effective", ct.c_double)]
 
 
 class place_job(ct.Structure):

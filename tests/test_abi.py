@@ -49,10 +49,43 @@ def test_default_params_match_the_oracle_reading(L):
 def test_struct_sizes_match_header_layout():
     assert ct.sizeof(place.place_netlist) == 4 * 4 + 10 * 8
     assert ct.sizeof(place.place_params) == 12 * 4
-    assert ct.sizeof(place.place_state) == 4 * 4 + 6 * 8
+    assert ct.sizeof(place.place_state) == 4 * 4 + 7 * 8
     assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 2 * 4
     assert ct.sizeof(place.place_job) == 4 * 4 + 8 + 8 + 8
     assert ct.sizeof(place.place_job_result) == 8 + 4 * 4 + 5 * 8 + 8 + 8
+
+
+def test_struct_layouts_match_the_compiled_header(tmp_path):
+    # every ctypes struct of the binding against a C compile of the header:
+    # same field names, offsets and total size
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [getattr(place, n) for n in dir(place)
+               if n.startswith("place_") and isinstance(getattr(place, n), type)
+               and issubclass(getattr(place, n), ct.Structure)]
+    assert len(structs) >= 8
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hybro_place.h"',
+             "int main(void) {"]
+    expect = []
+    for S in structs:
+        t = S.__name__
+        lines.append(f'  printf("%zu\\n", sizeof({t}));')
+        expect.append(ct.sizeof(S))
+        for f, _ in S._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({t}, {f.rstrip("_")}));')
+            expect.append(getattr(S, f).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got == expect
 
 
 def _design():
@@ -74,6 +107,18 @@ def test_create_rejects_malformed_input_on_host(L, mut, msg):
         place.place_create(d)
     assert ei.value.code == place.PLACE_EINVAL
     assert msg in str(ei.value)
+
+
+def test_create_rejects_a_cell_beyond_the_gradient_fixed_point(L):
+    # one net weighted so heavily that its pins' wirelength-gradient bound
+    # leaves fewer than 10 fraction bits in the 32-bit per-cell sums
+    d = _design()
+    d.net_w = np.ones(d.n_nets, np.float32)
+    d.net_w[d.n_nets // 2] = 1e7
+    with pytest.raises(place.PlaceError) as ei:
+        place.place_create(d)
+    assert ei.value.code == place.PLACE_ERANGE
+    assert "too many pins" in str(ei.value)
 
 
 def test_create_rejects_bad_params(L):

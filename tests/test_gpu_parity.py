@@ -276,6 +276,43 @@ def test_stages_scaled_20k_with_big_nets():
         h.close()
 
 
+def test_density_map_bit_exact_on_both_scatter_paths():
+    # The scatter merges the lanes of a warp that hit the same bin while the
+    # effective number of occupied bins of the previous pass, (sum M)^2 /
+    # sum M^2, is below 32 and adds straight to the map otherwise; both must
+    # give the oracle's map.
+    d = synth.scaled(20000, 128, seed=2)
+    h = Handle(d, tau_stop=-1.0, max_iters=5000)
+
+    def n_eff_of(M):
+        Mf = M.astype(np.float64)
+        return Mf.sum() ** 2 / (Mf ** 2).sum()
+
+    try:
+        seen, trace = set(), []
+        for it in range(12):
+            x, y = h.pos()
+            g, M, Fm, amov = oracle_maps(d, h.info, x, y)
+            s = place.place_get_state(h.h, 0)  # from the last density pass
+            if it == 0:  # that pass was the reset pass at these positions
+                assert s.bins_effective == pytest.approx(n_eff_of(M), rel=1e-3)
+            gm = np.empty(d.nx * d.ny, np.int64)
+            place.place_eval_density(h.h, 0, gm)
+            np.testing.assert_array_equal(gm.reshape(d.nx, d.ny), M)
+            seen.add(bool(s.bins_effective >= 32))
+            trace.append(round(s.bins_effective, 1))
+            if seen == {False, True}:
+                break
+            place.place_step(h.h, 100)
+        assert seen == {False, True}, trace
+        # the statistic at a spread placement (a reset runs one pass there)
+        place.place_set_positions(h.h, 0, x, y)
+        s = place.place_get_state(h.h, 0)
+        assert s.bins_effective == pytest.approx(n_eff_of(M), rel=1e-3)
+    finally:
+        h.close()
+
+
 def test_edge_cases_small_design():
     # empty and single-pin nets, one-cell design, cells at the die corners
     d = synth.make_design(n_movable=3, die=(0, 0, 32, 32), nx=16, ny=16, n_nets=4,
@@ -321,21 +358,25 @@ def test_tensor_core_spectral_path_scaled():
 
 
 def test_tensor_core_matches_fp32_path_trajectory():
-    # the two spectral paths drive the same 200-iteration trajectory to HPWL
-    # and overflow within 1e-3 (the BF16x3 field differs by ~1e-5 L2)
+    # The two spectral paths drive the same 100-iteration trajectory: HPWL
+    # within 2e-5 and overflow within 1e-5 (measured: 7e-7 and 1.4e-7; the
+    # BF16x3 field differs by ~1e-5 L2).  Later iterations amplify any
+    # difference: by iteration 200 moving every start x by one FP32 ulp changes
+    # the FP32 path's own HPWL by 1.6e-3, as much as switching paths does, so a
+    # later comparison would measure that sensitivity rather than precision.
     d = synth.scaled(20000, 128, seed=3)
     out = []
     for mode in (place.PLACE_DCT_FP32, place.PLACE_DCT_BF16X3):
         h = Handle(d, tau_stop=-1.0, max_iters=1000, dct_mode=mode)
         try:
-            place.place_step(h.h, 200)
+            place.place_step(h.h, 100)
             hp = np.empty(1); tv = np.empty(1)
             place.place_eval_hpwl_overflow(h.h, hp, tv)
             out.append((hp[0], tv[0]))
         finally:
             h.close()
-    assert out[1][0] == pytest.approx(out[0][0], rel=1e-3)
-    assert out[1][1] == pytest.approx(out[0][1], abs=1e-3)
+    assert out[1][0] == pytest.approx(out[0][0], rel=2e-5)
+    assert out[1][1] == pytest.approx(out[0][1], abs=1e-5)
 
 
 @pytest.mark.slow
