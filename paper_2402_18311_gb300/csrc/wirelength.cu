@@ -16,9 +16,10 @@
 // the max/min shift, and the terms with large |x| are the ones that vanish in
 // the sums, so the WA value and gradient stay well inside their tolerance.
 //
-// Nets are grouped by degree at create: one thread per net up to 4 pins
-// (pins in registers), groups of 4 lanes up to 16 pins, 16 lanes up to 64, a
-// warp up to 256, and a block of 512 threads beyond, which keeps the net's
+// Nets are grouped by degree at create: one thread per net up to 4 pins,
+// groups of 4 lanes up to 16 pins, 16 lanes up to 64, a warp up to 256 (the
+// pins of these nets stay in registers, 4 or 8 per lane), and a block of 512
+// threads beyond, which keeps the net's
 // coordinates in shared memory between its three passes.  Positions are
 // interleaved (x, y), so every pin costs one gather.  Each pin's gradient is
 // added to its cell as a packed fixed-point integer (add_pin_grad): one
@@ -103,15 +104,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int
         mxy = fmaxf(mxy, py[k]); mny = fminf(mny, py[k]);
       }
     }
-    float ax[D], bx[D], ay[D], by[D];
     float sxp = 0.f, txp = 0.f, sxm = 0.f, txm = 0.f, syp = 0.f, typ = 0.f, sym = 0.f, tym = 0.f;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       if (k < deg) {
-        ax[k] = __expf((px[k] - mxx) * ig); bx[k] = __expf((mnx - px[k]) * ig);
-        ay[k] = __expf((py[k] - mxy) * ig); by[k] = __expf((mny - py[k]) * ig);
-        sxp += ax[k]; txp += (px[k] - mxx) * ax[k]; sxm += bx[k]; txm += (px[k] - mnx) * bx[k];
-        syp += ay[k]; typ += (py[k] - mxy) * ay[k]; sym += by[k]; tym += (py[k] - mny) * by[k];
+        float a = __expf((px[k] - mxx) * ig), b = __expf((mnx - px[k]) * ig);
+        sxp += a; txp += (px[k] - mxx) * a; sxm += b; txm += (px[k] - mnx) * b;
+        a = __expf((py[k] - mxy) * ig); b = __expf((mny - py[k]) * ig);
+        syp += a; typ += (py[k] - mxy) * a; sym += b; tym += (py[k] - mny) * b;
       }
     }
     const float wn = d.net_w ? d.net_w[e] : 1.0f;
@@ -120,10 +120,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       if (k < deg) {
-        const float gx = ax[k] * isxp * (1.f + (px[k] - mxx - rxp) * ig) -
-                         bx[k] * isxm * (1.f - (px[k] - mnx - rxm) * ig);
-        const float gy = ay[k] * isyp * (1.f + (py[k] - mxy - ryp) * ig) -
-                         by[k] * isym * (1.f - (py[k] - mny - rym) * ig);
+        float a = __expf((px[k] - mxx) * ig), b = __expf((mnx - px[k]) * ig);
+        const float gx = a * isxp * (1.f + (px[k] - mxx - rxp) * ig) -
+                         b * isxm * (1.f - (px[k] - mnx - rxm) * ig);
+        a = __expf((py[k] - mxy) * ig); b = __expf((mny - py[k]) * ig);
+        const float gy = a * isyp * (1.f + (py[k] - mxy - ryp) * ig) -
+                         b * isym * (1.f - (py[k] - mny - rym) * ig);
         add_pin_grad(d, ga, cell[k], gx * wn, gy * wn);
       }
     }
@@ -139,8 +141,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int
   }
 }
 
-template <int G>
-__global__ void __launch_bounds__(kThreads) k_wa_group(Dev d, int copy0, int cls, int eval,
+// Nets of at most G * PPL pins: G lanes per net, each lane holding up to PPL
+// of the net's pins in registers, so every pin is gathered once.  MINB
+// resident blocks per SM bound the registers (no spills at the chosen values).
+template <int G, int PPL, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_wa_group(Dev d, int copy0, int cls, int eval,
                                                         const float *gamma_ovr) {
   __shared__ float sm[32];
   const int c = copy0 + blockIdx.y;
@@ -162,75 +167,64 @@ __global__ void __launch_bounds__(kThreads) k_wa_group(Dev d, int copy0, int cls
       p1 = d.net_ptr[e + 1];
     }
     const float wn = (valid && d.net_w) ? d.net_w[e] : 1.0f;
-    // coordinates relative to the net's first pin: (x_j - x_0) + (dx_j - dx_0)
-    // rounds relative to the pin spacing, not to the absolute position
-    float rx = 0.f, ry = 0.f, rdx = 0.f, rdy = 0.f;
+    // all of the net's loads in flight together; coordinates relative to the
+    // net's first pin, (x_j - x_0) + (dx_j - dx_0), round relative to the pin
+    // spacing, not to the absolute position
+    int cl[PPL];
+    float2 of[PPL], v[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+      const int j = p0 + lane + k * G;
+      cl[k] = j < p1 ? d.pin_cell[j] : -1;
+      of[k] = j < p1 ? d.pin_off[j] : make_float2(0.f, 0.f);
+    }
+    float2 r0 = make_float2(0.f, 0.f), o0 = make_float2(0.f, 0.f);
     if (p1 > p0) {
-      const float2 o = d.pin_off[p0];
-      const float2 v = xy[d.pin_cell[p0]];
-      rx = v.x; ry = v.y; rdx = o.x; rdy = o.y;
+      o0 = d.pin_off[p0];
+      r0 = xy[d.pin_cell[p0]];
     }
-    // first pin of each lane stays in registers; higher degrees reload
-    const int j0 = p0 + lane;
-    const bool has0 = j0 < p1;
-    float px0 = 0.f, py0 = 0.f;
-    int cell0 = 0;
-    if (has0) {
-      const float2 o = d.pin_off[j0];
-      cell0 = d.pin_cell[j0];
-      const float2 v = xy[cell0];
-      px0 = (v.x - rx) + (o.x - rdx);
-      py0 = (v.y - ry) + (o.y - rdy);
-    }
-    float mxx = has0 ? px0 : -FLT_MAX, mnx = has0 ? px0 : FLT_MAX;
-    float mxy = has0 ? py0 : -FLT_MAX, mny = has0 ? py0 : FLT_MAX;
-    for (int j = j0 + G; j < p1; j += G) {
-      const float2 o = d.pin_off[j];
-      const float2 v = xy[d.pin_cell[j]];
-      float px = (v.x - rx) + (o.x - rdx), py = (v.y - ry) + (o.y - rdy);
-      mxx = fmaxf(mxx, px); mnx = fminf(mnx, px);
-      mxy = fmaxf(mxy, py); mny = fminf(mny, py);
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) v[k] = cl[k] >= 0 ? xy[cl[k]] : make_float2(0.f, 0.f);
+    float px[PPL], py[PPL];
+    float mxx = -FLT_MAX, mnx = FLT_MAX, mxy = -FLT_MAX, mny = FLT_MAX;
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+      px[k] = (v[k].x - r0.x) + (of[k].x - o0.x);
+      py[k] = (v[k].y - r0.y) + (of[k].y - o0.y);
+      if (cl[k] >= 0) {
+        mxx = fmaxf(mxx, px[k]); mnx = fminf(mnx, px[k]);
+        mxy = fmaxf(mxy, py[k]); mny = fminf(mny, py[k]);
+      }
     }
     mxx = gmax<G>(mxx); mnx = gmin<G>(mnx);
     mxy = gmax<G>(mxy); mny = gmin<G>(mny);
     float sxp = 0.f, txp = 0.f, sxm = 0.f, txm = 0.f;
     float syp = 0.f, typ = 0.f, sym = 0.f, tym = 0.f;
-    float a0x = 0.f, b0x = 0.f, a0y = 0.f, b0y = 0.f;
-    if (has0) {
-      a0x = __expf((px0 - mxx) * ig); b0x = __expf((mnx - px0) * ig);
-      sxp += a0x; txp += (px0 - mxx) * a0x; sxm += b0x; txm += (px0 - mnx) * b0x;
-      a0y = __expf((py0 - mxy) * ig); b0y = __expf((mny - py0) * ig);
-      syp += a0y; typ += (py0 - mxy) * a0y; sym += b0y; tym += (py0 - mny) * b0y;
-    }
-    for (int j = j0 + G; j < p1; j += G) {
-      const float2 o = d.pin_off[j];
-      const float2 v = xy[d.pin_cell[j]];
-      float px = (v.x - rx) + (o.x - rdx), py = (v.y - ry) + (o.y - rdy);
-      float a = __expf((px - mxx) * ig), b = __expf((mnx - px) * ig);
-      sxp += a; txp += (px - mxx) * a; sxm += b; txm += (px - mnx) * b;
-      a = __expf((py - mxy) * ig); b = __expf((mny - py) * ig);
-      syp += a; typ += (py - mxy) * a; sym += b; tym += (py - mny) * b;
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+      if (cl[k] >= 0) {
+        float a = __expf((px[k] - mxx) * ig), b = __expf((mnx - px[k]) * ig);
+        sxp += a; txp += (px[k] - mxx) * a; sxm += b; txm += (px[k] - mnx) * b;
+        a = __expf((py[k] - mxy) * ig); b = __expf((mny - py[k]) * ig);
+        syp += a; typ += (py[k] - mxy) * a; sym += b; tym += (py[k] - mny) * b;
+      }
     }
     sxp = gsum<G>(sxp); txp = gsum<G>(txp); sxm = gsum<G>(sxm); txm = gsum<G>(txm);
     syp = gsum<G>(syp); typ = gsum<G>(typ); sym = gsum<G>(sym); tym = gsum<G>(tym);
     if (p1 > p0) {
       const float isxp = 1.f / sxp, isxm = 1.f / sxm, isyp = 1.f / syp, isym = 1.f / sym;
       const float rxp = txp * isxp, rxm = txm * isxm, ryp = typ * isyp, rym = tym * isym;
-      if (has0) {
-        float gx = a0x * isxp * (1.f + (px0 - mxx - rxp) * ig) - b0x * isxm * (1.f - (px0 - mnx - rxm) * ig);
-        float gy = a0y * isyp * (1.f + (py0 - mxy - ryp) * ig) - b0y * isym * (1.f - (py0 - mny - rym) * ig);
-        add_pin_grad(d, ga, cell0, gx * wn, gy * wn);
-      }
-      for (int j = j0 + G; j < p1; j += G) {
-        const float2 o = d.pin_off[j];
-        const int cj = d.pin_cell[j];
-        const float2 v = xy[cj];
-        float px = (v.x - rx) + (o.x - rdx), py = (v.y - ry) + (o.y - rdy);
-        float a = __expf((px - mxx) * ig), b = __expf((mnx - px) * ig);
-        float gx = a * isxp * (1.f + (px - mxx - rxp) * ig) - b * isxm * (1.f - (px - mnx - rxm) * ig);
-        a = __expf((py - mxy) * ig); b = __expf((mny - py) * ig);
-        float gy = a * isyp * (1.f + (py - mxy - ryp) * ig) - b * isym * (1.f - (py - mny - rym) * ig);
-        add_pin_grad(d, ga, cj, gx * wn, gy * wn);
+#pragma unroll
+      for (int k = 0; k < PPL; ++k) {
+        if (cl[k] >= 0) {
+          float a = __expf((px[k] - mxx) * ig), b = __expf((mnx - px[k]) * ig);
+          const float gx = a * isxp * (1.f + (px[k] - mxx - rxp) * ig) -
+                           b * isxm * (1.f - (px[k] - mnx - rxm) * ig);
+          a = __expf((py[k] - mxy) * ig); b = __expf((mny - py[k]) * ig);
+          const float gy = a * isyp * (1.f + (py[k] - mxy - ryp) * ig) -
+                           b * isym * (1.f - (py[k] - mny - rym) * ig);
+          add_pin_grad(d, ga, cl[k], gx * wn, gy * wn);
+        }
       }
       if (lane == 0) {
         hp_acc += wn * ((mxx - mnx) + (mxy - mny));
@@ -395,9 +389,9 @@ void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_
     dim3 grid(nb, ncopy);
     switch (cls) {
       case 0: k_wa_thread<4><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
-      case 1: k_wa_group<4><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
-      case 2: k_wa_group<16><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
-      case 3: k_wa_group<32><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
+      case 1: k_wa_group<4, 4, 6><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
+      case 2: k_wa_group<16, 4, 6><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
+      case 3: k_wa_group<32, 8, 1><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
       default:
         k_wa_big<<<grid, kBigNet, 2 * sizeof(float) * d.wa_big_cap, st>>>(d, copy0, cls, eval,
                                                                           gamma_ovr, d.wa_big_cap);
