@@ -155,6 +155,16 @@ int place_get_info(const place_t *h, place_info *out);
  * asynchronous. */
 int place_step(place_t *h, int32_t n_iters, int32_t *converged);
 
+/* place_step over n resident handles at once, as a job server would: the
+ * iterations are launched round-robin, one per handle per round, each on its
+ * handle's stream, so handles created on distinct streams run concurrently
+ * (handles sharing a stream run one after another, with the same results).
+ * hs: host [n] handles.  converged (nullable, host [sum of the handles' K])
+ * receives the stopped flags, handle by handle, which synchronises every
+ * handle's stream; with NULL the call is asynchronous.  EINVAL on a NULL
+ * handle or n < 1; nothing is launched then. */
+int place_step_multi(place_t *const *hs, int32_t n, int32_t n_iters, int32_t *converged);
+
 /* Perturb (the perturbation step of Algorithm 1; Section 4.2): Shuffle or
  * Shuffle (all) with strength p in [0, 1] applied to copy `copy` (-1: every copy, copy c using
  * seed + c), followed by a full optimiser reset of the perturbed copies.
@@ -167,6 +177,14 @@ int place_eval_hpwl_overflow(place_t *h, double *hpwl, double *overflow);
 
 /* Positions of copy `copy`: x, y are [n_cells] host or device buffers. */
 int place_get_positions(place_t *h, int32_t copy, float *x, float *y);
+
+/* Borrowed device pointers to the positions of copy `copy`, valid until
+ * place_destroy.  The library keeps each copy's positions interleaved,
+ * (x_0, y_0, x_1, y_1, ...), so that every pin costs one 8-byte gather: cell
+ * i is (*x)[2 i], (*y)[2 i], for i < n_cells.  Reads must be ordered after
+ * the handle's work on its stream; the arrays belong to the library and may
+ * not be written (place_set_positions does that). */
+int place_device_views(place_t *h, int32_t copy, float **x, float **y);
 
 /* Set the movable positions of copy `copy` (-1: all copies) from [n_cells]
  * host or device arrays (entries >= n_movable are ignored), clamp them into

@@ -676,6 +676,30 @@ int place_step(place_t *h, int32_t n_iters, int32_t *converged) {
   return PLACE_OK;
 }
 
+int place_step_multi(place_t *const *hs, int32_t n, int32_t n_iters, int32_t *converged) {
+  if (!hs || n < 1) return fail(PLACE_EINVAL, "need at least one handle");
+  if (n_iters < 0) return fail(PLACE_EINVAL, "n_iters < 0");
+  for (int i = 0; i < n; ++i)
+    if (!hs[i]) return fail(PLACE_EINVAL, "null handle %d", i);
+  if (n_iters > 0) {
+    for (int i = 0; i < n; ++i) {
+      int rc = ensure_graph(hs[i]);
+      if (rc) return rc;
+    }
+    for (int it = 0; it < n_iters; ++it)
+      for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(hs[i]->exec, hs[i]->stream));
+  }
+  if (converged) {
+    int off = 0;
+    for (int i = 0; i < n; ++i) {
+      int rc = place_step(hs[i], 0, converged + off);
+      if (rc) return rc;
+      off += hs[i]->d.K;
+    }
+  }
+  return PLACE_OK;
+}
+
 int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms) {
   if (!h || !stage_ms) return fail(PLACE_EINVAL, "null argument");
   const Dev &d = h->d;
@@ -735,6 +759,16 @@ int place_get_positions(place_t *h, int32_t copy, float *x, float *y) {
   if (rc) return rc;
   const size_t C = h->d.n_cells;
   return copy_out_xy(h, h->d.xy + copy * C, x, y);
+}
+
+int place_device_views(place_t *h, int32_t copy, float **x, float **y) {
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  if (!x || !y) return fail(PLACE_EINVAL, "null output");
+  float *base = reinterpret_cast<float *>(h->d.xy + (size_t)copy * h->d.n_cells);
+  *x = base;
+  *y = base + 1;
+  return PLACE_OK;
 }
 
 int place_set_positions(place_t *h, int32_t copy, const float *x, const float *y) {

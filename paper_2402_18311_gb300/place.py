@@ -106,6 +106,8 @@ _SIGS = {
     "place_get_positions": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
     "place_set_positions": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
     "place_get_state": (ct.c_int, [_VP, ct.c_int32, ct.POINTER(place_state)]),
+    "place_step_multi": (ct.c_int, [ct.POINTER(_VP), ct.c_int32, ct.c_int32, _VP]),
+    "place_device_views": (ct.c_int, [_VP, ct.c_int32, ct.POINTER(_VP), ct.POINTER(_VP)]),
     "place_eval_wirelength": (ct.c_int, [_VP, ct.c_int32, ct.c_float, _VP, _VP, _VP]),
     "place_eval_density": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
     "place_get_fixed_map": (ct.c_int, [_VP, _VP]),
@@ -244,6 +246,21 @@ def place_eval_hpwl_overflow(h, hpwl=None, overflow=None):
 
 def place_get_positions(h, copy, x, y):
     return _check(lib().place_get_positions(h, int(copy), _ptr(x), _ptr(y)))
+
+
+def place_step_multi(handles, n_iters, converged=None):
+    """Step several handles together; ``converged`` (optional int32 array of
+    the handles' total copy count) receives the stopped flags."""
+    arr = (_VP * len(handles))(*[hh.value if isinstance(hh, _VP) else hh for hh in handles])
+    return _check(lib().place_step_multi(arr, len(handles), int(n_iters), _ptr(converged)))
+
+
+def place_device_views(h, copy):
+    """(x, y) borrowed device addresses of copy ``copy``'s interleaved
+    positions: cell i is at element 2 i of each."""
+    x, y = _VP(), _VP()
+    _check(lib().place_device_views(h, int(copy), ct.byref(x), ct.byref(y)))
+    return x.value, y.value
 
 
 def place_set_positions(h, copy, x, y):

@@ -132,6 +132,11 @@ def test_create_rejects_bad_params(L):
 
 def test_null_handle_calls_fail_cleanly(L):
     assert L.place_step(None, 1, None) == place.PLACE_EINVAL
+    assert L.place_step_multi(None, 0, 1, None) == place.PLACE_EINVAL
+    arr = (ct.c_void_p * 2)(None, None)
+    assert L.place_step_multi(arr, 2, 1, None) == place.PLACE_EINVAL
+    x, y = ct.c_void_p(), ct.c_void_p()
+    assert L.place_device_views(None, 0, ct.byref(x), ct.byref(y)) == place.PLACE_EINVAL
     assert L.place_destroy(None) == place.PLACE_OK
     assert b"null" in L.place_last_error()
 

@@ -1,0 +1,78 @@
+"""Host-visible API calls beyond the parity path: borrowed device views of the
+positions and stepping several handles at once."""
+import numpy as np
+import pytest
+
+from paper_2402_18311_gb300 import place, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    if not os.path.exists(place.LIB_PATH):
+        from paper_2402_18311_gb300 import build
+        build.build()
+    place.lib()
+
+
+class _View:
+    """A device array described by __cuda_array_interface__ (zero copy; the
+    test only reads it, torch accepts no read-only flag)."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (n, 2), "typestr": "<f4", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def _positions(h, n):
+    x = np.empty(n, np.float32); y = np.empty(n, np.float32)
+    place.place_get_positions(h, 0, x, y)
+    return x, y
+
+
+def test_device_views_alias_the_interleaved_positions():
+    import torch
+    d = synth.tiny_1k(0)
+    h = place.place_create(d, place.place_default_params(tau_stop=-1.0, max_iters=100))
+    try:
+        place.place_step(h, 7)
+        x, y = _positions(h, d.n_cells)
+        px, py = place.place_device_views(h, 0)
+        assert py == px + 4
+        torch.cuda.synchronize()
+        t = torch.as_tensor(_View(px, d.n_cells), device="cuda").cpu().numpy()
+        np.testing.assert_array_equal(t[:, 0], x)
+        np.testing.assert_array_equal(t[:, 1], y)
+        with pytest.raises(place.PlaceError):
+            place.place_device_views(h, 1)  # one copy only
+    finally:
+        place.place_destroy(h)
+
+
+def test_step_multi_equals_separate_steps():
+    import torch
+    designs = [synth.tiny_1k(0), synth.scaled(5000, 64, seed=4)]
+    prm = place.place_default_params(tau_stop=-1.0, max_iters=1000)
+    streams = [torch.cuda.Stream() for _ in designs]
+    multi = [place.place_create(d, prm, stream=s.cuda_stream) for d, s in zip(designs, streams)]
+    solo = [place.place_create(d, prm) for d in designs]
+    try:
+        conv = np.full(2, -1, np.int32)
+        place.place_step_multi(multi, 60, conv)
+        assert conv.tolist() == [0, 0]
+        for h in solo:
+            place.place_step(h, 60)
+        for d, hm, hs in zip(designs, multi, solo):
+            xm, ym = _positions(hm, d.n_cells)
+            xs, ys = _positions(hs, d.n_cells)
+            np.testing.assert_array_equal(xm, xs)
+            np.testing.assert_array_equal(ym, ys)
+    finally:
+        for h in multi + solo:
+            place.place_destroy(h)
+        torch.cuda.synchronize()
