@@ -42,8 +42,10 @@ class Grid:
 
 def frac_bits(die, total_area):
     """Fixed-point fraction bits F: the largest F <= 24 with
-    max|coordinate| * 2^F < 2^30 and total_area * 2^(2F) < 2^62."""
-    ext = max(abs(float(v)) for v in die)
+    max(|coordinate|, die width, die height) * 2^F < 2^30 and
+    total_area * 2^(2F) < 2^62."""
+    xl, yl, xh, yh = (float(v) for v in die)
+    ext = max(abs(xl), abs(yl), abs(xh), abs(yh), xh - xl, yh - yl)
     for F in range(24, -1, -1):
         if ext * 2.0 ** F < 2.0 ** 30 and total_area * 2.0 ** (2 * F) < 2.0 ** 62:
             return F

@@ -384,10 +384,12 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     total_area += (double)nl->w[i] * (double)nl->h[i];
   }
 
-  // fixed-point resolution: the largest F <= 24 with |coordinate| 2^F < 2^30
-  // and total area 2^2F < 2^62
-  const double ext = std::max(std::max(std::fabs(die->xl), std::fabs(die->xh)),
-                              std::max(std::fabs(die->yl), std::fabs(die->yh)));
+  // fixed-point resolution: the largest F <= 24 with
+  // max(|coordinate|, die width, die height) 2^F < 2^30 and total area
+  // 2^2F < 2^62 (the extent bound keeps bin-relative coordinates in int32)
+  const double ext = std::max(std::max(std::max(std::fabs(die->xl), std::fabs(die->xh)),
+                                       std::max(std::fabs(die->yl), std::fabs(die->yh))),
+                              std::max(die->xh - die->xl, die->yh - die->yl));
   int F = -1;
   for (int f = 24; f >= 0; --f) {
     if (ext * std::ldexp(1.0, f) < std::ldexp(1.0, 30) && total_area * std::ldexp(1.0, 2 * f) < std::ldexp(1.0, 62)) {
@@ -424,6 +426,8 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     }
   }
   d.abin_q = (double)d.BW * (double)d.BH;
+  d.BW32 = (int)d.BW; d.BH32 = (int)d.BH;
+  d.ibw_q = (float)(1.0 / (double)d.BW); d.ibh_q = (float)(1.0 / (double)d.BH);
   d.die_xl = die->xl; d.die_yl = die->yl; d.die_xh = die->xh; d.die_yh = die->yh;
   d.fxl = (float)die->xl; d.fyl = (float)die->yl; d.fxh = (float)die->xh; d.fyh = (float)die->yh;
   d.fbw = (float)bw; d.fbh = (float)bh; d.fibw = (float)(1.0 / bw); d.fibh = (float)(1.0 / bh);

@@ -158,4 +158,58 @@ __device__ __forceinline__ long long overlap1(long long lo, long long size, long
   return o > 0 ? o : 0;
 }
 
+// The same rectangle in 32-bit integers, relative to the die's lower-left
+// corner.  The fixed-point resolution keeps nx * BW and ny * BH below 2^30,
+// and the edges are clipped to two bins beyond the die, which changes no
+// overlap with any bin; so every edge, quotient and overlap below fits int32
+// and only the area product needs 64 bits.
+struct QRect32 {
+  int x0, x1, y0, y1;      // edges [x0, x1) x [y0, y1), relative and clipped
+  int ix0, ix1, iy0, iy1;  // clipped bin range (empty when ix0 > ix1)
+};
+
+__device__ __forceinline__ int clip_to_int(long long v, long long lo, long long hi) {
+  return (int)(v < lo ? lo : (v > hi ? hi : v));
+}
+
+// floor(a / b) for b > 0 and |a| + 2b < 2^31: a float estimate of the
+// quotient (off by at most one here), then one exact correction each way.
+__device__ __forceinline__ int floordiv32(int a, int b, float inv_b) {
+  int q = (int)floorf((float)a * inv_b);
+  if (q * b > a) --q;
+  if ((q + 1) * b <= a) ++q;
+  return q;
+}
+
+__device__ __forceinline__ QRect32 qrect32(float x, float y, int W, int H, float scale,
+                                           long long XL, long long YL, int BW, int BH, int nx,
+                                           int ny, float inv_bw, float inv_bh) {
+  // x * 2^F is exact in FP32; rounding to the nearest integer, ties to even;
+  // non-finite or huge coordinates saturate far outside the die
+  const float lim = 4.0e18f;
+  float xs = x * scale, ys = y * scale;
+  xs = (xs == xs) ? fminf(fmaxf(xs, -lim), lim) : -lim;
+  ys = (ys == ys) ? fminf(fmaxf(ys, -lim), lim) : -lim;
+  const long long X = __float2ll_rn(xs) - XL, Y = __float2ll_rn(ys) - YL;
+  const long long lox = -2LL * BW, hix = (long long)(nx + 2) * BW;
+  const long long loy = -2LL * BH, hiy = (long long)(ny + 2) * BH;
+  QRect32 r;
+  r.x0 = clip_to_int(X, lox, hix);
+  r.x1 = clip_to_int(X + W, lox, hix);
+  r.y0 = clip_to_int(Y, loy, hiy);
+  r.y1 = clip_to_int(Y + H, loy, hiy);
+  r.ix0 = max(floordiv32(r.x0, BW, inv_bw), 0);
+  r.ix1 = min(floordiv32(r.x1 - 1, BW, inv_bw), nx - 1);
+  r.iy0 = max(floordiv32(r.y0, BH, inv_bh), 0);
+  r.iy1 = min(floordiv32(r.y1 - 1, BH, inv_bh), ny - 1);
+  return r;
+}
+
+// Overlap of the relative interval [lo, hi) with bin k of width b.
+__device__ __forceinline__ int overlap32(int lo, int hi, int k, int b) {
+  const int b0 = k * b;
+  const int o = min(hi, b0 + b) - max(lo, b0);
+  return o > 0 ? o : 0;
+}
+
 }  // namespace hp

@@ -83,14 +83,15 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
   if (d.cs[c].n_eff >= kAggregateBins) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += stride) {
       const float2 v = xy[i];
-      QRect r = qrect(v.x, v.y, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW, d.BH, d.nx, d.ny);
+      const QRect32 r = qrect32(v.x, v.y, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW32, d.BH32,
+                                d.nx, d.ny, d.ibw_q, d.ibh_q);
       for (int ix = r.ix0; ix <= r.ix1; ++ix) {
-        const long long ox = overlap1(r.X, r.W, d.XL + (long long)ix * d.BW, d.BW);
+        const int ox = overlap32(r.x0, r.x1, ix, d.BW32);
         if (ox == 0) continue;
         for (int iy = r.iy0; iy <= r.iy1; ++iy) {
-          const long long oy = overlap1(r.Y, r.H, d.YL + (long long)iy * d.BH, d.BH);
+          const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
           if (oy == 0) continue;
-          atomicAdd(&M[(size_t)ix * d.ny + iy], (unsigned long long)(ox * oy));
+          atomicAdd(&M[ix * d.ny + iy], (unsigned long long)((long long)ox * oy));
         }
       }
     }
@@ -100,12 +101,13 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
   for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < d.n_mov; i0 += stride) {
     const int i = i0 + (threadIdx.x & 31);
     const bool valid = i < d.n_mov;
-    QRect r;
+    QRect32 r;
     if (valid) {
       const float2 v = xy[i];
-      r = qrect(v.x, v.y, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW, d.BH, d.nx, d.ny);
+      r = qrect32(v.x, v.y, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW32, d.BH32, d.nx, d.ny,
+                  d.ibw_q, d.ibh_q);
     } else {
-      r.X = r.Y = r.W = r.H = 0;
+      r.x0 = r.x1 = r.y0 = r.y1 = 0;
       r.ix0 = r.iy0 = 0;
       r.ix1 = r.iy1 = -1;
     }
@@ -115,9 +117,9 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
       int b = -1;
       unsigned long long a = 0ull;
       if (ix <= r.ix1 && iy <= r.iy1) {
-        const long long ox = overlap1(r.X, r.W, d.XL + (long long)ix * d.BW, d.BW);
-        const long long oy = overlap1(r.Y, r.H, d.YL + (long long)iy * d.BH, d.BH);
-        a = (unsigned long long)(ox * oy);
+        const int ox = overlap32(r.x0, r.x1, ix, d.BW32);
+        const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
+        a = (unsigned long long)((long long)ox * oy);
         if (a != 0ull) b = ix * d.ny + iy;
       }
       const unsigned int mask = __match_any_sync(0xffffffffu, b);
@@ -134,13 +136,13 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
     // bins beyond the first 2 x 2 (cells larger than a bin)
     if (valid && (r.ix1 - r.ix0 > 1 || r.iy1 - r.iy0 > 1)) {
       for (int ix = r.ix0; ix <= r.ix1; ++ix) {
-        const long long ox = overlap1(r.X, r.W, d.XL + (long long)ix * d.BW, d.BW);
+        const int ox = overlap32(r.x0, r.x1, ix, d.BW32);
         if (ox == 0) continue;
         for (int iy = r.iy0; iy <= r.iy1; ++iy) {
           if (ix - r.ix0 <= 1 && iy - r.iy0 <= 1) continue;  // done above
-          const long long oy = overlap1(r.Y, r.H, d.YL + (long long)iy * d.BH, d.BH);
+          const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
           if (oy == 0) continue;
-          hash_add(keys, vals, M, ix * d.ny + iy, (unsigned long long)(ox * oy));
+          hash_add(keys, vals, M, ix * d.ny + iy, (unsigned long long)((long long)ox * oy));
         }
       }
     }
@@ -157,14 +159,15 @@ __global__ void __launch_bounds__(kThreads)
     k_scatter_range(Dev d, const float2 *xy, int n0, int n1, unsigned long long *out) {
   for (int i = n0 + blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += gridDim.x * blockDim.x) {
     const float2 v = xy[i];
-    QRect r = qrect(v.x, v.y, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW, d.BH, d.nx, d.ny);
+    const QRect32 r = qrect32(v.x, v.y, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW32, d.BH32,
+                              d.nx, d.ny, d.ibw_q, d.ibh_q);
     for (int ix = r.ix0; ix <= r.ix1; ++ix) {
-      long long ox = overlap1(r.X, r.W, d.XL + (long long)ix * d.BW, d.BW);
+      const int ox = overlap32(r.x0, r.x1, ix, d.BW32);
       if (ox == 0) continue;
       for (int iy = r.iy0; iy <= r.iy1; ++iy) {
-        long long oy = overlap1(r.Y, r.H, d.YL + (long long)iy * d.BH, d.BH);
+        const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
         if (oy == 0) continue;
-        atomicAdd(&out[(size_t)ix * d.ny + iy], (unsigned long long)(ox * oy));
+        atomicAdd(&out[ix * d.ny + iy], (unsigned long long)((long long)ox * oy));
       }
     }
   }

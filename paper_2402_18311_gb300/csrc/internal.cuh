@@ -63,6 +63,8 @@ struct Dev {
   double die_xl, die_yl, die_xh, die_yh;
   float fxl, fyl, fxh, fyh;
   float fbw, fbh, fibw, fibh;  // bin width/height and their inverses (FP32)
+  int BW32, BH32;             // BW, BH (below 2^26: nx, ny >= 16 and nx BW < 2^30)
+  float ibw_q, ibh_q;         // 1 / BW, 1 / BH
   double w_bin, dref;
   int nb_red;                 // partial slots per reduction per copy
   int cell_blocks;            // blocks per copy for per-cell kernels

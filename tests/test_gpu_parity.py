@@ -276,29 +276,50 @@ def test_stages_scaled_20k_with_big_nets():
         h.close()
 
 
-def test_density_map_bit_exact_on_both_scatter_paths():
-    # The scatter merges the lanes of a warp that hit the same bin while the
-    # effective number of occupied bins of the previous pass, (sum M)^2 /
-    # sum M^2, is below 32 and adds straight to the map otherwise; both must
-    # give the oracle's map.
+def test_density_map_bit_exact_on_every_scatter_path():
+    # Two ways to build the map, chosen from the previous density pass:
+    # direct atomics once the effective number of occupied bins,
+    # (sum M)^2 / sum M^2, is at least 32, and below that warp match/reduce
+    # plus a shared-memory hash.  Both must give the oracle's map bit for bit,
+    # on one concentrated cluster, on two far apart, and once spread.
     d = synth.scaled(20000, 128, seed=2)
     h = Handle(d, tau_stop=-1.0, max_iters=5000)
+    n = d.n_movable
 
     def n_eff_of(M):
         Mf = M.astype(np.float64)
         return Mf.sum() ** 2 / (Mf ** 2).sum()
 
+    def check_map(x, y):
+        g, M, Fm, amov = oracle_maps(d, h.info, x, y)
+        gm = np.empty(d.nx * d.ny, np.int64)
+        place.place_eval_density(h.h, 0, gm)
+        np.testing.assert_array_equal(gm.reshape(d.nx, d.ny), M)
+        return M
+
     try:
+        # two tight clusters in opposite corners (concentrated)
+        x, y = h.pos()
+        x2, y2 = x.copy(), y.copy()
+        half = n // 2
+        x2[:half] = x[:half] - (x[:half].mean() - 0.1 * d.die[2])
+        y2[:half] = y[:half] - (y[:half].mean() - 0.1 * d.die[3])
+        x2[half:n] = x[half:n] + (0.85 * d.die[2] - x[half:n].mean())
+        y2[half:n] = y[half:n] + (0.85 * d.die[3] - y[half:n].mean())
+        place.place_set_positions(h.h, 0, x2, y2)
+        x2, y2 = h.pos()
+        M = check_map(x2, y2)
+        assert n_eff_of(M) < 32
+        assert place.place_get_state(h.h, 0).bins_effective == pytest.approx(n_eff_of(M), rel=1e-3)
+        # the centred start (concentrated), then spreading until direct atomics
+        place.place_set_positions(h.h, 0, x, y)
+        M = check_map(x, y)
+        assert n_eff_of(M) < 32
         seen, trace = set(), []
         for it in range(12):
             x, y = h.pos()
-            g, M, Fm, amov = oracle_maps(d, h.info, x, y)
             s = place.place_get_state(h.h, 0)  # from the last density pass
-            if it == 0:  # that pass was the reset pass at these positions
-                assert s.bins_effective == pytest.approx(n_eff_of(M), rel=1e-3)
-            gm = np.empty(d.nx * d.ny, np.int64)
-            place.place_eval_density(h.h, 0, gm)
-            np.testing.assert_array_equal(gm.reshape(d.nx, d.ny), M)
+            check_map(x, y)
             seen.add(bool(s.bins_effective >= 32))
             trace.append(round(s.bins_effective, 1))
             if seen == {False, True}:
@@ -308,6 +329,7 @@ def test_density_map_bit_exact_on_both_scatter_paths():
         # the statistic at a spread placement (a reset runs one pass there)
         place.place_set_positions(h.h, 0, x, y)
         s = place.place_get_state(h.h, 0)
+        g, M, Fm, amov = oracle_maps(d, h.info, x, y)
         assert s.bins_effective == pytest.approx(n_eff_of(M), rel=1e-3)
     finally:
         h.close()

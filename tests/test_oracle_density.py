@@ -23,6 +23,10 @@ def test_frac_bits_examples():
     assert dens.frac_bits((0, 0, 4096, 4096), 1.1e7) == 17
     # area bound binds: 2^40 * 2^(2F) < 2^62 -> F = 10
     assert dens.frac_bits((0, 0, 8, 8), 2.0 ** 40) == 10
+    # a die across the origin: the extent, 1200, sets F (600 alone would
+    # allow 20), so that bin-relative coordinates stay below 2^30
+    assert dens.frac_bits((-600, -600, 600, 600), 1.0) == 19
+    assert dens.frac_bits((-600, 0, 0, 600), 1.0) == 20
 
 
 def test_hand_computed_2x2():
