@@ -69,6 +69,7 @@ int degree_class(int deg) {
 }
 constexpr int kNetsPerBlock[4] = {256, 64, 16, 8};
 constexpr int kBigCapMax = 12288;  // pins of a big net kept in shared memory (96 KB)
+constexpr int kMaxBigNetBlocks = 8192;  // one block per net above 256 pins, up to this many
 
 bool is_integer(double v) { return std::floor(v) == v && std::isfinite(v); }
 
@@ -462,6 +463,11 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     for (int c = 0; c <= 5; ++c) d.cls_begin[c] = cnt[c];
     std::vector<int> pos(cnt.begin(), cnt.end() - 1);
     for (int e = 0; e < E; ++e) order[pos[degree_class(nl->net_ptr[e + 1] - nl->net_ptr[e])]++] = e;
+    // nets above 256 pins (one block each) by descending degree: the longest
+    // start first, which balances the blocks
+    auto deg = [&](int e) { return nl->net_ptr[e + 1] - nl->net_ptr[e]; };
+    std::stable_sort(order.begin() + d.cls_begin[4], order.begin() + d.cls_begin[5],
+                     [&](int a, int b) { return deg(a) > deg(b); });
   }
   std::vector<int> net_ptr(E + 1), pin_cell(P);
   std::vector<float2> pin_off(P);
@@ -530,7 +536,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   for (int c = 0; c < 5; ++c) {
     int n = d.cls_begin[c + 1] - d.cls_begin[c];
     int nb = c < 4 ? (n + kNetsPerBlock[c] - 1) / kNetsPerBlock[c] : n;
-    nb = std::min(nb, kMaxCellBlocks);
+    nb = std::min(nb, c < 4 ? kMaxCellBlocks : kMaxBigNetBlocks);
     d.wa_blocks[c] = nb;
     d.wa_block_base[c] = d.wa_blocks_total;
     d.wa_blocks_total += nb;
@@ -996,7 +1002,7 @@ extern "C" int place_estimate_device_bytes(const place_netlist *nl, const place_
   d.tc = prm.dct_mode == PLACE_DCT_BF16X3 ? 1 : 0;
   const int cb = std::max(1, std::min((d.n_mov + kThreads - 1) / kThreads, kMaxCellBlocks));
   const int bb = std::max(1, std::min((d.G + kThreads - 1) / kThreads, kMaxCellBlocks));
-  d.nb_red = std::max(std::max(2 * cb + 2, bb), 5 * kMaxCellBlocks);
+  d.nb_red = std::max(std::max(2 * cb + 2, bb), 4 * kMaxCellBlocks + kMaxBigNetBlocks);
   int sn = 2;
   while (sn < d.n_cells) sn <<= 1;
   d.sort_n = sn;

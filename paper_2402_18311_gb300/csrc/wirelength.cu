@@ -18,7 +18,7 @@
 //
 // Nets are grouped by degree at create: one thread per net up to 4 pins,
 // groups of 4 lanes up to 16 pins, 16 lanes up to 64, a warp up to 256 (the
-// pins of these nets stay in registers, 4 or 8 per lane), and a block of 512
+// pins of these nets stay in registers, 4 or 8 per lane), and a block of 256
 // threads beyond, which keeps the net's
 // coordinates in shared memory between its three passes.  Positions are
 // interleaved (x, y), so every pin costs one gather.  Each pin's gradient is
@@ -241,31 +241,44 @@ __global__ void __launch_bounds__(kThreads, MINB) k_wa_group(Dev d, int copy0, i
   }
 }
 
-// Block-wide reductions for the one-block-per-net kernel.
-constexpr int kBigNet = 512;
-__device__ __forceinline__ float bred(float v, float *sm, int op) {
+// Block-wide reductions for the one-block-per-net kernel: N values per
+// thread, maxima or sums, in a fixed order, the results in every thread.
+constexpr int kBigNet = 256;
+constexpr int kBigWarps = kBigNet / 32;
+template <int N, bool MAX>
+__device__ __forceinline__ void block_all(float (&v)[N], float *sm) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float w = __shfl_xor_sync(0xffffffffu, v, o);
-    v = op == 0 ? fmaxf(v, w) : (op == 1 ? fminf(v, w) : v + w);
+  for (int k = 0; k < N; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float w = __shfl_xor_sync(0xffffffffu, v[k], o);
+      v[k] = MAX ? fmaxf(v[k], w) : v[k] + w;
+    }
+  }
+  __syncthreads();  // the previous readers of sm are done
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) sm[(threadIdx.x >> 5) * N + k] = v[k];
   }
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float r = sm[0];
 #pragma unroll
-  for (int i = 1; i < kBigNet / 32; ++i) r = op == 0 ? fmaxf(r, sm[i]) : (op == 1 ? fminf(r, sm[i]) : r + sm[i]);
-  return r;
+  for (int k = 0; k < N; ++k) {
+    float r = sm[k];
+#pragma unroll
+    for (int i = 1; i < kBigWarps; ++i) r = MAX ? fmaxf(r, sm[i * N + k]) : r + sm[i * N + k];
+    v[k] = r;
+  }
 }
 
-// One block per net (degree > 256).  Net-relative pin coordinates are kept
-// in dynamic shared memory when the net fits `cap` pins; longer nets reload
-// pins from global memory in every pass.
+// One block per net (degree > 256), the nets in descending degree so the
+// longest start first.  Net-relative pin coordinates are kept in dynamic
+// shared memory when the net fits `cap` pins; longer nets reload pins from
+// global memory in every pass.
 __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, int eval,
                                                     const float *gamma_ovr, int cap) {
   extern __shared__ float dyn[];
   float *spx = dyn, *spy = dyn + cap;
-  __shared__ float sm[32];
+  __shared__ float sm[kBigWarps * 8];
   const int c = copy0 + blockIdx.y;
   if (!eval && d.cs[c].stopped) return;
   const float g = copy_gamma(d, c, gamma_ovr);
@@ -280,18 +293,20 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
     const float2 o0 = d.pin_off[p0];
     const float2 v0 = xy[d.pin_cell[p0]];
     const float rx = v0.x, ry = v0.y, rdx = o0.x, rdy = o0.y;
-    float mxx = -FLT_MAX, mnx = FLT_MAX, mxy = -FLT_MAX, mny = FLT_MAX;
+    float ext[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};  // max x, -min x, max y, -min y
+#pragma unroll 4
     for (int j = p0 + threadIdx.x; j < p1; j += kBigNet) {
       const float2 o = d.pin_off[j];
       const float2 v = xy[d.pin_cell[j]];
       const float px = (v.x - rx) + (o.x - rdx), py = (v.y - ry) + (o.y - rdy);
       if (cached) { spx[j - p0] = px; spy[j - p0] = py; }
-      mxx = fmaxf(mxx, px); mnx = fminf(mnx, px);
-      mxy = fmaxf(mxy, py); mny = fminf(mny, py);
+      ext[0] = fmaxf(ext[0], px); ext[1] = fmaxf(ext[1], -px);
+      ext[2] = fmaxf(ext[2], py); ext[3] = fmaxf(ext[3], -py);
     }
-    mxx = bred(mxx, sm, 0); mnx = bred(mnx, sm, 1);
-    mxy = bred(mxy, sm, 0); mny = bred(mny, sm, 1);
-    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    block_all<4, true>(ext, sm);
+    const float mxx = ext[0], mnx = -ext[1], mxy = ext[2], mny = -ext[3];
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
     for (int j = p0 + threadIdx.x; j < p1; j += kBigNet) {
       float px, py;
       if (cached) {
@@ -306,9 +321,10 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
       a = __expf((py - mxy) * ig); b = __expf((mny - py) * ig);
       s[4] += a; s[5] += (py - mxy) * a; s[6] += b; s[7] += (py - mny) * b;
     }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) s[q] = bred(s[q], sm, 2);
-    const float rxp = s[1] / s[0], rxm = s[3] / s[2], ryp = s[5] / s[4], rym = s[7] / s[6];
+    block_all<8, false>(s, sm);
+    const float isxp = 1.f / s[0], isxm = 1.f / s[2], isyp = 1.f / s[4], isym = 1.f / s[6];
+    const float rxp = s[1] * isxp, rxm = s[3] * isxm, ryp = s[5] * isyp, rym = s[7] * isym;
+#pragma unroll 4
     for (int j = p0 + threadIdx.x; j < p1; j += kBigNet) {
       float px, py;
       const int cj = d.pin_cell[j];
@@ -320,14 +336,14 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
         px = (v.x - rx) + (o.x - rdx); py = (v.y - ry) + (o.y - rdy);
       }
       float a = __expf((px - mxx) * ig), b = __expf((mnx - px) * ig);
-      const float gx = a / s[0] * (1.f + (px - mxx - rxp) * ig) - b / s[2] * (1.f - (px - mnx - rxm) * ig);
+      const float gx = a * isxp * (1.f + (px - mxx - rxp) * ig) - b * isxm * (1.f - (px - mnx - rxm) * ig);
       a = __expf((py - mxy) * ig); b = __expf((mny - py) * ig);
-      const float gy = a / s[4] * (1.f + (py - mxy - ryp) * ig) - b / s[6] * (1.f - (py - mny - rym) * ig);
+      const float gy = a * isyp * (1.f + (py - mxy - ryp) * ig) - b * isym * (1.f - (py - mny - rym) * ig);
       add_pin_grad(d, ga, cj, gx * wn, gy * wn);
     }
     hp_acc += wn * ((mxx - mnx) + (mxy - mny));
     wl_acc += wn * (((mxx - mnx) + (rxp - rxm)) + ((mxy - mny) + (ryp - rym)));
-    __syncthreads();
+    __syncthreads();  // the shared pin cache is reused by the next net
   }
   if (threadIdx.x == 0) {
     size_t base = (size_t)c * S_COUNT * d.nb_red + d.wa_block_base[cls] + blockIdx.x;
