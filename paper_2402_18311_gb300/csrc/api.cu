@@ -427,6 +427,12 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     }
   }
   d.abin_q = (double)d.BW * (double)d.BH;
+  {
+    const unsigned __int128 tA = (unsigned __int128)(unsigned long long)d.t_mant *
+                                 (unsigned __int128)(unsigned long long)(d.BW * d.BH);
+    d.tA_lo = (unsigned long long)tA;
+    d.tA_hi = (unsigned long long)(tA >> 64);
+  }
   d.BW32 = (int)d.BW; d.BH32 = (int)d.BH;
   d.ibw_q = (float)(1.0 / (double)d.BW); d.ibh_q = (float)(1.0 / (double)d.BH);
   d.die_xl = die->xl; d.die_yl = die->yl; d.die_xh = die->xh; d.die_yh = die->yh;

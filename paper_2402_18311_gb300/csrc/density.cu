@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
   if (mode == FIN_ITER && cs->stopped) return;
   const unsigned long long *M = d.M + (size_t)c * d.G;
   float *rho = d.rho + (size_t)c * d.G;
-  const long long abin = d.BW * d.BH;
+  const u128 tA = ((u128)d.tA_hi << 64) | d.tA_lo;  // t_mant * A_bin
   const float inv_a = (float)(1.0 / d.abin_q);
   const float tf = (float)d.t;
   u128 acc = 0;
@@ -196,9 +196,13 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
     const float mq = (float)m * inv_a;
     q2 = fmaf(mq, mq, q2);
     const long long f = d.Fmap[b];
-    // excess * 2^s = m 2^s - t_mant (A - F): exact in 128 bits
-    const __int128 e = ((__int128)m << d.t_shift) - (__int128)d.t_mant * (__int128)(abin - f);
-    if (e > 0) acc += (u128)e;
+    // excess * 2^s = m 2^s + t_mant F - t_mant A: exact in unsigned 128 bits
+    // (below 2^124, and valid when overlapping fixed cells make F > A); the
+    // product t_mant A is a constant, t_mant F is formed only where fixed
+    // cells are
+    u128 lhs = (u128)(unsigned long long)m << d.t_shift;
+    if (f != 0) lhs += (u128)(unsigned long long)d.t_mant * (u128)(unsigned long long)f;
+    if (lhs > tA) acc += lhs - tA;
     const float rv = mq + tf * ((float)f * inv_a);
     if (d.tc) {
       const __nv_bfloat16 hi = __float2bfloat16_rn(rv);

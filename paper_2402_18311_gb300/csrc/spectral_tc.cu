@@ -175,6 +175,13 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t *done = empty + STAGES;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
   int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+  __shared__ float s_wv[BN], s_cv[BN];  // spectral epilogue: the tile's column weights
+  if (g.epi == TC_EPI_SPECTRAL) {
+    for (int i = threadIdx.x; i < BN; i += blockDim.x) {
+      s_wv[i] = g.wv[n0 + i];
+      s_cv[i] = g.cv[n0 + i];
+    }
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -277,14 +284,14 @@ __global__ void __launch_bounds__(128, 1)
         // spectral weights: a_uv = acc c_u c_v/(M N); (Bx, By, Bpsi) = a (w_u, w_v, 1)/(w_u^2 + w_v^2)
         const size_t G = (size_t)g.M * g.N;
         const size_t ob = (size_t)c * g.d_per_copy * G + (size_t)m * g.N + n;
-        const float cu = g.cu[m], wu = g.wu[m];
+        const float cu = g.cu[m], wu = g.wu[m], wu2 = wu * wu;
         float bx[32], by[32], bp[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const float wv = g.wv[n + i];
-          const float den = wu * wu + wv * wv;
-          const float inv = (m == 0 && n + i == 0) ? 0.f : 1.f / den;
-          const float a = v[i] * cu * g.cv[n + i] * inv;
+          const float wv = s_wv[cc + i];
+          // fast reciprocal (2 ulp), far below the BF16x3 error of the solve
+          const float inv = (m == 0 && n + i == 0) ? 0.f : __fdividef(1.f, fmaf(wv, wv, wu2));
+          const float a = v[i] * cu * s_cv[cc + i] * inv;
           bx[i] = a * wu;
           by[i] = a * wv;
           bp[i] = a;

@@ -355,6 +355,27 @@ def test_edge_cases_small_design():
         h.close()
 
 
+def test_overlapping_fixed_cells_overflow_exact():
+    # two fixed blocks stacked on the same spot: their bins hold more fixed
+    # area than the bin has (F_b > A_b), where t (A_b - F_b) is negative and
+    # every movable overlap counts as overflow
+    d = synth.make_design(n_movable=400, die=(0, 0, 64, 64), nx=16, ny=16, n_nets=300,
+                          n_pads=4, seed=5)
+    n = d.n_movable
+    for k in (0, 1):  # the first two pads become 10 x 10 blocks at (20, 20)
+        d.x[n + k], d.y[n + k] = 20.0, 20.0
+        d.w[n + k], d.h[n + k] = 10.0, 10.0
+    h = Handle(d, tau_stop=-1.0, max_iters=100)
+    try:
+        place.place_step(h.h, 30)
+        x, y = h.pos()
+        g, M, Fm, amov = oracle_maps(d, h.info, x, y)
+        assert (Fm > g.BW * g.BH).any()
+        check_stages(h, x, y, 2.0)
+    finally:
+        h.close()
+
+
 @pytest.mark.slow
 def test_full_size_2m_stages():
     d = synth.large_2m(0)
