@@ -38,7 +38,8 @@ __device__ __forceinline__ void hash_add(int *keys, unsigned long long *vals,
 
 // Exact sum of 64-bit values over the lanes in `mask` (all of which call
 // this with the same mask): three 21-bit limbs are summed with the 32-bit
-// warp reduction, which cannot overflow for 32 lanes.
+// warp reduction, which cannot overflow for 32 lanes.  The scatter calls it
+// with the full mask only.
 __device__ __forceinline__ unsigned long long group_sum_u64(unsigned int mask,
                                                             unsigned long long a) {
   const unsigned int l0 = (unsigned int)(a & 0x1FFFFF);
@@ -122,15 +123,24 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
         a = (unsigned long long)((long long)ox * oy);
         if (a != 0ull) b = ix * d.ny + iy;
       }
+      // one full-warp reduction per distinct bin of the warp (a per-group
+      // mask would serialise the groups inside every reduction); the lowest
+      // lane of each group adds the total, alone on its bin straight to the
+      // map, shared through the block table
       const unsigned int mask = __match_any_sync(0xffffffffu, b);
-      const unsigned long long tot = group_sum_u64(mask, a);
-      if (b >= 0 && (threadIdx.x & 31) == __ffs(mask) - 1) {
-        // lanes alone on their bin (spread placements) go straight to the map;
-        // shared bins (clustered placements) go through the block table
-        if (__popc(mask) == 1)
-          atomicAdd(&M[b], tot);
-        else
-          hash_add(keys, vals, M, b, tot);
+      const int lane = threadIdx.x & 31;
+      unsigned int leaders = __ballot_sync(0xffffffffu, b >= 0 && lane == __ffs(mask) - 1);
+      while (leaders) {
+        const int lead = __ffs(leaders) - 1;
+        leaders &= leaders - 1;
+        const int key = __shfl_sync(0xffffffffu, b, lead);
+        const unsigned long long tot = group_sum_u64(0xffffffffu, b == key ? a : 0ull);
+        if (lane == lead) {
+          if (__popc(mask) == 1)
+            atomicAdd(&M[key], tot);
+          else
+            hash_add(keys, vals, M, key, tot);
+        }
       }
     }
     // bins beyond the first 2 x 2 (cells larger than a bin)
