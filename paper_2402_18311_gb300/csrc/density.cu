@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
   if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_FINISH, &flag)) return;
   u128 v = 0;
   q2 = 0.f;
+#pragma unroll 4
   for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
     const unsigned long long *p = d.tau_part + ((size_t)c * d.nb_red + i) * 2;
     v += ((u128)p[1] << 64) | p[0];

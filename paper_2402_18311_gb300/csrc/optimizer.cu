@@ -28,13 +28,41 @@ __device__ __forceinline__ double *part_ptr(const Dev &d, int c, int slot) {
   return d.part + ((size_t)c * S_COUNT + slot) * d.nb_red;
 }
 
-// Fixed-order sum of one slot's partials by a whole block; valid in thread 0.
+// Fixed-order sums of NS slots' partials by a whole block; valid in thread
+// 0.  Four independent accumulators per slot keep 4 * NS loads in flight
+// (a single running sum would wait a full L2 round trip per partial).
+template <int NT, int NS>
+__device__ void sum_slots(const Dev &d, int c, const int (&slots)[NS], int n, double (&out)[NS],
+                          double *sm) {
+  const double *p[NS];
+  double v[NS][4];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    p[s] = part_ptr(d, c, slots[s]);
+    v[s][0] = v[s][1] = v[s][2] = v[s][3] = 0.0;
+  }
+  int i = threadIdx.x;
+  for (; i + 3 * NT < n; i += 4 * NT) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[s][u] += p[s][i + u * NT];
+    }
+  }
+  for (; i < n; i += NT) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) v[s][0] += p[s][i];
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) out[s] = block_sum<NT>((v[s][0] + v[s][1]) + (v[s][2] + v[s][3]), sm);
+}
+
 template <int NT>
 __device__ double sum_slot(const Dev &d, int c, int slot, int n, double *sm) {
-  const double *p = part_ptr(d, c, slot);
-  double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += NT) v += p[i];
-  return block_sum<NT>(v, sm);
+  const int slots[1] = {slot};
+  double out[1];
+  sum_slots<NT, 1>(d, c, slots, n, out, sm);
+  return out[0];
 }
 
 // Step length, momentum and lambda schedule of iteration k (thread 0 only).
@@ -146,12 +174,13 @@ __global__ void __launch_bounds__(kThreads, 6) k_cell_grad(Dev d, int copy0, int
   }
   if (eval) return;
   if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_CELL, &flag)) return;
-  const double hp = sum_slot<kThreads>(d, c, S_HPWL, d.wa_blocks_total, smd);
-  const double wl = sum_slot<kThreads>(d, c, S_WL, d.wa_blocks_total, smd);
-  const double s1 = sum_slot<kThreads>(d, c, S_GW1, gridDim.x, smd);
-  const double s2 = sum_slot<kThreads>(d, c, S_GD1, gridDim.x, smd);
-  const double s3 = sum_slot<kThreads>(d, c, S_DG2, gridDim.x, smd);
-  const double s4 = sum_slot<kThreads>(d, c, S_DV2, gridDim.x, smd);
+  const int wa_slots[2] = {S_HPWL, S_WL};
+  const int cg_slots[4] = {S_GW1, S_GD1, S_DG2, S_DV2};
+  double wa_sum[2], cg_sum[4];
+  sum_slots<kThreads, 2>(d, c, wa_slots, d.wa_blocks_total, wa_sum, smd);
+  sum_slots<kThreads, 4>(d, c, cg_slots, gridDim.x, cg_sum, smd);
+  const double hp = wa_sum[0], wl = wa_sum[1];
+  const double s1 = cg_sum[0], s2 = cg_sum[1], s3 = cg_sum[2], s4 = cg_sum[3];
   if (threadIdx.x == 0) {
     cs->hpwl = hp;
     cs->wl = wl;
