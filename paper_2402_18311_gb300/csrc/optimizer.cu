@@ -93,7 +93,7 @@ __device__ void advance_scalars(const Dev &d, CopyState *cs, bool first, double 
 // read and cleared for the next pass) and of the density (field gather -sum_b a_ib E_b) for every movable cell.
 // For k >= 1 (lambda known) the preconditioned gradient and the step-size
 // norms are formed here too, and the last block advances the scalars.
-__global__ void __launch_bounds__(kThreads, 6) k_cell_grad(Dev d, int copy0, int eval) {
+__global__ void __launch_bounds__(kThreads, 4) k_cell_grad(Dev d, int copy0, int eval) {
   __shared__ float smf[32];
   __shared__ double smd[32];
   __shared__ int flag;
@@ -133,16 +133,33 @@ __global__ void __launch_bounds__(kThreads, 6) k_cell_grad(Dev d, int copy0, int
     const float rx = xi - (d.fxl + (float)ix0 * d.fbw), ry = yi - (d.fyl + (float)iy0 * d.fbh);
     const float rx1 = rx + wi, ry1 = ry + hi;
     float dx = 0.f, dy = 0.f;
-    for (int kx = 0, ix = ix0; ix < d.nx && (float)kx * d.fbw < rx1; ++kx, ++ix) {
-      const float ox = fminf(rx1, (float)(kx + 1) * d.fbw) - fmaxf(rx, (float)kx * d.fbw);
-      if (!(ox > 0.f)) continue;
-      const float *exr = ex + (size_t)ix * d.ny, *eyr = ey + (size_t)ix * d.ny;
-      for (int ky = 0, iy = iy0; iy < d.ny && (float)ky * d.fbh < ry1; ++ky, ++iy) {
-        const float oy = fminf(ry1, (float)(ky + 1) * d.fbh) - fmaxf(ry, (float)ky * d.fbh);
-        if (!(oy > 0.f)) continue;
-        const float a = ox * oy;
-        dx = fmaf(-a, exr[iy], dx);
-        dy = fmaf(-a, eyr[iy], dy);
+    if (wi <= d.fbw && hi <= d.fbh) {
+      // no larger than a bin: at most the 2 x 2 bins from (ix0, iy0), the
+      // far ones loaded only where the cell reaches them
+      const float ox0 = fmaxf(fminf(rx1, d.fbw) - fmaxf(rx, 0.f), 0.f);
+      const float oy0 = fmaxf(fminf(ry1, d.fbh) - fmaxf(ry, 0.f), 0.f);
+      const float ox1 = ix0 + 1 < d.nx ? fmaxf(rx1 - d.fbw, 0.f) : 0.f;
+      const float oy1 = iy0 + 1 < d.ny ? fmaxf(ry1 - d.fbh, 0.f) : 0.f;
+      const size_t b0 = (size_t)ix0 * d.ny + iy0;
+      const float e00x = ex[b0], e00y = ey[b0];
+      const float e01x = oy1 > 0.f ? ex[b0 + 1] : 0.f, e01y = oy1 > 0.f ? ey[b0 + 1] : 0.f;
+      const float e10x = ox1 > 0.f ? ex[b0 + d.ny] : 0.f, e10y = ox1 > 0.f ? ey[b0 + d.ny] : 0.f;
+      const bool far = ox1 > 0.f && oy1 > 0.f;
+      const float e11x = far ? ex[b0 + d.ny + 1] : 0.f, e11y = far ? ey[b0 + d.ny + 1] : 0.f;
+      dx = -(ox0 * fmaf(oy0, e00x, oy1 * e01x) + ox1 * fmaf(oy0, e10x, oy1 * e11x));
+      dy = -(ox0 * fmaf(oy0, e00y, oy1 * e01y) + ox1 * fmaf(oy0, e10y, oy1 * e11y));
+    } else {
+      for (int kx = 0, ix = ix0; ix < d.nx && (float)kx * d.fbw < rx1; ++kx, ++ix) {
+        const float ox = fminf(rx1, (float)(kx + 1) * d.fbw) - fmaxf(rx, (float)kx * d.fbw);
+        if (!(ox > 0.f)) continue;
+        const float *exr = ex + (size_t)ix * d.ny, *eyr = ey + (size_t)ix * d.ny;
+        for (int ky = 0, iy = iy0; iy < d.ny && (float)ky * d.fbh < ry1; ++ky, ++iy) {
+          const float oy = fminf(ry1, (float)(ky + 1) * d.fbh) - fmaxf(ry, (float)ky * d.fbh);
+          if (!(oy > 0.f)) continue;
+          const float a = ox * oy;
+          dx = fmaf(-a, exr[iy], dx);
+          dy = fmaf(-a, eyr[iy], dy);
+        }
       }
     }
     if (!full) {  // raw gradients are read only by k = 0 (lambda_0) and evaluations
