@@ -51,6 +51,14 @@ __device__ __forceinline__ unsigned long long group_sum_u64(unsigned int mask,
   return s0 + (s1 << 21) + (s2 << 42);
 }
 
+// Exact warp sum of values below 2^42: two 21-bit limbs (the second below
+// 2^21, so each limb's sum over 32 lanes stays below 2^26).
+__device__ __forceinline__ unsigned long long warp_sum_u42(unsigned long long a) {
+  const unsigned long long s0 = __reduce_add_sync(0xffffffffu, (unsigned int)(a & 0x1FFFFF));
+  const unsigned long long s1 = __reduce_add_sync(0xffffffffu, (unsigned int)(a >> 21));
+  return s0 + (s1 << 21);
+}
+
 // Effective number of occupied bins, (sum M)^2 / sum M^2, below which the
 // scatter merges contributions before its global atomics.  Measured on the
 // 2.1M-cell design: at 3.5-4 effective bins (lanes of a warp hit about 4.5
@@ -98,6 +106,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
     }
     return;
   }
+  // one cell's overlap with one bin is at most the bin area
+  const bool two_limbs = (double)d.BW * (double)d.BH < 4398046511104.0;  // 2^42
   // warp-uniform trip count
   for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < d.n_mov; i0 += stride) {
     const int i = i0 + (threadIdx.x & 31);
@@ -123,24 +133,30 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
         a = (unsigned long long)((long long)ox * oy);
         if (a != 0ull) b = ix * d.ny + iy;
       }
-      // one full-warp reduction per distinct bin of the warp (a per-group
-      // mask would serialise the groups inside every reduction); the lowest
-      // lane of each group adds the total, alone on its bin straight to the
-      // map, shared through the block table
+      // one full-warp reduction per bin shared by several lanes (a per-group
+      // mask would serialise the groups inside every reduction); each
+      // group's lowest lane keeps the total, then all of them add at once:
+      // alone on its bin straight to the map, shared through the block table
       const unsigned int mask = __match_any_sync(0xffffffffu, b);
       const int lane = threadIdx.x & 31;
-      unsigned int leaders = __ballot_sync(0xffffffffu, b >= 0 && lane == __ffs(mask) - 1);
-      while (leaders) {
-        const int lead = __ffs(leaders) - 1;
-        leaders &= leaders - 1;
-        const int key = __shfl_sync(0xffffffffu, b, lead);
-        const unsigned long long tot = group_sum_u64(0xffffffffu, b == key ? a : 0ull);
-        if (lane == lead) {
-          if (__popc(mask) == 1)
-            atomicAdd(&M[key], tot);
-          else
-            hash_add(keys, vals, M, key, tot);
-        }
+      const bool lead = b >= 0 && lane == __ffs(mask) - 1;
+      const bool shared = __popc(mask) > 1;
+      unsigned long long tot = a;
+      unsigned int groups = __ballot_sync(0xffffffffu, lead && shared);
+      while (groups) {
+        const int l = __ffs(groups) - 1;
+        groups &= groups - 1;
+        const int key = __shfl_sync(0xffffffffu, b, l);
+        const unsigned long long mine = b == key ? a : 0ull;
+        const unsigned long long t =
+            two_limbs ? warp_sum_u42(mine) : group_sum_u64(0xffffffffu, mine);
+        if (lane == l) tot = t;
+      }
+      if (lead) {
+        if (shared)
+          hash_add(keys, vals, M, b, tot);
+        else
+          atomicAdd(&M[b], tot);
       }
     }
     // bins beyond the first 2 x 2 (cells larger than a bin)
