@@ -123,7 +123,7 @@ typedef struct place_state {
   double hpwl_wa;      /* HPWL measured in the last iteration's WA pass */
   double bins_effective; /* (sum M)^2 / sum M^2 over the movable-area map of the
                           * last density pass: the effective number of occupied
-                          * bins (0 before the first pass).  Below 32 the
+                          * bins (0 before the first pass).  Below 256 the
                           * density scatter merges the lanes of a warp that hit
                           * the same bin; the map is the same either way. */
 } place_state;
