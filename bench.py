@@ -170,8 +170,8 @@ def algorithmic(d, info):
         # field 8, pins/area 8, previous gradient 8, previous position 8,
         # gradient written 8 (the raw gradients are written only at k = 0)
         "cellgrad": {"bytes": 72 * C},
-        # read v, u, g 24, npins/area 8, gwl, gd 16, v_prev 8, g_prev 8; write u, v, v_prev, g 32
-        "update": {"bytes": 96 * C},
+        # read w, h 8, v 8, u 8, g 8; write v_prev 8, u 8, v 8 per cell
+        "update": {"bytes": 56 * C},
     }
 
 
