@@ -331,7 +331,8 @@ def run_restarts(args, place, torch, K=32, p=0.5):
     """Batched Hybro restarts (Algorithm 1, a population of perturbations of
     one converged solution): K Shuffle (all) perturbations of the 210k-cell
     design with seeds 0..K-1, re-optimised until every copy meets the overflow
-    target, as one K-copy handle against K sequential single-copy runs."""
+    target, as one K-copy handle against K sequential single-copy runs.  Also
+    the paper's baseline of independent runs from K random starts (batched)."""
     d = synth.medium_210k(0)
     mk = lambda k: place.place_default_params(tau_stop=0.07, max_iters=3000, dct_mode=args.dct,
                                               n_copies=k)
@@ -376,6 +377,23 @@ def run_restarts(args, place, torch, K=32, p=0.5):
         hp_s[c], tau_s[c] = a[0], b[0]
     t_s = time.perf_counter() - t0
     place.place_destroy(h1)
+    # the paper's baseline, independent runs ("multiple DMP"): K copies from
+    # independent random centred starts of the same netlist, batched the
+    # same way, to the same overflow target
+    hr = place.place_create(d, mk(K))
+    place.place_step(hr, 1)
+    starts = [synth.random_start(d, 1000 + c) for c in range(K)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, (xr, yr) in enumerate(starts):
+        place.place_set_positions(hr, c, xr, yr)
+    until_done(hr, K)
+    hp_r = np.empty(K); tau_r = np.empty(K)
+    place.place_eval_hpwl_overflow(hr, hp_r, tau_r)
+    t_r = time.perf_counter() - t0
+    iters_r = [place.place_get_state(hr, c).iter for c in range(K)]
+    place.place_destroy(hr)
+    br = int(np.argmin(np.where(tau_r <= 0.1, hp_r, np.inf)))
     bb, bs = int(np.argmin(np.where(tau_b <= 0.1, hp_b, np.inf))), int(np.argmin(np.where(tau_s <= 0.1, hp_s, np.inf)))
     return {"workload": "medium_210k: 210k cells, 220k nets, 512x512 bins, t=0.9",
             "copies": K, "operator": "Shuffle (all)", "p": p, "tau_stop": 0.07,
@@ -385,7 +403,13 @@ def run_restarts(args, place, torch, K=32, p=0.5):
             "best_hpwl_batched": float(hp_b[bb]), "best_hpwl_serial": float(hp_s[bs]),
             "best_overflow_batched": float(tau_b[bb]),
             "max_rel_hpwl_diff_batched_vs_serial": float(np.max(np.abs(hp_b - hp_s) / hp_s)),
-            "start_hpwl": float(base_hp[0]), "start_overflow": float(base_tau[0])}
+            "start_hpwl": float(base_hp[0]), "start_overflow": float(base_tau[0]),
+            "random_starts": {"copies": K, "seeds": "1000..%d" % (999 + K),
+                              "runs_per_s": K / t_r, "seconds": t_r,
+                              "iters_per_run_mean": float(np.mean(iters_r)),
+                              "best_hpwl": float(hp_r[br]), "best_overflow": float(tau_r[br]),
+                              "median_hpwl": float(np.median(hp_r)),
+                              "hybro_best_over_random_best": float(hp_b[bb] / hp_r[br])}}
 
 
 def serving_trace(n_jobs, min_cells, max_cells, seed=0):

@@ -161,6 +161,29 @@ def _pads(n_pads, die):
     return rects
 
 
+def _centred_start(rng, w, h, die, sigma_frac):
+    """Lower-left corners of cells whose centres are drawn from N(die centre,
+    (sigma_frac * die extent)^2) per axis, clamped into the die."""
+    xl, yl, xh, yh = die
+    n = w.shape[0]
+    cx = 0.5 * (xl + xh) + sigma_frac * (xh - xl) * rng.standard_normal(n)
+    cy = 0.5 * (yl + yh) + sigma_frac * (yh - yl) * rng.standard_normal(n)
+    mx = np.clip(cx - 0.5 * w, xl, xh - w)
+    my = np.clip(cy - 0.5 * h, yl, yh - h)
+    return mx.astype(np.float32), my.astype(np.float32)
+
+
+def random_start(design, seed, sigma_frac=1e-3):
+    """A fresh centred-Gaussian start of the same design (the random initial
+    placement of an independent run): positions of all cells, the fixed ones
+    unchanged, the movable ones redrawn from ``seed``."""
+    rng = np.random.default_rng(seed)
+    n = design.n_movable
+    x, y = design.x.copy(), design.y.copy()
+    x[:n], y[:n] = _centred_start(rng, design.w[:n], design.h[:n], design.die, sigma_frac)
+    return x, y
+
+
 def make_design(*, n_movable, die, nx, ny, n_nets, n_macros=0, macro_frac=0.0,
                 n_pads=0, target_density=1.0, big_frac=0.0, big_lo=0, big_hi=0,
                 big_log=False, seed=0, name="synthetic", init_sigma_frac=1e-3):
@@ -195,12 +218,8 @@ def make_design(*, n_movable, die, nx, ny, n_nets, n_macros=0, macro_frac=0.0,
     pdx = (rng.random(cells.shape[0]) * w[cells]).astype(np.float32)
     pdy = (rng.random(cells.shape[0]) * h[cells]).astype(np.float32)
 
-    cx = 0.5 * (xl + xh) + init_sigma_frac * (xh - xl) * rng.standard_normal(n_movable)
-    cy = 0.5 * (yl + yh) + init_sigma_frac * (yh - yl) * rng.standard_normal(n_movable)
-    mx = np.clip(cx - 0.5 * w[:n_movable], xl, xh - w[:n_movable])
-    my = np.clip(cy - 0.5 * h[:n_movable], yl, yh - h[:n_movable])
-    x[:n_movable] = mx.astype(np.float32)
-    y[:n_movable] = my.astype(np.float32)
+    x[:n_movable], y[:n_movable] = _centred_start(rng, w[:n_movable], h[:n_movable], die,
+                                                  init_sigma_frac)
 
     return Design(name=name, n_movable=n_movable, w=w, h=h, x=x, y=y,
                   net_ptr=ptr.astype(np.int32), pin_cell=cells.astype(np.int32),

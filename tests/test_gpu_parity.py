@@ -226,6 +226,33 @@ def test_batched_copies_equal_solo_runs():
         hb.close()
 
 
+def test_independent_random_starts_batched_equal_solo():
+    # the paper's baseline of independent runs: K copies from independent
+    # random starts in one handle, each equal bit for bit to its solo run
+    d = synth.tiny_1k(0)
+    K = 3
+    starts = [synth.random_start(d, 7 + c) for c in range(K)]
+    hb = Handle(d, tau_stop=-1.0, max_iters=1000, n_copies=K)
+    try:
+        for c, (x, y) in enumerate(starts):
+            place.place_set_positions(hb.h, c, x, y)
+        place.place_step(hb.h, 60)
+        finals = [hb.pos(c) for c in range(K)]
+    finally:
+        hb.close()
+    assert not np.array_equal(finals[0][0], finals[1][0])
+    for c, (x, y) in enumerate(starts):
+        hs = Handle(d, tau_stop=-1.0, max_iters=1000)
+        try:
+            place.place_set_positions(hs.h, 0, x, y)
+            place.place_step(hs.h, 60)
+            xs, ys = hs.pos()
+        finally:
+            hs.close()
+        np.testing.assert_array_equal(finals[c][0], xs)
+        np.testing.assert_array_equal(finals[c][1], ys)
+
+
 def test_convergence_stops_copy():
     d = synth.tiny_1k(0)
     h = Handle(d, tau_stop=0.3, max_iters=1000)
