@@ -80,6 +80,7 @@ constexpr double kAggregateBins = 256.0;
 __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval) {
   __shared__ int keys[kHash];
   __shared__ unsigned long long vals[kHash];
+  pdl_wait();
   const int c = copy0 + blockIdx.y;
   if (!eval && d.cs[c].stopped) return;
   for (int i = threadIdx.x; i < kHash; i += blockDim.x) {
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
   __shared__ u128 sm[32];
   __shared__ float smf[32];
   __shared__ int flag;
+  pdl_wait();
   const int c = copy0 + blockIdx.y;
   CopyState *cs = d.cs + c;
   if (mode == FIN_ITER && cs->stopped) return;
@@ -291,7 +293,7 @@ void launch_scatter_fixed(const Dev &d, const float2 *xy, int n0, int n1,
 
 void launch_density_finish(const Dev &d, int copy0, int ncopy, int mode, cudaStream_t st) {
   dim3 grid(d.bin_blocks, ncopy);
-  k_density_finish<<<grid, kThreads, 0, st>>>(d, copy0, mode);
+  launch_pdl(k_density_finish, grid, dim3(kThreads), 0, st, d, copy0, mode);
 }
 
 }  // namespace hp

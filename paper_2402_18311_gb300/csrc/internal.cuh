@@ -162,6 +162,30 @@ __device__ __forceinline__ float2 unpack_grad(const Dev &d, unsigned long long s
 
 // ---- launchers (all enqueue on `st`) ------------------------------------
 // eval != 0 ignores the stopped flag of the copy (stage-level evaluation).
+// Programmatic dependent launch.  launch_pdl lets a kernel be scheduled
+// while the kernel before it in the same stream drains; the kernel calls
+// pdl_wait() before its first access to memory, which returns once that
+// predecessor has completed and its writes are visible (for a kernel
+// launched normally it returns at once).  Results are those of plain stream
+// order; only the launch latency overlaps.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline void launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 void launch_scatter(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
 void launch_scatter_fixed(const Dev &d, const float2 *xy, int n0, int n1,
                           unsigned long long *out, cudaStream_t st);

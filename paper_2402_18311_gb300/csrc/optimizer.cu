@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_cell_grad(Dev d, int copy0, int
   __shared__ float smf[32];
   __shared__ double smd[32];
   __shared__ int flag;
+  pdl_wait();
   const int c = copy0 + blockIdx.y;
   CopyState *cs = d.cs + c;
   if (!eval && cs->stopped) return;
@@ -216,6 +217,7 @@ __global__ void __launch_bounds__(kThreads) k_precond0(Dev d, int copy0) {
   __shared__ float smf[32];
   __shared__ double smd[32];
   __shared__ int flag;
+  pdl_wait();
   const int c = copy0 + blockIdx.y;
   CopyState *cs = d.cs + c;
   if (cs->stopped || cs->k != 0) return;
@@ -245,6 +247,7 @@ __global__ void __launch_bounds__(kThreads) k_precond0(Dev d, int copy0) {
 // iteration (k, a_k, buffer parity, max_iters stop).
 __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
   __shared__ int flag;
+  pdl_wait();
   const int c = copy0 + blockIdx.y;
   CopyState *cs = d.cs + c;
   if (cs->stopped) return;
@@ -329,7 +332,7 @@ void launch_unpack_xy(float *x, float *y, const float2 *src, int n, cudaStream_t
 }
 
 void launch_cell_grad(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st) {
-  k_cell_grad<<<dim3(d.cg_blocks, ncopy), kThreads, 0, st>>>(d, copy0, eval);
+  launch_pdl(k_cell_grad, dim3(d.cg_blocks, ncopy), dim3(kThreads), 0, st, d, copy0, eval);
 }
 int cell_grad_blocks_per_sm() {
   int n = 0;
@@ -338,10 +341,10 @@ int cell_grad_blocks_per_sm() {
   return n;
 }
 void launch_precond0(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
-  k_precond0<<<dim3(d.cell_blocks, ncopy), kThreads, 0, st>>>(d, copy0);
+  launch_pdl(k_precond0, dim3(d.cell_blocks, ncopy), dim3(kThreads), 0, st, d, copy0);
 }
 void launch_update(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
-  k_update<<<dim3(d.cell_blocks, ncopy), kThreads, 0, st>>>(d, copy0);
+  launch_pdl(k_update, dim3(d.cell_blocks, ncopy), dim3(kThreads), 0, st, d, copy0);
 }
 void launch_reset(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
   k_reset<<<dim3(d.cell_blocks, ncopy), kThreads, 0, st>>>(d, copy0);

@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(128, 1)
                 const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
                 TcArgs g) {
   extern __shared__ unsigned char smem_raw[];
+  pdl_wait();
   const int z = blockIdx.z;
   const int which = z % g.nwhich;
   const int c = g.copy0 + z / g.nwhich;
@@ -320,11 +321,11 @@ void launch_tc_gemm(const CUtensorMap *maps4, const TcArgs &g, int ncopy, int bn
                     cudaStream_t st) {
   dim3 grid(g.N / bn, g.M / BM, g.nwhich * ncopy);
   if (bn == 64)
-    k_umma_gemm<64, 2><<<grid, 128, Cfg<64, 2>::SMEM_BYTES, st>>>(maps4[0], maps4[1], maps4[2],
-                                                                 maps4[3], g);
+    launch_pdl(k_umma_gemm<64, 2>, grid, dim3(128), Cfg<64, 2>::SMEM_BYTES, st, maps4[0], maps4[1],
+               maps4[2], maps4[3], g);
   else
-    k_umma_gemm<128, 3><<<grid, 128, Cfg<128, 3>::SMEM_BYTES, st>>>(maps4[0], maps4[1], maps4[2],
-                                                                   maps4[3], g);
+    launch_pdl(k_umma_gemm<128, 3>, grid, dim3(128), Cfg<128, 3>::SMEM_BYTES, st, maps4[0],
+               maps4[1], maps4[2], maps4[3], g);
 }
 
 int tc_prepare() {

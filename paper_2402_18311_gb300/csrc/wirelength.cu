@@ -61,6 +61,7 @@ template <int D>
 __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int cls, int eval,
                                                             const float *gamma_ovr) {
   __shared__ float sm[32];
+  pdl_wait();
   const int c = copy0 + blockIdx.y;
   if (!eval && d.cs[c].stopped) return;
   const float g = copy_gamma(d, c, gamma_ovr);
@@ -148,6 +149,7 @@ template <int G, int PPL, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_wa_group(Dev d, int copy0, int cls, int eval,
                                                         const float *gamma_ovr) {
   __shared__ float sm[32];
+  pdl_wait();
   const int c = copy0 + blockIdx.y;
   if (!eval && d.cs[c].stopped) return;
   const float g = copy_gamma(d, c, gamma_ovr);
@@ -279,6 +281,7 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
   extern __shared__ float dyn[];
   float *spx = dyn, *spy = dyn + cap;
   __shared__ float sm[kBigWarps * 8];
+  pdl_wait();
   const int c = copy0 + blockIdx.y;
   if (!eval && d.cs[c].stopped) return;
   const float g = copy_gamma(d, c, gamma_ovr);
@@ -399,19 +402,41 @@ __global__ void __launch_bounds__(kThreads) k_hpwl64(Dev d, int copy0, int e_beg
 
 void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_ovr,
                cudaStream_t st) {
+  int launched = 0;
   for (int cls = 0; cls < d.n_cls; ++cls) {
     int nb = d.wa_blocks[cls];
     if (nb == 0) continue;
     dim3 grid(nb, ncopy);
+    // the first class follows whatever precedes it in the stream (an event
+    // or a copy); the others follow a WA kernel and launch programmatically
+    const bool pdl = launched++ > 0;
+    const dim3 blk(kThreads);
     switch (cls) {
-      case 0: k_wa_thread<4><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
-      case 1: k_wa_group<4, 4, 6><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
-      case 2: k_wa_group<16, 4, 6><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
-      case 3: k_wa_group<32, 8, 1><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr); break;
-      default:
-        k_wa_big<<<grid, kBigNet, 2 * sizeof(float) * d.wa_big_cap, st>>>(d, copy0, cls, eval,
-                                                                          gamma_ovr, d.wa_big_cap);
+      case 0:
+        if (pdl) launch_pdl(k_wa_thread<4>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
+        else k_wa_thread<4><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
         break;
+      case 1:
+        if (pdl) launch_pdl(k_wa_group<4, 4, 6>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
+        else k_wa_group<4, 4, 6><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
+        break;
+      case 2:
+        if (pdl) launch_pdl(k_wa_group<16, 4, 6>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
+        else k_wa_group<16, 4, 6><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
+        break;
+      case 3:
+        if (pdl) launch_pdl(k_wa_group<32, 8, 1>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
+        else k_wa_group<32, 8, 1><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
+        break;
+      default: {
+        const size_t sm = 2 * sizeof(float) * d.wa_big_cap;
+        if (pdl)
+          launch_pdl(k_wa_big, grid, dim3(kBigNet), sm, st, d, copy0, cls, eval, gamma_ovr,
+                     d.wa_big_cap);
+        else
+          k_wa_big<<<grid, kBigNet, sm, st>>>(d, copy0, cls, eval, gamma_ovr, d.wa_big_cap);
+        break;
+      }
     }
   }
 }
