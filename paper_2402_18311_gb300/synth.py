@@ -238,6 +238,24 @@ def tiny_1k(seed=0):
                        name="tiny_1k")
 
 
+def mixed_size_1k(seed=0, n_macros=20):
+    """tiny_1k with n_macros of its movable cells enlarged into movable macros
+    of 8-24 units a side (2-6 bins), flagged as macros, so Shuffle (macros)
+    has candidates and cells span more than 2 x 2 bins.  Pin offsets stay
+    where they were, inside the enlarged cells."""
+    d = tiny_1k(seed)
+    rng = np.random.default_rng(seed + 7)
+    idx = rng.choice(d.n_movable, n_macros, replace=False)
+    d.w[idx] = rng.integers(8, 25, n_macros).astype(np.float32)
+    d.h[idx] = rng.integers(8, 25, n_macros).astype(np.float32)
+    xl, yl, xh, yh = d.die
+    d.x[idx] = np.clip(d.x[idx] - 0.5 * (d.w[idx] - 1.0), xl, xh - d.w[idx]).astype(np.float32)
+    d.y[idx] = np.clip(d.y[idx] - 0.5 * (d.h[idx] - 1.0), yl, yh - d.h[idx]).astype(np.float32)
+    d.is_macro[idx] = 1
+    d.name = "mixed_size_1k"
+    return d
+
+
 def medium_210k(seed=0):
     """210k movable cells on a 2000x2000 die, 10 fixed macros covering 20% of
     the area, 220k nets plus 0.1% nets of degree U[100, 2000], 512x512 bins,

@@ -200,6 +200,33 @@ def test_shuffle_bit_exact():
         h.close()
 
 
+def test_mixed_size_movable_macros_stages_and_shuffle():
+    # movable macros 2-6 bins a side: the scatter's and the field gather's
+    # loops over bins beyond 2 x 2, and Shuffle (macros) with candidates
+    d = synth.mixed_size_1k(0)
+    n = d.n_movable
+    assert d.is_macro[:n].sum() == 20 and (d.w[:n] > 4 * 256 / 64).any()
+    h = Handle(d, tau_stop=-1.0, max_iters=500)
+    try:
+        x, y = h.pos()
+        check_stages(h, x, y, 2.0)
+        x, y = spread(h, 150)
+        check_stages(h, x, y, 3.0)
+        cand = ohy.candidates(d, ohy.SHUFFLE_MACRO)
+        assert len(cand) == 20
+        for seed in (1, 9):
+            place.place_set_positions(h.h, 0, x, y)
+            place.place_perturb(h.h, place.PLACE_SHUFFLE_MACRO, 0.5, seed, 0)
+            gx, gy = h.pos()
+            ox, oy = opt.shuffle(x, y, d.w, d.h, cand, 0.5, seed, d.die)
+            np.testing.assert_array_equal(gx, ox)
+            np.testing.assert_array_equal(gy, oy)
+            moved = np.nonzero((gx != x) | (gy != y))[0]
+            assert len(moved) > 0 and set(moved.tolist()) <= set(cand.tolist())
+    finally:
+        h.close()
+
+
 def test_batched_copies_equal_solo_runs():
     d = synth.tiny_1k(1)
     K = 3
