@@ -253,6 +253,36 @@ def test_batched_copies_equal_solo_runs():
         hb.close()
 
 
+def test_batched_copies_equal_solo_runs_tensor_core():
+    # K copies in one handle run the tensor-core GEMMs batched over the copies
+    # (the copy is the third TMA coordinate); each equals its solo run
+    d = synth.scaled(5000, 128, seed=4)
+    K = 3
+    tc = place.PLACE_DCT_BF16X3
+    hb = Handle(d, tau_stop=-1.0, max_iters=300, n_copies=K, dct_mode=tc)
+    try:
+        place.place_step(hb.h, 40)
+        base_x, base_y = hb.pos(0)
+        place.place_set_positions(hb.h, -1, base_x, base_y)
+        place.place_perturb(hb.h, place.PLACE_SHUFFLE_ALL, 0.5, 7, -1)
+        place.place_step(hb.h, 50)
+        finals = [hb.pos(c) for c in range(K)]
+    finally:
+        hb.close()
+    assert not np.array_equal(finals[0][0], finals[1][0])
+    for c in range(K):
+        hs = Handle(d, tau_stop=-1.0, max_iters=300, dct_mode=tc)
+        try:
+            place.place_set_positions(hs.h, 0, base_x, base_y)
+            place.place_perturb(hs.h, place.PLACE_SHUFFLE_ALL, 0.5, 7 + c, 0)
+            place.place_step(hs.h, 50)
+            sx, sy = hs.pos()
+        finally:
+            hs.close()
+        np.testing.assert_array_equal(finals[c][0], sx)
+        np.testing.assert_array_equal(finals[c][1], sy)
+
+
 def test_independent_random_starts_batched_equal_solo():
     # the paper's baseline of independent runs: K copies from independent
     # random starts in one handle, each equal bit for bit to its solo run
