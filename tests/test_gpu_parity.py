@@ -471,6 +471,22 @@ def test_full_size_2m_stages():
         h.close()
 
 
+@pytest.mark.parametrize("mode", [place.PLACE_DCT_FP32, place.PLACE_DCT_BF16X3])
+def test_stages_non_square_grid(mode):
+    # a 1024 x 512 die with 256 x 128 bins: the transform stages swap the
+    # roles of nx and ny, which a square grid cannot tell apart
+    d = synth.make_design(n_movable=6000, die=(0, 0, 1024, 512), nx=256, ny=128, n_nets=6500,
+                          n_pads=16, target_density=0.9, seed=11)
+    h = Handle(d, tau_stop=-1.0, max_iters=1000, dct_mode=mode)
+    try:
+        x, y = h.pos()
+        check_stages(h, x, y, 2.0)
+        x, y = spread(h, 200)
+        check_stages(h, x, y, 2.0)
+    finally:
+        h.close()
+
+
 def test_tensor_core_spectral_path_scaled():
     # BF16x3 on tcgen05: field within the same 1e-4 L2 tolerance
     d = synth.scaled(20000, 128, seed=2)
