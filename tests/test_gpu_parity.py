@@ -471,11 +471,13 @@ def test_full_size_2m_stages():
         h.close()
 
 
+@pytest.mark.parametrize("die", [(0, 0, 1024, 512), (-512, -256, 512, 256), (1000, 3000, 2024, 3512)])
 @pytest.mark.parametrize("mode", [place.PLACE_DCT_FP32, place.PLACE_DCT_BF16X3])
-def test_stages_non_square_grid(mode):
+def test_stages_non_square_grid(mode, die):
     # a 1024 x 512 die with 256 x 128 bins: the transform stages swap the
-    # roles of nx and ny, which a square grid cannot tell apart
-    d = synth.make_design(n_movable=6000, die=(0, 0, 1024, 512), nx=256, ny=128, n_nets=6500,
+    # roles of nx and ny, which a square grid cannot tell apart; the die also
+    # sits at the origin, across it (the extent then sets F) and away from it
+    d = synth.make_design(n_movable=6000, die=die, nx=256, ny=128, n_nets=6500,
                           n_pads=16, target_density=0.9, seed=11)
     h = Handle(d, tau_stop=-1.0, max_iters=1000, dct_mode=mode)
     try:
