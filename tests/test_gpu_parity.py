@@ -76,7 +76,9 @@ def check_stages(handle, x, y, gamma):
     # WA wirelength and gradient (Eq. 3)
     gx = np.empty(n, np.float32); gy = np.empty(n, np.float32)
     wl = place.place_eval_wirelength(handle.h, 0, gamma, gx, gy)
-    owl_v, ogx, ogy = owl.wa_wirelength(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, x, y, gamma, n)
+    net_w = getattr(d, "net_w", None)
+    owl_v, ogx, ogy = owl.wa_wirelength(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, x, y, gamma, n,
+                                        net_w=net_w)
     assert wl == pytest.approx(owl_v, rel=1e-5)
     assert rel_l2(np.concatenate([gx, gy]), np.concatenate([ogx, ogy])) < 1e-4
     # density map: bit-exact
@@ -108,7 +110,8 @@ def check_stages(handle, x, y, gamma):
     # FP64 HPWL (Eq. 1)
     hp = np.empty(1); tv = np.empty(1)
     place.place_eval_hpwl_overflow(handle.h, hp, tv)
-    assert hp[0] == pytest.approx(owl.hpwl(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, x, y), rel=1e-12)
+    assert hp[0] == pytest.approx(owl.hpwl(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, x, y,
+                                           net_w=net_w), rel=1e-12)
     assert tv[0] == pytest.approx(otau, rel=1e-12, abs=1e-15)
 
 
@@ -174,6 +177,20 @@ def test_trajectory_300_iterations():
         ohp = o.hpwl(o.vx, o.vy)
         assert hp[0] == pytest.approx(ohp, rel=1e-3), f"first divergence beyond 1e-3: {first_bad}"
         assert tv[0] == pytest.approx(o.tau, abs=5e-3)
+    finally:
+        h.close()
+
+
+def test_stages_with_net_weights():
+    # weighted nets (Eq. 1 and Eq. 3 scaled per net) through every stage
+    d = synth.tiny_1k(3)
+    d.net_w = np.random.default_rng(3).uniform(0.5, 2.0, d.n_nets).astype(np.float32)
+    h = Handle(d, tau_stop=-1.0, max_iters=300)
+    try:
+        x, y = h.pos()
+        check_stages(h, x, y, 2.5)
+        x, y = spread(h, 120)
+        check_stages(h, x, y, 2.5)
     finally:
         h.close()
 
