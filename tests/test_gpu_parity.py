@@ -300,6 +300,35 @@ def test_batched_copies_equal_solo_runs_tensor_core():
         np.testing.assert_array_equal(finals[c][1], sy)
 
 
+def test_copies_in_different_phases_equal_solo_runs():
+    # one launch with a spread copy (direct scatter) and a restarted,
+    # concentrated copy (merged scatter): each equals its solo run
+    d = synth.scaled(20000, 128, seed=2)
+    hb = Handle(d, tau_stop=-1.0, max_iters=5000, n_copies=2)
+    try:
+        x0, y0 = hb.pos(0)
+        n0 = 0
+        while place.place_get_state(hb.h, 0).bins_effective < 256 and n0 < 2000:
+            place.place_step(hb.h, 100)
+            n0 += 100
+        assert place.place_get_state(hb.h, 0).bins_effective >= 256
+        place.place_set_positions(hb.h, 1, x0, y0)  # copy 1 back to the start
+        assert place.place_get_state(hb.h, 1).bins_effective < 256
+        place.place_step(hb.h, 40)
+        b0, b1 = hb.pos(0), hb.pos(1)
+    finally:
+        hb.close()
+    for iters, got in ((n0 + 40, b0), (40, b1)):
+        hs = Handle(d, tau_stop=-1.0, max_iters=5000)
+        try:
+            place.place_step(hs.h, iters)
+            sx, sy = hs.pos()
+        finally:
+            hs.close()
+        np.testing.assert_array_equal(got[0], sx)
+        np.testing.assert_array_equal(got[1], sy)
+
+
 def test_independent_random_starts_batched_equal_solo():
     # the paper's baseline of independent runs: K copies from independent
     # random starts in one handle, each equal bit for bit to its solo run
