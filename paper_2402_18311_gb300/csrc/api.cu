@@ -432,6 +432,9 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
                                  (unsigned __int128)(unsigned long long)(d.BW * d.BH);
     d.tA_lo = (unsigned long long)tA;
     d.tA_hi = (unsigned long long)(tA >> 64);
+    const unsigned __int128 fl = tA >> d.t_shift;
+    d.tA_floor = fl > (unsigned __int128)0x7fffffffffffffffull ? 0x7fffffffffffffffull
+                                                                 : (unsigned long long)fl;
   }
   d.BW32 = (int)d.BW; d.BH32 = (int)d.BH;
   d.ibw_q = (float)(1.0 / (double)d.BW); d.ibh_q = (float)(1.0 / (double)d.BH);

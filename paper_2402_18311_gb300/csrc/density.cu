@@ -219,19 +219,30 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
   const float inv_a = (float)(1.0 / d.abin_q);
   const float tf = (float)d.t;
   u128 acc = 0;
+  // bins without fixed cells: their excess times 2^s is m 2^s - t_mant A,
+  // positive exactly when m > floor(t_mant A / 2^s); the sum over those bins
+  // is 2^s (sum of m) - count * t_mant A, formed once after the loop (the
+  // sum of m stays below the movable area, below 2^62)
+  unsigned long long m_over = 0ull;
+  unsigned int n_over = 0u;
   float q2 = 0.f;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < d.G; b += gridDim.x * blockDim.x) {
     const long long m = (long long)M[b];
     const float mq = (float)m * inv_a;
     q2 = fmaf(mq, mq, q2);
     const long long f = d.Fmap[b];
-    // excess * 2^s = m 2^s + t_mant F - t_mant A: exact in unsigned 128 bits
-    // (below 2^124, and valid when overlapping fixed cells make F > A); the
-    // product t_mant A is a constant, t_mant F is formed only where fixed
-    // cells are
-    u128 lhs = (u128)(unsigned long long)m << d.t_shift;
-    if (f != 0) lhs += (u128)(unsigned long long)d.t_mant * (u128)(unsigned long long)f;
-    if (lhs > tA) acc += lhs - tA;
+    if (f == 0) {
+      if ((unsigned long long)m > d.tA_floor) {
+        m_over += (unsigned long long)m;
+        ++n_over;
+      }
+    } else {
+      // excess * 2^s = m 2^s + t_mant F - t_mant A: exact in unsigned 128
+      // bits (below 2^124, and valid when overlapping fixed cells make F > A)
+      u128 lhs = (u128)(unsigned long long)m << d.t_shift;
+      lhs += (u128)(unsigned long long)d.t_mant * (u128)(unsigned long long)f;
+      if (lhs > tA) acc += lhs - tA;
+    }
     const float rv = mq + tf * ((float)f * inv_a);
     if (d.tc) {
       const __nv_bfloat16 hi = __float2bfloat16_rn(rv);
@@ -241,6 +252,7 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
       rho[b] = rv;
     }
   }
+  acc += ((u128)m_over << d.t_shift) - (u128)n_over * tA;
   q2 = block_sum_f<kThreads>(q2, smf);
   u128 r = block_sum_u128<kThreads>(acc, sm);
   if (threadIdx.x == 0) {

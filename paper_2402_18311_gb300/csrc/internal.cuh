@@ -59,6 +59,8 @@ struct Dev {
   long long t_mant;           // t = t_mant * 2^-t_shift exactly
   int t_shift;
   unsigned long long tA_lo, tA_hi;  // t_mant * A_bin as a 128-bit integer
+  unsigned long long tA_floor;      // floor(t_mant * A_bin / 2^t_shift): a bin
+                                    // without fixed cells overflows iff M > this
   double abin_q;              // BW * BH
   double mov_area_q;
   double die_xl, die_yl, die_xh, die_yh;
