@@ -329,6 +329,43 @@ def test_copies_in_different_phases_equal_solo_runs():
         np.testing.assert_array_equal(got[1], sy)
 
 
+def test_tensor_core_copies_stopping_at_different_iterations():
+    # a batched tensor-core handle whose copies meet the overflow target at
+    # different iterations: a stopped copy's GEMM tiles are skipped while the
+    # other copy runs on, and each copy equals its solo run
+    d = synth.scaled(5000, 128, seed=6)
+    tc = place.PLACE_DCT_BF16X3
+    hb = Handle(d, tau_stop=0.35, max_iters=2000, n_copies=2, dct_mode=tc)
+    try:
+        conv = np.zeros(2, np.int32)
+        place.place_step(hb.h, 150, conv)
+        base_x, base_y = hb.pos(0)
+        place.place_set_positions(hb.h, -1, base_x, base_y)
+        place.place_perturb(hb.h, place.PLACE_SHUFFLE_ALL, 0.9, 3, 1)  # copy 1 only
+        while not conv.all():
+            place.place_step(hb.h, 10, conv)
+        st = [place.place_get_state(hb.h, c) for c in range(2)]
+        assert st[0].converged and st[1].converged and st[0].iter != st[1].iter
+        finals = [hb.pos(c) for c in range(2)]
+    finally:
+        hb.close()
+    for c in range(2):
+        hs = Handle(d, tau_stop=0.35, max_iters=2000, dct_mode=tc)
+        try:
+            place.place_set_positions(hs.h, 0, base_x, base_y)
+            if c == 1:
+                place.place_perturb(hs.h, place.PLACE_SHUFFLE_ALL, 0.9, 3, 0)
+            one = np.zeros(1, np.int32)
+            while not one.all():
+                place.place_step(hs.h, 10, one)
+            assert place.place_get_state(hs.h, 0).iter == st[c].iter
+            sx, sy = hs.pos()
+        finally:
+            hs.close()
+        np.testing.assert_array_equal(finals[c][0], sx)
+        np.testing.assert_array_equal(finals[c][1], sy)
+
+
 def test_independent_random_starts_batched_equal_solo():
     # the paper's baseline of independent runs: K copies from independent
     # random starts in one handle, each equal bit for bit to its solo run
