@@ -128,6 +128,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// One 32-byte global store (a whole sector); p is 32-byte aligned.
+__device__ __forceinline__ void st_v8(void *p, uint4 a, uint4 b) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a.x),
+               "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+               : "memory");
+}
+
 __device__ __forceinline__ void split_store(__nv_bfloat16 *hi, __nv_bfloat16 *lo, const float *v) {
   // 32 consecutive values -> 32 bf16 hi and 32 bf16 lo (64 bytes each)
   __align__(16) __nv_bfloat16 h[32];
@@ -140,9 +147,9 @@ __device__ __forceinline__ void split_store(__nv_bfloat16 *hi, __nv_bfloat16 *lo
   uint4 *dh = reinterpret_cast<uint4 *>(hi), *dl = reinterpret_cast<uint4 *>(lo);
   const uint4 *sh = reinterpret_cast<const uint4 *>(h), *sl = reinterpret_cast<const uint4 *>(l);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    dh[i] = sh[i];
-    dl[i] = sl[i];
+  for (int i = 0; i < 4; i += 2) {
+    st_v8(dh + i, sh[i], sh[i + 1]);
+    st_v8(dl + i, sl[i], sl[i + 1]);
   }
 }
 
@@ -276,9 +283,11 @@ __global__ void __launch_bounds__(128, 1)
       const int n = n0 + cc;
       const size_t o = (size_t)dz * g.M * g.N + (size_t)m * g.N + n;
       if (g.epi == TC_EPI_F32) {
-        float4 *dst = reinterpret_cast<float4 *>(g.Df + o);
+        uint4 *dst = reinterpret_cast<uint4 *>(g.Df + o);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        for (int i = 0; i < 8; i += 2)
+          st_v8(dst + i, make_uint4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]),
+                make_uint4(r[4 * i + 4], r[4 * i + 5], r[4 * i + 6], r[4 * i + 7]));
       } else if (g.epi == TC_EPI_SPLIT) {
         split_store(g.Dh + o, g.Dl + o, v);
       } else {
