@@ -1,9 +1,8 @@
 /*
  * hybro_place.h -- C ABI of the GB300 (sm_103a) electrostatic global-placement
  * library: the inner loop that every perturb-and-reoptimise round of Hybro
- * (Algorithm 1, "Execute DREAMPlace for global placement ... until it reaches
- * convergence") re-runs, plus the Shuffle perturbations and best-result
- * selection of Algorithm 1.
+ * re-runs (the global-placement step of Algorithm 1, run until it converges),
+ * plus the Shuffle perturbations and best-result selection of Algorithm 1.
  *
  * Conventions
  *  - Every function returns PLACE_OK (0) or a negative PLACE_E* code; the

@@ -16,8 +16,8 @@ definitions:
 * ``poisson`` -- the spectral (cosine-series) Poisson solve for potential and
   field, in a naive O(n^4) and a separable O(n^3) form.
 * ``placer`` -- the Nesterov/Lipschitz iteration with its lambda and gamma
-  schedules that minimises Eq. 2 ("Execute DREAMPlace ... until it reaches
-  convergence", Algorithm 1).
+  schedules that minimises Eq. 2 (the global-placement step of Algorithm 1,
+  run until it converges).
 * ``perturb`` -- SplitMix64 and the Shuffle / Shuffle (all) operators
   (Algorithm 1; Section 4.2).
 * ``hybro`` -- the Hybro loop and best-solution selection (Algorithm 1).

@@ -3,8 +3,8 @@ method with a Lipschitz step estimate), float64.
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
-Algorithm 1 runs "DREAMPlace for global placement ... until it reaches
-convergence"; Eq. 2 is the objective sum_e WL_e + lambda D, with lambda small
+Algorithm 1 runs a DREAMPlace global placement to convergence in every
+round; Eq. 2 is the objective sum_e WL_e + lambda D, with lambda small
 at the start (Section 3.1).  The optimiser, the schedules and the stop test are
 cited (ePlace, "... Nesterov's method") but not restated.  The reading below is
 the one the CUDA library implements; every constant is a field of ``Params``.
