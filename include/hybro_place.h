@@ -70,7 +70,9 @@ typedef struct place_netlist {
 
 /* Placement region [xl, xh) x [yl, yh).  xl, yl and the bin size must be
  * exact multiples of 2^-F for the fixed-point resolution F chosen at create
- * (any die with integer or dyadic-rational bounds qualifies). */
+ * (any die with integer or dyadic-rational bounds qualifies).  F is the
+ * largest value <= 24 with max(|xl|, |yl|, |xh|, |yh|, xh - xl, yh - yl) 2^F
+ * < 2^30 and (total cell area) 2^2F < 2^62. */
 typedef struct place_die { double xl, yl, xh, yh; } place_die;
 
 /* nx x ny density bins and the target density t of the overflow test
