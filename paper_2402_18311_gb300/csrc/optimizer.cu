@@ -111,11 +111,22 @@ __global__ void __launch_bounds__(kThreads, 4) k_cell_grad(Dev d, int copy0, int
   const float *ex = d.E + (size_t)c * 3 * d.G, *ey = ex + d.G;
   float n1 = 0.f, d1 = 0.f, dg2 = 0.f, dv2 = 0.f;
   const float *gxo = d.gx[par ^ 1] + cm, *gyo = d.gy[par ^ 1] + cm;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
+  // the next cell's position and size are loaded while this cell's field
+  // gather is in flight (the gather depends on the position)
+  const int stride = gridDim.x * blockDim.x;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float2 vnext = i < d.n_mov ? xy[i] : make_float2(0.f, 0.f);
+  float wnext = i < d.n_mov ? d.w[i] : 0.f, hnext = i < d.n_mov ? d.h[i] : 0.f;
+  for (; i < d.n_mov; i += stride) {
     // every load that does not depend on the position first, so they overlap
     const unsigned long long gs = ga[i];
-    const float2 vi = xy[i];
-    const float wi = d.w[i], hi = d.h[i];
+    const float2 vi = vnext;
+    const float wi = wnext, hi = hnext;
+    if (i + stride < d.n_mov) {
+      vnext = xy[i + stride];
+      wnext = d.w[i + stride];
+      hnext = d.h[i + stride];
+    }
     float np = 0.f, ar = 0.f, gxp = 0.f, gyp = 0.f, vpx = 0.f, vpy = 0.f;
     if (full) {
       np = d.npins[i]; ar = d.area[i];
