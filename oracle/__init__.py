@@ -20,5 +20,7 @@ definitions:
   run until it converges).
 * ``perturb`` -- SplitMix64 and the Shuffle / Shuffle (all) operators
   (Algorithm 1; Section 4.2).
+* ``wiremask`` -- the WireMask perturbation (Section 4.2): every movable macro
+  in turn to the grid position of least HPWL.
 * ``hybro`` -- the Hybro loop and best-solution selection (Algorithm 1).
 """

@@ -16,9 +16,11 @@ import numpy as np
 
 from . import perturb
 from . import placer as pl
+from . import wiremask
 
 SHUFFLE_MACRO = 0
 SHUFFLE_ALL = 1
+WIREMASK = 2
 
 
 def candidates(design, op):
@@ -58,7 +60,12 @@ def run(design, params: pl.Params, n_rounds, op=SHUFFLE_ALL, p=0.5, seed=0,
         hp = placer.hpwl(placer.vx, placer.vy)
         tau = placer.tau
         rounds.append((hp, tau, fx.copy(), fy.copy()))
-        if i < n_rounds:
+        if i < n_rounds and op == WIREMASK:
+            nx_, ny_ = wiremask.wiremask(fx, fy, design.w, design.h, design.net_ptr,
+                                         design.pin_cell, design.pin_dx, design.pin_dy, n,
+                                         design.is_macro, design.die, design.nx, design.ny)
+            sx, sy = nx_[:n], ny_[:n]
+        elif i < n_rounds:
             nx_, ny_ = perturb.shuffle(fx, fy, design.w, design.h, cand, p,
                                        seed + i, design.die)
             sx, sy = nx_[:n], ny_[:n]
