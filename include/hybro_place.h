@@ -43,6 +43,8 @@ extern "C" {
 /* Perturbation operators of Algorithm 1 (Section 4.2). */
 #define PLACE_SHUFFLE_MACRO 0 /* Shuffle: p% of the movable macros */
 #define PLACE_SHUFFLE_ALL 1   /* Shuffle (all): p% of all movable cells */
+#define PLACE_WIREMASK 2      /* WireMask: every movable macro in turn to the
+                                 grid position of least HPWL */
 
 /* Spectral-solve arithmetic. */
 #define PLACE_DCT_FP32 0   /* FP32 CUDA-core GEMMs (any grid, multiples of 16) */
@@ -57,7 +59,8 @@ typedef struct place_t place_t;
  * Net e owns pins net_ptr[e] .. net_ptr[e+1]-1; pin j sits on cell
  * pin_cell[j] at offset (pin_dx[j], pin_dy[j]) from the cell's lower-left.
  * net_w (nullable: all 1) weights a net in HPWL (Eq. 1) and WL (Eq. 2).
- * is_macro (nullable: none) marks cells that Shuffle may pick. */
+ * is_macro (nullable: none) marks the macros: Shuffle picks among the movable
+ * ones and WireMask moves them. */
 typedef struct place_netlist {
   int32_t n_cells, n_movable, n_nets, n_pins;
   const float *w, *h, *x0, *y0;
@@ -166,10 +169,26 @@ int place_step(place_t *h, int32_t n_iters, int32_t *converged);
  * handle or n < 1; nothing is launched then. */
 int place_step_multi(place_t *const *hs, int32_t n, int32_t n_iters, int32_t *converged);
 
-/* Perturb (the perturbation step of Algorithm 1; Section 4.2): Shuffle or
- * Shuffle (all) with strength p in [0, 1] applied to copy `copy` (-1: every copy, copy c using
- * seed + c), followed by a full optimiser reset of the perturbed copies.
- * Selection draws SplitMix64 keys from `seed`. */
+/* Perturb (the perturbation step of Algorithm 1; Section 4.2) copy `copy`
+ * (-1: every copy), then fully reset the optimiser of the perturbed copies.
+ *
+ * Shuffle / Shuffle (all): strength p in [0, 1].  Selection draws
+ * SplitMix64 keys from `seed`; with copy -1, copy c uses seed + c.
+ *
+ * PLACE_WIREMASK ignores p and seed; it is deterministic.  The movable macros
+ * (is_macro) move one at a time, by decreasing area (ties by index), each to
+ * the bin corner that minimises the weighted HPWL (Eq. 1) of its nets.  The
+ * other pins stay where they are; macros moved earlier count at their new
+ * places.  A macro stays inside the die and off every fixed cell and every
+ * macro moved before it; touching edges is allowed.  Ties go to the smallest
+ * L1 distance from the macro's old corner, then the lowest bin row, then the
+ * lowest column.  A macro with no free corner stays where it is.  The first
+ * WireMask call allocates device scratch: about
+ * 8 (K (nx + ny + 8 max_nets_per_macro) + 2 K nx ny / 256) bytes, freed by
+ * place_destroy.  It costs four kernel launches per macro.  A design
+ * without movable macros only resets the optimiser.  EINVAL on an unknown
+ * op or, for Shuffle, p outside [0, 1]; ENOMEM if the scratch cannot be
+ * allocated. */
 int place_perturb(place_t *h, int32_t op, float p, uint64_t seed, int32_t copy);
 
 /* Exact FP64 HPWL (Eq. 1) and overflow of every copy at its current
@@ -304,7 +323,7 @@ typedef struct place_server place_server;
 
 typedef struct place_job {
   int32_t kind;      /* PLACE_JOB_* */
-  int32_t op;        /* restart: PLACE_SHUFFLE_* */
+  int32_t op;        /* restart: PLACE_SHUFFLE_* or PLACE_WIREMASK */
   float p;           /* restart: strength */
   int32_t pad;
   uint64_t seed;     /* restart: SplitMix64 seed */

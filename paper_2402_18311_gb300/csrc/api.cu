@@ -92,6 +92,11 @@ struct place_t {
   cudaGraphExec_t exec = nullptr;
   CUtensorMap maps[16];              // tensor maps of the tcgen05 spectral path
   int n_cand_all = 0, n_cand_macro = 0;
+  // WireMask: host tables built at create, device copy made on first use
+  std::vector<int> wm_order, wm_ptr, wm_net, wm_obst;
+  int wm_max_nets = 1;
+  void *wm_mem = nullptr;
+  WmDev wm{};
   // Hybro bookkeeping (host)
   std::vector<double> best_hpwl, best_tau;
   std::vector<int> best_round;
@@ -127,6 +132,7 @@ int place_destroy(place_t *h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->mem) cudaFreeAsync(h->mem, h->stream);  // stream-ordered: no device-wide sync
+  if (h->wm_mem) cudaFreeAsync(h->wm_mem, h->stream);
   delete h;
   return PLACE_OK;
 }
@@ -322,6 +328,53 @@ int check_copy(const place_t *h, int copy, bool allow_all) {
   if (copy == -1 && allow_all) return PLACE_OK;
   if (copy < 0 || copy >= h->d.K) return fail(PLACE_EINVAL, "copy %d out of range [0,%d)", copy, h->d.K);
   return PLACE_OK;
+}
+
+// Device copy of the WireMask tables, and its scratch, made on the first
+// WireMask call and freed with the handle (stream-ordered).
+int ensure_wiremask(place_t *h) {
+  if (h->wm_mem) return PLACE_OK;
+  const Dev &d = h->d;
+  WmDev &w = h->wm;
+  w.n_macros = (int)h->wm_order.size();
+  w.n_fixed = d.n_cells - d.n_mov;
+  w.max_nets = h->wm_max_nets;
+  w.nblk = wm_select_blocks(d.G);
+  const size_t K = d.K;
+  Arena a;
+  int *order = nullptr, *mptr = nullptr, *mnet = nullptr, *obst = nullptr;
+  auto lay = [&]() {
+    order = a.take<int>(w.n_macros);
+    mptr = a.take<int>(w.n_macros + 1);
+    mnet = a.take<int>(std::max<size_t>(h->wm_net.size(), 1));
+    obst = a.take<int>(h->wm_obst.size());
+    w.box = a.take<double>(K * w.max_nets * 8);
+    w.fx = a.take<double>(K * d.nx);
+    w.fy = a.take<double>(K * d.ny);
+    w.bobj = a.take<double>(K * w.nblk);
+    w.bdist = a.take<double>(K * w.nblk);
+    w.bidx = a.take<int>(K * w.nblk);
+  };
+  lay();
+  void *mem = nullptr;
+  cudaError_t e = cudaMallocAsync(&mem, a.off + 256, h->stream);
+  if (e != cudaSuccess)
+    return fail(PLACE_ENOMEM, "WireMask scratch of %zu bytes: %s", a.off, cudaGetErrorString(e));
+  h->wm_mem = mem;
+  a = Arena();
+  a.base = (char *)mem;
+  lay();
+  w.order = order; w.mptr = mptr; w.mnet = mnet; w.obst = obst;
+  auto up = [&](int *dst, const std::vector<int> &src) -> int {
+    if (!src.empty())
+      CK(cudaMemcpyAsync(dst, src.data(), sizeof(int) * src.size(), cudaMemcpyHostToDevice, h->stream));
+    return PLACE_OK;
+  };
+  int rc = up(order, h->wm_order);
+  if (!rc) rc = up(mptr, h->wm_ptr);
+  if (!rc) rc = up(mnet, h->wm_net);
+  if (!rc) rc = up(obst, h->wm_obst);
+  return rc;
 }
 
 void host_dct_tables(int n, double h, std::vector<float> &C, std::vector<float> &CT,
@@ -537,6 +590,35 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   h->n_cand_all = Mv;
   h->n_cand_macro = 0;
   for (int i = 0; i < Mv; ++i) h->n_cand_macro += macro[i];
+  if (h->n_cand_macro > 0) {
+    // WireMask tables: the movable macros by decreasing area (exact in
+    // double; ties keep index order), each macro's nets as library indices
+    // in netlist order, and the obstacle list (fixed cells, then the macros)
+    std::vector<int> lib_of(E);
+    for (int ne = 0; ne < E; ++ne) lib_of[order[ne]] = ne;
+    std::vector<int> &mo = h->wm_order;
+    for (int i = 0; i < Mv; ++i)
+      if (macro[i]) mo.push_back(i);
+    std::stable_sort(mo.begin(), mo.end(), [&](int a, int b) {
+      return (double)nl->w[a] * (double)nl->h[a] > (double)nl->w[b] * (double)nl->h[b];
+    });
+    std::vector<int> slot(C, -1);
+    for (size_t t = 0; t < mo.size(); ++t) slot[mo[t]] = (int)t;
+    std::vector<std::vector<int>> nets(mo.size());
+    for (int e = 0; e < E; ++e)
+      for (int j = nl->net_ptr[e]; j < nl->net_ptr[e + 1]; ++j) {
+        const int t = slot[nl->pin_cell[j]];
+        if (t >= 0 && (nets[t].empty() || nets[t].back() != lib_of[e])) nets[t].push_back(lib_of[e]);
+      }
+    h->wm_ptr.assign(1, 0);
+    for (size_t t = 0; t < mo.size(); ++t) {
+      h->wm_net.insert(h->wm_net.end(), nets[t].begin(), nets[t].end());
+      h->wm_ptr.push_back((int)h->wm_net.size());
+      h->wm_max_nets = std::max(h->wm_max_nets, (int)nets[t].size());
+    }
+    for (int i = Mv; i < C; ++i) h->wm_obst.push_back(i);
+    h->wm_obst.insert(h->wm_obst.end(), mo.begin(), mo.end());
+  }
 
   // launch plan
   d.cell_blocks = std::max(1, std::min((Mv + kThreads - 1) / kThreads, kMaxCellBlocks));
@@ -917,6 +999,15 @@ int place_eval_hpwl_overflow(place_t *h, double *hpwl, double *overflow) {
 int place_perturb(place_t *h, int32_t op, float p, uint64_t seed, int32_t copy) {
   int rc = check_copy(h, copy, true);
   if (rc) return rc;
+  if (op == PLACE_WIREMASK) {
+    const int c0 = copy < 0 ? 0 : copy, n = copy < 0 ? h->d.K : 1;
+    if (!h->wm_order.empty()) {
+      if ((rc = ensure_wiremask(h))) return rc;
+      launch_wiremask(h->d, h->wm, h->wm_ptr.data(), c0, n, h->stream);
+      CKL();
+    }
+    return enqueue_reset(h, c0, n);
+  }
   if (op != PLACE_SHUFFLE_MACRO && op != PLACE_SHUFFLE_ALL) return fail(PLACE_EINVAL, "unknown perturbation op %d", op);
   if (!(p >= 0.f && p <= 1.f)) return fail(PLACE_EINVAL, "p must be in [0, 1]");
   Dev &d = h->d;

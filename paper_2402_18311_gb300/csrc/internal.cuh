@@ -143,6 +143,22 @@ struct Dev {
   int wa_big_cap;             // pins of a > 256-pin net kept in shared memory
 };
 
+// WireMask tables (built at create) and scratch (allocated on first use).
+struct WmDev {
+  int n_macros;         // movable macros
+  int n_fixed;          // fixed cells: the obstacles every macro avoids
+  int max_nets;         // most nets on one macro (at least 1)
+  int nblk;             // candidate blocks per copy
+  const int *order;     // [n_macros] macros by decreasing area, ties by index
+  const int *mptr;      // [n_macros + 1] macro t's nets: mnet[mptr[t] .. mptr[t+1])
+  const int *mnet;      // library net indices, in netlist order per macro
+  const int *obst;      // [n_fixed + n_macros] fixed cells, then `order`
+  double *box;          // [K][max_nets][8] per-net extents of the current macro
+  double *fx, *fy;      // [K][nx], [K][ny] wire-mask axes
+  double *bobj, *bdist; // [K][nblk] per-block winners
+  int *bidx;            // [K][nblk]
+};
+
 // WA gradient sums per movable cell.  Each pin adds its (gx, gy), rounded to
 // the fixed-point grid 2^-Fg, to its cell as the one 64-bit integer
 // qy * 2^32 + qx.  Integer addition is exact and independent of order, so the
@@ -207,6 +223,9 @@ void launch_reset(const Dev &d, int copy0, int ncopy, cudaStream_t st);
 void launch_reduce_slot(const Dev &d, int slot, int nvals, int copy0, int ncopy, cudaStream_t st);
 int launch_shuffle(const Dev &d, int copy, int op, float p, uint64_t seed, cudaStream_t st);
 void launch_shuffle_finish(const Dev &d, int copy, int kcount, cudaStream_t st);
+int wm_select_blocks(int G);
+void launch_wiremask(const Dev &d, const WmDev &w, const int *mptr_host, int copy0, int ncopy,
+                     cudaStream_t st);
 
 // hooks for the job server (api.cu)
 int step_async(place_t *h, int n, int *stopped_host, cudaEvent_t ev);

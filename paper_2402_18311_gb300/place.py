@@ -25,6 +25,7 @@ PLACE_ETIMEOUT = -5
 PLACE_EINTERNAL = -6
 PLACE_SHUFFLE_MACRO = 0
 PLACE_SHUFFLE_ALL = 1
+PLACE_WIREMASK = 2
 PLACE_DCT_FP32 = 0
 PLACE_DCT_BF16X3 = 1
 PLACE_STAGES = ("density", "spectral", "wirelength", "cellgrad", "update")
