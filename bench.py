@@ -250,6 +250,7 @@ def run_ours(args):
     restarts = None
     if not args.no_restarts:
         restarts = run_restarts(args, place, torch)
+        restarts["hybro_wiremask"] = run_wiremask(args, place, torch)
     serving = None
     if args.serving_jobs > 0:
         serving = run_serving(args, place, args.serving_jobs, 10_000, args.serving_max_cells)
@@ -410,6 +411,55 @@ def run_restarts(args, place, torch, K=32, p=0.5):
                               "best_hpwl": float(hp_r[br]), "best_overflow": float(tau_r[br]),
                               "median_hpwl": float(np.median(hp_r)),
                               "hybro_best_over_random_best": float(hp_b[bb] / hp_r[br])}}
+
+
+def run_wiremask(args, place, torch, rounds=3, reps=5):
+    """Hybro-WireMask (Algorithm 1 with the WireMask perturbation of Section
+    4.2) on the mixed-size 210k-cell design with 32 movable macros.  Measures
+    one WireMask pass on a converged placement, then `rounds` Hybro rounds
+    with WireMask and with Shuffle (all) (p = 0.5) from that placement, on
+    one copy, with the best HPWL of each."""
+    d = synth.medium_mixed_210k(0)
+    prm = place.place_default_params(tau_stop=0.07, max_iters=3000, dct_mode=args.dct, n_copies=1)
+    h = place.place_create(d, prm)
+    conv = np.zeros(1, np.int32)
+    while not conv.all():
+        place.place_step(h, 50, conv)
+    x0 = torch.empty(d.n_cells, dtype=torch.float32, device="cuda")
+    y0 = torch.empty(d.n_cells, dtype=torch.float32, device="cuda")
+    place.place_get_positions(h, 0, x0, y0)
+    hp0 = np.empty(1); tau0 = np.empty(1)
+    place.place_eval_hpwl_overflow(h, hp0, tau0)
+    # the first pass allocates the scratch; the timed passes each restore the
+    # converged placement (a device copy plus an optimiser reset) and run
+    # WireMask (four launches per macro)
+    place.place_set_positions(h, 0, x0, y0)
+    place.place_perturb(h, place.PLACE_WIREMASK, 0.0, 0, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        place.place_set_positions(h, 0, x0, y0)
+        place.place_perturb(h, place.PLACE_WIREMASK, 0.0, 0, 0)
+    torch.cuda.synchronize()
+    t_wm = (time.perf_counter() - t0) / reps
+    hp1 = np.empty(1); tau1 = np.empty(1)
+    place.place_eval_hpwl_overflow(h, hp1, tau1)
+    out = {"workload": "medium_mixed_210k: medium_210k with 32 movable macros of 16-64 units",
+           "macros": int(d.is_macro[:d.n_movable].sum()), "grid": f"{d.nx}x{d.ny}",
+           "wiremask_pass_ms": 1e3 * t_wm, "launches_per_pass": 4 * 32,
+           "converged_hpwl": float(hp0[0]), "converged_overflow": float(tau0[0]),
+           "hpwl_after_wiremask": float(hp1[0]), "rounds": rounds}
+    for name, op, p in (("wiremask", place.PLACE_WIREMASK, 0.0),
+                        ("shuffle_all", place.PLACE_SHUFFLE_ALL, 0.5)):
+        place.place_set_positions(h, 0, x0, y0)
+        bh = np.empty(1); bt = np.empty(1); br = np.empty(1, np.int32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        place.place_hybro(h, rounds, op, p, 0, 0.1, bh, bt, br)
+        out[name] = {"best_hpwl": float(bh[0]), "best_overflow": float(bt[0]),
+                     "best_round": int(br[0]), "seconds": time.perf_counter() - t0}
+    place.place_destroy(h)
+    return out
 
 
 def serving_trace(n_jobs, min_cells, max_cells, seed=0):

@@ -256,6 +256,31 @@ def mixed_size_1k(seed=0, n_macros=20):
     return d
 
 
+def _enlarge_into_macros(d, rng, n_macros, lo, hi):
+    """Turn n_macros random movable cells into movable macros of lo..hi units
+    a side, flagged, their lower-left corners moved so that the centres stay
+    and the macros stay inside the die.  Pin offsets stay where they were,
+    inside the enlarged cells."""
+    idx = rng.choice(d.n_movable, n_macros, replace=False)
+    w0, h0 = d.w[idx].copy(), d.h[idx].copy()
+    d.w[idx] = rng.integers(lo, hi + 1, n_macros).astype(np.float32)
+    d.h[idx] = rng.integers(lo, hi + 1, n_macros).astype(np.float32)
+    xl, yl, xh, yh = d.die
+    d.x[idx] = np.clip(d.x[idx] - 0.5 * (d.w[idx] - w0), xl, xh - d.w[idx]).astype(np.float32)
+    d.y[idx] = np.clip(d.y[idx] - 0.5 * (d.h[idx] - h0), yl, yh - d.h[idx]).astype(np.float32)
+    d.is_macro[idx] = 1
+    return d
+
+
+def medium_mixed_210k(seed=0, n_macros=32):
+    """medium_210k with n_macros of its movable cells enlarged into movable
+    macros of 16-64 units a side (4-16 bins), flagged as macros: the
+    mixed-size case where Shuffle (macros) and WireMask have work."""
+    d = _enlarge_into_macros(medium_210k(seed), np.random.default_rng(seed + 11), n_macros, 16, 64)
+    d.name = "medium_mixed_210k"
+    return d
+
+
 def medium_210k(seed=0):
     """210k movable cells on a 2000x2000 die, 10 fixed macros covering 20% of
     the area, 220k nets plus 0.1% nets of degree U[100, 2000], 512x512 bins,

@@ -28,3 +28,20 @@ def test_designs_are_reproducible():
     a, b = synth.tiny_1k(0), synth.tiny_1k(0)
     for f in ("w", "h", "x", "y", "net_ptr", "pin_cell", "pin_dx", "pin_dy"):
         np.testing.assert_array_equal(getattr(a, f), getattr(b, f))
+
+
+def test_medium_mixed_has_movable_macros_inside_the_die():
+    base, d = synth.medium_210k(0), synth.medium_mixed_210k(0)
+    n = d.n_movable
+    mac = np.nonzero(d.is_macro[:n])[0]
+    assert mac.size == 32
+    assert np.all((d.w[mac] >= 16) & (d.w[mac] <= 64) & (d.h[mac] >= 16) & (d.h[mac] <= 64))
+    xl, yl, xh, yh = d.die
+    assert np.all(d.x[mac] >= xl) and np.all(d.x[mac] + d.w[mac] <= xh)
+    assert np.all(d.y[mac] >= yl) and np.all(d.y[mac] + d.h[mac] <= yh)
+    # everything else is the medium design, and the fixed macros stay flagged
+    other = np.setdiff1d(np.arange(d.n_cells), mac)
+    for f in ("w", "h", "x", "y"):
+        np.testing.assert_array_equal(getattr(d, f)[other], getattr(base, f)[other])
+    np.testing.assert_array_equal(d.is_macro[n:], base.is_macro[n:])
+    np.testing.assert_array_equal(d.pin_cell, base.pin_cell)
