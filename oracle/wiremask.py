@@ -64,11 +64,8 @@ def grid_corners(lo, hi, n):
 def nets_of(net_ptr, pin_cell, m):
     """Indices of the nets holding a pin of cell m, increasing."""
     net_ptr = np.asarray(net_ptr, np.int64)
-    out = []
-    for e in range(net_ptr.shape[0] - 1):
-        if np.any(np.asarray(pin_cell[net_ptr[e]:net_ptr[e + 1]]) == m):
-            out.append(e)
-    return out
+    net_of_pin = np.repeat(np.arange(net_ptr.shape[0] - 1), np.diff(net_ptr))
+    return np.unique(net_of_pin[np.asarray(pin_cell) == m]).tolist()
 
 
 def axis_mask(corners, nets, net_ptr, pin_cell, pin_d, pos, m, net_w):
@@ -117,16 +114,15 @@ def wiremask(x, y, w, h, net_ptr, pin_cell, pin_dx, pin_dy, n_movable, is_macro,
             by = (Y < oy + h64[o]) & (oy < Y + h64[m])
             ok &= ~(by[:, None] & bx[None, :])
         dist = np.abs(Y - float(y[m]))[:, None] + np.abs(X - float(x[m]))[None, :]
-        best = None
-        for j, i in zip(*np.nonzero(ok)):  # row-major: increasing (j, i)
-            key = (obj[j, i], dist[j, i])
-            if best is None or key < best[0]:
-                best = (key, int(i), int(j))
+        # lexicographic minimum of (obj, dist, j, i) over the free candidates:
+        # flat row-major index q = j nx + i orders (j, i)
+        q = np.flatnonzero(ok)
         chosen = None
-        if best is not None:
-            chosen = (best[1], best[2])
-            x[m] = X[best[1]]
-            y[m] = Y[best[2]]
+        if q.size:
+            first = q[np.lexsort((q, dist.ravel()[q], obj.ravel()[q]))[0]]
+            chosen = (int(first % nx), int(first // nx))
+            x[m] = X[chosen[0]]
+            y[m] = Y[chosen[1]]
         if trace is not None:
             trace.append((m, fx, fy, chosen))
         obstacles.append(m)

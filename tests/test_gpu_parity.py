@@ -477,6 +477,26 @@ def test_wiremask_weighted_nets_and_fixed_macros():
         h.close()
 
 
+def test_wiremask_bit_exact_medium_mixed_converged():
+    # the bench's WireMask workload: 210k cells, 32 movable macros, 512 x 512
+    # bins, from the converged placement the bench perturbs
+    d = synth.medium_mixed_210k(0)
+    h = Handle(d, tau_stop=0.07, max_iters=3000, dct_mode=place.PLACE_DCT_BF16X3)
+    try:
+        conv = np.zeros(1, np.int32)
+        while not conv.all():
+            place.place_step(h.h, 50, conv)
+        x, y = h.pos()
+        place.place_perturb(h.h, place.PLACE_WIREMASK, 0.0, 0, 0)
+        gx, gy = h.pos()
+        ox, oy = _wiremask_oracle(d, x, y)
+        np.testing.assert_array_equal(gx, ox)
+        np.testing.assert_array_equal(gy, oy)
+        assert ((gx != x) | (gy != y)).sum() > 0
+    finally:
+        h.close()
+
+
 def test_wiremask_without_movable_macros_only_resets():
     d = synth.tiny_1k(0)
     h = Handle(d, tau_stop=-1.0, max_iters=300)
