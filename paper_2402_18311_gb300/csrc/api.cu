@@ -68,7 +68,9 @@ int degree_class(int deg) {
   return 4;
 }
 constexpr int kNetsPerBlock[4] = {256, 64, 16, 8};
-constexpr int kBigCapMax = 12288;  // pins of a big net kept in shared memory (96 KB)
+// pins of a big net kept in shared memory: 3072 (24 KB) is the most that
+// still lets eight 256-thread blocks share an SM; longer nets re-gather the rest
+constexpr int kBigCapMax = 3072;
 constexpr int kMaxBigNetBlocks = 8192;  // one block per net above 256 pins, up to this many
 
 bool is_integer(double v) { return std::floor(v) == v && std::isfinite(v); }

@@ -19,9 +19,9 @@
 // Nets are grouped by degree at create: one thread per net up to 4 pins,
 // groups of 4 lanes up to 16 pins, 16 lanes up to 64, a warp up to 256 (the
 // pins of these nets stay in registers, 4 or 8 per lane), and a block of 256
-// threads beyond, which keeps the net's
-// coordinates in shared memory between its three passes.  Positions are
-// interleaved (x, y), so every pin costs one gather.  Each pin's gradient is
+// threads beyond, which keeps the coordinates of up to 3072 of the net's pins
+// in shared memory between its three passes.  Positions are interleaved
+// (x, y), so every pin costs one gather.  Each pin's gradient is
 // added to its cell as a packed fixed-point integer (add_pin_grad): one
 // 64-bit reduction per pin into an array that stays in L2, no floating-point
 // atomics, deterministic results.
@@ -273,9 +273,10 @@ __device__ __forceinline__ void block_all(float (&v)[N], float *sm) {
 }
 
 // One block per net (degree > 256), the nets in descending degree so the
-// longest start first.  Net-relative pin coordinates are kept in dynamic
-// shared memory when the net fits `cap` pins; longer nets reload pins from
-// global memory in every pass.
+// longest start first.  The net-relative coordinates of a net's first `cap`
+// pins stay in dynamic shared memory between the three passes; pins beyond
+// `cap` are gathered again in each pass.  A small cap keeps more blocks
+// resident, which matters more than the re-gathers of the longest nets.
 __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, int eval,
                                                     const float *gamma_ovr, int cap) {
   extern __shared__ float dyn[];
@@ -291,7 +292,6 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
   float hp_acc = 0.f, wl_acc = 0.f;
   for (int e = d.cls_begin[cls] + blockIdx.x; e < d.cls_begin[cls + 1]; e += gridDim.x) {
     const int p0 = d.net_ptr[e], p1 = d.net_ptr[e + 1];
-    const bool cached = (p1 - p0) <= cap;
     const float wn = d.net_w ? d.net_w[e] : 1.0f;
     const float2 o0 = d.pin_off[p0];
     const float2 v0 = xy[d.pin_cell[p0]];
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
       const float2 o = d.pin_off[j];
       const float2 v = xy[d.pin_cell[j]];
       const float px = (v.x - rx) + (o.x - rdx), py = (v.y - ry) + (o.y - rdy);
-      if (cached) { spx[j - p0] = px; spy[j - p0] = py; }
+      if (j - p0 < cap) { spx[j - p0] = px; spy[j - p0] = py; }
       ext[0] = fmaxf(ext[0], px); ext[1] = fmaxf(ext[1], -px);
       ext[2] = fmaxf(ext[2], py); ext[3] = fmaxf(ext[3], -py);
     }
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
 #pragma unroll 4
     for (int j = p0 + threadIdx.x; j < p1; j += kBigNet) {
       float px, py;
-      if (cached) {
+      if (j - p0 < cap) {
         px = spx[j - p0]; py = spy[j - p0];
       } else {
         const float2 o = d.pin_off[j];
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
     for (int j = p0 + threadIdx.x; j < p1; j += kBigNet) {
       float px, py;
       const int cj = d.pin_cell[j];
-      if (cached) {
+      if (j - p0 < cap) {
         px = spx[j - p0]; py = spy[j - p0];
       } else {
         const float2 o = d.pin_off[j];
