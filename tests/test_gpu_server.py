@@ -105,3 +105,39 @@ def test_budget_bounds_admission():
     budget2 = 2 * need + need // 5
     res2, (peak_bytes2, peak_active2) = run_trace(8, budget=budget2)
     assert len(res2) == 7 and peak_bytes2 <= budget2 and 1 <= peak_active2 <= 2
+
+
+def test_wiremask_restart_job_equals_plain_handle_run():
+    # a restart job with the WireMask perturbation (Section 4.2) perturbs its
+    # parent's converged result exactly as place_perturb on a plain handle
+    d = synth.scaled(6000, 128, seed=14, name="m")
+    rng = np.random.default_rng(14)
+    mac = rng.choice(d.n_movable, 10, replace=False)
+    d.w[mac] = rng.integers(6, 24, 10).astype(np.float32)
+    d.h[mac] = rng.integers(6, 24, 10).astype(np.float32)
+    d.x[mac] = np.minimum(d.x[mac], d.die[2] - d.w[mac]).astype(np.float32)
+    d.y[mac] = np.minimum(d.y[mac], d.die[3] - d.h[mac]).astype(np.float32)
+    d.is_macro[mac] = 1
+    s = place.Server(8 << 30, 4, iters_per_tick=16)
+    try:
+        a = s.submit(d, params())
+        b = s.submit(d, params(), kind=place.PLACE_JOB_RESTART, parent=a, op=place.PLACE_WIREMASK)
+        s.run(timeout_s=300)
+        res = {r.id: r for r in s.results()}
+    finally:
+        s.close()
+    h = place.place_create(d, params())
+    try:
+        conv = np.zeros(1, np.int32)
+        hp = np.empty(1); tv = np.empty(1)
+        for phase in range(2):
+            if phase == 1:
+                place.place_perturb(h, place.PLACE_WIREMASK, 0.0, 0, 0)
+                conv[:] = 0
+            while not conv[0]:
+                place.place_step(h, 16, conv)
+            place.place_eval_hpwl_overflow(h, hp, tv)
+            r = res[a if phase == 0 else b]
+            assert r.hpwl == hp[0] and r.overflow == tv[0], phase
+    finally:
+        place.place_destroy(h)
