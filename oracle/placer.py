@@ -28,6 +28,17 @@ Iteration k at reference point v_k (movable lower-left corners):
 with a_0 = 1, u_0 = v_0 = the start, tau_{-1} = tau(v_0),
 dref = hpwl_ref * n_nets * w_bin, w_bin = sqrt(bin_w * bin_h), and clamp
 keeping each cell inside the die (x in [xl, xh - w]).
+
+Optional backtracking (``max_backtracks`` > 0; the step-length prediction
+with backtracking of ePlace's Nesterov method, which the paper cites but does
+not restate).  At k >= 1 the estimate alpha_k above is also a test of the
+step that led to v_k.  If alpha_k < 0.95 alpha_{k-1}, that step was too long.
+At most ``max_backtracks`` times in a row, v_k is rejected:
+* alpha_{k-1} := alpha_k;
+* u_k and v_k are recomputed from v_{k-1}, u_{k-1}, g_{k-1}, a_{k-1};
+* v_k is evaluated again.
+lambda, gamma, the HPWL and overflow references and k advance only when v_k
+is accepted.  The overflow stop test applies at every evaluated point.
 """
 from __future__ import annotations
 
@@ -60,6 +71,17 @@ def nesterov_update(v, u, g, a, alpha, clamp):
     return u_new, v_new, a_new
 
 
+BACKTRACK_RATIO = 0.95
+
+
+def backtrack(alpha_hat, alpha_used, n_back, max_back, ratio=BACKTRACK_RATIO):
+    """True when the step of length alpha_used that led to the current point
+    is to be redone with alpha_hat: the step length estimated at the point
+    is below ratio * alpha_used, and fewer than max_back steps have been
+    redone in a row."""
+    return max_back > 0 and n_back < max_back and alpha_hat < ratio * alpha_used
+
+
 def lambda_multiplier(d_hpwl, dref, mu_base, mu_lo, mu_hi):
     """Density-weight growth factor mu = clamp(mu_base^(1 - dHPWL/dref),
     mu_lo, mu_hi): lambda grows fastest while the wirelength is flat and
@@ -80,6 +102,7 @@ class Params:
     tau_stop: float = 0.07
     max_iters: int = 1000
     constant_gamma: float = 0.0  # > 0: use this gamma every iteration
+    max_backtracks: int = 0      # > 0: redo a too-long step at most this often in a row
 
 
 class Placer:
@@ -167,6 +190,11 @@ class Placer:
         self.lam = 0.0
         self.alpha = 0.0
         self.vpx = self.vpy = self.gpx = self.gpy = None
+        self.upx = self.upy = None
+        self.a_prev = 1.0
+        self.n_back = 0          # steps redone in a row
+        self.n_back_total = 0
+        self.evals = 0
         self.hpwl_prev = 0.0
         self.tau_prev = self.overflow(self.density_map(x, y))
         self.tau = self.tau_prev
@@ -175,13 +203,15 @@ class Placer:
         self.history = []
 
     def step(self):
-        """One iteration at v_k.  Returns False once stopped."""
+        """One evaluation at the current point: an iteration, or with
+        backtracking a redone step.  Returns False once stopped."""
         if self.stopped:
             return False
         if self.k >= self.p.max_iters:
             self.stopped = True
             return False
         p = self.p
+        self.evals += 1
         gamma = self.gamma(self.tau_prev)
         vx, vy = self.vx, self.vy
         wl, gwx, gwy = self.wirelength(vx, vy, gamma)
@@ -209,6 +239,16 @@ class Placer:
         else:
             alpha = lipschitz_step((vx, vy), (self.vpx, self.vpy), (gx, gy),
                                    (self.gpx, self.gpy), self.alpha)
+            if backtrack(alpha, self.alpha, self.n_back, p.max_backtracks):
+                # redo the step that led here, shorter, from the saved state
+                self.n_back += 1
+                self.n_back_total += 1
+                self.alpha = alpha
+                (self.ux, self.uy), (self.vx, self.vy), _ = nesterov_update(
+                    (self.vpx, self.vpy), (self.upx, self.upy), (self.gpx, self.gpy),
+                    self.a_prev, alpha, self.clamp)
+                return True
+            self.n_back = 0
         self.alpha = alpha
         (nux, nuy), (nvx, nvy), a_new = nesterov_update(
             (vx, vy), (self.ux, self.uy), (gx, gy), self.a, alpha, self.clamp)
@@ -218,6 +258,7 @@ class Placer:
         self.hpwl_prev = hp
         self.tau_prev = tau
         self.vpx, self.vpy, self.gpx, self.gpy = vx, vy, gx, gy
+        self.upx, self.upy, self.a_prev = self.ux, self.uy, self.a
         self.ux, self.uy = nux, nuy
         self.vx, self.vy = nvx, nvy
         self.a = a_new

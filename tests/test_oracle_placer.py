@@ -105,3 +105,54 @@ def test_lambda_schedule_follows_hpwl_in_placer():
         mu = pl.lambda_multiplier(dh, p.dref, 1.1, 0.95, 1.05)
         assert h[k][4] == pytest.approx(h[k - 1][4] * mu, rel=1e-14)
     assert h[1][4] > 0 and h[0][4] == 0.0
+
+
+def test_backtrack_decision_special_cases():
+    assert not pl.backtrack(0.1, 1.0, 0, 0)           # off
+    assert pl.backtrack(0.1, 1.0, 0, 1)
+    assert not pl.backtrack(0.1, 1.0, 1, 1)           # cap reached
+    assert not pl.backtrack(0.95, 1.0, 0, 3)          # exactly at the ratio: accept
+    assert pl.backtrack(0.95 - 1e-12, 1.0, 0, 3)
+    assert not pl.backtrack(2.0, 1.0, 0, 3)           # longer estimates never reject
+
+
+def test_backtracking_on_a_quadratic_redoes_the_first_step_once():
+    # f = c/2 |x|^2, g = c x: every step-length estimate is 1/c exactly.  A
+    # first step of 3/c is too long; the estimate at the point it reaches
+    # rejects it, and the redone step of 1/c lands on the minimum.
+    c = 7.0
+    v0 = (np.array([1.0, -2.0, 0.5]),)
+    u, v, a, alpha = v0, v0, 1.0, 3.0 / c
+    g = (c * v[0],)
+    u1, v1, a1 = pl.nesterov_update(v, u, g, a, alpha, _noclamp)
+    g1 = (c * v1[0],)
+    alpha_hat = pl.lipschitz_step(v1, v, g1, g, alpha)
+    assert alpha_hat == pytest.approx(1.0 / c, rel=1e-14)
+    assert pl.backtrack(alpha_hat, alpha, 0, 4)
+    u1, v1, a1 = pl.nesterov_update(v, u, g, a, alpha_hat, _noclamp)
+    np.testing.assert_allclose(u1[0], 0.0, atol=1e-15)
+    np.testing.assert_allclose(v1[0], 0.0, atol=1e-15)   # a_0 = 1: no momentum yet
+
+
+def test_placer_backtracking_invariants():
+    d = synth.tiny_1k(0)
+    base = pl.Placer(d, pl.Params(tau_stop=-1.0, max_iters=120))
+    base.run(120)
+    off = pl.Placer(d, pl.Params(tau_stop=-1.0, max_iters=120, max_backtracks=0))
+    off.run(120)
+    assert off.history == base.history and off.n_back_total == 0
+    on = pl.Placer(d, pl.Params(tau_stop=-1.0, max_iters=120, max_backtracks=2))
+    alphas, backs = [], []
+    for _ in range(200):
+        k, nb = on.k, on.n_back
+        if not on.step():
+            break
+        alphas.append((k, on.k, on.alpha, nb, on.n_back))
+    assert on.evals == on.k + on.n_back_total and on.n_back_total > 0
+    for (k0, k1, a, nb0, nb1), (k0n, k1n, an, _, nbn) in zip(alphas, alphas[1:]):
+        if k1n == k1 + 1 and k1 >= 1:
+            # accepted: its estimate passed the test, or the cap was reached
+            assert an >= 0.95 * a or nb1 == 2
+        if k1n == k1:
+            # a redone step: shorter, counted, at most twice in a row
+            assert an < 0.95 * a and nbn == nb1 + 1 <= 2
