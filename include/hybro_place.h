@@ -91,7 +91,14 @@ typedef struct place_bins { int32_t nx, ny; float target_density; } place_bins;
  *   lambda_{k+1} = lambda_k * clamp(mu_base^(1 - dHPWL/dref), mu_lo, mu_hi),
  *     dref = hpwl_ref * n_nets * w_bin
  *   alpha_0 = alpha0 * w_bin / rms(g_0); then |dv| / |dg|
- *   stop when overflow <= tau_stop (tau_stop < 0: never) or after max_iters. */
+ *   stop when overflow <= tau_stop (tau_stop < 0: never) or after max_iters.
+ * Backtracking (max_backtracks > 0; ePlace's step-length prediction with
+ * backtracking).  At k >= 1 the estimate |v_k - v_{k-1}| / |g_k - g_{k-1}|
+ * also tests the step that led to v_k.  Below 0.95 times that step's length,
+ * the step is redone from v_{k-1} with the estimate as its length, at most
+ * max_backtracks times in a row.  lambda, gamma and k advance only on accepted
+ * steps.  The overflow stop test applies at every evaluated point.  It costs
+ * 8 bytes per movable cell and copy. */
 typedef struct place_params {
   int32_t n_copies;       /* K >= 1 */
   float gamma_base;       /* 4 */
@@ -103,6 +110,8 @@ typedef struct place_params {
   int32_t max_iters;      /* 1000 */
   float constant_gamma;   /* > 0: fixed gamma (tests) */
   int32_t dct_mode;       /* PLACE_DCT_* */
+  int32_t max_backtracks; /* 0 (off) .. 64: redo a too-long step at most this
+                             often in a row (see below) */
 } place_params;
 
 /* Read-only facts about a handle. */
@@ -121,7 +130,7 @@ typedef struct place_state {
   int32_t iter;        /* iterations done since the last reset */
   int32_t converged;   /* 1: stopped by the overflow test */
   int32_t stopped;     /* 1: converged or reached max_iters */
-  int32_t pad;
+  int32_t backtracks;  /* steps redone since the last reset */
   double lambda, gamma, alpha, a;
   double overflow;     /* tau at the current reference point */
   double hpwl_wa;      /* HPWL measured in the last iteration's WA pass */
@@ -153,7 +162,8 @@ int place_destroy(place_t *h);
 int place_get_info(const place_t *h, place_info *out);
 
 /* Run up to n_iters Nesterov iterations of Eq. 2 on every active copy (the
- * global-placement step of Algorithm 1).  A copy stops updating once
+ * global-placement step of Algorithm 1).  With backtracking, n_iters counts
+ * gradient evaluations, and a redone step is one of them.  A copy stops updating once
  * converged or at max_iters; the others continue.  converged (nullable, host [K]) receives
  * the stopped flags, which synchronises the stream; with NULL the call is
  * asynchronous. */

@@ -122,6 +122,7 @@ void place_default_params(place_params *p) {
   p->max_iters = 1000;
   p->constant_gamma = 0.0f;
   p->dct_mode = PLACE_DCT_FP32;
+  p->max_backtracks = 0;
 }
 
 int place_destroy(place_t *h) {
@@ -170,6 +171,8 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.gwy = a.take<float>(K * Mv);
   d.gdx = a.take<float>(K * Mv);
   d.gdy = a.take<float>(K * Mv);
+  d.upx = d.prm.max_backtracks > 0 ? a.take<float>(K * Mv) : nullptr;
+  d.upy = d.prm.max_backtracks > 0 ? a.take<float>(K * Mv) : nullptr;
   d.gacc = a.take<unsigned long long>(K * std::max<size_t>(Mv, 1));
   d.M = a.take<unsigned long long>(K * G);
   d.Fmap = a.take<long long>(G);
@@ -417,6 +420,8 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     return fail(PLACE_EINVAL, "null netlist array");
   if (prm.n_copies < 1 || prm.n_copies > 4096) return fail(PLACE_EINVAL, "n_copies must be in [1, 4096]");
   if (prm.max_iters < 0) return fail(PLACE_EINVAL, "max_iters < 0");
+  if (prm.max_backtracks < 0 || prm.max_backtracks > 64)
+    return fail(PLACE_EINVAL, "max_backtracks must be in [0, 64]");
   if (prm.dct_mode != PLACE_DCT_FP32 && prm.dct_mode != PLACE_DCT_BF16X3)
     return fail(PLACE_EINVAL, "unknown dct_mode %d", prm.dct_mode);
   if (prm.dct_mode == PLACE_DCT_BF16X3 && (bins->nx % 128 || bins->ny % 128))
@@ -851,7 +856,8 @@ int place_get_state(place_t *h, int32_t copy, place_state *o) {
   CK(cudaMemcpyAsync(&cs, h->d.cs + copy, sizeof cs, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if ((rc = check_dev_err(h))) return rc;
-  o->iter = cs.k; o->converged = cs.converged; o->stopped = cs.stopped; o->pad = 0;
+  o->iter = cs.k; o->converged = cs.converged; o->stopped = cs.stopped;
+  o->backtracks = cs.n_back_total;
   o->lambda = cs.lam; o->gamma = cs.gamma; o->alpha = cs.alpha; o->a = cs.a;
   o->overflow = cs.tau; o->hpwl_wa = cs.hpwl; o->bins_effective = cs.n_eff;
   return PLACE_OK;
@@ -1102,6 +1108,7 @@ extern "C" int place_estimate_device_bytes(const place_netlist *nl, const place_
   d.nx = bins->nx; d.ny = bins->ny; d.G = bins->nx * bins->ny;
   d.has_net_w = nl->net_w ? 1 : 0;
   d.tc = prm.dct_mode == PLACE_DCT_BF16X3 ? 1 : 0;
+  d.prm = prm;
   const int cb = std::max(1, std::min((d.n_mov + kThreads - 1) / kThreads, kMaxCellBlocks));
   const int bb = std::max(1, std::min((d.G + kThreads - 1) / kThreads, kMaxCellBlocks));
   d.nb_red = std::max(std::max(2 * cb + 2, bb), 4 * kMaxCellBlocks + kMaxBigNetBlocks);

@@ -32,7 +32,9 @@ struct CopyState {
   int stopped;
   int parity;        // selects the current / previous gradient buffer
   int err;
-  int pad[3];
+  int n_back;        // steps redone in a row (backtracking)
+  int reject;        // 1: the update redoes the last step (backtracking)
+  int n_back_total;  // steps redone since reset
   double n_eff;      // effective number of occupied bins of the last density
                      // pass, (sum M)^2 / sum M^2; 0 before the first pass
 };
@@ -94,6 +96,7 @@ struct Dev {
   float *vpx, *vpy;          // [K][n_mov]
   float *gx[2], *gy[2];      // [K][n_mov] preconditioned gradient, by parity
   float *gwx, *gwy, *gdx, *gdy;  // [K][n_mov] raw gradients
+  float *upx, *upy;          // [K][n_mov] u_k of the last accepted step (backtracking only)
   unsigned long long *gacc;  // [K][n_mov] WA gradient sums, two int32 fixed-point
                              // values packed as y * 2^32 + x (see add_pin_grad)
   unsigned long long *M;     // [K][G]

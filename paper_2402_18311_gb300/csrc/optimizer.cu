@@ -216,7 +216,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_cell_grad(Dev d, int copy0, int
     if (k == 0) {
       cs->lam = s2 > 0 ? (double)d.prm.lambda_eta * s1 / s2 : (double)d.prm.lambda_eta;
     } else {
-      advance_scalars(d, cs, false, 0.0, s4, s3);
+      // backtracking: a step-length estimate below 0.95 times the step that
+      // led here sends k_update back to redo that step with the estimate
+      const double est = s3 > 0 ? sqrt(s4) / sqrt(s3) : cs->alpha;
+      if (d.prm.max_backtracks > 0 && cs->n_back < d.prm.max_backtracks && est < 0.95 * cs->alpha) {
+        cs->alpha = est;
+        cs->n_back += 1;
+        cs->n_back_total += 1;
+        cs->reject = 1;
+      } else {
+        cs->n_back = 0;
+        advance_scalars(d, cs, false, 0.0, s4, s3);
+      }
     }
     d.ctr[(size_t)c * C_COUNT + C_CELL] = 0u;
   }
@@ -255,7 +266,9 @@ __global__ void __launch_bounds__(kThreads) k_precond0(Dev d, int copy0) {
 }
 
 // Nesterov step with clamping into the die; the last block closes the
-// iteration (k, a_k, buffer parity, max_iters stop).
+// iteration (k, a_k, buffer parity, max_iters stop).  A rejected step
+// (backtracking) is redone instead, from v_{k-1}, u_{k-1} and g_{k-1}, with
+// the shorter length; k, a and the parity stay.
 __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
   __shared__ int flag;
   pdl_wait();
@@ -265,6 +278,26 @@ __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
   const float alpha = (float)cs->alpha, coef = (float)cs->coef;
   const int par = cs->parity;
   const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
+  if (cs->reject) {
+    const float *gxo = d.gx[par ^ 1] + cm, *gyo = d.gy[par ^ 1] + cm;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
+      const float xh = d.fxh - d.w[i], yh = d.fyh - d.h[i];
+      const float vx = d.vpx[cm + i], vy = d.vpy[cm + i];
+      const float ux = d.upx[cm + i], uy = d.upy[cm + i];
+      const float nux = fmaxf(d.fxl, fminf(vx - alpha * gxo[i], xh));
+      const float nuy = fmaxf(d.fyl, fminf(vy - alpha * gyo[i], yh));
+      d.ux[cm + i] = nux; d.uy[cm + i] = nuy;
+      d.xy[cn + i] = make_float2(fmaxf(d.fxl, fminf(nux + coef * (nux - ux), xh)),
+                                 fmaxf(d.fyl, fminf(nuy + coef * (nuy - uy), yh)));
+    }
+    if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_UPDATE, &flag)) return;
+    if (threadIdx.x == 0) {
+      cs->reject = 0;
+      d.ctr[(size_t)c * C_COUNT + C_UPDATE] = 0u;
+    }
+    return;
+  }
+  const bool keep_u = d.upx != nullptr;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
     const float xh = d.fxh - d.w[i], yh = d.fyh - d.h[i];
     const float2 v = d.xy[cn + i];
@@ -275,6 +308,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
     float nvx = fmaxf(d.fxl, fminf(nux + coef * (nux - ux), xh));
     float nvy = fmaxf(d.fyl, fminf(nuy + coef * (nuy - uy), yh));
     d.vpx[cm + i] = vx; d.vpy[cm + i] = vy;
+    if (keep_u) { d.upx[cm + i] = ux; d.upy[cm + i] = uy; }
     d.ux[cm + i] = nux; d.uy[cm + i] = nuy;
     d.xy[cn + i] = make_float2(nvx, nvy);
   }

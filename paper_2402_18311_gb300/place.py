@@ -58,7 +58,8 @@ class place_params(ct.Structure):
     _fields_ = [("n_copies", ct.c_int32), ("gamma_base", ct.c_float), ("lambda_eta", ct.c_float),
                 ("alpha0", ct.c_float), ("hpwl_ref", ct.c_float), ("mu_base", ct.c_float),
                 ("mu_lo", ct.c_float), ("mu_hi", ct.c_float), ("tau_stop", ct.c_float),
-                ("max_iters", ct.c_int32), ("constant_gamma", ct.c_float), ("dct_mode", ct.c_int32)]
+                ("max_iters", ct.c_int32), ("constant_gamma", ct.c_float), ("dct_mode", ct.c_int32),
+                ("max_backtracks", ct.c_int32)]
 
 
 class place_info(ct.Structure):
@@ -72,7 +73,7 @@ class place_info(ct.Structure):
 
 class place_state(ct.Structure):
     _fields_ = [("iter", ct.c_int32), ("converged", ct.c_int32), ("stopped", ct.c_int32),
-                ("pad", ct.c_int32), ("lambda_", ct.c_double), ("gamma", ct.c_double),
+                ("backtracks", ct.c_int32), ("lambda_", ct.c_double), ("gamma", ct.c_double),
                 ("alpha", ct.c_double), ("a", ct.c_double), ("overflow", ct.c_double),
                 ("hpwl_wa", ct.c_double), ("bins_effective", ct.c_double)]
 

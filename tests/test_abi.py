@@ -44,11 +44,12 @@ def test_default_params_match_the_oracle_reading(L):
               "tau_stop"):
         assert getattr(p, f) == pytest.approx(getattr(o, f), rel=1e-7), f
     assert p.max_iters == o.max_iters
+    assert p.max_backtracks == o.max_backtracks == 0
 
 
 def test_struct_sizes_match_header_layout():
     assert ct.sizeof(place.place_netlist) == 4 * 4 + 10 * 8
-    assert ct.sizeof(place.place_params) == 12 * 4
+    assert ct.sizeof(place.place_params) == 13 * 4
     assert ct.sizeof(place.place_state) == 4 * 4 + 7 * 8
     assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 2 * 4
     assert ct.sizeof(place.place_job) == 4 * 4 + 8 + 8 + 8
@@ -128,6 +129,10 @@ def test_create_rejects_bad_params(L):
     assert ei.value.code == place.PLACE_EINVAL
     with pytest.raises(place.PlaceError):
         place.place_create(d, place.place_default_params(dct_mode=7))
+    for mb in (-1, 65):
+        with pytest.raises(place.PlaceError) as ei:
+            place.place_create(d, place.place_default_params(max_backtracks=mb))
+        assert ei.value.code == place.PLACE_EINVAL and "max_backtracks" in str(ei.value)
 
 
 def test_null_handle_calls_fail_cleanly(L):
@@ -162,3 +167,6 @@ def test_footprint_estimate_grows_with_the_design(L):
     assert 0 < a < b
     b4 = place.place_estimate_device_bytes(big, place.place_default_params(n_copies=4))
     assert b < b4 < 4 * b  # the netlist and transform tables are shared by the copies
+    # backtracking keeps u_k: 8 bytes per movable cell and copy (plus alignment)
+    bb = place.place_estimate_device_bytes(big, place.place_default_params(max_backtracks=3))
+    assert 8 * big.n_movable <= bb - b <= 8 * big.n_movable + 512

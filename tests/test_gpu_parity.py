@@ -394,6 +394,27 @@ def test_independent_random_starts_batched_equal_solo():
         np.testing.assert_array_equal(finals[c][1], ys)
 
 
+def test_backtracking_trajectory_matches_oracle():
+    # ePlace's step-length backtracking (max_backtracks > 0): the library
+    # redoes the same steps as the oracle, evaluation by evaluation
+    d = synth.tiny_1k(0)
+    h = Handle(d, tau_stop=-1.0, max_iters=300, max_backtracks=3)
+    try:
+        o = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=300, max_backtracks=3))
+        hp = np.empty(1); tv = np.empty(1)
+        for k in range(0, 160, 20):
+            place.place_step(h.h, 20)
+            o.run(20)
+            st = place.place_get_state(h.h, 0)
+            assert (st.iter, st.backtracks) == (o.k, o.n_back_total), k
+            place.place_eval_hpwl_overflow(h.h, hp, tv)
+            assert hp[0] == pytest.approx(o.hpwl(o.vx, o.vy), rel=1e-3), k
+        assert o.n_back_total > 0
+        assert st.alpha == pytest.approx(o.alpha, rel=1e-3)
+    finally:
+        h.close()
+
+
 def test_convergence_stops_copy():
     d = synth.tiny_1k(0)
     h = Handle(d, tau_stop=0.3, max_iters=1000)
