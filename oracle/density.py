@@ -14,6 +14,15 @@ DREAMPlace (Sections 1 and 3.1).  The reading used here:
   F_b is the same over fixed cells.  No small-cell stretching.
 * Overflow tau = sum_b max(0, M_b - t (A_b - F_b)) / (total movable area).
 * Bin density rho_b = (M_b + t F_b) / A_b, t the target density.
+
+Optional density stretching (ePlace's local smoothing, off by default):
+* along each axis, a movable cell narrower than sqrt(2) bins widens to
+  Ws = rint(sqrt(2) BW) about its centre, Xs = X - floor((Ws - W) / 2);
+* its density is scaled by W H / (Ws Hs) so that its charge stays its
+  area.  In the map this is the fixed-point scale R = floor(W H 2^31 /
+  (Ws Hs)), each (cell, bin) term floor(ov R / 2^31);
+* the stretched map drives the field and the density gradient; the
+  overflow keeps the unstretched map.
 """
 from __future__ import annotations
 
@@ -155,3 +164,66 @@ def field_gather(X, Y, W, H, g: Grid, Ex, Ey):
             gx -= np.where(ok, a * Ex[kxs, kys], 0.0)
             gy -= np.where(ok, a * Ey[kxs, kys], 0.0)
     return gx, gy
+
+
+STRETCH = math.sqrt(2.0)
+
+
+def stretch_axis(X, W, BW):
+    """One axis of the local smoothing: widths below sqrt(2) bins become
+    Ws = rint(sqrt(2) BW) (ties to even), with Xs = X - floor((Ws - W) / 2)."""
+    X = np.asarray(X, np.int64); W = np.asarray(W, np.int64)
+    ws = int(np.rint(STRETCH * float(BW)))
+    Ws = np.maximum(W, ws)
+    return X - (Ws - W) // 2, Ws
+
+
+def stretch_scale(W, H, Ws, Hs):
+    """R = floor(W H 2^31 / (Ws Hs)) per cell, exact (python integers)."""
+    return np.array([(int(w) * int(h) << 31) // (int(a) * int(b))
+                     for w, h, a, b in zip(W, H, Ws, Hs)], np.int64)
+
+
+def scaled_term(ov, R):
+    """floor(ov R / 2^31) for 0 <= ov < 2^62 and 0 <= R <= 2^31, exact in
+    int64: ov = q 2^31 + r gives q R + floor(r R / 2^31)."""
+    ov = np.asarray(ov, np.int64); R = np.asarray(R, np.int64)
+    q, r = ov >> 31, ov & ((1 << 31) - 1)
+    return q * R + ((r * R) >> 31)
+
+
+def overlap_map_scaled(X, Y, W, H, R, g: Grid):
+    """M_b = sum_i floor(ov(i, b) R_i / 2^31), int64 [nx, ny]: the map of
+    overlap_map with every (cell, bin) term scaled by R_i / 2^31."""
+    X = np.asarray(X, np.int64); Y = np.asarray(Y, np.int64)
+    W = np.asarray(W, np.int64); H = np.asarray(H, np.int64)
+    R = np.asarray(R, np.int64)
+    M = np.zeros((g.nx, g.ny), np.int64)
+    if X.size == 0:
+        return M
+    ix0 = np.floor_divide(X - g.XL, g.BW)
+    ix1 = np.floor_divide(X + W - 1 - g.XL, g.BW)
+    iy0 = np.floor_divide(Y - g.YL, g.BH)
+    iy1 = np.floor_divide(Y + H - 1 - g.YL, g.BH)
+    for dx in range(int(np.max(ix1 - ix0)) + 1):
+        kx = ix0 + dx
+        okx = (kx <= ix1) & (kx >= 0) & (kx < g.nx)
+        ox = _axis_overlap(X, W, g.XL, g.BW, kx)
+        for dy in range(int(np.max(iy1 - iy0)) + 1):
+            ky = iy0 + dy
+            ok = okx & (ky <= iy1) & (ky >= 0) & (ky < g.ny)
+            oy = _axis_overlap(Y, H, g.YL, g.BH, ky)
+            term = scaled_term(ox * oy, R)
+            sel = ok & (term > 0)
+            np.add.at(M, (kx[sel], ky[sel]), term[sel])
+    return M
+
+
+def stretched(X, Y, W, H, g: Grid):
+    """Stretched rectangles (Xs, Ys, Ws, Hs), the map scale R and the
+    gradient weight W H / (Ws Hs) (float64) of cells (X, Y, W, H)."""
+    Xs, Ws = stretch_axis(X, W, g.BW)
+    Ys, Hs = stretch_axis(Y, H, g.BH)
+    R = stretch_scale(W, H, Ws, Hs)
+    wgt = (np.asarray(W, np.float64) * np.asarray(H, np.float64)) / (Ws.astype(np.float64) * Hs)
+    return Xs, Ys, Ws, Hs, R, wgt

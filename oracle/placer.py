@@ -39,6 +39,10 @@ At most ``max_backtracks`` times in a row, v_k is rejected:
 * v_k is evaluated again.
 lambda, gamma, the HPWL and overflow references and k advance only when v_k
 is accepted.  The overflow stop test applies at every evaluated point.
+
+Optional density stretching (``stretch``; oracle.density): the field and the
+density gradient come from the stretched cells; the overflow, the stop test
+and gamma keep the exact unstretched map.
 """
 from __future__ import annotations
 
@@ -103,6 +107,7 @@ class Params:
     max_iters: int = 1000
     constant_gamma: float = 0.0  # > 0: use this gamma every iteration
     max_backtracks: int = 0      # > 0: redo a too-long step at most this often in a row
+    stretch: bool = False        # ePlace density stretching for the field
 
 
 class Placer:
@@ -149,6 +154,14 @@ class Placer:
         Y = dens.quantize(y, self.F)
         return dens.overlap_map(X, Y, self.W[:self.n], self.H[:self.n], self.g)
 
+    def stretched_map(self, x, y):
+        """Map of the stretched cells (oracle.density), which drives the field
+        when ``stretch`` is set."""
+        X = dens.quantize(x, self.F)
+        Y = dens.quantize(y, self.F)
+        Xs, Ys, Ws, Hs, R, _ = dens.stretched(X, Y, self.W[:self.n], self.H[:self.n], self.g)
+        return dens.overlap_map_scaled(Xs, Ys, Ws, Hs, R, self.g)
+
     def overflow(self, M):
         return dens.overflow(M, self.Fmap, self.t, self.g, self.mov_area_q)
 
@@ -175,7 +188,12 @@ class Placer:
     def density_grad(self, x, y, ex, ey):
         X = dens.quantize(x, self.F)
         Y = dens.quantize(y, self.F)
-        return dens.field_gather(X, Y, self.W[:self.n], self.H[:self.n], self.g, ex, ey)
+        W, H = self.W[:self.n], self.H[:self.n]
+        if self.p.stretch:
+            X, Y, W, H, _, wgt = dens.stretched(X, Y, W, H, self.g)
+            gx, gy = dens.field_gather(X, Y, W, H, self.g, ex, ey)
+            return wgt * gx, wgt * gy
+        return dens.field_gather(X, Y, W, H, self.g, ex, ey)
 
     # -- optimiser ------------------------------------------------------------
     def reset(self, x, y):
@@ -223,7 +241,7 @@ class Placer:
         if tau <= p.tau_stop:
             self.converged = self.stopped = True
             return False
-        _, ex, ey = self.field(M)
+        _, ex, ey = self.field(self.stretched_map(vx, vy) if p.stretch else M)
         gdx, gdy = self.density_grad(vx, vy, ex, ey)
         if self.k == 0:
             n1 = np.sum(np.abs(gwx)) + np.sum(np.abs(gwy))

@@ -100,3 +100,68 @@ def test_gather_is_overlap_weighted():
     gx, _ = dens.field_gather(dens.quantize([0.5], 4), dens.quantize([0.5], 4),
                               dens.quantize([1.0], 4), dens.quantize([1.0], 4), g, ex, ey)
     assert gx[0] == pytest.approx(-0.25 * 1111.0, rel=1e-15)
+
+
+def test_stretch_axis_widens_narrow_cells_about_their_centre():
+    # BW = 100: sqrt(2) * 100 = 141.42... -> 141
+    Xs, Ws = dens.stretch_axis([1000, 1000, 1000, 5], [40, 141, 300, 41], 100)
+    assert Ws.tolist() == [141, 141, 300, 141]
+    # growth 101 -> 50 to the left (floor), 51 to the right; unchanged cells stay
+    assert Xs.tolist() == [950, 1000, 1000, -45]
+    # the centre moves by at most half a unit
+    for x, w, xs, ws in zip([1000, 1000, 1000, 5], [40, 141, 300, 41], Xs, Ws):
+        assert abs((2 * xs + ws) - (2 * x + w)) <= 1
+
+
+def test_stretch_scale_is_the_floored_area_ratio():
+    R = dens.stretch_scale([40, 300], [10, 300], [141, 300], [141, 300])
+    assert R[0] == (40 * 10 << 31) // (141 * 141) and R[1] == 1 << 31
+
+
+def test_scaled_map_keeps_each_cells_charge():
+    # cells inside the die: the stretched, scaled map sums to the cells' areas
+    # up to one unit per (cell, bin) term lost to the floor; a cell that is
+    # not stretched contributes its exact overlaps
+    g = dens.Grid((0.0, 0.0, 64.0, 64.0), 8, 8, 4)
+    rng = np.random.default_rng(5)
+    n = 40
+    W = rng.integers(1, 200, n); H = rng.integers(1, 200, n)
+    X = rng.integers(300, 600, n); Y = rng.integers(300, 600, n)
+    Xs, Ys, Ws, Hs, R, wgt = dens.stretched(X, Y, W, H, g)
+    M = dens.overlap_map_scaled(Xs, Ys, Ws, Hs, R, g)
+    terms = sum(len(range((x - g.XL) // g.BW, (x + w - 1 - g.XL) // g.BW + 1)) *
+                len(range((y - g.YL) // g.BH, (y + h - 1 - g.YL) // g.BH + 1))
+                for x, y, w, h in zip(Xs, Ys, Ws, Hs))
+    area = int(np.sum(W * H))
+    assert area - terms <= int(M.sum()) <= area
+    # R = 2^31 (no stretch in either axis) reproduces the exact map
+    big = (W >= 181) & (H >= 181)
+    np.testing.assert_array_equal(
+        dens.overlap_map_scaled(X[big], Y[big], W[big], H[big], np.full(big.sum(), 1 << 31), g),
+        dens.overlap_map(X[big], Y[big], W[big], H[big], g))
+
+
+def test_scaled_map_against_brute_force():
+    g = dens.Grid((0.0, 0.0, 16.0, 16.0), 4, 4, 3)
+    X = np.array([5, 40, 70]); Y = np.array([9, 33, 100]); W = np.array([7, 30, 2]); H = np.array([3, 30, 50])
+    Xs, Ys, Ws, Hs, R, _ = dens.stretched(X, Y, W, H, g)
+    M = np.zeros((4, 4), np.int64)
+    for i in range(3):
+        for kx in range(4):
+            ox = max(0, min(int(Xs[i] + Ws[i]), (kx + 1) * g.BW) - max(int(Xs[i]), kx * g.BW))
+            for ky in range(4):
+                oy = max(0, min(int(Ys[i] + Hs[i]), (ky + 1) * g.BH) - max(int(Ys[i]), ky * g.BH))
+                M[kx, ky] += (ox * oy * int(R[i])) >> 31
+    np.testing.assert_array_equal(dens.overlap_map_scaled(Xs, Ys, Ws, Hs, R, g), M)
+
+
+def test_stretched_gradient_in_a_uniform_field_is_minus_area_times_field():
+    # the gradient weight restores the charge: r * sum_b a'_ib E = W H E
+    g = dens.Grid((0.0, 0.0, 64.0, 64.0), 8, 8, 4)
+    X = np.array([400, 520]); Y = np.array([410, 300]); W = np.array([20, 37]); H = np.array([16, 90])
+    Xs, Ys, Ws, Hs, R, wgt = dens.stretched(X, Y, W, H, g)
+    Ex = np.full((8, 8), 0.75); Ey = np.full((8, 8), -2.0)
+    gx, gy = dens.field_gather(Xs, Ys, Ws, Hs, g, Ex, Ey)
+    area = (W * H).astype(np.float64) * 2.0 ** (-2 * g.F)
+    np.testing.assert_allclose(wgt * gx, -0.75 * area, rtol=1e-12)
+    np.testing.assert_allclose(wgt * gy, 2.0 * area, rtol=1e-12)
