@@ -98,7 +98,16 @@ typedef struct place_bins { int32_t nx, ny; float target_density; } place_bins;
  * the step is redone from v_{k-1} with the estimate as its length, at most
  * max_backtracks times in a row.  lambda, gamma and k advance only on accepted
  * steps.  The overflow stop test applies at every evaluated point.  It costs
- * 8 bytes per movable cell and copy. */
+ * 8 bytes per movable cell and copy.
+ * Density stretching (stretch = 1; ePlace's local smoothing).  Along each
+ * axis, a movable cell narrower than sqrt(2) bins widens to
+ * W' = rint(sqrt(2) BW) in fixed point, about its centre: the left edge
+ * moves by floor((W' - W) / 2).  Its density is scaled by
+ * R = floor(W H 2^31 / (W' H')) / 2^31.  Each (cell, bin) term of this second
+ * map is floor(overlap R), exact in integers.  The stretched map drives the
+ * field and the density gradient, which is scaled by R.  The overflow, the
+ * stop test and gamma keep the exact unstretched map.  It costs 8 bytes per
+ * bin and copy and 20 bytes per movable cell. */
 typedef struct place_params {
   int32_t n_copies;       /* K >= 1 */
   float gamma_base;       /* 4 */
@@ -112,6 +121,7 @@ typedef struct place_params {
   int32_t dct_mode;       /* PLACE_DCT_* */
   int32_t max_backtracks; /* 0 (off) .. 64: redo a too-long step at most this
                              often in a row (see below) */
+  int32_t stretch;        /* 0 (off) or 1: density stretching (see below) */
 } place_params;
 
 /* Read-only facts about a handle. */
@@ -237,6 +247,12 @@ int place_eval_wirelength(place_t *h, int32_t copy, float gamma, double *wl,
 /* Movable-cell density map M (int64, units of 2^-2F, [nx*ny] x-major,
  * host or device, nullable) and the overflow tau (host, nullable). */
 int place_eval_density(place_t *h, int32_t copy, int64_t *map, double *overflow);
+
+/* The stretched map of copy `copy` from its last density pass (int64,
+ * units of 2^-2F, [nx*ny] x-major, host or device).  Every density pass
+ * (an iteration, place_eval_density, place_eval_field) writes it beside M.
+ * Synchronises.  EINVAL when the handle was created without stretching. */
+int place_get_stretched_map(place_t *h, int32_t copy, int64_t *map);
 
 /* Fixed-cell map F (int64, [nx*ny], host or device). */
 int place_get_fixed_map(place_t *h, int64_t *map);

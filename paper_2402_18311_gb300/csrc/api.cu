@@ -123,6 +123,7 @@ void place_default_params(place_params *p) {
   p->constant_gamma = 0.0f;
   p->dct_mode = PLACE_DCT_FP32;
   p->max_backtracks = 0;
+  p->stretch = 0;
 }
 
 int place_destroy(place_t *h) {
@@ -158,6 +159,9 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.npins = a.take<float>(Mv);
   d.area = a.take<float>(Mv);
   d.is_macro = a.take<unsigned char>(C);
+  d.st = d.prm.stretch ? a.take<int4>(std::max<size_t>(Mv, 1)) : nullptr;
+  d.sR = d.prm.stretch ? a.take<unsigned int>(std::max<size_t>(Mv, 1)) : nullptr;
+  d.Ms = d.prm.stretch ? a.take<unsigned long long>(K * G) : nullptr;
   d.xy = a.take<float2>(K * C);
   d.ux = a.take<float>(K * Mv);
   d.uy = a.take<float>(K * Mv);
@@ -422,6 +426,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   if (prm.max_iters < 0) return fail(PLACE_EINVAL, "max_iters < 0");
   if (prm.max_backtracks < 0 || prm.max_backtracks > 64)
     return fail(PLACE_EINVAL, "max_backtracks must be in [0, 64]");
+  if (prm.stretch != 0 && prm.stretch != 1) return fail(PLACE_EINVAL, "stretch must be 0 or 1");
   if (prm.dct_mode != PLACE_DCT_FP32 && prm.dct_mode != PLACE_DCT_BF16X3)
     return fail(PLACE_EINVAL, "unknown dct_mode %d", prm.dct_mode);
   if (prm.dct_mode == PLACE_DCT_BF16X3 && (bins->nx % 128 || bins->ny % 128))
@@ -471,6 +476,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   d.nx = nx; d.ny = ny; d.G = nx * ny;
   d.F = F;
   d.scale = (float)s;
+  d.inv_scale = (float)std::ldexp(1.0, -F);
   d.inv_area_q = (float)std::ldexp(1.0, -2 * F);
   d.XL = (long long)(die->xl * s); d.YL = (long long)(die->yl * s);
   d.BW = (long long)(bw * s); d.BH = (long long)(bh * s);
@@ -684,6 +690,23 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   up(d.npins, npins.data(), sizeof(float) * Mv);
   up(d.area, area.data(), sizeof(float) * Mv);
   up(d.is_macro, macro.data(), C);
+  if (d.st) {
+    // density stretching: along each axis a cell narrower than sqrt(2) bins
+    // widens to rint(sqrt(2) BW) about its centre (shift floor((W' - W) / 2));
+    // its density scale is R = floor(W H 2^31 / (W' H'))
+    const long long ws = (long long)std::nearbyint(std::sqrt(2.0) * (double)d.BW);
+    const long long hs = (long long)std::nearbyint(std::sqrt(2.0) * (double)d.BH);
+    std::vector<int4> st(std::max(Mv, 1));
+    std::vector<unsigned int> sR(std::max(Mv, 1));
+    for (int i = 0; i < Mv; ++i) {
+      const long long W2 = std::max<long long>(Wq[i], ws), H2 = std::max<long long>(Hq[i], hs);
+      st[i] = make_int4((int)((W2 - Wq[i]) >> 1), (int)((H2 - Hq[i]) >> 1), (int)W2, (int)H2);
+      const unsigned __int128 num = ((unsigned __int128)((unsigned long long)Wq[i] * (unsigned long long)Hq[i])) << 31;
+      sR[i] = (unsigned int)(num / (unsigned __int128)((unsigned long long)W2 * (unsigned long long)H2));
+    }
+    up(d.st, st.data(), sizeof(int4) * Mv);
+    up(d.sR, sR.data(), sizeof(unsigned int) * Mv);
+  }
   if (d.net_w) up(d.net_w, net_w.data(), sizeof(float) * E);
   {
     std::vector<float> Cn, CTn, Sn, STn, Cm, CTm, Sm, STm, wu, wv, cu, cv;
@@ -860,6 +883,17 @@ int place_get_state(place_t *h, int32_t copy, place_state *o) {
   o->backtracks = cs.n_back_total;
   o->lambda = cs.lam; o->gamma = cs.gamma; o->alpha = cs.alpha; o->a = cs.a;
   o->overflow = cs.tau; o->hpwl_wa = cs.hpwl; o->bins_effective = cs.n_eff;
+  return PLACE_OK;
+}
+
+int place_get_stretched_map(place_t *h, int32_t copy, int64_t *map) {
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  if (!map) return fail(PLACE_EINVAL, "null output");
+  if (!h->d.Ms) return fail(PLACE_EINVAL, "density stretching is off for this handle");
+  CK(cudaMemcpyAsync(map, h->d.Ms + (size_t)copy * h->d.G, sizeof(int64_t) * h->d.G,
+                     cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   return PLACE_OK;
 }
 

@@ -182,6 +182,49 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
   }
 }
 
+// Density stretching (ePlace local smoothing): the map that drives the field
+// when it is on.  Every movable cell enters as its stretched rectangle
+// (create-time offsets and sizes in d.st) and each (cell, bin) term is
+// floor(ov R / 2^31) with the cell's fixed-point scale R = d.sR[i] <= 2^31:
+// ov = q 2^31 + r gives q R + floor(r R / 2^31), exact in 64 bits.  Terms go
+// through the block's shared-memory table (the centred start is dense).
+__global__ void __launch_bounds__(kThreads) k_scatter_stretch(Dev d, int copy0, int eval) {
+  __shared__ int keys[kHash];
+  __shared__ unsigned long long vals[kHash];
+  const int c = copy0 + blockIdx.y;
+  if (!eval && d.cs[c].stopped) return;
+  for (int i = threadIdx.x; i < kHash; i += blockDim.x) {
+    keys[i] = -1;
+    vals[i] = 0ull;
+  }
+  __syncthreads();
+  const float2 *xy = d.xy + (size_t)c * d.n_cells;
+  unsigned long long *M = d.Ms + (size_t)c * d.G;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
+    const float2 v = xy[i];
+    const int4 st = d.st[i];  // {x shift, y shift, stretched W, stretched H}
+    const unsigned long long R = d.sR[i];
+    const QRect32 r = qrect32(v.x, v.y, st.z, st.w, d.scale, d.XL + st.x, d.YL + st.y, d.BW32,
+                              d.BH32, d.nx, d.ny, d.ibw_q, d.ibh_q);
+    for (int ix = r.ix0; ix <= r.ix1; ++ix) {
+      const int ox = overlap32(r.x0, r.x1, ix, d.BW32);
+      if (ox == 0) continue;
+      for (int iy = r.iy0; iy <= r.iy1; ++iy) {
+        const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
+        if (oy == 0) continue;
+        const unsigned long long ov = (unsigned long long)((long long)ox * oy);
+        const unsigned long long t = (ov >> 31) * R + (((ov & 0x7fffffffull) * R) >> 31);
+        if (t) hash_add(keys, vals, M, ix * d.ny + iy, t);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kHash; i += blockDim.x) {
+    int k = keys[i];
+    if (k >= 0) atomicAdd(&M[k], vals[i]);
+  }
+}
+
 // Same map for an arbitrary cell range (the fixed cells, once at create).
 __global__ void __launch_bounds__(kThreads)
     k_scatter_range(Dev d, const float2 *xy, int n0, int n1, unsigned long long *out) {
@@ -214,6 +257,8 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
   CopyState *cs = d.cs + c;
   if (mode == FIN_ITER && cs->stopped) return;
   const unsigned long long *M = d.M + (size_t)c * d.G;
+  // the field's map: the stretched one when density stretching is on
+  const unsigned long long *Mf = d.Ms ? d.Ms + (size_t)c * d.G : M;
   float *rho = d.rho + (size_t)c * d.G;
   const u128 tA = ((u128)d.tA_hi << 64) | d.tA_lo;  // t_mant * A_bin
   const float inv_a = (float)(1.0 / d.abin_q);
@@ -243,7 +288,8 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
       lhs += (u128)(unsigned long long)d.t_mant * (u128)(unsigned long long)f;
       if (lhs > tA) acc += lhs - tA;
     }
-    const float rv = mq + tf * ((float)f * inv_a);
+    const float mf = d.Ms ? (float)(long long)Mf[b] * inv_a : mq;
+    const float rv = mf + tf * ((float)f * inv_a);
     if (d.tc) {
       const __nv_bfloat16 hi = __float2bfloat16_rn(rv);
       d.rho_h[(size_t)c * d.G + b] = hi;
@@ -293,6 +339,10 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
 void launch_scatter(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st) {
   dim3 grid(d.cell_blocks, ncopy);
   k_scatter<<<grid, kThreads, 0, st>>>(d, copy0, eval);
+  if (d.Ms) {
+    cudaMemsetAsync(d.Ms + (size_t)copy0 * d.G, 0, sizeof(unsigned long long) * d.G * ncopy, st);
+    k_scatter_stretch<<<grid, kThreads, 0, st>>>(d, copy0, eval);
+  }
 }
 
 void launch_scatter_fixed(const Dev &d, const float2 *xy, int n0, int n1,

@@ -89,6 +89,13 @@ struct Dev {
   float *npins;      // [n_mov] pin count per movable cell
   float *area;       // [n_mov]
   unsigned char *is_macro;  // [n_cells]
+  // density stretching (null when off): per movable cell {x shift, y shift,
+  // stretched W, stretched H} in fixed point, the density scale R (2^31 = 1),
+  // and the stretched map that drives the field
+  int4 *st;                  // [n_mov]
+  unsigned int *sR;          // [n_mov]
+  unsigned long long *Ms;    // [K][G]
+  float inv_scale;           // 2^-F
 
   // per-copy state
   float2 *xy;                // [K][n_cells] reference positions v, interleaved (fixed part replicated)

@@ -93,6 +93,9 @@ __device__ void advance_scalars(const Dev &d, CopyState *cs, bool first, double 
 // read and cleared for the next pass) and of the density (field gather -sum_b a_ib E_b) for every movable cell.
 // For k >= 1 (lambda known) the preconditioned gradient and the step-size
 // norms are formed here too, and the last block advances the scalars.
+// STRETCH (density stretching on): the field is gathered over the cell's
+// stretched rectangle and scaled by its density scale R / 2^31.
+template <bool STRETCH>
 __global__ void __launch_bounds__(kThreads, 4) k_cell_grad(Dev d, int copy0, int eval) {
   __shared__ float smf[32];
   __shared__ double smd[32];
@@ -140,12 +143,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_cell_grad(Dev d, int copy0, int
     // in FP32 with coordinates relative to the first bin's corner (exact
     // subtractions, so each overlap keeps FP32 relative precision)
     const float xi = vi.x, yi = vi.y;
-    const int ix0 = min(max((int)floorf((xi - d.fxl) * d.fibw), 0), d.nx - 1);
-    const int iy0 = min(max((int)floorf((yi - d.fyl) * d.fibh), 0), d.ny - 1);
-    const float rx = xi - (d.fxl + (float)ix0 * d.fbw), ry = yi - (d.fyl + (float)iy0 * d.fbh);
-    const float rx1 = rx + wi, ry1 = ry + hi;
+    float xg = xi, yg = yi, wg = wi, hg = hi, scale_g = 1.f;
+    if constexpr (STRETCH) {
+      const int4 st = d.st[i];
+      xg = xi - (float)st.x * d.inv_scale;
+      yg = yi - (float)st.y * d.inv_scale;
+      wg = (float)st.z * d.inv_scale;
+      hg = (float)st.w * d.inv_scale;
+      scale_g = (float)d.sR[i] * 4.656612873077393e-10f;  // 2^-31
+    }
+    const int ix0 = min(max((int)floorf((xg - d.fxl) * d.fibw), 0), d.nx - 1);
+    const int iy0 = min(max((int)floorf((yg - d.fyl) * d.fibh), 0), d.ny - 1);
+    const float rx = xg - (d.fxl + (float)ix0 * d.fbw), ry = yg - (d.fyl + (float)iy0 * d.fbh);
+    const float rx1 = rx + wg, ry1 = ry + hg;
     float dx = 0.f, dy = 0.f;
-    if (wi <= d.fbw && hi <= d.fbh) {
+    if (wg <= d.fbw && hg <= d.fbh) {
       // no larger than a bin: at most the 2 x 2 bins from (ix0, iy0), the
       // far ones loaded only where the cell reaches them
       const float ox0 = fmaxf(fminf(rx1, d.fbw) - fmaxf(rx, 0.f), 0.f);
@@ -173,6 +185,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_cell_grad(Dev d, int copy0, int
           dy = fmaf(-a, eyr[iy], dy);
         }
       }
+    }
+    if constexpr (STRETCH) {
+      dx *= scale_g;
+      dy *= scale_g;
     }
     if (!full) {  // raw gradients are read only by k = 0 (lambda_0) and evaluations
       d.gwx[cm + i] = sx; d.gwy[cm + i] = sy;
@@ -377,11 +393,14 @@ void launch_unpack_xy(float *x, float *y, const float2 *src, int n, cudaStream_t
 }
 
 void launch_cell_grad(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st) {
-  launch_pdl(k_cell_grad, dim3(d.cg_blocks, ncopy), dim3(kThreads), 0, st, d, copy0, eval);
+  if (d.Ms)
+    launch_pdl(k_cell_grad<true>, dim3(d.cg_blocks, ncopy), dim3(kThreads), 0, st, d, copy0, eval);
+  else
+    launch_pdl(k_cell_grad<false>, dim3(d.cg_blocks, ncopy), dim3(kThreads), 0, st, d, copy0, eval);
 }
 int cell_grad_blocks_per_sm() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cell_grad, kThreads, 0) != cudaSuccess || n < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cell_grad<false>, kThreads, 0) != cudaSuccess || n < 1)
     n = 1;
   return n;
 }

@@ -59,7 +59,7 @@ class place_params(ct.Structure):
                 ("alpha0", ct.c_float), ("hpwl_ref", ct.c_float), ("mu_base", ct.c_float),
                 ("mu_lo", ct.c_float), ("mu_hi", ct.c_float), ("tau_stop", ct.c_float),
                 ("max_iters", ct.c_int32), ("constant_gamma", ct.c_float), ("dct_mode", ct.c_int32),
-                ("max_backtracks", ct.c_int32)]
+                ("max_backtracks", ct.c_int32), ("stretch", ct.c_int32)]
 
 
 class place_info(ct.Structure):
@@ -113,6 +113,7 @@ _SIGS = {
     "place_eval_wirelength": (ct.c_int, [_VP, ct.c_int32, ct.c_float, _VP, _VP, _VP]),
     "place_eval_density": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
     "place_get_fixed_map": (ct.c_int, [_VP, _VP]),
+    "place_get_stretched_map": (ct.c_int, [_VP, ct.c_int32, _VP]),
     "place_eval_field": (ct.c_int, [_VP, ct.c_int32, _VP, _VP, _VP]),
     "place_eval_density_grad": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
     "place_hybro": (ct.c_int, [_VP, ct.c_int32, ct.c_int32, ct.c_float, ct.c_uint64, ct.c_float,
@@ -290,6 +291,10 @@ def place_eval_density(h, copy, out_map=None):
 
 def place_get_fixed_map(h, out_map):
     return _check(lib().place_get_fixed_map(h, _ptr(out_map)))
+
+
+def place_get_stretched_map(h, copy, out_map):
+    return _check(lib().place_get_stretched_map(h, int(copy), _ptr(out_map)))
 
 
 def place_eval_field(h, copy, psi=None, ex=None, ey=None):

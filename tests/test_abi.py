@@ -49,7 +49,7 @@ def test_default_params_match_the_oracle_reading(L):
 
 def test_struct_sizes_match_header_layout():
     assert ct.sizeof(place.place_netlist) == 4 * 4 + 10 * 8
-    assert ct.sizeof(place.place_params) == 13 * 4
+    assert ct.sizeof(place.place_params) == 14 * 4
     assert ct.sizeof(place.place_state) == 4 * 4 + 7 * 8
     assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 2 * 4
     assert ct.sizeof(place.place_job) == 4 * 4 + 8 + 8 + 8
@@ -129,6 +129,9 @@ def test_create_rejects_bad_params(L):
     assert ei.value.code == place.PLACE_EINVAL
     with pytest.raises(place.PlaceError):
         place.place_create(d, place.place_default_params(dct_mode=7))
+    with pytest.raises(place.PlaceError) as ei:
+        place.place_create(d, place.place_default_params(stretch=2))
+    assert ei.value.code == place.PLACE_EINVAL and "stretch" in str(ei.value)
     for mb in (-1, 65):
         with pytest.raises(place.PlaceError) as ei:
             place.place_create(d, place.place_default_params(max_backtracks=mb))

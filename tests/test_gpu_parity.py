@@ -415,6 +415,58 @@ def test_backtracking_trajectory_matches_oracle():
         h.close()
 
 
+def test_density_stretching_maps_field_and_trajectory():
+    # ePlace's density stretching (stretch = 1): the exact map still gives
+    # the overflow, the stretched map is bit-exact, the field and the scaled
+    # density gradient follow from it, and a trajectory follows the oracle's
+    d = synth.tiny_1k(0)
+    G = d.nx * d.ny
+    h = Handle(d, tau_stop=-1.0, max_iters=300, stretch=1)
+    try:
+        n = d.n_movable
+        for it in (0, 60):
+            place.place_step(h.h, it)
+            x, y = h.pos()
+            g, M, Fm, amov = oracle_maps(d, h.info, x, y)
+            gm = np.empty(G, np.int64)
+            tau = place.place_eval_density(h.h, 0, gm)
+            np.testing.assert_array_equal(gm.reshape(d.nx, d.ny), M)
+            assert tau == pytest.approx(odens.overflow(M, Fm, np.float32(d.target_density), g, amov),
+                                        rel=1e-12, abs=1e-15)
+            ms = np.empty(G, np.int64)
+            place.place_get_stretched_map(h.h, 0, ms)
+            X, Y = odens.quantize(x[:n], g.F), odens.quantize(y[:n], g.F)
+            W, H = odens.quantize(d.w[:n], g.F), odens.quantize(d.h[:n], g.F)
+            Xs, Ys, Ws, Hs, R, wgt = odens.stretched(X, Y, W, H, g)
+            oms = odens.overlap_map_scaled(Xs, Ys, Ws, Hs, R, g)
+            np.testing.assert_array_equal(ms.reshape(d.nx, d.ny), oms)
+            assert not np.array_equal(oms, M)
+            rho = odens.bin_density(oms, Fm, np.float32(d.target_density), g)
+            opsi, oex, oey = opois.poisson(rho, g.bin_w, g.bin_h)
+            psi = np.empty(G, np.float32); ex = np.empty(G, np.float32); ey = np.empty(G, np.float32)
+            place.place_eval_field(h.h, 0, psi, ex, ey)
+            assert rel_l2(ex, oex.ravel()) < 1e-4 and rel_l2(ey, oey.ravel()) < 1e-4
+            dgx = np.empty(n, np.float32); dgy = np.empty(n, np.float32)
+            place.place_eval_density_grad(h.h, 0, dgx, dgy)
+            ogx, ogy = odens.field_gather(Xs, Ys, Ws, Hs, g, oex, oey)
+            assert rel_l2(np.concatenate([dgx, dgy]),
+                          np.concatenate([wgt * ogx, wgt * ogy])) < 1e-4
+    finally:
+        h.close()
+    h = Handle(d, tau_stop=-1.0, max_iters=300, stretch=1)
+    try:
+        o = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=300, stretch=True))
+        hp = np.empty(1); tv = np.empty(1)
+        for k in range(0, 100, 20):
+            place.place_step(h.h, 20)
+            o.run(20)
+        place.place_eval_hpwl_overflow(h.h, hp, tv)
+        assert hp[0] == pytest.approx(o.hpwl(o.vx, o.vy), rel=1e-3)
+        assert tv[0] == pytest.approx(o.tau, abs=5e-3)
+    finally:
+        h.close()
+
+
 def test_convergence_stops_copy():
     d = synth.tiny_1k(0)
     h = Handle(d, tau_stop=0.3, max_iters=1000)
