@@ -11,7 +11,8 @@ DREAMPlace (Sections 1 and 3.1).  The reading used here:
   pure integer function of the float32 positions.
 * The movable map M_b is the sum over movable cells of the exact overlap area
   of the cell rectangle with bin b, in units of 2^-2F (int64).  The fixed map
-  F_b is the same over fixed cells.  No small-cell stretching.
+  F_b is the same over fixed cells.  No small-cell stretching here; the
+  optional stretching below keeps this map for the overflow.
 * Overflow tau = sum_b max(0, M_b - t (A_b - F_b)) / (total movable area).
 * Bin density rho_b = (M_b + t F_b) / A_b, t the target density.
 
