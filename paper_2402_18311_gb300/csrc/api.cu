@@ -383,6 +383,10 @@ int ensure_wiremask(place_t *h) {
   if (!rc) rc = up(mptr, h->wm_ptr);
   if (!rc) rc = up(mnet, h->wm_net);
   if (!rc) rc = up(obst, h->wm_obst);
+  if (rc) {  // the next WireMask call starts over
+    cudaFreeAsync(h->wm_mem, h->stream);
+    h->wm_mem = nullptr;
+  }
   return rc;
 }
 

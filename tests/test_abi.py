@@ -173,3 +173,7 @@ def test_footprint_estimate_grows_with_the_design(L):
     # backtracking keeps u_k: 8 bytes per movable cell and copy (plus alignment)
     bb = place.place_estimate_device_bytes(big, place.place_default_params(max_backtracks=3))
     assert 8 * big.n_movable <= bb - b <= 8 * big.n_movable + 512
+    # stretching: a second map (8 bytes per bin) and 20 bytes per movable cell
+    bs = place.place_estimate_device_bytes(big, place.place_default_params(stretch=1))
+    extra = 8 * big.nx * big.ny + 20 * big.n_movable
+    assert extra <= bs - b <= extra + 768
