@@ -787,8 +787,9 @@ int place_get_info(const place_t *h, place_info *o) {
   o->device_bytes = (int64_t)h->mem_bytes;
   int wa = 0;
   for (int c = 0; c < d.n_cls; ++c) wa += d.wa_blocks[c] > 0;
-  // scatter, finish, 4 GEMMs, WA classes, cell grad, precond0, update
-  o->kernels_per_iter = 2 + 4 + wa + 3;
+  // scatter, finish, 4 GEMMs, WA classes, cell grad, precond0, update; the
+  // stretched scatter with density stretching, the step redo with backtracking
+  o->kernels_per_iter = 2 + 4 + wa + 3 + (d.Ms ? 1 : 0) + (d.upx ? 1 : 0);
   o->pad = 0;
   return PLACE_OK;
 }

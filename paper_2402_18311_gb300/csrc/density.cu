@@ -247,7 +247,9 @@ __global__ void __launch_bounds__(kThreads)
 // Per bin: exact overflow excess and rho in FP32; the last block of each copy
 // reduces the excess and, by mode, records the overflow as the iteration's
 // tau (with the stop test), as an evaluation result, or as the reset value
-// tau_{-1} that sets the first gamma.
+// tau_{-1} that sets the first gamma.  STRETCH: rho comes from the
+// stretched map (density stretching on); the overflow always from M.
+template <bool STRETCH>
 __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, int mode) {
   __shared__ u128 sm[32];
   __shared__ float smf[32];
@@ -257,8 +259,6 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
   CopyState *cs = d.cs + c;
   if (mode == FIN_ITER && cs->stopped) return;
   const unsigned long long *M = d.M + (size_t)c * d.G;
-  // the field's map: the stretched one when density stretching is on
-  const unsigned long long *Mf = d.Ms ? d.Ms + (size_t)c * d.G : M;
   float *rho = d.rho + (size_t)c * d.G;
   const u128 tA = ((u128)d.tA_hi << 64) | d.tA_lo;  // t_mant * A_bin
   const float inv_a = (float)(1.0 / d.abin_q);
@@ -288,7 +288,8 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
       lhs += (u128)(unsigned long long)d.t_mant * (u128)(unsigned long long)f;
       if (lhs > tA) acc += lhs - tA;
     }
-    const float mf = d.Ms ? (float)(long long)Mf[b] * inv_a : mq;
+    float mf = mq;
+    if constexpr (STRETCH) mf = (float)(long long)d.Ms[(size_t)c * d.G + b] * inv_a;
     const float rv = mf + tf * ((float)f * inv_a);
     if (d.tc) {
       const __nv_bfloat16 hi = __float2bfloat16_rn(rv);
@@ -355,7 +356,10 @@ void launch_scatter_fixed(const Dev &d, const float2 *xy, int n0, int n1,
 
 void launch_density_finish(const Dev &d, int copy0, int ncopy, int mode, cudaStream_t st) {
   dim3 grid(d.bin_blocks, ncopy);
-  launch_pdl(k_density_finish, grid, dim3(kThreads), 0, st, d, copy0, mode);
+  if (d.Ms)
+    launch_pdl(k_density_finish<true>, grid, dim3(kThreads), 0, st, d, copy0, mode);
+  else
+    launch_pdl(k_density_finish<false>, grid, dim3(kThreads), 0, st, d, copy0, mode);
 }
 
 }  // namespace hp

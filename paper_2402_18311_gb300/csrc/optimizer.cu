@@ -282,38 +282,22 @@ __global__ void __launch_bounds__(kThreads) k_precond0(Dev d, int copy0) {
 }
 
 // Nesterov step with clamping into the die; the last block closes the
-// iteration (k, a_k, buffer parity, max_iters stop).  A rejected step
-// (backtracking) is redone instead, from v_{k-1}, u_{k-1} and g_{k-1}, with
-// the shorter length; k, a and the parity stay.
+// iteration (k, a_k, buffer parity, max_iters stop).  KEEP_U (backtracking
+// on) also saves u_k, and a step that the cell-gradient pass rejected is
+// left to k_redo_step.
+template <bool KEEP_U>
 __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
   __shared__ int flag;
   pdl_wait();
   const int c = copy0 + blockIdx.y;
   CopyState *cs = d.cs + c;
   if (cs->stopped) return;
+  if constexpr (KEEP_U) {
+    if (cs->reject) return;
+  }
   const float alpha = (float)cs->alpha, coef = (float)cs->coef;
   const int par = cs->parity;
   const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
-  if (cs->reject) {
-    const float *gxo = d.gx[par ^ 1] + cm, *gyo = d.gy[par ^ 1] + cm;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
-      const float xh = d.fxh - d.w[i], yh = d.fyh - d.h[i];
-      const float vx = d.vpx[cm + i], vy = d.vpy[cm + i];
-      const float ux = d.upx[cm + i], uy = d.upy[cm + i];
-      const float nux = fmaxf(d.fxl, fminf(vx - alpha * gxo[i], xh));
-      const float nuy = fmaxf(d.fyl, fminf(vy - alpha * gyo[i], yh));
-      d.ux[cm + i] = nux; d.uy[cm + i] = nuy;
-      d.xy[cn + i] = make_float2(fmaxf(d.fxl, fminf(nux + coef * (nux - ux), xh)),
-                                 fmaxf(d.fyl, fminf(nuy + coef * (nuy - uy), yh)));
-    }
-    if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_UPDATE, &flag)) return;
-    if (threadIdx.x == 0) {
-      cs->reject = 0;
-      d.ctr[(size_t)c * C_COUNT + C_UPDATE] = 0u;
-    }
-    return;
-  }
-  const bool keep_u = d.upx != nullptr;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
     const float xh = d.fxh - d.w[i], yh = d.fyh - d.h[i];
     const float2 v = d.xy[cn + i];
@@ -324,7 +308,10 @@ __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
     float nvx = fmaxf(d.fxl, fminf(nux + coef * (nux - ux), xh));
     float nvy = fmaxf(d.fyl, fminf(nuy + coef * (nuy - uy), yh));
     d.vpx[cm + i] = vx; d.vpy[cm + i] = vy;
-    if (keep_u) { d.upx[cm + i] = ux; d.upy[cm + i] = uy; }
+    if constexpr (KEEP_U) {
+      d.upx[cm + i] = ux;
+      d.upy[cm + i] = uy;
+    }
     d.ux[cm + i] = nux; d.uy[cm + i] = nuy;
     d.xy[cn + i] = make_float2(nvx, nvy);
   }
@@ -334,6 +321,36 @@ __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
     cs->a = cs->a_next;
     cs->parity ^= 1;
     if (cs->k >= d.prm.max_iters) cs->stopped = 1;
+    d.ctr[(size_t)c * C_COUNT + C_UPDATE] = 0u;
+  }
+}
+
+// Backtracking: redo the rejected step from v_{k-1}, u_{k-1} and g_{k-1}
+// with the shorter length the cell-gradient pass stored; k, a_k and the
+// buffer parity stay.  Launched after k_update on handles with backtracking.
+__global__ void __launch_bounds__(kThreads) k_redo_step(Dev d, int copy0) {
+  __shared__ int flag;
+  pdl_wait();
+  const int c = copy0 + blockIdx.y;
+  CopyState *cs = d.cs + c;
+  if (cs->stopped || !cs->reject) return;
+  const float alpha = (float)cs->alpha, coef = (float)cs->coef;
+  const int par = cs->parity;
+  const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
+  const float *gxo = d.gx[par ^ 1] + cm, *gyo = d.gy[par ^ 1] + cm;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
+    const float xh = d.fxh - d.w[i], yh = d.fyh - d.h[i];
+    const float vx = d.vpx[cm + i], vy = d.vpy[cm + i];
+    const float ux = d.upx[cm + i], uy = d.upy[cm + i];
+    const float nux = fmaxf(d.fxl, fminf(vx - alpha * gxo[i], xh));
+    const float nuy = fmaxf(d.fyl, fminf(vy - alpha * gyo[i], yh));
+    d.ux[cm + i] = nux; d.uy[cm + i] = nuy;
+    d.xy[cn + i] = make_float2(fmaxf(d.fxl, fminf(nux + coef * (nux - ux), xh)),
+                               fmaxf(d.fyl, fminf(nuy + coef * (nuy - uy), yh)));
+  }
+  if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_UPDATE, &flag)) return;
+  if (threadIdx.x == 0) {
+    cs->reject = 0;
     d.ctr[(size_t)c * C_COUNT + C_UPDATE] = 0u;
   }
 }
@@ -408,7 +425,13 @@ void launch_precond0(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
   launch_pdl(k_precond0, dim3(d.cell_blocks, ncopy), dim3(kThreads), 0, st, d, copy0);
 }
 void launch_update(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
-  launch_pdl(k_update, dim3(d.cell_blocks, ncopy), dim3(kThreads), 0, st, d, copy0);
+  const dim3 grid(d.cell_blocks, ncopy);
+  if (d.upx) {
+    launch_pdl(k_update<true>, grid, dim3(kThreads), 0, st, d, copy0);
+    launch_pdl(k_redo_step, grid, dim3(kThreads), 0, st, d, copy0);
+  } else {
+    launch_pdl(k_update<false>, grid, dim3(kThreads), 0, st, d, copy0);
+  }
 }
 void launch_reset(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
   k_reset<<<dim3(d.cell_blocks, ncopy), kThreads, 0, st>>>(d, copy0);
