@@ -174,3 +174,31 @@ def test_hybro_loop_runs_wiremask():
     prm = pl.Params(max_iters=20, tau_stop=0.0)
     best, rounds = hybro.run(d, prm, 1, op=hybro.WIREMASK)
     assert len(rounds) == 2 and best in (0, 1)
+
+
+def test_weighted_mask_is_weighted_total_hpwl_up_to_a_constant():
+    # with net weights the mask is the weighted Eq. 1 HPWL up to a constant
+    d = synth.make_design(n_movable=120, die=(0, 0, 64, 64), nx=16, ny=16, n_nets=140,
+                          n_pads=8, target_density=1.0, seed=9, name="wm_weighted")
+    rng = np.random.default_rng(4)
+    mac = rng.choice(d.n_movable, 4, replace=False)
+    d.w[mac] = rng.integers(5, 11, 4).astype(np.float32)
+    d.h[mac] = rng.integers(5, 11, 4).astype(np.float32)
+    d.is_macro[:] = 0
+    d.is_macro[mac] = 1
+    net_w = rng.uniform(0.5, 2.0, d.n_nets).astype(np.float32)
+    trace = []
+    wm.wiremask(d.x, d.y, d.w, d.h, d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, d.n_movable,
+                d.is_macro, d.die, d.nx, d.ny, net_w=net_w, trace=trace)
+    X = wm.grid_corners(d.die[0], d.die[2], d.nx)
+    Y = wm.grid_corners(d.die[1], d.die[3], d.ny)
+    x, y = d.x.copy(), d.y.copy()
+    m, fx, fy, chosen = trace[0]
+    diffs = []
+    for j in range(0, d.ny, 3):
+        for i in range(0, d.nx, 3):
+            xx, yy = x.copy(), y.copy()
+            xx[m], yy[m] = X[i], Y[j]
+            tot = hpwl(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, xx, yy, net_w=net_w)
+            diffs.append(tot - (fx[i] + fy[j]))
+    assert np.ptp(diffs) <= 1e-9 * abs(max(diffs, key=abs))
