@@ -526,9 +526,46 @@ def run_serving(args, place, n_jobs, min_cells, max_cells, max_active=16):
     return out
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, then /proc/cpuinfo), else its
+    architecture."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_one_core(workload, n_iters=1):
+    """Oracle iterations/s on one core: a child process with the BLAS and
+    OpenMP thread pools set to one thread before numpy loads."""
+    code = ("import sys, time; sys.path.insert(0, %r); "
+            "from paper_2402_18311_gb300 import synth; from oracle import placer as opl; "
+            "d = getattr(synth, %r)(0); o = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=1 << 30)); "
+            "t = time.perf_counter(); o.run(%d); print(%d / (time.perf_counter() - t))"
+            % (ROOT, workload, n_iters, n_iters))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=600)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return None
+
+
 def cpu_baseline(d, args, n_iters=1):
     """The FP64 oracle as it stands, on the same workload: n_iters full
-    iterations after its set-up."""
+    iterations after its set-up, on all host cores and on one core."""
     from oracle import placer as opl
     t0 = time.perf_counter()
     o = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=1 << 30))
@@ -537,9 +574,10 @@ def cpu_baseline(d, args, n_iters=1):
     o.run(n_iters)
     el = time.perf_counter() - t0
     return {"value": n_iters / el, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_model": cpu_model(), "value_1_core": oracle_one_core(args.workload, n_iters),
             "sample": f"{n_iters} full iteration(s) of the {args.workload} workload after "
                       f"{setup:.1f} s of oracle set-up; numpy float64 (elementwise work single-"
-                      f"threaded, BLAS matmuls multi-threaded)"}
+                      f"threaded, BLAS matmuls multi-threaded; value_1_core with one BLAS thread)"}
 
 
 def run_reference(args):
