@@ -2,7 +2,8 @@
  * hybro_place.h -- C ABI of the GB300 (sm_103a) electrostatic global-placement
  * library: the inner loop that every perturb-and-reoptimise round of Hybro
  * re-runs (the global-placement step of Algorithm 1, run until it converges),
- * plus the Shuffle perturbations and best-result selection of Algorithm 1.
+ * plus the perturbations (Shuffle, Shuffle (all), WireMask; Section 4.2) and
+ * best-result selection of Algorithm 1, and a job server.
  *
  * Conventions
  *  - Every function returns PLACE_OK (0) or a negative PLACE_E* code; the
@@ -173,10 +174,10 @@ int place_get_info(const place_t *h, place_info *out);
 
 /* Run up to n_iters Nesterov iterations of Eq. 2 on every active copy (the
  * global-placement step of Algorithm 1).  With backtracking, n_iters counts
- * gradient evaluations, and a redone step is one of them.  A copy stops updating once
- * converged or at max_iters; the others continue.  converged (nullable, host [K]) receives
- * the stopped flags, which synchronises the stream; with NULL the call is
- * asynchronous. */
+ * gradient evaluations, and a redone step is one of them.  A copy stops
+ * updating once converged or at max_iters; the others continue.  converged
+ * (nullable, host [K]) receives the stopped flags, which synchronises the
+ * stream; with NULL the call is asynchronous. */
 int place_step(place_t *h, int32_t n_iters, int32_t *converged);
 
 /* place_step over n resident handles at once, as a job server would: the
@@ -203,9 +204,9 @@ int place_step_multi(place_t *const *hs, int32_t n, int32_t n_iters, int32_t *co
  * macro moved before it; touching edges is allowed.  Ties go to the smallest
  * L1 distance from the macro's old corner, then the lowest bin row, then the
  * lowest column.  A macro with no free corner stays where it is.  The first
- * WireMask call allocates device scratch: about
- * 8 (K (nx + ny + 8 max_nets_per_macro) + 2 K nx ny / 256) bytes, freed by
- * place_destroy.  It costs four kernel launches per macro.  A design
+ * WireMask call allocates device scratch of about
+ * 8 K (nx + ny + 8 max_nets_per_macro) + 20 K min(nx ny / 256, 1216) bytes,
+ * freed by place_destroy.  It costs four kernel launches per macro.  A design
  * without movable macros only resets the optimiser.  EINVAL on an unknown
  * op or, for Shuffle, p outside [0, 1]; ENOMEM if the scratch cannot be
  * allocated. */
@@ -257,12 +258,15 @@ int place_get_stretched_map(place_t *h, int32_t copy, int64_t *map);
 /* Fixed-cell map F (int64, [nx*ny], host or device). */
 int place_get_fixed_map(place_t *h, int64_t *map);
 
-/* Spectral Poisson solve of rho = (M + t F) / A_bin at the current positions:
- * psi, ex, ey are [nx*ny] host or device float buffers (nullable). */
+/* Spectral Poisson solve of rho = (M + t F) / A_bin at the current positions
+ * (M: the stretched map when density stretching is on): psi, ex, ey are
+ * [nx*ny] host or device float buffers (nullable). */
 int place_eval_field(place_t *h, int32_t copy, float *psi, float *ex, float *ey);
 
 /* Density gradient -sum_b a_ib E_b for the movable cells using the field of
- * the current positions: grad_x/grad_y [n_movable] host or device. */
+ * the current positions: grad_x/grad_y [n_movable] host or device.  With
+ * density stretching, a_ib is the stretched rectangle's overlap times the
+ * cell's density scale. */
 int place_eval_density_grad(place_t *h, int32_t copy, float *grad_x, float *grad_y);
 
 /* Hybro (Algorithm 1) on every copy: rounds 0..n_rounds place each copy until
