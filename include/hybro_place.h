@@ -205,7 +205,7 @@ int place_step_multi(place_t *const *hs, int32_t n, int32_t n_iters, int32_t *co
  * L1 distance from the macro's old corner, then the lowest bin row, then the
  * lowest column.  A macro with no free corner stays where it is.  The first
  * WireMask call allocates device scratch of about
- * 8 K (nx + ny + 8 max_nets_per_macro) + 20 K min(nx ny / 256, 1216) bytes,
+ * 8 K (nx + ny + 8 max_nets_per_macro) + 20 K min(nx ny / 256, 304) bytes,
  * freed by place_destroy.  It costs four kernel launches per macro.  A design
  * without movable macros only resets the optimiser.  EINVAL on an unknown
  * op or, for Shuffle, p outside [0, 1]; ENOMEM if the scratch cannot be

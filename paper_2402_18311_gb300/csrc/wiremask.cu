@@ -20,11 +20,14 @@
 // Every value that decides a comparison is FP64 from a fixed sequence of
 // correctly rounded operations (explicit _rn intrinsics, so no contraction
 // into fused multiply-adds), so the result is bit-exact and
-// independent of the launch shape.  Per macro: one warp per net computes
-// the net's extents, one thread per grid line sums a mask axis, and one
-// thread per candidate tests the obstacles (staged in shared memory) and
-// takes part in a block argmin; a last kernel reduces the blocks' winners and
-// moves the macro.  Copies run side by side (blockIdx.y).
+// independent of the launch shape.  Per macro:
+//   - one warp per net computes the net's extents;
+//   - one thread per grid line sums a mask axis;
+//   - each block turns every obstacle into the exact range of candidate
+//     columns and rows it blocks (binary searches); each candidate then
+//     tests integer ranges and takes part in a block argmin;
+//   - a last kernel reduces the blocks' winners and moves the macro.
+// Copies run side by side (blockIdx.y).
 #include <cmath>
 
 #include "common.cuh"
@@ -36,9 +39,40 @@ namespace {
 
 constexpr int kWmThreads = 256;
 
-__device__ __forceinline__ double wm_corner(double lo, double hi, int n, int i) {
-  const double b = __ddiv_rn(__dsub_rn(hi, lo), (double)n);
+__device__ __forceinline__ double wm_step(double lo, double hi, int n) {
+  return __ddiv_rn(__dsub_rn(hi, lo), (double)n);
+}
+// Candidate corner i: fl32(lo + i b) with b = (hi - lo) / n.
+__device__ __forceinline__ double wm_corner_b(double lo, double b, int i) {
   return (double)__double2float_rn(__dadd_rn(lo, __dmul_rn((double)i, b)));
+}
+__device__ __forceinline__ double wm_corner(double lo, double hi, int n, int i) {
+  return wm_corner_b(lo, wm_step(lo, hi, n), i);
+}
+
+// First k in [0, n] at which a predicate that is false and then true over
+// [0, n) holds (n when it never does).
+template <typename P>
+__device__ __forceinline__ int first_true(int n, P pred) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (pred(mid)) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// The corners i whose macro rectangle [X_i, X_i + w) overlaps [o0, o1) with
+// positive length: X_i < o1 and o0 < X_i + w.  The corners are
+// nondecreasing in i (rounding is monotone), so the first test holds for i
+// below some bound and the second from some bound on.  Two binary searches
+// over the same FP64 expressions give the range [i0, i1] exactly.
+__device__ __forceinline__ int2 blocked_range(double lo, double b, int n, double w, double o0,
+                                              double o1) {
+  const int i0 = first_true(n, [&](int i) { return o0 < __dadd_rn(wm_corner_b(lo, b, i), w); });
+  const int i1 = first_true(n, [&](int i) { return !(wm_corner_b(lo, b, i) < o1); }) - 1;
+  return make_int2(i0, i1);
 }
 
 struct Best {
@@ -154,9 +188,13 @@ __global__ void __launch_bounds__(kWmThreads) k_wm_profile(Dev d, WmDev w, int t
 }
 
 // One thread per candidate: inside the die, free of obstacles, key; the
-// block's best goes to its partial slot.
+// block's best goes to its partial slot.  Each obstacle becomes the range of
+// candidate columns and rows it blocks (blocked_range, one thread per
+// obstacle, staged in shared memory), so a candidate's test is integer
+// compares; with up to one block's worth of obstacles the ranges are
+// formed once per block.
 __global__ void __launch_bounds__(kWmThreads) k_wm_select(Dev d, WmDev w, int t, int copy0) {
-  __shared__ double so[kWmThreads][4];
+  __shared__ int4 so[kWmThreads];  // blocked columns [x, y], rows [z, w]
   const int c = copy0 + blockIdx.y;
   const float2 *xy = d.xy + (size_t)c * d.n_cells;
   const int m = w.order[t];
@@ -164,36 +202,48 @@ __global__ void __launch_bounds__(kWmThreads) k_wm_select(Dev d, WmDev w, int t,
   const float2 pm = xy[m];
   const int nob = w.n_fixed + t;
   const int G = d.nx * d.ny;
+  const double bx = wm_step(d.die_xl, d.die_xh, d.nx), by = wm_step(d.die_yl, d.die_yh, d.ny);
   const double *fx = w.fx + (size_t)blockIdx.y * d.nx, *fy = w.fy + (size_t)blockIdx.y * d.ny;
+  auto stage = [&](int o0) {
+    if (o0 + (int)threadIdx.x < nob) {
+      const int oc = w.obst[o0 + threadIdx.x];
+      const float2 p = xy[oc];
+      const int2 rx = blocked_range(d.die_xl, bx, d.nx, mw, (double)p.x,
+                                    __dadd_rn((double)p.x, (double)d.w[oc]));
+      const int2 ry = blocked_range(d.die_yl, by, d.ny, mh, (double)p.y,
+                                    __dadd_rn((double)p.y, (double)d.h[oc]));
+      so[threadIdx.x] = make_int4(rx.x, rx.y, ry.x, ry.y);
+    }
+  };
+  const bool once = nob <= kWmThreads;
+  if (once) {
+    stage(0);
+    __syncthreads();
+  }
   Best best{0.0, 0.0, -1};
   for (int base = blockIdx.x * kWmThreads; base < G; base += gridDim.x * kWmThreads) {
     const int q = base + threadIdx.x;
     bool ok = q < G;
     int i = 0, j = 0;
-    double X = 0.0, Y = 0.0, Xr = 0.0, Yr = 0.0;
+    double X = 0.0, Y = 0.0;
     if (ok) {
       j = q / d.nx;
       i = q - j * d.nx;
-      X = wm_corner(d.die_xl, d.die_xh, d.nx, i);
-      Y = wm_corner(d.die_yl, d.die_yh, d.ny, j);
-      Xr = __dadd_rn(X, mw);
-      Yr = __dadd_rn(Y, mh);
-      ok = Xr <= d.die_xh && Yr <= d.die_yh;
+      X = wm_corner_b(d.die_xl, bx, i);
+      Y = wm_corner_b(d.die_yl, by, j);
+      ok = __dadd_rn(X, mw) <= d.die_xh && __dadd_rn(Y, mh) <= d.die_yh;
     }
     for (int o0 = 0; o0 < nob; o0 += kWmThreads) {
-      __syncthreads();  // the previous chunk has been read
-      if (o0 + (int)threadIdx.x < nob) {
-        const int oc = w.obst[o0 + threadIdx.x];
-        const float2 p = xy[oc];
-        so[threadIdx.x][0] = (double)p.x;
-        so[threadIdx.x][1] = __dadd_rn((double)p.x, (double)d.w[oc]);
-        so[threadIdx.x][2] = (double)p.y;
-        so[threadIdx.x][3] = __dadd_rn((double)p.y, (double)d.h[oc]);
+      if (!once) {
+        __syncthreads();  // the previous chunk has been read
+        stage(o0);
+        __syncthreads();
       }
-      __syncthreads();
       const int cnt = min(kWmThreads, nob - o0);
-      for (int k = 0; ok && k < cnt; ++k)
-        if (X < so[k][1] && so[k][0] < Xr && Y < so[k][3] && so[k][2] < Yr) ok = false;
+      for (int k = 0; ok && k < cnt; ++k) {
+        const int4 r = so[k];
+        if (i >= r.x && i <= r.y && j >= r.z && j <= r.w) ok = false;
+      }
     }
     if (ok) {
       const Best v{__dadd_rn(fx[i], fy[j]),
@@ -231,9 +281,11 @@ __global__ void __launch_bounds__(kWmThreads) k_wm_apply(Dev d, WmDev w, int t, 
 
 }  // namespace
 
+// Two blocks per SM: each block forms the obstacle ranges once and strides
+// over its candidates.
 int wm_select_blocks(int G) {
   const int b = (G + kWmThreads - 1) / kWmThreads;
-  return b < 1 ? 1 : (b > kMaxCellBlocks ? kMaxCellBlocks : b);
+  return b < 1 ? 1 : (b > 304 ? 304 : b);
 }
 
 void launch_wiremask(const Dev &d, const WmDev &w, const int *mptr_host, int copy0, int ncopy,
