@@ -66,6 +66,13 @@ __device__ __forceinline__ unsigned long long warp_sum_u42(unsigned long long a)
 // 0.092 against 0.083.
 constexpr double kAggregateBins = 256.0;
 
+// In the merged path, a warp slot whose lanes form more shared-bin groups
+// than this adds every term to the block table instead.  Measured on the
+// 2.1M-cell design, density stage at iterations 5 / 155: 0.112 / 0.144 ms
+// with per-group reductions always, 0.100 / 0.126 with this cut-off (8: no
+// change; always adding directly: 0.151 / 0.064, but 0.271 at iteration 55).
+constexpr int kMaxMergeGroups = 4;
+
 // Cells are processed grid-stride, a warp at a time, in one of two ways,
 // chosen per copy from how concentrated the previous density pass was:
 //  * dense (the centred start of a placement, where millions of cells share
@@ -143,8 +150,14 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
       const int lane = threadIdx.x & 31;
       const bool lead = b >= 0 && lane == __ffs(mask) - 1;
       const bool shared = __popc(mask) > 1;
-      unsigned long long tot = a;
       unsigned int groups = __ballot_sync(0xffffffffu, lead && shared);
+      if (__popc(groups) > kMaxMergeGroups) {
+        // many small groups: one reduction per group would cost more than
+        // the few same-address conflicts of adding every term to the table
+        if (b >= 0) hash_add(keys, vals, M, b, a);
+        continue;
+      }
+      unsigned long long tot = a;
       while (groups) {
         const int l = __ffs(groups) - 1;
         groups &= groups - 1;
