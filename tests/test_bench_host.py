@@ -2,9 +2,6 @@
 hashes, the serving trace, and the CPU description (no GPU needed)."""
 import hashlib
 import math
-import os
-
-import numpy as np
 
 import bench
 
