@@ -156,3 +156,99 @@ def test_placer_backtracking_invariants():
         if k1n == k1:
             # a redone step: shorter, counted, at most twice in a row
             assert an < 0.95 * a and nbn == nb1 + 1 <= 2
+
+
+def _hand_design():
+    """Four movable cells and one fixed pad on an 8 x 8 die with 2 x 2 bins of
+    4 x 4; every movable cell lies inside one bin, and every net has two pins.
+
+    cell  corner   size     bin     pins
+    0     (1, 1)   1 x 1    (0, 0)  2 (nets A, B)
+    1     (5, 1)   2 x 1    (1, 0)  1 (net A)
+    2     (1, 4)   1 x 3    (0, 1)  0
+    3     (5, 5)   .5 x .5  (1, 1)  0
+    4     (6, 6)   1 x 1    (1, 1)  fixed pad, 1 (net B)
+
+    Net A: cell 0 at offset (.5, .5), cell 1 at (1, .5): pins (1.5, 1.5) and
+    (6, 1.5).  Net B: cell 0 at (.5, .5), pad at (.5, .5): pins (1.5, 1.5) and
+    (6.5, 6.5)."""
+    f32 = lambda v: np.array(v, np.float32)
+    return synth.Design(
+        name="hand", n_movable=4,
+        w=f32([1, 2, 1, 0.5, 1]), h=f32([1, 1, 3, 0.5, 1]),
+        x=f32([1, 5, 1, 5, 6]), y=f32([1, 1, 4, 5, 6]),
+        net_ptr=np.array([0, 2, 4], np.int32), pin_cell=np.array([0, 1, 0, 4], np.int32),
+        pin_dx=f32([0.5, 1.0, 0.5, 0.5]), pin_dy=f32([0.5, 0.5, 0.5, 0.5]),
+        die=(0.0, 0.0, 8.0, 8.0), nx=2, ny=2, target_density=1.0)
+
+
+def test_first_step_composition_worked_by_hand():
+    """The placer's first iteration assembled from quantities worked out in
+    closed form, none of them through the oracle's own WA, density or Poisson
+    code: the two-pin WA gradient d tanh(d / 2g) differentiated, the 2 x 2
+    cosine series of the field written out term by term, the gather of a cell
+    inside one bin (-area E_b), then lambda_0, the preconditioner
+    max(1, pins_i + lambda area_i), alpha_0 and the first Nesterov step.  A
+    preconditioner that counted the pad's pin, dropped lambda area_i or the
+    floor at 1, or a step length normalised over n instead of 2n coordinates,
+    fails here."""
+    d = _hand_design()
+    eta, alpha0 = 0.25, 0.05
+    p = pl.Placer(d, pl.Params(tau_stop=-1.0, max_iters=10, lambda_eta=eta, alpha0=alpha0))
+    x0, y0 = p.vx.copy(), p.vy.copy()
+    assert p.step()
+
+    # gamma_0 from tau_{-1} = 0 (no bin holds more than it may): w_bin = 4
+    w_bin = 4.0
+    gamma = 4.0 * w_bin * 10.0 ** (-11.0 / 9.0)
+    assert p.history[0][3] == pytest.approx(gamma, rel=1e-14)
+    assert p.history[0][2] == 0.0
+
+    # WA gradient of a two-pin net along one axis, pins a < b, d = b - a:
+    # dWL/db = tanh(d/2g) + (d/2g) sech^2(d/2g) = -dWL/da
+    def fp(dist):
+        z = dist / (2.0 * gamma)
+        return math.tanh(z) + z / math.cosh(z) ** 2
+    gwl_x = np.array([-fp(4.5) - fp(5.0), fp(4.5), 0.0, 0.0])
+    gwl_y = np.array([-fp(5.0), 0.0, 0.0, 0.0])   # net A is flat in y
+
+    # rho = (M + t F) / A_bin per bin (x-major), A_bin = 16
+    r00, r10, r01, r11 = 1.0 / 16, 2.0 / 16, 3.0 / 16, (0.25 + 1.0) / 16
+    s = math.sqrt(0.5)               # cos and sin of pi/4; cos(3 pi/4) = -s
+    w1 = math.pi / 8.0               # pi u / (M h) for u = 1, M = 2, h = 4
+    a10 = 0.5 * s * ((r00 + r01) - (r10 + r11))
+    a01 = 0.5 * s * ((r00 + r10) - (r01 + r11))
+    a11 = 0.5 * (r00 - r01 - r10 + r11)
+    # Ex = a10/w1 sin(w1 X) + a11 w1/(2 w1^2) sin(w1 X) cos(w1 Y); sin(w1 X) = s
+    # at both bin centres, cos(w1 Y) = +s (y = 0) or -s (y = 1)
+    ex = {(ix, iy): s * a10 / w1 + s * (s if iy == 0 else -s) * a11 / (2 * w1)
+          for ix in (0, 1) for iy in (0, 1)}
+    ey = {(ix, iy): s * a01 / w1 + s * (s if ix == 0 else -s) * a11 / (2 * w1)
+          for ix in (0, 1) for iy in (0, 1)}
+    bins = [(0, 0), (1, 0), (0, 1), (1, 1)]
+    area = np.array([1.0, 2.0, 3.0, 0.25])
+    gd_x = np.array([-area[i] * ex[b] for i, b in enumerate(bins)])
+    gd_y = np.array([-area[i] * ey[b] for i, b in enumerate(bins)])
+
+    lam = eta * (np.abs(gwl_x).sum() + np.abs(gwl_y).sum()) / (np.abs(gd_x).sum() + np.abs(gd_y).sum())
+    pins = np.array([2.0, 1.0, 0.0, 0.0])
+    P = np.maximum(1.0, pins + lam * area)
+    assert P[3] == 1.0 and P[2] > 1.0 and P[0] > pins[0]   # every branch of the preconditioner
+    gx = (gwl_x + lam * gd_x) / P
+    gy = (gwl_y + lam * gd_y) / P
+    alpha = alpha0 * w_bin / math.sqrt((np.sum(gx ** 2) + np.sum(gy ** 2)) / (2 * 4))
+    ux = np.clip(x0 - alpha * gx, 0.0, 8.0 - np.array([1, 2, 1, 0.5]))
+    uy = np.clip(y0 - alpha * gy, 0.0, 8.0 - np.array([1, 1, 3, 0.5]))
+
+    assert p.lam == pytest.approx(lam, rel=1e-12)
+    assert p.alpha == pytest.approx(alpha, rel=1e-12)
+    np.testing.assert_allclose(p.gpx, gx, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(p.gpy, gy, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(p.ux, ux, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(p.uy, uy, rtol=1e-13, atol=0)
+    # a_0 = 1: no momentum on the first step, v_1 = u_1; a_1 = golden ratio
+    np.testing.assert_allclose(p.vx, ux, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(p.vy, uy, rtol=1e-13, atol=0)
+    assert p.a == pytest.approx((1 + math.sqrt(5)) / 2, rel=1e-15)
+    np.testing.assert_array_equal(p.vpx, x0)
+    assert p.k == 1

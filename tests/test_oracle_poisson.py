@@ -105,3 +105,29 @@ def test_spectral_laplacian_of_potential():
     cy, _ = pois.cos_sin_tables(N)
     lap = cx.T @ lap_coef @ cy
     np.testing.assert_allclose(lap, -(rho - rho.mean()), atol=1e-12)
+
+
+@pytest.mark.parametrize("u,v", [(1, 0), (0, 3), (2, 5)])
+def test_density_energy_of_single_modes(u, v):
+    # rho = cos(wu X) cos(wv Y) has psi = rho / (wu^2 + wv^2), so
+    # D = 1/2 hx hy sum rho psi = 1/2 hx hy (Sx Sy) / (wu^2 + wv^2) with
+    # Sx = sum_x cos^2(pi u (x + 1/2) / M) = M/2 for 0 < u < M and M for u = 0
+    M, N, hx, hy = 16, 8, 2.0, 1.25
+    X = (np.arange(M) + 0.5) * hx
+    Y = (np.arange(N) + 0.5) * hy
+    wu, wv = math.pi * u / (M * hx), math.pi * v / (N * hy)
+    rho = np.outer(np.cos(wu * X), np.cos(wv * Y))
+    psi, _, _ = pois.poisson(rho, hx, hy)
+    Sx = M / 2 if u else M
+    Sy = N / 2 if v else N
+    D = 0.5 * hx * hy * Sx * Sy / (wu * wu + wv * wv)
+    assert pois.density_energy(rho, psi, hx, hy) == pytest.approx(D, rel=1e-12)
+    # a constant offset carries no energy (the (0, 0) mode is dropped), and
+    # two orthogonal modes add their energies
+    psi_c, _, _ = pois.poisson(rho + 3.0, hx, hy)
+    assert pois.density_energy(rho, psi_c, hx, hy) == pytest.approx(D, rel=1e-12)
+    rho2 = np.outer(np.cos(math.pi * 3 * X / (M * hx)), np.cos(math.pi * 1 * Y / (N * hy)))
+    psi2, _, _ = pois.poisson(rho2, hx, hy)
+    psi12, _, _ = pois.poisson(rho + rho2, hx, hy)
+    assert pois.density_energy(rho + rho2, psi12, hx, hy) == pytest.approx(
+        D + pois.density_energy(rho2, psi2, hx, hy), rel=1e-12)
