@@ -57,8 +57,10 @@ def run(design, params: pl.Params, n_rounds, op=SHUFFLE_ALL, p=0.5, seed=0,
         placer.reset(sx, sy)
         placer.run(iters_per_round)
         fx, fy = placer.positions()
+        # both measures of the round's result at the same placement s_i: the
+        # placer's last overflow belongs to v_{k-1} when it stopped at max_iters
         hp = placer.hpwl(placer.vx, placer.vy)
-        tau = placer.tau
+        tau = placer.overflow(placer.density_map(placer.vx, placer.vy))
         rounds.append((hp, tau, fx.copy(), fy.copy()))
         if i < n_rounds and op == WIREMASK:
             nx_, ny_ = wiremask.wiremask(fx, fy, design.w, design.h, design.net_ptr,
