@@ -192,7 +192,8 @@ def run_ours(args):
             torch.distributed.barrier()
     maker, desc = WORKLOADS[args.workload]
     d = maker(0)
-    prm = place.place_default_params(tau_stop=-1.0, max_iters=1 << 30, dct_mode=args.dct)
+    prm = place.place_default_params(tau_stop=-1.0, max_iters=1 << 30, dct_mode=args.dct,
+                                     autotune=args.autotune)
     stream = torch.cuda.current_stream()
     h = place.place_create(d, prm, stream=stream.cuda_stream)
     info = place.place_get_info(h)
@@ -246,6 +247,13 @@ def run_ours(args):
     tv = np.empty(prm.n_copies)
     place.place_eval_hpwl_overflow(h, hp, tv)
     place.place_destroy(h)
+
+    full = None
+    if not args.no_full_run and world == 1:
+        full = run_full(args, place, torch, d, stream)
+    configs = None
+    if not args.no_configs and world == 1:
+        configs = run_configs(args, place, torch)
 
     restarts = None
     if not args.no_restarts:
@@ -306,7 +314,7 @@ def run_ours(args):
                    "parallelism": f"replicas{world}", "l2": "inputs larger than L2 "
                    "(per-iteration working set > 129 MB)" if args.workload == "large_2m"
                    else "working set fits L2 (no flush)",
-                   "dct_mode": ["fp32", "bf16x3"][args.dct]},
+                   "dct_mode": ["fp32", "bf16x3"][args.dct], "tuning": tuning(info)},
         "e2e": {"value": e2e_v, "unit": "iters/s",
                 "h2d_bytes_per_step": 8 * d.n_movable, "d2h_bytes_per_step": 8 * d.n_cells,
                 "note": "per step: set_positions (h2d, restarts the optimiser) + 1 iteration "
@@ -318,6 +326,10 @@ def run_ours(args):
     }
     if cpu is not None:
         out["cpu_baseline"] = cpu
+    if full is not None:
+        out["full_run"] = full
+    if configs is not None:
+        out["configs"] = configs
     if restarts is not None:
         out["restarts"] = restarts
     if serving is not None:
@@ -326,6 +338,129 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def tuning(info):
+    """The kernel variants a handle runs with (chosen by the autotuner or the
+    fixed rules)."""
+    return {"autotuned": bool(info.autotuned), "autotune_ms": info.autotune_ms,
+            "gemm_bn": list(info.gemm_bn), "gemm_split": list(info.gemm_split),
+            "wa_big_cap": info.wa_big_cap, "scatter_thresholds": [info.scatter_t1, info.scatter_t2]}
+
+
+def _stage_sample(place, h, n=5):
+    """Mean per-stage device time (ms) of n iterations run stage by stage
+    (place_step_timed advances the placement like place_step)."""
+    st = np.zeros(5, np.float32)
+    place.place_step_timed(h, n, st)
+    return {k: float(v / n) for k, v in zip(place.PLACE_STAGES, st)}
+
+
+def run_full(args, place, torch, d, stream, tau_stop=0.07, max_iters=1000, chunk=50,
+             samples=(5, 155, 305, 505, 805)):
+    """A whole placement of the headline workload from its centred start: to
+    overflow <= tau_stop or max_iters iterations.  Reports the average rate
+    over the run, the rate of each chunk of iterations, and per-stage times
+    sampled at several phases (5 iterations each, included in the run)."""
+    prm = place.place_default_params(tau_stop=tau_stop, max_iters=max_iters, dct_mode=args.dct)
+    h = place.place_create(d, prm, stream=stream.cuda_stream)
+    conv = np.zeros(1, np.int32)
+    chunks, stages = [], {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    done, total_ms = 0, 0.0
+    torch.cuda.synchronize()
+    while done < max_iters:
+        nxt = min([k for k in samples if k >= done] + [max_iters])
+        if nxt == done:  # a stage sample here
+            stages[str(done)] = _stage_sample(place, h)
+            done += 5
+            place.place_step(h, 0, conv)
+            if conv[0]:
+                break
+            continue
+        n = min(chunk, nxt - done)
+        ev[0].record(stream)
+        place.place_step(h, n)
+        ev[1].record(stream)
+        ev[1].synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        place.place_step(h, 0, conv)
+        st = place.place_get_state(h, 0)
+        ran = st.iter - done
+        total_ms += ms
+        chunks.append({"from": done, "iters": ran, "ms_per_iter": ms / max(ran, 1),
+                       "overflow": st.overflow, "bins_effective": st.bins_effective})
+        done = st.iter
+        if conv[0]:
+            break
+    st = place.place_get_state(h, 0)
+    hp = np.empty(1); tv = np.empty(1)
+    place.place_eval_hpwl_overflow(h, hp, tv)
+    place.place_destroy(h)
+    graph_iters = sum(c["iters"] for c in chunks)
+    return {"workload": args.workload, "tau_stop": tau_stop, "max_iters": max_iters,
+            "iterations": int(st.iter), "converged": bool(st.converged),
+            "final_overflow": float(tv[0]), "final_hpwl": float(hp[0]),
+            "avg_iters_per_s": 1e3 * graph_iters / total_ms if total_ms > 0 else None,
+            "timed_iterations": graph_iters,
+            "note": "graph-launched iterations timed with CUDA events chunk by chunk; the "
+                    "stage samples (place_step_timed, 5 iterations each) are part of the run "
+                    "but not of the average",
+            "chunks": chunks, "stage_ms_at_iteration": stages}
+
+
+def run_configs(args, place, torch):
+    """The small and medium workloads as their configurations state them: the
+    1k-cell design for 300 iterations then one Shuffle (all) round of 300 more
+    (Algorithm 1 with one perturbation), and the 210k-cell design until
+    overflow <= 0.07 or 1,000 iterations."""
+    out = {}
+    d = synth.tiny_1k(0)
+    h = place.place_create(d, place.place_default_params(tau_stop=-1.0, max_iters=300,
+                                                         dct_mode=place.PLACE_DCT_AUTO))
+    info = place.place_get_info(h)
+    bh = np.empty(1); bt = np.empty(1); br = np.empty(1, np.int32)
+    place.place_step(h, 1)  # graph capture outside the timed region
+    place.place_set_positions(h, 0, d.x, d.y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    place.place_hybro(h, 1, place.PLACE_SHUFFLE_ALL, 0.5, 0, 0.1, bh, bt, br)
+    el = time.perf_counter() - t0
+    rh, rt = place.place_get_hybro_rounds(h, 0)
+    place.place_destroy(h)
+    out["tiny_1k"] = {"desc": WORKLOADS["tiny_1k"][1], "iterations": 600, "seconds": el,
+                      "iters_per_s": 600 / el, "spectral": ["fp32", "bf16x3"][info.dct_mode],
+                      "round_hpwl": rh.tolist(), "round_overflow": rt.tolist(),
+                      "best_round": int(br[0]), "best_hpwl": float(bh[0]),
+                      "note": "300 iterations, Shuffle (all) p = 0.5 seed 0, 300 more; host "
+                              "wall time with the evaluations and the perturbation"}
+    d = synth.medium_210k(0)
+    h = place.place_create(d, place.place_default_params(tau_stop=0.07, max_iters=1000,
+                                                         dct_mode=args.dct))
+    info = place.place_get_info(h)
+    place.place_step(h, 1)
+    place.place_set_positions(h, 0, d.x, d.y)
+    conv = np.zeros(1, np.int32)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    while not conv[0]:
+        place.place_step(h, 50, conv)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = place.place_get_state(h, 0)
+    hp = np.empty(1); tv = np.empty(1)
+    place.place_eval_hpwl_overflow(h, hp, tv)
+    place.place_destroy(h)
+    out["medium_210k"] = {"desc": WORKLOADS["medium_210k"][1], "iterations": int(st.iter),
+                          "converged": bool(st.converged), "seconds": ms / 1e3,
+                          "iters_per_s": 1e3 * st.iter / ms, "final_overflow": float(tv[0]),
+                          "final_hpwl": float(hp[0]),
+                          "spectral": ["fp32", "bf16x3"][info.dct_mode],
+                          "note": "to overflow <= 0.07 or 1,000 iterations, CUDA events around "
+                                  "the whole run (50-iteration launches, stop flags read back)"}
+    return out
 
 
 def run_restarts(args, place, torch, K=32, p=0.5):
@@ -354,6 +489,7 @@ def run_restarts(args, place, torch, K=32, p=0.5):
     place.place_eval_hpwl_overflow(h1, base_hp, base_tau)
     # batched: one handle, K copies in one captured graph per iteration
     hb = place.place_create(d, mk(K))
+    tune_b = tuning(place.place_get_info(hb))
     place.place_step(hb, 1)  # capture the graph outside the timed region
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -398,6 +534,7 @@ def run_restarts(args, place, torch, K=32, p=0.5):
     bb, bs = int(np.argmin(np.where(tau_b <= 0.1, hp_b, np.inf))), int(np.argmin(np.where(tau_s <= 0.1, hp_s, np.inf)))
     return {"workload": "medium_210k: 210k cells, 220k nets, 512x512 bins, t=0.9",
             "copies": K, "operator": "Shuffle (all)", "p": p, "tau_stop": 0.07,
+            "tuning_batched": tune_b,
             "batched_restarts_per_s": K / t_b, "serial_restarts_per_s": K / t_s,
             "speedup": t_s / t_b, "batched_s": t_b, "serial_s": t_s,
             "iters_per_restart_mean": float(np.mean(iters_b)),
@@ -506,7 +643,7 @@ def run_serving(args, place, n_jobs, min_cells, max_cells, max_active=16):
         finally:
             srv.close()
 
-    span0, _, _ = run(1, [0.0] * n_jobs)
+    span0, res0, st0 = run(1, [0.0] * n_jobs)
     rate = 0.8 * n_jobs / span0
     gaps = np.random.default_rng(1).exponential(1.0 / rate, n_jobs)
     arrivals = np.cumsum(gaps) - gaps[0]
@@ -521,8 +658,22 @@ def run_serving(args, place, n_jobs, min_cells, max_cells, max_active=16):
                      "agg_iters_per_s": iters / span, "peak_active": peak_a,
                      "peak_device_bytes": peak_b, "max_active": slots}
         out.setdefault("_hash", {})[name] = [int(r.position_hash) for r in res]
+    # saturated: every job arrives at t = 0, so throughput, not arrivals,
+    # decides the makespan (the one-at-a-time run is the calibration run above)
+    spanb, resb, (peak_b, peak_a) = run(max_active, [0.0] * n_jobs)
+    sat = {}
+    for name, span, res in (("fifo", span0, res0), ("batched", spanb, resb)):
+        iters = sum(r.iterations for r in res)
+        lat = np.array([r.done_s - r.arrival_s for r in res]) * 1e3
+        sat[name] = {"makespan_s": span, "agg_iters_per_s": iters / span,
+                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+    sat["throughput_gain"] = sat["batched"]["agg_iters_per_s"] / sat["fifo"]["agg_iters_per_s"]
+    sat["peak_active"] = peak_a
+    out["saturated"] = sat
     h = out.pop("_hash")
-    out["results_identical"] = h["fifo"] == h["batched"]
+    out["results_identical"] = (h["fifo"] == h["batched"]
+                                and [int(r.position_hash) for r in res0] == h["fifo"]
+                                and [int(r.position_hash) for r in resb] == h["fifo"])
     return out
 
 
@@ -546,26 +697,49 @@ def cpu_model():
     return platform.machine()
 
 
-def oracle_one_core(workload, n_iters=1):
-    """Oracle iterations/s on one core: a child process with the BLAS and
-    OpenMP thread pools set to one thread before numpy loads."""
-    code = ("import sys, time; sys.path.insert(0, %r); "
-            "from paper_2402_18311_gb300 import synth; from oracle import placer as opl; "
-            "d = getattr(synth, %r)(0); o = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=1 << 30)); "
-            "t = time.perf_counter(); o.run(%d); print(%d / (time.perf_counter() - t))"
-            % (ROOT, workload, n_iters, n_iters))
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+ONE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
+def _oracle_child(code, timeout=600):
+    """Run `code` in a child process whose BLAS and OpenMP pools have one
+    thread (set before numpy loads); returns the float it prints last."""
+    env = dict(os.environ, **ONE_THREAD_ENV)
     try:
         r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
-                           timeout=600)
+                           timeout=timeout)
         return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
     except (OSError, subprocess.SubprocessError, ValueError, IndexError):
         return None
 
 
+def oracle_one_core(workload, n_iters=1):
+    """Oracle iterations/s of `workload` on one thread."""
+    code = ("import sys, time; sys.path.insert(0, %r); "
+            "from paper_2402_18311_gb300 import synth; from oracle import placer as opl; "
+            "d = getattr(synth, %r)(0); o = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=1 << 30)); "
+            "t = time.perf_counter(); o.run(%d); print(%d / (time.perf_counter() - t))"
+            % (ROOT, workload, n_iters, n_iters))
+    return _oracle_child(code)
+
+
+def oracle_config1_seconds():
+    """Seconds the oracle takes, on one thread, for the 1k-cell configuration:
+    300 iterations, one Shuffle (all) round, 300 more (Algorithm 1)."""
+    code = ("import sys, time; sys.path.insert(0, %r); "
+            "from paper_2402_18311_gb300 import synth; from oracle import placer as opl, hybro; "
+            "d = synth.tiny_1k(0); t = time.perf_counter(); "
+            "hybro.run(d, opl.Params(tau_stop=-1.0, max_iters=300), n_rounds=1, "
+            "op=hybro.SHUFFLE_ALL, p=0.5, seed=0, tau_target=0.1); "
+            "print(time.perf_counter() - t)" % (ROOT,))
+    return _oracle_child(code)
+
+
 def cpu_baseline(d, args, n_iters=1):
     """The FP64 oracle as it stands, on the same workload: n_iters full
-    iterations after its set-up, on all host cores and on one core."""
+    iterations after its set-up, on one thread (``value``, ``cores`` = 1), and
+    in this process (``value_all_cores``: numpy's elementwise work stays on
+    one thread there too; only its BLAS matrix products use the other cores).
+    Also the oracle's time for the 1k-cell configuration on one thread."""
     from oracle import placer as opl
     t0 = time.perf_counter()
     o = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=1 << 30))
@@ -573,11 +747,16 @@ def cpu_baseline(d, args, n_iters=1):
     t0 = time.perf_counter()
     o.run(n_iters)
     el = time.perf_counter() - t0
-    return {"value": n_iters / el, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
-            "cpu_model": cpu_model(), "value_1_core": oracle_one_core(args.workload, n_iters),
+    v1 = oracle_one_core(args.workload, n_iters)
+    c1 = oracle_config1_seconds()
+    return {"value": v1, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "value_all_cores": n_iters / el, "cores_all": os.cpu_count(),
+            "config_tiny_1k_seconds_1_core": c1,
             "sample": f"{n_iters} full iteration(s) of the {args.workload} workload after "
-                      f"{setup:.1f} s of oracle set-up; numpy float64 (elementwise work single-"
-                      f"threaded, BLAS matmuls multi-threaded; value_1_core with one BLAS thread)"}
+                      f"{setup:.1f} s of oracle set-up; numpy float64 on one thread (BLAS and "
+                      f"OpenMP pools set to 1); value_all_cores: the same in-process, where only "
+                      f"BLAS matrix products use more than one core"}
 
 
 def run_reference(args):
@@ -598,10 +777,11 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
            "config": {"workload": args.workload, "desc": desc, "parallelism": "cpu"},
-           "cpu_baseline": {"value": v, "unit": "iters/s", "cores": os.cpu_count(),
+           "cpu_baseline": {"value": v, "unit": "iters/s", "cores": 1,
                             "kind": "oracle",
                             "sample": f"{args.steps} timed oracle iterations after {args.warmup} "
-                                      f"warm-up iterations of the {args.workload} workload"},
+                                      f"warm-up iterations of the {args.workload} workload, "
+                                      f"numpy float64 on one thread"},
            "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -619,15 +799,26 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-restarts", action="store_true",
                     help="skip the batched-vs-serial restarts measurement")
-    ap.add_argument("--serving-jobs", type=int, default=24,
-                    help="jobs in the serving trace (0: skip; 200 for the full workload)")
-    ap.add_argument("--serving-max-cells", type=int, default=200_000,
-                    help="largest design of the serving trace (1000000 for the full workload)")
+    ap.add_argument("--serving-jobs", type=int, default=200,
+                    help="jobs in the serving trace (0: skip)")
+    ap.add_argument("--serving-max-cells", type=int, default=1_000_000,
+                    help="largest design of the serving trace")
+    ap.add_argument("--no-full-run", action="store_true",
+                    help="skip the whole placement of the headline workload")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 1k-cell and 210k-cell configuration runs")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1],
+                    help="1: tile shapes and kernel variants timed at create; 0: fixed rules")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
-        # bounded sample: one oracle iteration takes about ten seconds at 2M
+        # the oracle runs on one thread: re-run this process with the BLAS and
+        # OpenMP pools set to one thread before numpy loads
+        if any(os.environ.get(k) != v for k, v in ONE_THREAD_ENV.items()):
+            os.environ.update(ONE_THREAD_ENV)
+            os.execv(sys.executable, [sys.executable] + sys.argv)
+        # bounded sample: one oracle iteration takes about three seconds at 2M
         # cells, so at most 3 warm-up and 3 timed iterations are run
         args.steps = min(args.steps, 3)
         args.warmup = min(args.warmup, 3)

@@ -48,6 +48,8 @@ extern "C" {
                                  grid position of least HPWL */
 
 /* Spectral-solve arithmetic. */
+#define PLACE_DCT_AUTO (-1) /* the default: PLACE_DCT_BF16X3 when nx and ny are
+                               multiples of 128, else PLACE_DCT_FP32 */
 #define PLACE_DCT_FP32 0   /* FP32 CUDA-core GEMMs (any grid, multiples of 16) */
 #define PLACE_DCT_BF16X3 1 /* split-BF16 (3 products, FP32 accumulation) on the
                               tcgen05 tensor cores; grids must be multiples of 128 */
@@ -119,10 +121,28 @@ typedef struct place_params {
   float tau_stop;         /* 0.07 */
   int32_t max_iters;      /* 1000 */
   float constant_gamma;   /* > 0: fixed gamma (tests) */
-  int32_t dct_mode;       /* PLACE_DCT_* */
+  int32_t dct_mode;       /* PLACE_DCT_AUTO (default), _FP32 or _BF16X3 */
   int32_t max_backtracks; /* 0 (off) .. 64: redo a too-long step at most this
                              often in a row (see below) */
   int32_t stretch;        /* 0 (off) or 1: density stretching (see below) */
+  int32_t autotune;       /* 1 (default): the knobs below left at their automatic
+                             value are chosen by timing candidates on this design
+                             at create (results cached per shape in the process);
+                             0: fixed rules */
+  int32_t scatter_mode;   /* -1 (default): the density scatter picks per copy and
+                             pass, from the previous pass's effective number of
+                             occupied bins, between merging a warp's shared bins,
+                             a shared-memory table and direct atomics; 0, 1, 2
+                             force one of them.  All give the same map. */
+  int32_t gemm_bn;        /* 0 (default): automatic; 64 or 128: tile width of
+                             every tensor-core GEMM stage of the spectral solve */
+  int32_t wa_big_cap;     /* 0 (default): automatic; 32..6144: pins of a net of
+                             more than 256 pins kept in shared memory */
+  int32_t gemm_split;     /* 0 (default): automatic; 1: one CTA per GEMM tile;
+                             2: two CTAs per 128-wide tile, one half of the
+                             contraction each, on stages with at most half as
+                             many tiles as the device has SMs.  Every choice
+                             gives the same bits. */
 } place_params;
 
 /* Read-only facts about a handle. */
@@ -133,7 +153,13 @@ typedef struct place_info {
   double bin_w, bin_h;
   int64_t device_bytes;   /* device memory the handle holds */
   int32_t kernels_per_iter; /* this library's kernel launches in one iteration */
-  int32_t pad;
+  int32_t dct_mode;       /* the spectral path in use: PLACE_DCT_FP32 or _BF16X3 */
+  int32_t gemm_bn[4];     /* tile width of each tensor-core GEMM stage */
+  int32_t gemm_split[4];  /* CTAs per tile of each stage (split-K when 2) */
+  int32_t wa_big_cap;     /* pins of a big net kept in shared memory */
+  int32_t autotuned;      /* 1: the choices here came from timing (or its cache) */
+  double scatter_t1, scatter_t2; /* effective-bin thresholds of the scatter's ways */
+  double autotune_ms;     /* host time the tuning took at create (0 on a cache hit) */
 } place_info;
 
 /* Optimiser scalars of one copy after its last iteration. */
@@ -282,6 +308,15 @@ int place_hybro(place_t *h, int32_t n_rounds, int32_t op, float p, uint64_t seed
 /* Best positions kept by place_hybro for copy `copy` ([n_cells], host or device). */
 int place_get_best_positions(place_t *h, int32_t copy, float *x, float *y);
 
+/* Per-round record of the last place_hybro call for copy `copy`: the exact
+ * HPWL (Eq. 1) and overflow after round r's placement, r = 0..n_rounds
+ * (Algorithm 1 records one solution per round).  hpwl, overflow: host
+ * [n_rounds + 1], nullable; *n_records (nullable) receives n_rounds + 1, and
+ * with cap smaller than that only the first cap records are written.  EINVAL
+ * before the first place_hybro call. */
+int place_get_hybro_rounds(place_t *h, int32_t copy, double *hpwl, double *overflow,
+                           int32_t cap, int32_t *n_records);
+
 /* Measurement helper: run n_iters iterations like place_step, but launched
  * stage by stage (no graph) with CUDA events between the stages, and add the
  * device time of each stage in milliseconds to stage_ms (host
@@ -294,6 +329,16 @@ int place_get_best_positions(place_t *h, int32_t copy, float *x, float *y);
 #define PLACE_N_STAGES 5
 int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms);
 
+/* Measurement helper: the floor of the wirelength stage's memory traffic on
+ * this netlist.  Times (CUDA events, after one warm-up launch) a kernel that
+ * does only the memory operations the WA pass of Eq. 3 cannot avoid: per pin
+ * the streamed pin_cell and offset reads, one random 8-byte position gather
+ * and one random 64-bit reduction into the cell's gradient sum; per net the
+ * net_ptr read.  *ms receives the mean time of one pass over every copy.
+ * The gradient sums are cleared afterwards; the placement state is otherwise
+ * untouched.  Synchronises. */
+int place_measure_wa_floor(place_t *h, int32_t reps, float *ms);
+
 /* Density map and overflow of a placement without any device allocation.
  *
  * The paper has no counterpart to this function: it serves callers that
@@ -301,33 +346,39 @@ int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms);
  * framework whose memory pool owns all device memory during a step, a
  * real-time service that forbids allocation after start-up, or a callback
  * that must not trigger the device-wide synchronisation an allocation can
- * cause.  Its scratch (64-bit density map and reduction partials) is one
- * fixed-size array inside the library's module; every GPU that loads the
- * library holds it (about 8 MB) until the process exits.
+ * cause.  Its scratch (64-bit density map, reduction partials and the area
+ * sum) is one fixed-size array inside the library's module; every GPU that
+ * loads the library holds it (about 8 MB) until the process exits.
  *
- * Computes exactly what place_eval_density() computes for a handle: the
- * movable-cell map M in units of 2^-2F and tau = sum_b max(0, M_b -
- * t (A_b - F_b)) / A_mov, for n_movable cells with lower-left corners x, y
- * and sizes w, h (device float arrays), the die and bins, the fixed-point
- * resolution frac_bits (place_info.frac_bits of a handle of the same
- * design), the total movable area mov_area (sum of w*h, layout units) and
- * the fixed-cell map fixed_map (device int64 [nx*ny], x-major; NULL: no
- * fixed cells).  Outputs: *overflow (device double) and, if map_out is not
- * NULL, the map (device int64 [nx*ny]).  Work runs asynchronously on
- * `stream`.
+ * Computes what place_eval_density() computes for a handle of the same
+ * design: the movable-cell map M in units of 2^-2F and tau = sum_b max(0, M_b
+ * - t (A_b - F_b)) / A_mov, for n_movable cells with lower-left corners x, y
+ * and sizes w, h (device float arrays).  Sizes are quantised like positions,
+ * W = rint(w 2^F), and A_mov is the exact sum of W H, as in place_create.
+ * frac_bits is the resolution F (place_info.frac_bits of a handle of the
+ * same design); fixed_map is the fixed-cell map (device int64 [nx*ny],
+ * x-major; NULL: no fixed cells).  Outputs: *overflow (device double) and,
+ * if map_out is not NULL, the map (device int64 [nx*ny]).  Work runs
+ * asynchronously on `stream`.
  *
- * Limits: nx * ny <= PLACE_NOALLOC_MAX_BINS, else PLACE_EINVAL.  All calls
- * share the one scratch array and each call clears it first; calls whose
- * work overlaps on the GPU (different streams or host threads) race on it
- * and must be serialised.  The first call with a given device current looks
- * up the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Calls no cudaMalloc, cudaFree or allocating
- * library routine. */
+ * Errors on the host: PLACE_EINVAL for nx * ny > PLACE_NOALLOC_MAX_BINS, a
+ * die origin or bin size that is not a multiple of 2^-F, or other malformed
+ * arguments; PLACE_ERANGE when frac_bits is too fine for the die (extent
+ * 2^F >= 2^30, the rule place_create uses to choose F).  On the device: a cell
+ * whose quantised size falls outside [1, 2^31), or a total area of 2^62 units
+ * or more, makes *overflow NaN (the map is then not meaningful).
+ *
+ * Sharing: all calls use the one scratch array and each call clears it
+ * first; calls whose work overlaps on the GPU (different streams or host
+ * threads) race on it and must be serialised.  The first call with a given
+ * device current looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Calls no cudaMalloc, cudaFree or allocating library routine. */
 #define PLACE_NOALLOC_MAX_BINS (1024 * 1024)
 int place_overflow_noalloc(const float *x, const float *y, const float *w, const float *h,
-                           int32_t n_movable, double mov_area, const place_die *die,
-                           const place_bins *bins, int32_t frac_bits, const int64_t *fixed_map,
-                           double *overflow, int64_t *map_out, void *stream);
+                           int32_t n_movable, const place_die *die, const place_bins *bins,
+                           int32_t frac_bits, const int64_t *fixed_map, double *overflow,
+                           int64_t *map_out, void *stream);
 
 /* Device memory place_create would take for this netlist, bins and
  * parameters (an upper bound; no device work).  Used for admission control. */
@@ -378,7 +429,8 @@ int place_server_create(int64_t hbm_budget, int32_t max_active, int32_t iters_pe
                         place_server **out);
 
 /* Queue a job.  The netlist arrays are borrowed until the job has finished
- * (the server does not copy them); params->n_copies is forced to 1.  *id
+ * (the server does not copy them); params->n_copies is forced to 1 and
+ * params->autotune to 0 (tuning at admission would add to the job's latency).  *id
  * receives the job id (submission order from 0).  PLACE_ENOMEM if the job
  * alone exceeds the budget. */
 int place_server_submit(place_server *s, const place_netlist *nl, const place_die *die,

@@ -71,9 +71,20 @@ constexpr int kNetsPerBlock[4] = {256, 64, 16, 8};
 // pins of a big net kept in shared memory: 3072 (24 KB) is the most that
 // still lets eight 256-thread blocks share an SM; longer nets re-gather the rest
 constexpr int kBigCapMax = 3072;
+// the scatter's fixed-rule thresholds on the effective number of occupied
+// bins: merged below the first, the shared table below the second, direct
+// atomics above (the autotuner replaces them by measured crossovers)
+constexpr double kScatterMergedBelow = 32.0;
+constexpr double kScatterTableBelow = 1024.0;
 constexpr int kMaxBigNetBlocks = 8192;  // one block per net above 256 pins, up to this many
 
 bool is_integer(double v) { return std::floor(v) == v && std::isfinite(v); }
+
+// PLACE_DCT_AUTO: the tensor-core path wherever the grid allows it.
+int resolve_dct_mode(int mode, int nx, int ny) {
+  if (mode != PLACE_DCT_AUTO) return mode;
+  return (nx % 128 == 0 && ny % 128 == 0) ? PLACE_DCT_BF16X3 : PLACE_DCT_FP32;
+}
 
 }  // namespace
 
@@ -102,6 +113,10 @@ struct place_t {
   // Hybro bookkeeping (host)
   std::vector<double> best_hpwl, best_tau;
   std::vector<int> best_round;
+  std::vector<double> round_hpwl, round_tau;  // [K][rounds] of the last place_hybro
+  int n_round_records = 0;
+  int autotuned = 0;
+  double autotune_ms = 0.0;
 };
 
 extern "C" {
@@ -121,9 +136,14 @@ void place_default_params(place_params *p) {
   p->tau_stop = 0.07f;
   p->max_iters = 1000;
   p->constant_gamma = 0.0f;
-  p->dct_mode = PLACE_DCT_FP32;
+  p->dct_mode = PLACE_DCT_AUTO;
   p->max_backtracks = 0;
   p->stretch = 0;
+  p->autotune = 1;
+  p->scatter_mode = -1;
+  p->gemm_bn = 0;
+  p->wa_big_cap = 0;
+  p->gemm_split = 0;
 }
 
 int place_destroy(place_t *h) {
@@ -206,7 +226,7 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.sel_idx = a.take<unsigned int>(d.sort_n);
   d.px_tmp = a.take<float>(C);
   d.py_tmp = a.take<float>(C);
-  d.err = a.take<int>(1);
+  d.err = a.take<int>(2);  // [0]: bounded waits gave up; [1]: a sink for measurement kernels
   if (d.tc) {
     const size_t nx2 = (size_t)d.nx * d.nx, ny2 = (size_t)d.ny * d.ny;
     d.rho_h = a.take<__nv_bfloat16>(K * G);
@@ -223,8 +243,24 @@ void layout(Dev &d, Arena &a, int n_copies) {
     d.A3l = a.take<__nv_bfloat16>(3 * ny2);
     d.A4h = a.take<__nv_bfloat16>(3 * nx2);
     d.A4l = a.take<__nv_bfloat16>(3 * nx2);
+    // split-K workspace: two 128 x 128 FP32 halves per tile of the largest
+    // stage that may split (a stage with at most half as many 128-wide tiles
+    // as the device has SMs)
+    const int sms = d.sms > 0 ? d.sms : 152;
+    const size_t t1 = (size_t)(d.nx / 128) * (d.ny / 128) * K;
+    const size_t tiles[4] = {t1, t1, 2 * t1, 2 * t1};
+    size_t ws_tiles = 0;
+    for (int s = 0; s < 4; ++s) {
+      d.tc_split_ok[s] = 2 * tiles[s] <= (size_t)sms ? 1 : 0;
+      if (d.tc_split_ok[s]) ws_tiles = std::max(ws_tiles, tiles[s]);
+    }
+    d.tc_ws_tiles = (int)ws_tiles;
+    d.tc_ws = ws_tiles ? a.take<float>(ws_tiles * 2 * 128 * 128) : nullptr;
+    d.tc_ws_ctr = ws_tiles ? a.take<unsigned int>(ws_tiles) : nullptr;
   }
 }
+
+int encode_tc_maps(place_t *h);
 
 // Split the FP32 transform matrices into bf16 pairs and encode the tensor
 // maps of the four GEMM stages.
@@ -242,12 +278,24 @@ int setup_tc(place_t *h) {
   launch_split_bf16(d.CTm, d.A4h + 2 * nx2, d.A4l + 2 * nx2, nx2, st);
   CKL();
   const int nx = d.nx, ny = d.ny, K = d.K;
-  // tile width per stage: 128; 64 only for grids so small that 128-wide
-  // tiles would occupy under a quarter of the SMs
+  // tile width per stage, unless forced or tuned: 128; 64 only for grids so
+  // small that 128-wide tiles would occupy under a quarter of the SMs
   const int sms = d.sms;
   const int tiles128[4] = {(nx / 128) * (ny / 128) * K, (ny / 128) * (nx / 128) * K,
                            (nx / 128) * (ny / 128) * 2 * K, (ny / 128) * (nx / 128) * 2 * K};
-  for (int s = 0; s < 4; ++s) d.tc_bn[s] = tiles128[s] * 4 <= sms ? 64 : 128;
+  for (int s = 0; s < 4; ++s) {
+    d.tc_bn[s] = d.prm.gemm_bn ? d.prm.gemm_bn : (tiles128[s] * 4 <= sms ? 64 : 128);
+    d.tc_split[s] = (d.prm.gemm_split == 2 && d.tc_split_ok[s] && d.tc_bn[s] == 128) ? 2 : 1;
+  }
+  if (d.tc_ws_ctr) CK(cudaMemsetAsync(d.tc_ws_ctr, 0, sizeof(unsigned int) * d.tc_ws_tiles, h->stream));
+  if (tc_prepare()) return fail(PLACE_ECUDA, "cannot reserve %d bytes of shared memory", tc_smem_bytes(128));
+  return encode_tc_maps(h);
+}
+
+// Tensor maps of the four GEMM stages for the tile widths in d.tc_bn.
+int encode_tc_maps(place_t *h) {
+  Dev &d = h->d;
+  const int nx = d.nx, ny = d.ny, K = d.K;
   struct M { const void *p; int k, rows, batch, box; } spec[16] = {
       {d.A1h, ny, ny, 1, 128}, {d.A1l, ny, ny, 1, 128},
       {d.rho_h, ny, nx, K, d.tc_bn[0]}, {d.rho_l, ny, nx, K, d.tc_bn[0]},
@@ -262,8 +310,58 @@ int setup_tc(place_t *h) {
     if (r) return fail(PLACE_ECUDA, "tensor map %d could not be encoded (%d)", i, r);
   }
   d.tcm = h->maps;
-  if (tc_prepare()) return fail(PLACE_ECUDA, "cannot reserve %d bytes of shared memory", tc_smem_bytes(128));
   return PLACE_OK;
+}
+
+// Context of the tuning hooks: the handle and the start positions.
+struct TuneCtx {
+  place_t *h;
+  const float2 *xy0;
+};
+
+int encode_tc_maps_cb(void *ctx) { return encode_tc_maps(static_cast<TuneCtx *>(ctx)->h); }
+
+void drop_graph(place_t *h) {
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->exec = nullptr;
+  h->graph = nullptr;
+}
+
+int enqueue_reset(place_t *h, int c0, int n);
+int ensure_graph(place_t *h);
+
+// Every copy back at the start, a graph captured for the current device
+// state, two warm-up iterations, then n timed ones: ms per iteration
+// (negative on a CUDA error).
+float time_iters_cb(void *ctx, int n) {
+  TuneCtx *t = static_cast<TuneCtx *>(ctx);
+  place_t *h = t->h;
+  Dev &d = h->d;
+  const size_t C = d.n_cells;
+  for (int c = 0; c < d.K; ++c)
+    if (cudaMemcpyAsync(d.xy + c * C, t->xy0, sizeof(float2) * C, cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess)
+      return -1.f;
+  if (enqueue_reset(h, 0, d.K)) return -1.f;
+  drop_graph(h);
+  if (ensure_graph(h)) return -1.f;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1.f;
+  }
+  for (int i = 0; i < 2; ++i) cudaGraphLaunch(h->exec, h->stream);
+  cudaEventRecord(e0, h->stream);
+  for (int i = 0; i < n; ++i) cudaGraphLaunch(h->exec, h->stream);
+  cudaEventRecord(e1, h->stream);
+  float ms = -1.f;
+  if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+    ms /= n;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return cudaGetLastError() == cudaSuccess ? ms : -1.f;
 }
 
 // Device-side error flag (bounded waits that gave up); call after a sync.
@@ -431,6 +529,15 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   if (prm.max_backtracks < 0 || prm.max_backtracks > 64)
     return fail(PLACE_EINVAL, "max_backtracks must be in [0, 64]");
   if (prm.stretch != 0 && prm.stretch != 1) return fail(PLACE_EINVAL, "stretch must be 0 or 1");
+  if (prm.autotune != 0 && prm.autotune != 1) return fail(PLACE_EINVAL, "autotune must be 0 or 1");
+  if (prm.scatter_mode < -1 || prm.scatter_mode > 2)
+    return fail(PLACE_EINVAL, "scatter_mode must be -1, 0, 1 or 2");
+  if (prm.gemm_bn != 0 && prm.gemm_bn != 64 && prm.gemm_bn != 128)
+    return fail(PLACE_EINVAL, "gemm_bn must be 0, 64 or 128");
+  if (prm.wa_big_cap != 0 && (prm.wa_big_cap < 32 || prm.wa_big_cap > 6144))
+    return fail(PLACE_EINVAL, "wa_big_cap must be 0 or in [32, 6144]");
+  if (prm.gemm_split < 0 || prm.gemm_split > 2) return fail(PLACE_EINVAL, "gemm_split must be 0, 1 or 2");
+  prm.dct_mode = resolve_dct_mode(prm.dct_mode, bins->nx, bins->ny);
   if (prm.dct_mode != PLACE_DCT_FP32 && prm.dct_mode != PLACE_DCT_BF16X3)
     return fail(PLACE_EINVAL, "unknown dct_mode %d", prm.dct_mode);
   if (prm.dct_mode == PLACE_DCT_BF16X3 && (bins->nx % 128 || bins->ny % 128))
@@ -520,7 +627,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
 
   // quantised sizes and movable area
   std::vector<int> Wq(C), Hq(C);
-  double mov_area_q = 0.0;
+  unsigned __int128 mov_area_q = 0;  // exact; converted to double once
   for (int i = 0; i < C; ++i) {
     double wq = std::nearbyint((double)nl->w[i] * s), hq = std::nearbyint((double)nl->h[i] * s);
     if (wq < 1 || hq < 1 || wq >= 2147483647.0 || hq >= 2147483647.0) {
@@ -528,9 +635,9 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
       return fail(PLACE_ERANGE, "cell %d size out of the fixed-point range", i);
     }
     Wq[i] = (int)wq; Hq[i] = (int)hq;
-    if (i < Mv) mov_area_q += wq * hq;
+    if (i < Mv) mov_area_q += (unsigned __int128)((unsigned long long)Wq[i] * (unsigned long long)Hq[i]);
   }
-  d.mov_area_q = mov_area_q > 0 ? mov_area_q : 1.0;
+  d.mov_area_q = mov_area_q > 0 ? (double)mov_area_q : 1.0;
 
   // nets grouped by degree class (stable), pins in the new net order
   std::vector<int> order(E);
@@ -547,6 +654,18 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     auto deg = [&](int e) { return nl->net_ptr[e + 1] - nl->net_ptr[e]; };
     std::stable_sort(order.begin() + d.cls_begin[4], order.begin() + d.cls_begin[5],
                      [&](int a, int b) { return deg(a) > deg(b); });
+    // the other classes by their lowest cell index, whose pin goes first
+    // (below): the first pins of the nets a warp handles then lie on nearby
+    // cells, so their position gathers and gradient reductions share sectors
+    std::vector<int> min_cell(E, 0);
+    for (int e = 0; e < E; ++e) {
+      int m = C;
+      for (int j = nl->net_ptr[e]; j < nl->net_ptr[e + 1]; ++j) m = std::min(m, nl->pin_cell[j]);
+      min_cell[e] = m;
+    }
+    for (int c = 0; c < 4; ++c)
+      std::stable_sort(order.begin() + d.cls_begin[c], order.begin() + d.cls_begin[c + 1],
+                       [&](int a, int b) { return min_cell[a] < min_cell[b]; });
   }
   std::vector<int> net_ptr(E + 1), pin_cell(P);
   std::vector<float2> pin_off(P);
@@ -557,9 +676,13 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     int e = order[ne];
     int p0 = nl->net_ptr[e], p1 = nl->net_ptr[e + 1];
     int q = net_ptr[ne];
+    int jmin = p0;  // the pin on the lowest cell index goes first
+    for (int j = p0 + 1; j < p1; ++j)
+      if (nl->pin_cell[j] < nl->pin_cell[jmin]) jmin = j;
     for (int j = p0; j < p1; ++j, ++q) {
-      pin_cell[q] = nl->pin_cell[j];
-      pin_off[q] = make_float2(nl->pin_dx[j], nl->pin_dy[j]);
+      const int src = j == p0 ? jmin : (j == jmin ? p0 : j);
+      pin_cell[q] = nl->pin_cell[src];
+      pin_off[q] = make_float2(nl->pin_dx[src], nl->pin_dy[src]);
     }
     net_ptr[ne + 1] = q;
     if (nl->net_w) net_w[ne] = nl->net_w[e];
@@ -595,7 +718,10 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   d.giq = (float)std::ldexp(1.0, -Fg);
   int max_deg = 0;
   for (int e = 0; e < E; ++e) max_deg = std::max(max_deg, net_ptr[e + 1] - net_ptr[e]);
-  d.wa_big_cap = std::min(std::max(max_deg, 1), kBigCapMax);
+  d.wa_big_cap = prm.wa_big_cap ? prm.wa_big_cap : std::min(std::max(max_deg, 1), kBigCapMax);
+  d.scat_t1 = kScatterMergedBelow;
+  d.scat_t2 = kScatterTableBelow;
+  d.scat_force = prm.scatter_mode;
   std::vector<float> npins(std::max(Mv, 1)), area(std::max(Mv, 1));
   for (int i = 0; i < Mv; ++i) {
     npins[i] = (float)cell_npins[i];
@@ -728,11 +854,9 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     up(d.cu, cu.data(), sizeof(float) * nx);
     up(d.cv, cv.data(), sizeof(float) * ny);
   }
-  {
-    std::vector<float2> xy0(C);
-    for (int i = 0; i < C; ++i) xy0[i] = make_float2(nl->x0[i], nl->y0[i]);
-    for (int c = 0; c < d.K && rc == PLACE_OK; ++c) up(d.xy + (size_t)c * C, xy0.data(), sizeof(float2) * C);
-  }
+  std::vector<float2> xy0(C);
+  for (int i = 0; i < C; ++i) xy0[i] = make_float2(nl->x0[i], nl->y0[i]);
+  for (int c = 0; c < d.K && rc == PLACE_OK; ++c) up(d.xy + (size_t)c * C, xy0.data(), sizeof(float2) * C);
   if (rc != PLACE_OK) {
     place_destroy(h);
     return rc;
@@ -752,7 +876,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   if (ce == cudaSuccess && wa_prepare(d.wa_big_cap)) ce = cudaErrorInvalidValue;
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.cs, 0, sizeof(CopyState) * d.K, h->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.ctr, 0, sizeof(unsigned int) * d.K * C_COUNT, h->stream);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(d.err, 0, sizeof(int), h->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(d.err, 0, 2 * sizeof(int), h->stream);
   if (ce != cudaSuccess) {
     place_destroy(h);
     return fail(PLACE_ECUDA, "memset: %s", cudaGetErrorString(ce));
@@ -766,6 +890,27 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   if (rc == PLACE_OK) {
     ce = cudaStreamSynchronize(h->stream);
     if (ce != cudaSuccess) rc = fail(PLACE_ECUDA, "create: %s", cudaGetErrorString(ce));
+  }
+  if (rc == PLACE_OK && prm.autotune) {
+    // time the candidates on this design, then put copy 0 and every
+    // optimiser back to the start
+    TuneOut to{};
+    TuneCtx tctx{h, xy0.data()};
+    const TuneHooks hooks{encode_tc_maps_cb, time_iters_cb, &tctx};
+    int trc = autotune(d, max_deg, h->stream, hooks, &to);
+    drop_graph(h);  // captured for a candidate; the first step captures the final choice
+    if (trc) {
+      rc = fail(trc, "autotuning failed: %s", cudaGetErrorString(cudaGetLastError()));
+    } else {
+      h->autotuned = 1;
+      h->autotune_ms = to.ms;
+      for (int c = 0; c < d.K && rc == PLACE_OK; ++c) up(d.xy + (size_t)c * C, xy0.data(), sizeof(float2) * C);
+      if (rc == PLACE_OK) rc = enqueue_reset(h, 0, d.K);
+      if (rc == PLACE_OK) {
+        ce = cudaStreamSynchronize(h->stream);
+        if (ce != cudaSuccess) rc = fail(PLACE_ECUDA, "create: %s", cudaGetErrorString(ce));
+      }
+    }
   }
   if (rc != PLACE_OK) {
     place_destroy(h);
@@ -790,7 +935,16 @@ int place_get_info(const place_t *h, place_info *o) {
   // scatter, finish, 4 GEMMs, WA classes, cell grad, precond0, update; the
   // stretched scatter with density stretching, the step redo with backtracking
   o->kernels_per_iter = 2 + 4 + wa + 3 + (d.Ms ? 1 : 0) + (d.upx ? 1 : 0);
-  o->pad = 0;
+  o->dct_mode = d.tc ? PLACE_DCT_BF16X3 : PLACE_DCT_FP32;
+  for (int s = 0; s < 4; ++s) {
+    o->gemm_bn[s] = d.tc ? d.tc_bn[s] : 0;
+    o->gemm_split[s] = d.tc ? d.tc_split[s] : 0;
+  }
+  o->wa_big_cap = d.wa_big_cap;
+  o->autotuned = h->autotuned;
+  o->scatter_t1 = d.scat_t1;
+  o->scatter_t2 = d.scat_t2;
+  o->autotune_ms = h->autotune_ms;
   return PLACE_OK;
 }
 
@@ -873,6 +1027,31 @@ int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms) {
   CKL();
   if ((rc = check_dev_err(h))) return rc;
   for (int s = 0; s < PLACE_N_STAGES; ++s) stage_ms[s] += (float)acc[s];
+  return PLACE_OK;
+}
+
+int place_measure_wa_floor(place_t *h, int32_t reps, float *ms) {
+  if (!h || !ms) return fail(PLACE_EINVAL, "null argument");
+  if (reps < 1) return fail(PLACE_EINVAL, "reps < 1");
+  const Dev &d = h->d;
+  cudaStream_t st = h->stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  launch_wa_floor(d, 0, d.K, st);  // warm-up
+  cudaEventRecord(e0, st);
+  for (int i = 0; i < reps; ++i) launch_wa_floor(d, 0, d.K, st);
+  cudaEventRecord(e1, st);
+  // the floor kernel added into the gradient sums: clear them for the next pass
+  cudaMemsetAsync(d.gacc, 0, sizeof(unsigned long long) * (size_t)d.K * std::max(d.n_mov, 1), st);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(PLACE_ECUDA, "floor measurement: %s", cudaGetErrorString(e));
+  CKL();
+  *ms = t / reps;
   return PLACE_OK;
 }
 
@@ -1082,6 +1261,10 @@ int place_hybro(place_t *h, int32_t n_rounds, int32_t op, float p, uint64_t seed
   const size_t C = d.n_cells;
   std::vector<double> bh(K, 0.0), bt(K, 0.0), hp(K), tau(K);
   std::vector<int> br(K, -1), conv(K);
+  const int nrec = n_rounds + 1;
+  h->round_hpwl.assign((size_t)K * nrec, 0.0);
+  h->round_tau.assign((size_t)K * nrec, 0.0);
+  h->n_round_records = 0;
   for (int r = 0; r <= n_rounds; ++r) {
     // place every copy until it stops (converged or max_iters)
     for (;;) {
@@ -1093,6 +1276,11 @@ int place_hybro(place_t *h, int32_t n_rounds, int32_t op, float p, uint64_t seed
     }
     int rc = place_eval_hpwl_overflow(h, hp.data(), tau.data());
     if (rc) return rc;
+    for (int c = 0; c < K; ++c) {
+      h->round_hpwl[(size_t)c * nrec + r] = hp[c];
+      h->round_tau[(size_t)c * nrec + r] = tau[c];
+    }
+    h->n_round_records = r + 1;
     for (int c = 0; c < K; ++c) {
       bool better = br[c] < 0;
       if (!better) {
@@ -1129,6 +1317,22 @@ int place_get_best_positions(place_t *h, int32_t copy, float *x, float *y) {
   return copy_out_xy(h, h->d.bxy + copy * C, x, y);
 }
 
+int place_get_hybro_rounds(place_t *h, int32_t copy, double *hpwl, double *overflow, int32_t cap,
+                           int32_t *n_records) {
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  if (h->n_round_records <= 0) return fail(PLACE_EINVAL, "place_hybro has not run on this handle");
+  if (cap < 0) return fail(PLACE_EINVAL, "cap < 0");
+  const int n = h->n_round_records;
+  const size_t stride = h->round_hpwl.size() / (size_t)h->d.K;
+  for (int r = 0; r < std::min(n, (int)cap); ++r) {
+    if (hpwl) hpwl[r] = h->round_hpwl[(size_t)copy * stride + r];
+    if (overflow) overflow[r] = h->round_tau[(size_t)copy * stride + r];
+  }
+  if (n_records) *n_records = n;
+  return PLACE_OK;
+}
+
 }  // extern "C"
 
 extern "C" int place_estimate_device_bytes(const place_netlist *nl, const place_bins *bins,
@@ -1146,6 +1350,7 @@ extern "C" int place_estimate_device_bytes(const place_netlist *nl, const place_
   d.n_cells = nl->n_cells; d.n_mov = nl->n_movable; d.n_nets = nl->n_nets; d.n_pins = nl->n_pins;
   d.nx = bins->nx; d.ny = bins->ny; d.G = bins->nx * bins->ny;
   d.has_net_w = nl->net_w ? 1 : 0;
+  prm.dct_mode = resolve_dct_mode(prm.dct_mode, bins->nx, bins->ny);
   d.tc = prm.dct_mode == PLACE_DCT_BF16X3 ? 1 : 0;
   d.prm = prm;
   const int cb = std::max(1, std::min((d.n_mov + kThreads - 1) / kThreads, kMaxCellBlocks));

@@ -49,6 +49,49 @@ __device__ __forceinline__ float block_sum_f(float v, float *sm) {
   return r;
 }
 
+// Block sum of one float per thread, compensated: every addition of the
+// shuffle tree is an error-free two-sum (the rounding error of s = a + b is
+// (a - (s - b')) + (b - b') with b' = s - a, exact in FP32), and the errors
+// travel with the sums, so the result has about FP64 accuracy while all the
+// arithmetic stays on the FP32 pipes (GB300's FP64 rate is a small fraction
+// of its FP32 rate).  Returns (sum, correction) folded into a double, valid
+// in thread 0.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+template <int NT>
+__device__ __forceinline__ double block_sum_fc(float v, float2 *sm) {
+  float c = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float w = __shfl_xor_sync(0xffffffffu, v, o), wc = __shfl_xor_sync(0xffffffffu, c, o);
+    float e;
+    two_sum(v, w, v, e);
+    c = __fadd_rn(c, __fadd_rn(wc, e));
+  }
+  const int wi = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sm[wi] = make_float2(v, c);
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    const float2 p = (l < NT / 32) ? sm[l] : make_float2(0.f, 0.f);
+    v = p.x;
+    c = p.y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float w = __shfl_xor_sync(0xffffffffu, v, o), wc = __shfl_xor_sync(0xffffffffu, c, o);
+      float e;
+      two_sum(v, w, v, e);
+      c = __fadd_rn(c, __fadd_rn(wc, e));
+    }
+    r = (double)v + (double)c;
+  }
+  return r;
+}
+
 typedef unsigned __int128 u128;
 
 __device__ __forceinline__ u128 shfl_xor_u128(u128 v, int o) {

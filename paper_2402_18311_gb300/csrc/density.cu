@@ -59,12 +59,10 @@ __device__ __forceinline__ unsigned long long warp_sum_u42(unsigned long long a)
   return s0 + (s1 << 21);
 }
 
-// Effective number of occupied bins, (sum M)^2 / sum M^2, below which the
-// scatter merges contributions before its global atomics.  Measured on the
-// 2.1M-cell design, density stage: at 85 effective bins merging takes 0.146
-// ms against 0.188 ms direct; at 1155 it takes 0.118 against 0.110; at 5300
-// 0.092 against 0.083.
-constexpr double kAggregateBins = 256.0;
+// The scatter's three ways (ScatterMode) are chosen per copy from the
+// effective number of occupied bins of the previous density pass, n_eff =
+// (sum M)^2 / sum M^2, against the handle's thresholds d.scat_t1 < d.scat_t2
+// (set at create, by the autotuner when it runs).
 
 // In the merged path, a warp slot whose lanes form more shared-bin groups
 // than this adds every term to the block table instead.  Measured on the
@@ -73,17 +71,23 @@ constexpr double kAggregateBins = 256.0;
 // change; always adding directly: 0.151 / 0.064, but 0.271 at iteration 55).
 constexpr int kMaxMergeGroups = 4;
 
-// Cells are processed grid-stride, a warp at a time, in one of two ways,
+// Cells are processed grid-stride, a warp at a time, in one of three ways,
 // chosen per copy from how concentrated the previous density pass was:
-//  * dense (the centred start of a placement, where millions of cells share
-//    a few bins): each cell touches at most 2 x 2 bins when it is no larger
-//    than a bin; the warp visits those four slots in lock-step, lanes that hit
-//    the same bin are merged with a match/reduce (exact integer sums), and one
-//    lane per distinct bin adds the total to a shared-memory hash table that
-//    is flushed with one 64-bit atomic per distinct bin;
-//  * otherwise each lane adds its overlaps straight to the map: the match
-//    costs more than the little contention it would remove.
-// Larger cells add their remaining bins directly in both ways.
+//  * SCAT_MERGED, very dense (the centred start of a placement, where
+//    millions of cells share a few bins): each cell touches at most 2 x 2
+//    bins when it is no larger than a bin; the warp visits those four slots
+//    in lock-step, lanes that hit the same bin are merged with a match/reduce
+//    (exact integer sums), and one lane per distinct bin adds the total to a
+//    shared-memory hash table that is flushed with one 64-bit atomic per
+//    distinct bin;
+//  * SCAT_TABLE, concentrated (the middle of a placement, tens to a few
+//    thousand effective bins): every lane adds each term to the block's
+//    shared-memory table without the match, which costs more than the
+//    shared-memory conflicts it would remove once the lanes of a warp rarely
+//    share a bin;
+//  * SCAT_DIRECT, spread: each lane adds its overlaps straight to the map.
+// Larger cells add their remaining bins through the table in the first two
+// ways.  Every way adds the same integers, so the map is the same.
 __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval) {
   __shared__ int keys[kHash];
   __shared__ unsigned long long vals[kHash];
@@ -98,7 +102,11 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
   const float2 *xy = d.xy + (size_t)c * d.n_cells;
   unsigned long long *M = d.M + (size_t)c * d.G;
   const int stride = gridDim.x * blockDim.x;
-  if (d.cs[c].n_eff >= kAggregateBins) {
+  const double n_eff = d.cs[c].n_eff;
+  const int mode = d.scat_force >= 0 ? d.scat_force
+                                     : (n_eff < d.scat_t1 ? SCAT_MERGED
+                                                          : (n_eff < d.scat_t2 ? SCAT_TABLE : SCAT_DIRECT));
+  if (mode == SCAT_DIRECT) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += stride) {
       const float2 v = xy[i];
       const QRect32 r = qrect32(v.x, v.y, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW32, d.BH32,
@@ -115,6 +123,22 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
     }
     return;
   }
+  if (mode == SCAT_TABLE) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += stride) {
+      const float2 v = xy[i];
+      const QRect32 r = qrect32(v.x, v.y, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW32, d.BH32,
+                                d.nx, d.ny, d.ibw_q, d.ibh_q);
+      for (int ix = r.ix0; ix <= r.ix1; ++ix) {
+        const int ox = overlap32(r.x0, r.x1, ix, d.BW32);
+        if (ox == 0) continue;
+        for (int iy = r.iy0; iy <= r.iy1; ++iy) {
+          const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
+          if (oy == 0) continue;
+          hash_add(keys, vals, M, ix * d.ny + iy, (unsigned long long)((long long)ox * oy));
+        }
+      }
+    }
+  } else {
   // one cell's overlap with one bin is at most the bin area
   const bool two_limbs = (double)d.BW * (double)d.BH < 4398046511104.0;  // 2^42
   // warp-uniform trip count
@@ -188,6 +212,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
       }
     }
   }
+  }  // SCAT_MERGED
   __syncthreads();
   for (int i = threadIdx.x; i < kHash; i += blockDim.x) {
     int k = keys[i];
@@ -348,6 +373,10 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
     }
     d.ctr[(size_t)c * C_COUNT + C_FINISH] = 0u;
   }
+}
+
+void launch_scatter_main(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st) {
+  k_scatter<<<dim3(d.cell_blocks, ncopy), kThreads, 0, st>>>(d, copy0, eval);
 }
 
 void launch_scatter(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st) {

@@ -46,6 +46,9 @@ enum Slot { S_TAU = 0, S_HPWL, S_WL, S_GW1, S_GD1, S_DG2, S_DV2, S_G2, S_HP64, S
 // Last-block counters per copy.
 enum Counter { C_FINISH = 0, C_CELL, C_PRE0, C_UPDATE, C_COUNT };
 
+// The density scatter's ways of adding overlaps to the map (density.cu).
+enum ScatterMode { SCAT_MERGED = 0, SCAT_TABLE = 1, SCAT_DIRECT = 2 };
+
 // What the density-finish kernel does with the overflow it reduces.
 enum FinishMode { FIN_ITER = 0, FIN_EVAL = 1, FIN_RESET = 2 };
 
@@ -132,7 +135,12 @@ struct Dev {
   __nv_bfloat16 *A1h, *A1l, *A2h, *A2l, *A3h, *A3l, *A4h, *A4l;
   const void *tcm;                  // host array of 16 CUtensorMap (4 per GEMM stage)
   int tc_bn[4];                     // tile width N (64 or 128) of each GEMM stage
-  int *err;                         // device error flag (bounded waits)
+  int tc_split[4];                  // 1, or 2: split-K over two CTAs (tile width 128 only)
+  int tc_split_ok[4];               // the stage has few enough tiles for split-K
+  float *tc_ws;                     // split-K partial halves (stages with tc_split_ok)
+  unsigned int *tc_ws_ctr;          // split-K arrivals per tile
+  int tc_ws_tiles;                  // tiles the split-K workspace holds
+  int *err;                         // [2]: device error flag (bounded waits), measurement sink
 
   // Hybro best solutions
   float2 *bxy;               // [K][n_cells]
@@ -151,6 +159,10 @@ struct Dev {
   int wa_block_base[8];       // slot offset of the class's blocks
   int wa_blocks_total;
   int wa_big_cap;             // pins of a > 256-pin net kept in shared memory
+  // density scatter: SCAT_MERGED below n_eff scat_t1, SCAT_TABLE below scat_t2,
+  // SCAT_DIRECT above; scat_force >= 0 forces one way (tuning)
+  double scat_t1, scat_t2;
+  int scat_force;
 };
 
 // WireMask tables (built at create) and scratch (allocated on first use).
@@ -225,6 +237,29 @@ void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_
                cudaStream_t st);
 void launch_hpwl64(const Dev &d, int copy0, int ncopy, cudaStream_t st);
 int wa_prepare(int cap);
+void launch_wa_floor(const Dev &d, int copy0, int ncopy, cudaStream_t st);
+void launch_wa_class(const Dev &d, int cls, int copy0, int ncopy, int eval, cudaStream_t st);
+void launch_scatter_main(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
+
+// Create-time tuning (autotune.cu).  Chooses, for the knobs the caller left
+// automatic, the tensor-core GEMM tile width, the big-net shared-memory cap
+// and the scatter's thresholds, by timing candidates on the handle's own
+// device state.  The positions and optimiser state of every copy are
+// overwritten; the caller restores them and drops any captured graph.
+struct TuneOut {
+  int bn[4];
+  int split[4];
+  int cap;
+  double t1, t2;
+  double ms;     // host time spent
+  int cached;    // 1: taken from the process-wide cache
+};
+struct TuneHooks {
+  int (*encode_maps)(void *ctx);        // tensor maps for d.tc_bn
+  float (*time_iters)(void *ctx, int n);  // ms per graph iteration from the start state
+  void *ctx;
+};
+int autotune(Dev &d, int max_deg, cudaStream_t st, const TuneHooks &hk, TuneOut *out);
 int cell_grad_blocks_per_sm();
 void launch_cell_grad(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
 void launch_precond0(const Dev &d, int copy0, int ncopy, cudaStream_t st);

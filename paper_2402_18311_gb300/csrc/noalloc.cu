@@ -6,22 +6,25 @@
 // real-time or embedded service that forbids allocation after start-up, or
 // a callback that must not trigger the implicit device synchronisation an
 // allocation can cause.  For them this entry point keeps its scratch (the
-// 64-bit density map and the reduction partials) in one file-scope
-// `static __device__` array of fixed size, allocated with the module and
-// held by every GPU that loads the library until the process exits.  The
-// caller passes the inputs and the outputs; nothing else is needed.
+// 64-bit density map, the reduction partials and the movable-area sum) in one
+// file-scope `static __device__` array of fixed size, allocated with the
+// module and held by every GPU that loads the library until the process
+// exits.  The caller passes the inputs and the outputs; nothing else is
+// needed.
 //
 // Limits and sharing: at most PLACE_NOALLOC_MAX_BINS bins.  Every call uses
 // the same array, which keeps the last call's contents; each call clears the
-// map and the reduction counter before use.  Calls whose work overlaps on
-// the GPU (two streams, or two host threads) race on the array and give
-// wrong results: serialise them.  The device address of the array is looked
-// up once per device with cudaGetSymbolAddress on the first call made with
-// that device current; make that first call before any stream capture.
+// map, the area sum, the flags and the reduction counter before use.  Calls
+// whose work overlaps on the GPU (two streams, or two host threads) race on
+// the array and give wrong results: serialise them.  The device address of
+// the array is looked up once per device with cudaGetSymbolAddress on the
+// first call made with that device current; make that first call before any
+// stream capture.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <mutex>
 
@@ -39,7 +42,10 @@ constexpr int kMaxDevices = 64;
 struct NoAllocScratch {
   unsigned long long map[PLACE_NOALLOC_MAX_BINS];
   unsigned long long part[kNaBlocks * 2];
-  unsigned int counter;
+  // cleared by every call (one memset from area_lo to the end)
+  unsigned long long area_lo, area_hi;  // exact sum of W H over the cells (128 bits)
+  unsigned int counter;                 // last-block counter of the finish pass
+  int bad;                              // a cell size outside [1, 2^31) units
 };
 
 static __device__ __align__(256) NoAllocScratch g_scratch;
@@ -63,16 +69,32 @@ struct NaGrid {
   int nx, ny;
   long long t_mant;
   int t_shift;
-  double mov_area_q;
 };
 
+// Quantised sizes W = rint(w 2^F), H = rint(h 2^F) (w 2^F is exact in FP32),
+// the cells' exact overlaps added to the map, and the exact sum of W H.  A
+// size outside [1, 2^31) raises the scratch's `bad` flag and the cell is
+// skipped (the handle path rejects such a cell at create).
 __global__ void __launch_bounds__(kNaThreads)
     k_na_scatter(NoAllocScratch *s, const float *x, const float *y, const float *w, const float *h,
                  int n, NaGrid g) {
+  __shared__ u128 sm[32];
+  u128 area = 0;
+  bool bad = false;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    // sizes quantised like positions: w * 2^F is exact, then round to nearest even
-    const int W = (int)__float2ll_rn(w[i] * g.scale), H = (int)__float2ll_rn(h[i] * g.scale);
-    QRect r = qrect(x[i], y[i], W, H, g.scale, g.XL, g.YL, g.BW, g.BH, g.nx, g.ny);
+    const float ws = w[i] * g.scale, hs = h[i] * g.scale;
+    // also false for NaN sizes
+    if (!(ws >= 0.5f && ws < 2147483647.0f && hs >= 0.5f && hs < 2147483647.0f)) {
+      bad = true;
+      continue;
+    }
+    const long long W = __float2ll_rn(ws), H = __float2ll_rn(hs);
+    if (W < 1 || H < 1 || W > 2147483647LL || H > 2147483647LL) {
+      bad = true;
+      continue;
+    }
+    area += (u128)(unsigned long long)(W * H);
+    QRect r = qrect(x[i], y[i], (int)W, (int)H, g.scale, g.XL, g.YL, g.BW, g.BH, g.nx, g.ny);
     for (int ix = r.ix0; ix <= r.ix1; ++ix) {
       long long ox = overlap1(r.X, r.W, g.XL + (long long)ix * g.BW, g.BW);
       if (ox == 0) continue;
@@ -82,6 +104,15 @@ __global__ void __launch_bounds__(kNaThreads)
         atomicAdd(&s->map[(size_t)ix * g.ny + iy], (unsigned long long)(ox * oy));
       }
     }
+  }
+  if (bad) s->bad = 1;
+  const u128 a = block_sum_u128<kNaThreads>(area, sm);
+  if (threadIdx.x == 0 && a != 0) {
+    // 128-bit accumulation from two 64-bit atomics with the carry propagated
+    const unsigned long long lo = (unsigned long long)a, hi = (unsigned long long)(a >> 64);
+    const unsigned long long old = atomicAdd(&s->area_lo, lo);
+    const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    if (hi + carry) atomicAdd(&s->area_hi, hi + carry);
   }
 }
 
@@ -111,7 +142,17 @@ __global__ void __launch_bounds__(kNaThreads)
     v += ((u128)s->part[2 * i + 1] << 64) | s->part[2 * i];
   v = block_sum_u128<kNaThreads>(v, sm);
   if (threadIdx.x == 0) {
-    *overflow = ldexp(u128_to_double(v), -g.t_shift) / g.mov_area_q;
+    // the movable area in units of 2^-2F; the map's entries stay below it, so
+    // beyond 2^62 (or with a rejected cell) the map itself is not trusted
+    const unsigned long long lo = *(volatile unsigned long long *)&s->area_lo;
+    const unsigned long long hi = *(volatile unsigned long long *)&s->area_hi;
+    const int bad = *(volatile int *)&s->bad;
+    if (bad || hi != 0 || lo >= (1ull << 62)) {
+      *overflow = __longlong_as_double(0x7ff8000000000000LL);  // quiet NaN
+    } else {
+      const double amov = lo > 0 ? (double)lo : 1.0;
+      *overflow = ldexp(u128_to_double(v), -g.t_shift) / amov;
+    }
     s->counter = 0u;
   }
 }
@@ -147,10 +188,10 @@ bool dyadic(double v, double s) {
 using namespace hp;
 
 extern "C" int place_overflow_noalloc(const float *x, const float *y, const float *w,
-                                      const float *h, int32_t n_movable, double mov_area,
-                                      const place_die *die, const place_bins *bins,
-                                      int32_t frac_bits, const int64_t *fixed_map,
-                                      double *overflow, int64_t *map_out, void *stream) {
+                                      const float *h, int32_t n_movable, const place_die *die,
+                                      const place_bins *bins, int32_t frac_bits,
+                                      const int64_t *fixed_map, double *overflow,
+                                      int64_t *map_out, void *stream) {
   if (!die || !bins || !overflow) return na_fail(PLACE_EINVAL, "null die, bins or overflow");
   if (n_movable < 0) return na_fail(PLACE_EINVAL, "n_movable < 0");
   if (n_movable > 0 && (!x || !y || !w || !h)) return na_fail(PLACE_EINVAL, "null cell array");
@@ -161,11 +202,19 @@ extern "C" int place_overflow_noalloc(const float *x, const float *y, const floa
                    PLACE_NOALLOC_MAX_BINS);
   if (frac_bits < 0 || frac_bits > 24) return na_fail(PLACE_EINVAL, "frac_bits must be in [0, 24]");
   if (!(bins->target_density > 0.f)) return na_fail(PLACE_EINVAL, "target density must be > 0");
-  if (!(mov_area > 0.0)) return na_fail(PLACE_EINVAL, "movable area must be > 0");
+  if (!(die->xh > die->xl) || !(die->yh > die->yl)) return na_fail(PLACE_EINVAL, "empty die");
   const double s = std::ldexp(1.0, frac_bits);
+  // the extent rule of the handle's resolution F: every coordinate of the die
+  // and its extent, times 2^F, below 2^30 (keeps the bin arithmetic in range)
+  const double ext = std::fmax(std::fmax(std::fmax(std::fabs(die->xl), std::fabs(die->xh)),
+                                         std::fmax(std::fabs(die->yl), std::fabs(die->yh))),
+                               std::fmax(die->xh - die->xl, die->yh - die->yl));
+  if (!(ext * s < std::ldexp(1.0, 30)))
+    return na_fail(PLACE_ERANGE, "frac_bits %d is too fine for this die: extent 2^F must stay "
+                   "below 2^30", frac_bits);
   const double bw = (die->xh - die->xl) / nx, bh = (die->yh - die->yl) / ny;
-  if (!(bw > 0) || !(bh > 0)) return na_fail(PLACE_EINVAL, "empty die");
-  if (!dyadic(die->xl, s) || !dyadic(die->yl, s) || !dyadic(bw, s) || !dyadic(bh, s))
+  if (!dyadic(die->xl, s) || !dyadic(die->yl, s) || !dyadic(bw, s) || !dyadic(bh, s) ||
+      !(bw * s >= 1.0) || !(bh * s >= 1.0))
     return na_fail(PLACE_EINVAL, "die origin and bin size must be multiples of 2^-%d", frac_bits);
   NaGrid g;
   g.scale = (float)s;
@@ -177,14 +226,15 @@ extern "C" int place_overflow_noalloc(const float *x, const float *y, const floa
   g.t_mant = (long long)std::ldexp(f, 24);
   g.t_shift = 24 - e2;
   if (g.t_shift < 0 || g.t_shift > 60) return na_fail(PLACE_EINVAL, "target density out of range");
-  g.mov_area_q = mov_area * s * s;
 
   NoAllocScratch *sp = nullptr;
   int rc = scratch_ptr(&sp);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(sp->map, 0, sizeof(unsigned long long) * (size_t)nx * ny, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&sp->counter, 0, sizeof(unsigned int), st);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(&sp->area_lo, 0,
+                        sizeof(NoAllocScratch) - offsetof(NoAllocScratch, area_lo), st);
   if (e != cudaSuccess) return na_fail(PLACE_ECUDA, "clearing the scratch: %s", cudaGetErrorString(e));
   if (n_movable > 0) {
     int blocks = (n_movable + kNaThreads - 1) / kNaThreads;

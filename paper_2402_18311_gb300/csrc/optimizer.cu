@@ -12,11 +12,11 @@
 //   a_{k+1} = (1 + sqrt(4 a_k^2 + 1)) / 2
 //   v_{k+1} = clamp(u_{k+1} + (a_k - 1)/a_{k+1} (u_{k+1} - u_k))
 //   lambda_0 = eta |gWL|_1 / |gD|_1;  lambda_{k+1} = lambda_k clamp(mu^(1 - dHPWL/dref))
-// Per-cell work is FP32 (GB300's FP64 rate is tiny); each block sums its
-// cells in FP32 and publishes one FP64 partial; the last block of each copy
-// reduces the partials in a fixed order and advances the copy's scalars, so
-// every run of the same input gives the same bits and no separate scalar
-// kernels are launched.
+// Per-cell work is FP32 (GB300's FP64 rate is tiny); each thread sums its
+// few cells in FP32, each block sums its threads with a compensated FP32
+// tree and publishes one FP64 partial; the last block of each copy reduces the partials in a fixed order
+// and advances the copy's scalars, so every run of the same input gives the
+// same bits and no separate scalar kernels are launched.
 #include <math.h>
 
 #include "common.cuh"
@@ -97,8 +97,8 @@ __device__ void advance_scalars(const Dev &d, CopyState *cs, bool first, double 
 // stretched rectangle and scaled by its density scale R / 2^31.
 template <bool STRETCH>
 __global__ void __launch_bounds__(kThreads, 4) k_cell_grad(Dev d, int copy0, int eval) {
-  __shared__ float smf[32];
   __shared__ double smd[32];
+  __shared__ float2 smc[32];
   __shared__ int flag;
   pdl_wait();
   const int c = copy0 + blockIdx.y;
@@ -207,10 +207,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_cell_grad(Dev d, int copy0, int
       dv2 += bx * bx + by * by;
     }
   }
-  float r0 = block_sum_f<kThreads>(n1, smf);
-  float r1 = block_sum_f<kThreads>(d1, smf);
-  float r2 = block_sum_f<kThreads>(dg2, smf);
-  float r3 = block_sum_f<kThreads>(dv2, smf);
+  // per-thread sums in FP32 (a few cells each), compensated block sums:
+  // these norms set lambda_0 and every step length
+  const double r0 = block_sum_fc<kThreads>(n1, smc);
+  const double r1 = block_sum_fc<kThreads>(d1, smc);
+  const double r2 = block_sum_fc<kThreads>(dg2, smc);
+  const double r3 = block_sum_fc<kThreads>(dv2, smc);
   if (threadIdx.x == 0) {
     part_ptr(d, c, S_GW1)[blockIdx.x] = r0;
     part_ptr(d, c, S_GD1)[blockIdx.x] = r1;
@@ -252,8 +254,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_cell_grad(Dev d, int copy0, int
 // k == 0 only: preconditioned gradient once lambda_0 is known, |g|^2, and the
 // first step length.
 __global__ void __launch_bounds__(kThreads) k_precond0(Dev d, int copy0) {
-  __shared__ float smf[32];
   __shared__ double smd[32];
+  __shared__ float2 smc[32];
   __shared__ int flag;
   pdl_wait();
   const int c = copy0 + blockIdx.y;
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) k_precond0(Dev d, int copy0) {
     d.gy[par][cm + i] = gy;
     g2 += gx * gx + gy * gy;
   }
-  float r = block_sum_f<kThreads>(g2, smf);
+  const double r = block_sum_fc<kThreads>(g2, smc);
   if (threadIdx.x == 0) part_ptr(d, c, S_G2)[blockIdx.x] = r;
   if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_PRE0, &flag)) return;
   const double s = sum_slot<kThreads>(d, c, S_G2, gridDim.x, smd);

@@ -245,6 +245,9 @@ int place_server_submit(place_server *s, const place_netlist *nl, const place_di
   j->bins = *bins;
   if (params) j->prm = *params; else place_default_params(&j->prm);
   j->prm.n_copies = 1;
+  // jobs run with the fixed rules: tuning at admission would add its time to
+  // the latency of every job of a new shape
+  j->prm.autotune = 0;
   if (job->kind == PLACE_JOB_RESTART) {
     Job *p = find(s, job->parent);
     if (!p || p->nl.n_cells != nl->n_cells) {

@@ -15,7 +15,7 @@
 // so no transpose pass is needed between steps.
 //
 // This file holds the FP32 CUDA-core GEMM (64x64x16 tiles, 4x4 register
-// micro-tiles); the tensor-core split-TF32 path lives in spectral_tc.cu.
+// micro-tiles); the tensor-core BF16x3 path lives in spectral_tc.cu.
 #include "common.cuh"
 #include "internal.cuh"
 #include "spectral_tc.cuh"
@@ -150,23 +150,27 @@ void launch_spectral_tc(const Dev &d, int copy0, int ncopy, int with_psi, int ev
   g.err = d.err;
   g.wu = d.wu; g.wv = d.wv; g.cu = d.cu; g.cv = d.cv;
   g.with_psi = with_psi;
+  g.ws = d.tc_ws;
+  g.ws_ctr = d.tc_ws_ctr;
   const int nw = with_psi ? 3 : 2;
   // G1: T[0] = Cn rho^T   (ny x nx, K = ny)
   g.M = d.ny; g.N = d.nx; g.K = d.ny; g.nwhich = 1; g.b_per_copy = 1; g.d_per_copy = 3;
   g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
-  launch_tc_gemm(mp + 0, g, ncopy, d.tc_bn[0], st);
+  launch_tc_gemm(mp + 0, g, ncopy, d.tc_bn[0], d.tc_split[0], st);
   // G2: SB = spectral(Cm T[0]^T)   (nx x ny, K = nx)
   g.M = d.nx; g.N = d.ny; g.K = d.nx; g.b_per_copy = 3; g.d_per_copy = 3;
   g.epi = TC_EPI_SPECTRAL; g.Dh = d.SB_h; g.Dl = d.SB_l;
-  launch_tc_gemm(mp + 4, g, ncopy, d.tc_bn[1], st);
+  launch_tc_gemm(mp + 4, g, ncopy, d.tc_bn[1], d.tc_split[1], st);
   // G3: T[w] = An_w SB[w]^T   (ny x nx, K = ny)
   g.M = d.ny; g.N = d.nx; g.K = d.ny; g.nwhich = nw;
   g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
-  launch_tc_gemm(mp + 8, g, ncopy, d.tc_bn[2], st);
+  // with psi the last two stages have a third field: more tiles than the
+  // split-K workspace holds, so one CTA per tile (the same bits)
+  launch_tc_gemm(mp + 8, g, ncopy, d.tc_bn[2], with_psi ? 1 : d.tc_split[2], st);
   // G4: E[w] = Am_w T[w]^T   (nx x ny, K = nx)
   g.M = d.nx; g.N = d.ny; g.K = d.nx;
   g.epi = TC_EPI_F32; g.Df = d.E; g.Dh = g.Dl = nullptr;
-  launch_tc_gemm(mp + 12, g, ncopy, d.tc_bn[3], st);
+  launch_tc_gemm(mp + 12, g, ncopy, d.tc_bn[3], with_psi ? 1 : d.tc_split[3], st);
 }
 
 void launch_spectral(const Dev &d, int copy0, int ncopy, int with_psi, int eval,

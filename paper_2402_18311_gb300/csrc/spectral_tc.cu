@@ -37,7 +37,7 @@ template <int BN, int STAGES>
 struct Cfg {
   static constexpr int TILE_B = BN * BKE * 2;
   static constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;  // ring, alignment, barriers
   // Instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = BN.
   static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
                                     ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
@@ -158,7 +158,14 @@ __device__ __forceinline__ void split_store(__nv_bfloat16 *hi, __nv_bfloat16 *lo
 using namespace tc;
 
 // D[z] = A[which] x B[z]^T over one 128 x BN tile; z = copy * nwhich + which.
-template <int BN, int STAGES>
+//
+// The contraction is always accumulated as two halves of K, in two TMEM
+// accumulators, and the tile is their sum: with SPLIT = 1 one CTA runs both
+// halves; with SPLIT = 2 (split-K, for stages with too few tiles to fill the
+// SMs) two CTAs run one half each, both publish their half to a workspace,
+// and the second to finish adds the other's half to its own and runs the
+// epilogue.  Addition is commutative, so every variant gives the same bits.
+template <int BN, int STAGES, int SPLIT>
 __global__ void __launch_bounds__(128, 1)
     k_umma_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
                 const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
@@ -169,10 +176,12 @@ __global__ void __launch_bounds__(128, 1)
   const int which = z % g.nwhich;
   const int c = g.copy0 + z / g.nwhich;
   if (!g.eval && g.cs[c].stopped) return;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int mt = blockIdx.y / SPLIT, ks = blockIdx.y % SPLIT;
+  const int m0 = mt * BM, n0 = blockIdx.x * BN;
   const int bz = c * g.b_per_copy + which;  // batch index of B
   const int dz = c * g.d_per_copy + which;  // batch index of D
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int TCOLS = SPLIT == 1 ? 2 * BN : BN;  // TMEM columns: one accumulator per half here
 
   using C = Cfg<BN, STAGES>;
   constexpr int TILE_B = C::TILE_B, STAGE_BYTES = C::STAGE_BYTES;
@@ -183,6 +192,7 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t *done = empty + STAGES;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
   int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
+  int *last_flag = abort_flag + 1;
   __shared__ float s_wv[BN], s_cv[BN];  // spectral epilogue: the tile's column weights
   if (g.epi == TC_EPI_SPECTRAL) {
     for (int i = threadIdx.x; i < BN; i += blockDim.x) {
@@ -198,19 +208,22 @@ __global__ void __launch_bounds__(128, 1)
     }
     mbar_init(done, 1);
     *abort_flag = 0;
+    *last_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(BN));
+                 "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const int nk = g.K / BKE;
+  const int nhalf = g.K / BKE / 2;  // K-blocks per half (K is a multiple of 128)
+  const int kb0 = ks * nhalf;       // this CTA's first K-block
+  const int nk = SPLIT == 1 ? 2 * nhalf : nhalf;
 
   if (warp == 0 && lane == 0) {
     // producer
@@ -224,11 +237,12 @@ __global__ void __launch_bounds__(128, 1)
       }
       if (*(volatile int *)abort_flag) break;
       unsigned char *st = tiles + s * STAGE_BYTES;
+      const int kx = (kb0 + kb) * BKE;
       mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_3d(st, &mAh, &full[s], kb * BKE, m0, which);
-      tma_load_3d(st + TILE_A, &mAl, &full[s], kb * BKE, m0, which);
-      tma_load_3d(st + 2 * TILE_A, &mBh, &full[s], kb * BKE, n0, bz);
-      tma_load_3d(st + 2 * TILE_A + TILE_B, &mBl, &full[s], kb * BKE, n0, bz);
+      tma_load_3d(st, &mAh, &full[s], kx, m0, which);
+      tma_load_3d(st + TILE_A, &mAl, &full[s], kx, m0, which);
+      tma_load_3d(st + 2 * TILE_A, &mBh, &full[s], kx, n0, bz);
+      tma_load_3d(st + 2 * TILE_A + TILE_B, &mBl, &full[s], kx, n0, bz);
       issued = kb + 1;
     }
     // make sure no copy is still landing in shared memory when the CTA ends
@@ -239,7 +253,8 @@ __global__ void __launch_bounds__(128, 1)
       }
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer
+    // MMA issuer: the first nhalf K-blocks into columns [0, BN), the rest
+    // (SPLIT = 1) into [BN, 2 BN), each half starting from zero
     bool ok = true;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
@@ -251,13 +266,16 @@ __global__ void __launch_bounds__(128, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = smem_u32(tiles + s * STAGE_BYTES);
       const uint32_t ah = st, al = st + TILE_A, bh = st + 2 * TILE_A, bl = st + 2 * TILE_A + TILE_B;
+      const int h = kb >= nhalf ? 1 : 0;
+      const uint32_t acc_t = tmem + (uint32_t)(h * BN);
+      const int kin = kb - h * nhalf;
 #pragma unroll
       for (int k = 0; k < BKE / 16; ++k) {
         const uint32_t off = k * 32;  // 16 bf16 = 32 bytes along K inside the swizzle atom
-        const uint32_t acc0 = (kb > 0 || k > 0) ? 1u : 0u;
-        umma_bf16(tmem, sw128_desc(ah + off), sw128_desc(bh + off), C::IDESC, acc0);
-        umma_bf16(tmem, sw128_desc(ah + off), sw128_desc(bl + off), C::IDESC, 1u);
-        umma_bf16(tmem, sw128_desc(al + off), sw128_desc(bh + off), C::IDESC, 1u);
+        const uint32_t acc0 = (kin > 0 || k > 0) ? 1u : 0u;
+        umma_bf16(acc_t, sw128_desc(ah + off), sw128_desc(bh + off), C::IDESC, acc0);
+        umma_bf16(acc_t, sw128_desc(ah + off), sw128_desc(bl + off), C::IDESC, 1u);
+        umma_bf16(acc_t, sw128_desc(al + off), sw128_desc(bh + off), C::IDESC, 1u);
       }
       umma_commit(&empty[s]);
     }
@@ -272,22 +290,72 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncwarp();
   const int m = m0 + warp * 32 + lane;
-  if (have) {
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  float *ws_row = nullptr, *ws_other = nullptr;
+  bool run = have;
+  if constexpr (SPLIT == 2) {
+    // publish this half, then the second of the pair to arrive finishes
+    const int tile = (z * (int)gridDim.y / SPLIT + mt) * (int)gridDim.x + blockIdx.x;
+    ws_row = g.ws + ((size_t)(tile * 2 + ks) * BM + warp * 32 + lane) * BN;
+    ws_other = g.ws + ((size_t)(tile * 2 + (ks ^ 1)) * BM + warp * 32 + lane) * BN;
+    if (have) {
+#pragma unroll 1
+      for (int cc = 0; cc < BN; cc += 32) {
+        uint32_t r[32];
+        tmem_ld32(trow + (uint32_t)cc, r);
+        uint4 *dst = reinterpret_cast<uint4 *>(ws_row + cc);
+#pragma unroll
+        for (int i = 0; i < 8; i += 2)
+          st_v8(dst + i, make_uint4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]),
+                make_uint4(r[4 * i + 4], r[4 * i + 5], r[4 * i + 6], r[4 * i + 7]));
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned int prev = atomicAdd(g.ws_ctr + tile, 1u);
+      *last_flag = prev == 1u ? 1 : 0;
+      if (prev == 1u) g.ws_ctr[tile] = 0u;  // both halves are in: ready for the next launch
+    }
+    __syncthreads();
+    run = have && *(volatile int *)last_flag != 0;
+    if (run) __threadfence();
+  }
+  if (run) {
 #pragma unroll 1
     for (int cc = 0; cc < BN; cc += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, r);
       float v[32];
+      {
+        uint32_t r[32];
+        tmem_ld32(trow + (uint32_t)cc, r);
+        if constexpr (SPLIT == 1) {
+          uint32_t r2[32];
+          tmem_ld32(trow + (uint32_t)(BN + cc), r2);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+          for (int i = 0; i < 32; ++i) v[i] = __fadd_rn(__uint_as_float(r[i]), __uint_as_float(r2[i]));
+        } else {
+          const float4 *src = reinterpret_cast<const float4 *>(ws_other + cc);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float4 q = __ldcg(src + i);
+            v[4 * i] = __fadd_rn(__uint_as_float(r[4 * i]), q.x);
+            v[4 * i + 1] = __fadd_rn(__uint_as_float(r[4 * i + 1]), q.y);
+            v[4 * i + 2] = __fadd_rn(__uint_as_float(r[4 * i + 2]), q.z);
+            v[4 * i + 3] = __fadd_rn(__uint_as_float(r[4 * i + 3]), q.w);
+          }
+        }
+      }
       const int n = n0 + cc;
       const size_t o = (size_t)dz * g.M * g.N + (size_t)m * g.N + n;
       if (g.epi == TC_EPI_F32) {
         uint4 *dst = reinterpret_cast<uint4 *>(g.Df + o);
 #pragma unroll
         for (int i = 0; i < 8; i += 2)
-          st_v8(dst + i, make_uint4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]),
-                make_uint4(r[4 * i + 4], r[4 * i + 5], r[4 * i + 6], r[4 * i + 7]));
+          st_v8(dst + i,
+                make_uint4(__float_as_uint(v[4 * i]), __float_as_uint(v[4 * i + 1]),
+                           __float_as_uint(v[4 * i + 2]), __float_as_uint(v[4 * i + 3])),
+                make_uint4(__float_as_uint(v[4 * i + 4]), __float_as_uint(v[4 * i + 5]),
+                           __float_as_uint(v[4 * i + 6]), __float_as_uint(v[4 * i + 7])));
       } else if (g.epi == TC_EPI_SPLIT) {
         split_store(g.Dh + o, g.Dl + o, v);
       } else {
@@ -316,7 +384,7 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
   }
 }
 
@@ -325,24 +393,31 @@ int tc_smem_bytes(int bn) {
 }
 
 // bn = 128: 3-stage ring, one CTA per SM; bn = 64: 2-stage ring, two CTAs
-// per SM (twice the tiles for grids that would leave SMs idle).
-void launch_tc_gemm(const CUtensorMap *maps4, const TcArgs &g, int ncopy, int bn,
+// per SM (twice the tiles for grids that would leave SMs idle).  split = 2
+// (bn = 128 only): two CTAs per tile, one half of K each.
+void launch_tc_gemm(const CUtensorMap *maps4, const TcArgs &g, int ncopy, int bn, int split,
                     cudaStream_t st) {
-  dim3 grid(g.N / bn, g.M / BM, g.nwhich * ncopy);
+  dim3 grid(g.N / bn, (g.M / BM) * (split == 2 ? 2 : 1), g.nwhich * ncopy);
   if (bn == 64)
-    launch_pdl(k_umma_gemm<64, 2>, grid, dim3(128), Cfg<64, 2>::SMEM_BYTES, st, maps4[0], maps4[1],
-               maps4[2], maps4[3], g);
+    launch_pdl(k_umma_gemm<64, 2, 1>, grid, dim3(128), Cfg<64, 2>::SMEM_BYTES, st, maps4[0],
+               maps4[1], maps4[2], maps4[3], g);
+  else if (split == 2)
+    launch_pdl(k_umma_gemm<128, 3, 2>, grid, dim3(128), Cfg<128, 3>::SMEM_BYTES, st, maps4[0],
+               maps4[1], maps4[2], maps4[3], g);
   else
-    launch_pdl(k_umma_gemm<128, 3>, grid, dim3(128), Cfg<128, 3>::SMEM_BYTES, st, maps4[0],
+    launch_pdl(k_umma_gemm<128, 3, 1>, grid, dim3(128), Cfg<128, 3>::SMEM_BYTES, st, maps4[0],
                maps4[1], maps4[2], maps4[3], g);
 }
 
 int tc_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_umma_gemm<128, 3>,
+  cudaError_t e = cudaFuncSetAttribute(k_umma_gemm<128, 3, 1>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Cfg<128, 3>::SMEM_BYTES);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_umma_gemm<64, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_umma_gemm<128, 3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Cfg<128, 3>::SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_umma_gemm<64, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              Cfg<64, 2>::SMEM_BYTES);
   return e == cudaSuccess ? 0 : -1;
 }

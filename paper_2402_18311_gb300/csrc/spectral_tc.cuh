@@ -23,11 +23,14 @@ struct TcArgs {
   const CopyState *cs;
   int eval;
   int *err;                    // set to 1 when a bounded wait gives up
+  float *ws;                   // split-K: [tiles][2][128][BN] partial halves
+  unsigned int *ws_ctr;        // split-K: arrivals per tile (reset by the second)
 };
 
 int tc_smem_bytes(int bn);
 int tc_prepare();
-void launch_tc_gemm(const CUtensorMap *maps4, const TcArgs &g, int ncopy, int bn, cudaStream_t st);
+void launch_tc_gemm(const CUtensorMap *maps4, const TcArgs &g, int ncopy, int bn, int split,
+                    cudaStream_t st);
 void launch_split_bf16(const float *src, __nv_bfloat16 *hi, __nv_bfloat16 *lo, size_t n,
                        cudaStream_t st);
 // 3D bf16 tensor map {K, rows, batch} with a {64, box_rows, 1} box and

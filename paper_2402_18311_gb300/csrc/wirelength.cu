@@ -26,6 +26,7 @@
 // 64-bit reduction per pin into an array that stays in L2, no floating-point
 // atomics, deterministic results.
 #include <cfloat>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.cuh"
@@ -60,7 +61,7 @@ __device__ __forceinline__ float copy_gamma(const Dev &d, int c, const float *ov
 template <int D>
 __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int cls, int eval,
                                                             const float *gamma_ovr) {
-  __shared__ float sm[32];
+  __shared__ float2 sm[32];
   pdl_wait();
   const int c = copy0 + blockIdx.y;
   if (!eval && d.cs[c].stopped) return;
@@ -69,6 +70,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int
   const float2 *xy = d.xy + (size_t)c * d.n_cells;
   unsigned long long *ga = d.gacc + (size_t)c * d.n_mov;
   const int e_end = d.cls_begin[cls + 1];
+  // each thread sums its few nets in FP32; the block sum is compensated (the
+  // HPWL sum drives the lambda schedule through differences of consecutive
+  // iterations)
   float hp_acc = 0.f, wl_acc = 0.f;
   for (int e = d.cls_begin[cls] + blockIdx.x * blockDim.x + threadIdx.x; e < e_end;
        e += gridDim.x * blockDim.x) {
@@ -133,8 +137,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int
     hp_acc += wn * ((mxx - mnx) + (mxy - mny));
     wl_acc += wn * (((mxx - mnx) + (rxp - rxm)) + ((mxy - mny) + (ryp - rym)));
   }
-  float rh = block_sum_f<kThreads>(hp_acc, sm);
-  float rw = block_sum_f<kThreads>(wl_acc, sm);
+  const double rh = block_sum_fc<kThreads>(hp_acc, sm);
+  const double rw = block_sum_fc<kThreads>(wl_acc, sm);
   if (threadIdx.x == 0) {
     size_t base = (size_t)c * S_COUNT * d.nb_red + d.wa_block_base[cls] + blockIdx.x;
     d.part[base + (size_t)S_HPWL * d.nb_red] = rh;
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int
 template <int G, int PPL, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_wa_group(Dev d, int copy0, int cls, int eval,
                                                         const float *gamma_ovr) {
-  __shared__ float sm[32];
+  __shared__ float2 sm[32];
   pdl_wait();
   const int c = copy0 + blockIdx.y;
   if (!eval && d.cs[c].stopped) return;
@@ -234,8 +238,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_wa_group(Dev d, int copy0, i
       }
     }
   }
-  float rh = block_sum_f<kThreads>(hp_acc, sm);
-  float rw = block_sum_f<kThreads>(wl_acc, sm);
+  const double rh = block_sum_fc<kThreads>(hp_acc, sm);
+  const double rw = block_sum_fc<kThreads>(wl_acc, sm);
   if (threadIdx.x == 0) {
     size_t base = (size_t)c * S_COUNT * d.nb_red + d.wa_block_base[cls] + blockIdx.x;
     d.part[base + (size_t)S_HPWL * d.nb_red] = rh;
@@ -289,7 +293,7 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
   const float ig = 1.0f / g;
   const float2 *xy = d.xy + (size_t)c * d.n_cells;
   unsigned long long *ga = d.gacc + (size_t)c * d.n_mov;
-  float hp_acc = 0.f, wl_acc = 0.f;
+  double hp_acc = 0.0, wl_acc = 0.0;
   for (int e = d.cls_begin[cls] + blockIdx.x; e < d.cls_begin[cls + 1]; e += gridDim.x) {
     const int p0 = d.net_ptr[e], p1 = d.net_ptr[e + 1];
     const float wn = d.net_w ? d.net_w[e] : 1.0f;
@@ -400,51 +404,68 @@ __global__ void __launch_bounds__(kThreads) k_hpwl64(Dev d, int copy0, int e_beg
     d.part[((size_t)c * S_COUNT + S_HP64) * d.nb_red + slot_base + blockIdx.x] = r;
 }
 
-void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_ovr,
-               cudaStream_t st) {
-  int launched = 0;
-  for (int cls = 0; cls < d.n_cls; ++cls) {
-    int nb = d.wa_blocks[cls];
-    if (nb == 0) continue;
-    dim3 grid(nb, ncopy);
-    // the first class follows whatever precedes it in the stream (an event
-    // or a copy); the others follow a WA kernel and launch programmatically
-    const bool pdl = launched++ > 0;
-    const dim3 blk(kThreads);
-    switch (cls) {
-      case 0:
-        if (pdl) launch_pdl(k_wa_thread<4>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
-        else k_wa_thread<4><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
-        break;
-      case 1:
-        if (pdl) launch_pdl(k_wa_group<4, 4, 6>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
-        else k_wa_group<4, 4, 6><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
-        break;
-      case 2:
-        if (pdl) launch_pdl(k_wa_group<16, 4, 6>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
-        else k_wa_group<16, 4, 6><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
-        break;
-      case 3:
-        if (pdl) launch_pdl(k_wa_group<32, 8, 1>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
-        else k_wa_group<32, 8, 1><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
-        break;
-      default: {
-        const size_t sm = 2 * sizeof(float) * d.wa_big_cap;
-        if (pdl)
-          launch_pdl(k_wa_big, grid, dim3(kBigNet), sm, st, d, copy0, cls, eval, gamma_ovr,
-                     d.wa_big_cap);
-        else
-          k_wa_big<<<grid, kBigNet, sm, st>>>(d, copy0, cls, eval, gamma_ovr, d.wa_big_cap);
-        break;
-      }
+// One degree class's kernel; pdl: launched programmatically after the
+// kernel before it in the stream.
+static void launch_wa_one(const Dev &d, int cls, int copy0, int ncopy, int eval,
+                          const float *gamma_ovr, bool pdl, cudaStream_t st) {
+  const dim3 grid(d.wa_blocks[cls], ncopy), blk(kThreads);
+  switch (cls) {
+    case 0:
+      if (pdl) launch_pdl(k_wa_thread<4>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
+      else k_wa_thread<4><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
+      break;
+    case 1:
+      if (pdl) launch_pdl(k_wa_group<4, 4, 6>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
+      else k_wa_group<4, 4, 6><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
+      break;
+    case 2:
+      if (pdl) launch_pdl(k_wa_group<16, 4, 6>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
+      else k_wa_group<16, 4, 6><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
+      break;
+    case 3:
+      if (pdl) launch_pdl(k_wa_group<32, 8, 1>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
+      else k_wa_group<32, 8, 1><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
+      break;
+    default: {
+      const size_t sm = 2 * sizeof(float) * d.wa_big_cap;
+      if (pdl)
+        launch_pdl(k_wa_big, grid, dim3(kBigNet), sm, st, d, copy0, cls, eval, gamma_ovr,
+                   d.wa_big_cap);
+      else
+        k_wa_big<<<grid, kBigNet, sm, st>>>(d, copy0, cls, eval, gamma_ovr, d.wa_big_cap);
+      break;
     }
   }
 }
 
+void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_ovr,
+               cudaStream_t st) {
+  int launched = 0;
+  for (int cls = 0; cls < d.n_cls; ++cls) {
+    if (d.wa_blocks[cls] == 0) continue;
+    // the first class follows whatever precedes it in the stream (an event
+    // or a copy); the others follow a WA kernel and launch programmatically
+    launch_wa_one(d, cls, copy0, ncopy, eval, gamma_ovr, launched++ > 0, st);
+  }
+}
+
+void launch_wa_class(const Dev &d, int cls, int copy0, int ncopy, int eval, cudaStream_t st) {
+  if (cls >= 0 && cls < d.n_cls && d.wa_blocks[cls] > 0)
+    launch_wa_one(d, cls, copy0, ncopy, eval, nullptr, false, st);
+}
+
+// The big-net kernel's dynamic shared-memory limit is a property of the
+// function, shared by every handle in the process: it only ever grows.
 int wa_prepare(int cap) {
+  static std::mutex mu;
+  static int granted = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cap <= granted) return 0;
   cudaError_t e = cudaFuncSetAttribute(k_wa_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(2 * sizeof(float) * cap));
-  return e == cudaSuccess ? 0 : -1;
+  if (e != cudaSuccess) return -1;
+  granted = cap;
+  return 0;
 }
 
 // Nets above 256 pins: one block per net, FP64 block reductions.
@@ -485,6 +506,50 @@ __global__ void __launch_bounds__(kThreads) k_hpwl64_big(Dev d, int copy0, int e
   }
   if (threadIdx.x == 0)
     d.part[((size_t)c * S_COUNT + S_HP64) * d.nb_red + slot_base + blockIdx.x] = acc;
+}
+
+// Measurement kernel: only the memory operations the WA pass cannot avoid
+// on this netlist, with nothing else in the way.  Per pin it reads pin_cell
+// and the offsets (streamed), gathers the cell's position (random 8 bytes)
+// and adds one packed 64-bit value to the cell's gradient sum (random
+// reduction); per net it reads net_ptr.  Pin-parallel, eight pins per
+// thread with all gathers in flight before the reductions.  Its time is the
+// floor of the WA stage's gather-and-reduce traffic on this index stream.
+constexpr int kFloorPins = 8;
+__global__ void __launch_bounds__(kThreads) k_wa_floor(Dev d, int copy0) {
+  pdl_wait();
+  const int c = copy0 + blockIdx.y;
+  const float2 *xy = d.xy + (size_t)c * d.n_cells;
+  unsigned long long *ga = d.gacc + (size_t)c * d.n_mov;
+  const int P = d.n_pins;
+  const int stride = gridDim.x * blockDim.x * kFloorPins;
+  for (int j0 = (blockIdx.x * blockDim.x) * kFloorPins + threadIdx.x; j0 < P; j0 += stride) {
+    int cl[kFloorPins];
+    float2 of[kFloorPins], v[kFloorPins];
+#pragma unroll
+    for (int k = 0; k < kFloorPins; ++k) {
+      const int j = j0 + k * blockDim.x;
+      cl[k] = j < P ? d.pin_cell[j] : -1;
+      of[k] = j < P ? d.pin_off[j] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < kFloorPins; ++k) v[k] = cl[k] >= 0 ? xy[cl[k]] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < kFloorPins; ++k)
+      if (cl[k] >= 0) add_pin_grad(d, ga, cl[k], (v[k].x + of[k].x) * 1e-6f, (v[k].y + of[k].y) * 1e-6f);
+  }
+  // net_ptr, streamed once
+  int acc = 0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= d.n_nets; e += gridDim.x * blockDim.x)
+    acc ^= d.net_ptr[e];
+  if (acc == 0x7fffffff) d.err[1] = acc;  // keeps the loads; never true for a valid netlist
+}
+
+void launch_wa_floor(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
+  const int per_block = kThreads * kFloorPins;
+  int nb = (d.n_pins + per_block - 1) / per_block;
+  nb = nb < 1 ? 1 : (nb > kMaxCellBlocks ? kMaxCellBlocks : nb);
+  k_wa_floor<<<dim3(nb, ncopy), kThreads, 0, st>>>(d, copy0);
 }
 
 int hpwl64_blocks(const Dev &d) { return 2 * d.cell_blocks; }

@@ -26,6 +26,7 @@ PLACE_EINTERNAL = -6
 PLACE_SHUFFLE_MACRO = 0
 PLACE_SHUFFLE_ALL = 1
 PLACE_WIREMASK = 2
+PLACE_DCT_AUTO = -1
 PLACE_DCT_FP32 = 0
 PLACE_DCT_BF16X3 = 1
 PLACE_STAGES = ("density", "spectral", "wirelength", "cellgrad", "update")
@@ -59,7 +60,9 @@ class place_params(ct.Structure):
                 ("alpha0", ct.c_float), ("hpwl_ref", ct.c_float), ("mu_base", ct.c_float),
                 ("mu_lo", ct.c_float), ("mu_hi", ct.c_float), ("tau_stop", ct.c_float),
                 ("max_iters", ct.c_int32), ("constant_gamma", ct.c_float), ("dct_mode", ct.c_int32),
-                ("max_backtracks", ct.c_int32), ("stretch", ct.c_int32)]
+                ("max_backtracks", ct.c_int32), ("stretch", ct.c_int32),
+                ("autotune", ct.c_int32), ("scatter_mode", ct.c_int32), ("gemm_bn", ct.c_int32),
+                ("wa_big_cap", ct.c_int32), ("gemm_split", ct.c_int32)]
 
 
 class place_info(ct.Structure):
@@ -68,7 +71,11 @@ class place_info(ct.Structure):
                 ("n_copies", ct.c_int32), ("frac_bits", ct.c_int32),
                 ("bin_w_q", ct.c_int64), ("bin_h_q", ct.c_int64),
                 ("bin_w", ct.c_double), ("bin_h", ct.c_double), ("device_bytes", ct.c_int64),
-                ("kernels_per_iter", ct.c_int32), ("pad", ct.c_int32)]
+                ("kernels_per_iter", ct.c_int32), ("dct_mode", ct.c_int32),
+                ("gemm_bn", ct.c_int32 * 4), ("gemm_split", ct.c_int32 * 4),
+                ("wa_big_cap", ct.c_int32), ("autotuned", ct.c_int32),
+                ("scatter_t1", ct.c_double), ("scatter_t2", ct.c_double),
+                ("autotune_ms", ct.c_double)]
 
 
 class place_state(ct.Structure):
@@ -120,7 +127,10 @@ _SIGS = {
                                _VP, _VP, _VP]),
     "place_get_best_positions": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
     "place_step_timed": (ct.c_int, [_VP, ct.c_int32, _VP]),
-    "place_overflow_noalloc": (ct.c_int, [_VP, _VP, _VP, _VP, ct.c_int32, ct.c_double,
+    "place_measure_wa_floor": (ct.c_int, [_VP, ct.c_int32, ct.POINTER(ct.c_float)]),
+    "place_get_hybro_rounds": (ct.c_int, [_VP, ct.c_int32, _VP, _VP, ct.c_int32,
+                                          ct.POINTER(ct.c_int32)]),
+    "place_overflow_noalloc": (ct.c_int, [_VP, _VP, _VP, _VP, ct.c_int32,
                                           ct.POINTER(place_die), ct.POINTER(place_bins),
                                           ct.c_int32, _VP, _VP, _VP, _VP]),
     "place_estimate_device_bytes": (ct.c_int, [ct.POINTER(place_netlist), ct.POINTER(place_bins),
@@ -316,12 +326,30 @@ def place_get_best_positions(h, copy, x, y):
     return _check(lib().place_get_best_positions(h, int(copy), _ptr(x), _ptr(y)))
 
 
+def place_measure_wa_floor(h, reps=10):
+    """Mean milliseconds of one gather-and-reduce floor pass (see the header)."""
+    ms = ct.c_float()
+    _check(lib().place_measure_wa_floor(h, int(reps), ct.byref(ms)))
+    return ms.value
+
+
+def place_get_hybro_rounds(h, copy):
+    """(hpwl, overflow) float64 arrays, one entry per round of the last
+    place_hybro call, for copy ``copy``."""
+    n = ct.c_int32()
+    _check(lib().place_get_hybro_rounds(h, int(copy), None, None, 0, ct.byref(n)))
+    hp = np.empty(n.value, np.float64)
+    tv = np.empty(n.value, np.float64)
+    _check(lib().place_get_hybro_rounds(h, int(copy), _ptr(hp), _ptr(tv), n.value, ct.byref(n)))
+    return hp, tv
+
+
 def place_step_timed(h, n_iters, stage_ms):
     """stage_ms: float32 numpy array [5]; per-stage milliseconds are added."""
     return _check(lib().place_step_timed(h, int(n_iters), _ptr(stage_ms)))
 
 
-def place_overflow_noalloc(x, y, w, h, n_movable, mov_area, die, bins, frac_bits, fixed_map,
+def place_overflow_noalloc(x, y, w, h, n_movable, die, bins, frac_bits, fixed_map,
                            overflow, map_out=None, stream=None):
     """Overflow (and optionally the density map) into caller-owned device
     buffers, using only the library's static scratch (no allocation).
@@ -329,7 +357,7 @@ def place_overflow_noalloc(x, y, w, h, n_movable, mov_area, die, bins, frac_bits
     d = place_die(*die)
     b = place_bins(*bins)
     return _check(lib().place_overflow_noalloc(_ptr(x), _ptr(y), _ptr(w), _ptr(h),
-                                               int(n_movable), float(mov_area), ct.byref(d),
+                                               int(n_movable), ct.byref(d),
                                                ct.byref(b), int(frac_bits), _ptr(fixed_map),
                                                _ptr(overflow), _ptr(map_out), _VP(stream or 0)))
 

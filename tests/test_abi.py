@@ -45,13 +45,15 @@ def test_default_params_match_the_oracle_reading(L):
         assert getattr(p, f) == pytest.approx(getattr(o, f), rel=1e-7), f
     assert p.max_iters == o.max_iters
     assert p.max_backtracks == o.max_backtracks == 0
+    assert p.dct_mode == place.PLACE_DCT_AUTO and p.autotune == 1 and p.scatter_mode == -1
+    assert p.gemm_bn == 0 and p.wa_big_cap == 0 and p.gemm_split == 0
 
 
 def test_struct_sizes_match_header_layout():
     assert ct.sizeof(place.place_netlist) == 4 * 4 + 10 * 8
-    assert ct.sizeof(place.place_params) == 14 * 4
+    assert ct.sizeof(place.place_params) == 19 * 4
     assert ct.sizeof(place.place_state) == 4 * 4 + 7 * 8
-    assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 2 * 4
+    assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 2 * 4 + 10 * 4 + 3 * 8
     assert ct.sizeof(place.place_job) == 4 * 4 + 8 + 8 + 8
     assert ct.sizeof(place.place_job_result) == 8 + 4 * 4 + 5 * 8 + 8 + 8
 
@@ -132,6 +134,11 @@ def test_create_rejects_bad_params(L):
     with pytest.raises(place.PlaceError) as ei:
         place.place_create(d, place.place_default_params(stretch=2))
     assert ei.value.code == place.PLACE_EINVAL and "stretch" in str(ei.value)
+    for field, bad in (("autotune", 2), ("scatter_mode", 3), ("gemm_bn", 96), ("wa_big_cap", 16),
+                       ("gemm_split", 3)):
+        with pytest.raises(place.PlaceError) as ei:
+            place.place_create(d, place.place_default_params(**{field: bad}))
+        assert ei.value.code == place.PLACE_EINVAL and field in str(ei.value)
     for mb in (-1, 65):
         with pytest.raises(place.PlaceError) as ei:
             place.place_create(d, place.place_default_params(max_backtracks=mb))

@@ -159,27 +159,118 @@ def test_first_step_matches_oracle():
         h.close()
 
 
+def trajectory(handle, design, n_iters, every=20, oracle_params=None, lag=2):
+    """Run the GPU handle and the FP64 oracle side by side from the same start.
+    At every checkpoint k: the HPWL of both at v_k, the GPU's overflow at v_k,
+    and the range of the oracle's overflow over v_{k-lag} .. v_{k+lag} (the
+    oracle runs lag iterations past the last checkpoint)."""
+    o = opl.Placer(design, oracle_params or opl.Params(tau_stop=-1.0, max_iters=10 ** 6))
+    gpu, ohp = [], {}
+    hp = np.empty(1); tv = np.empty(1)
+    for k in range(every, n_iters + 1, every):
+        place.place_step(handle.h, every)
+        o.run(every)
+        place.place_eval_hpwl_overflow(handle.h, hp, tv)
+        gpu.append((k, float(hp[0]), float(tv[0])))
+        ohp[k] = float(o.hpwl(o.vx, o.vy))
+    o.run(lag)
+    otau = [r[2] for r in o.history] + [o.overflow(o.density_map(o.vx, o.vy))]  # tau(v_j), j = 0..
+    rows = []
+    for k, h, t in gpu:
+        win = otau[max(0, k - lag):k + lag + 1]
+        rows.append((k, h, ohp[k], t, (min(win), max(win))))
+    return o, rows
+
+
+def check_trajectory(rows, upto=None, hp_rel=1e-3, tau_abs=2e-3):
+    """HPWL within hp_rel at every checkpoint up to `upto` (the final-HPWL
+    tolerance of the parity contract, applied all along).  The overflow is
+    held to the oracle's own overflow within two iterations either side,
+    widened by tau_abs: late in a placement tau falls by several 1e-3 per
+    iteration, so trajectories whose HPWL agrees to 1e-3 can be an iteration
+    apart in overflow (measured: 0.0039 at iteration 300 of the 1k-cell
+    design on 128 x 128 bins, where tau falls 0.003 per iteration)."""
+    for k, hp, ohp, tau, (lo, hi) in rows:
+        if upto is not None and k > upto:
+            break
+        assert abs(hp - ohp) <= hp_rel * ohp, f"iteration {k}: HPWL {hp} vs oracle {ohp}"
+        assert lo - tau_abs <= tau <= hi + tau_abs, f"iteration {k}: overflow {tau} vs oracle {lo}..{hi}"
+
+
 def test_trajectory_300_iterations():
     d = synth.tiny_1k(0)
     h = Handle(d, tau_stop=-1.0, max_iters=300)
     try:
-        o = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=300))
-        first_bad = None
-        hp = np.empty(1); tv = np.empty(1)
-        for k in range(0, 300, 20):
-            place.place_step(h.h, 20)
-            o.run(20)
-            place.place_eval_hpwl_overflow(h.h, hp, tv)
-            ohp = o.hpwl(o.vx, o.vy)
-            if first_bad is None and abs(hp[0] - ohp) > 1e-3 * ohp:
-                first_bad = (k + 20, hp[0], ohp)
+        assert h.info.dct_mode == place.PLACE_DCT_FP32  # 64 x 64 bins: the FP32 path
+        o, rows = trajectory(h, d, 300)
         st = place.place_get_state(h.h, 0)
-        assert st.iter == 300 and o.k == 300
-        ohp = o.hpwl(o.vx, o.vy)
-        assert hp[0] == pytest.approx(ohp, rel=1e-3), f"first divergence beyond 1e-3: {first_bad}"
-        assert tv[0] == pytest.approx(o.tau, abs=5e-3)
+        assert st.iter == 300 and rows[-1][0] == 300
+        check_trajectory(rows)
     finally:
         h.close()
+
+
+def test_trajectory_300_iterations_tensor_core():
+    # the BF16x3 tcgen05 spectral path over a whole 300-iteration placement of
+    # a 1k-cell design on 128 x 128 bins (the default path for such grids)
+    d = synth.make_design(n_movable=1000, die=(0, 0, 256, 256), nx=128, ny=128, n_nets=1100,
+                          n_pads=16, target_density=1.0, seed=0, name="tiny_1k_128")
+    h = Handle(d, tau_stop=-1.0, max_iters=300)
+    try:
+        assert h.info.dct_mode == place.PLACE_DCT_BF16X3
+        o, rows = trajectory(h, d, 300)
+        check_trajectory(rows)
+    finally:
+        h.close()
+
+
+def test_trajectory_tensor_core_20k_to_its_chaos_horizon():
+    # The 20k-cell design on the tensor-core path.  Its spreading phase is
+    # chaotic: the FP64 oracle started from positions one FP32 ulp apart
+    # differs from itself by more than 1e-3 in HPWL within 300 iterations
+    # (measured: 5.8e-4 at 200, 7.3e-3 at 240).  So the GPU is held to 1e-3
+    # along the trajectory up to iteration 220, where the oracle's own ulp
+    # sensitivity is still below that, and beyond it by shadowing: from the
+    # oracle's state at 240 and 280 both sides restart and run 20 iterations
+    # of identical input, again within 1e-3.
+    d = synth.scaled(20000, 128, seed=2)
+    h = Handle(d, tau_stop=-1.0, max_iters=1000)
+    try:
+        assert h.info.dct_mode == place.PLACE_DCT_BF16X3
+        o, rows = trajectory(h, d, 220, lag=0)  # the oracle stays at 220 for the twin below
+        check_trajectory(rows)
+        # the oracle against itself, one ulp apart: the horizon is chaos
+        d2 = synth.scaled(20000, 128, seed=2)
+        n = d2.n_movable
+        d2.x[:n] = np.nextafter(d2.x[:n], np.float32(np.inf))
+        twin = opl.Placer(d2, opl.Params(tau_stop=-1.0, max_iters=10 ** 6))
+        twin.run(220)
+        worst = 0.0
+        for _ in range(4):
+            o.run(20)
+            twin.run(20)
+            a, b = o.hpwl(o.vx, o.vy), twin.hpwl(twin.vx, twin.vy)
+            worst = max(worst, abs(a - b) / a)
+            if o.k in (240, 280):
+                fx, fy = o.positions()
+                fx, fy = fx.astype(np.float32), fy.astype(np.float32)
+                place.place_set_positions(h.h, 0, fx, fy)
+                seg = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=10 ** 6))
+                seg.reset(fx[:n], fy[:n])
+                _, srows = trajectory_from(h, seg, 20)
+                check_trajectory(srows)
+        assert worst > 1e-3, worst
+    finally:
+        h.close()
+
+
+def trajectory_from(handle, o, n_iters):
+    hp = np.empty(1); tv = np.empty(1)
+    place.place_step(handle.h, n_iters)
+    o.run(n_iters)
+    place.place_eval_hpwl_overflow(handle.h, hp, tv)
+    t = o.overflow(o.density_map(o.vx, o.vy))
+    return o, [(o.k, float(hp[0]), float(o.hpwl(o.vx, o.vy)), float(tv[0]), (t, t))]
 
 
 def test_stages_with_net_weights():
@@ -455,36 +546,53 @@ def test_density_stretching_maps_field_and_trajectory():
         h.close()
     h = Handle(d, tau_stop=-1.0, max_iters=300, stretch=1)
     try:
-        o = opl.Placer(d, opl.Params(tau_stop=-1.0, max_iters=300, stretch=True))
-        hp = np.empty(1); tv = np.empty(1)
-        for k in range(0, 100, 20):
-            place.place_step(h.h, 20)
-            o.run(20)
-        place.place_eval_hpwl_overflow(h.h, hp, tv)
-        assert hp[0] == pytest.approx(o.hpwl(o.vx, o.vy), rel=1e-3)
-        assert tv[0] == pytest.approx(o.tau, abs=5e-3)
+        _, rows = trajectory(h, d, 100,
+                             oracle_params=opl.Params(tau_stop=-1.0, max_iters=300, stretch=True))
+        check_trajectory(rows)
     finally:
         h.close()
 
 
-def test_convergence_stops_copy():
+@pytest.mark.parametrize("tau_stop", [0.3, 0.15, 0.07])
+def test_convergence_stops_copy(tau_stop):
+    # The stop test (overflow at v_k <= tau_stop) against the oracle's,
+    # iteration by iteration: the GPU is stepped one iteration at a time and
+    # its overflow read back.  Both sides stop exactly where their own overflow
+    # first reaches the target; the two stop iterations are equal unless the
+    # two overflows at the earlier one lie on opposite sides of the target,
+    # which the overflow tolerance allows only within 2e-3 of it.  Measured:
+    # equal at 0.3 (220) and 0.15 (231); at 0.07 the oracle's overflow at
+    # iteration 247 is 0.0687 while the GPU's is just above 0.07, and it stops
+    # at 248.
     d = synth.tiny_1k(0)
-    h = Handle(d, tau_stop=0.3, max_iters=1000)
+    h = Handle(d, tau_stop=tau_stop, max_iters=1000)
     try:
         conv = np.zeros(1, np.int32)
-        for _ in range(30):
-            place.place_step(h.h, 20, conv)
-            if conv[0]:
-                break
+        gtau = []
+        while not conv[0]:
+            place.place_step(h.h, 1, conv)
+            gtau.append(place.place_get_state(h.h, 0).overflow)  # tau at v_k of this step
         st = place.place_get_state(h.h, 0)
-        assert conv[0] == 1 and st.converged == 1 and st.overflow <= 0.3
+        assert st.converged == 1 and st.overflow <= tau_stop
+        # the GPU stopped at the first v_k whose overflow reached the target
+        assert all(t > tau_stop for t in gtau[:-1]) and gtau[-1] <= tau_stop
         x, y = h.pos()
         place.place_step(h.h, 5)
         x2, _ = h.pos()
         np.testing.assert_array_equal(x, x2)
-        o = opl.Placer(d, opl.Params(tau_stop=0.3, max_iters=1000))
+        o = opl.Placer(d, opl.Params(tau_stop=tau_stop, max_iters=1000))
         o.run()
-        assert abs(st.iter - o.k) <= 3
+        otau = [r[2] for r in o.history]
+        assert o.converged and all(t > tau_stop for t in otau[:-1]) and otau[-1] <= tau_stop
+        kg, ko = len(gtau) - 1, len(otau) - 1
+        if kg == ko:
+            assert st.iter == o.k
+        else:
+            k = min(kg, ko)
+            assert (gtau[k] - tau_stop) * (otau[k] - tau_stop) < 0
+            assert abs(gtau[k] - otau[k]) <= 2e-3 and abs(kg - ko) == 1
+        if tau_stop >= 0.15:
+            assert kg == ko
     finally:
         h.close()
 
@@ -584,6 +692,28 @@ def test_wiremask_without_movable_macros_only_resets():
         h.close()
 
 
+def check_hybro_rounds(h, d, rounds, best, br, bh, bt):
+    """Round by round against oracle.hybro (Algorithm 1): every round's HPWL
+    within 1e-3, the same best round, and the kept solution's HPWL recomputed
+    exactly from its positions.  The overflow is held to 2e-3 or a tenth of
+    its value, whichever is larger: each round starts from the previous
+    round's perturbed result, so the rounds compound the trajectories'
+    differences, and late in a placement the overflow falls by several 1e-3
+    per iteration (measured: after four rounds of 150 iterations the HPWL
+    still agrees to 5e-4 while the overflow differs by 0.0065 at 0.08)."""
+    ghp, gtv = place.place_get_hybro_rounds(h.h, 0)
+    assert len(ghp) == len(rounds)
+    for r, (hp, tau, _, _) in enumerate(rounds):
+        assert ghp[r] == pytest.approx(hp, rel=1e-3), f"round {r}"
+        assert abs(gtv[r] - tau) <= max(2e-3, 0.1 * tau), f"round {r}: {gtv[r]} vs {tau}"
+    assert br[0] == best
+    assert bh[0] == ghp[best] and bt[0] == gtv[best]
+    bx = np.empty(d.n_cells, np.float32); by = np.empty(d.n_cells, np.float32)
+    place.place_get_best_positions(h.h, 0, bx, by)
+    hp = owl.hpwl(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, bx, by)
+    assert hp == pytest.approx(bh[0], rel=1e-12)
+
+
 def test_hybro_wiremask_rounds():
     # Hybro-WireMask (Algorithm 1 with the WireMask perturbation)
     d = synth.mixed_size_1k(0)
@@ -593,30 +723,21 @@ def test_hybro_wiremask_rounds():
         place.place_hybro(h.h, 2, place.PLACE_WIREMASK, 0.0, 0, 0.1, bh, bt, br)
         best, rounds = ohy.run(d, opl.Params(tau_stop=-1.0, max_iters=100), n_rounds=2,
                                op=ohy.WIREMASK, tau_target=0.1)
-        assert 0 <= br[0] <= 2
-        bx = np.empty(d.n_cells, np.float32); by = np.empty(d.n_cells, np.float32)
-        place.place_get_best_positions(h.h, 0, bx, by)
-        hp = owl.hpwl(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, bx, by)
-        assert hp == pytest.approx(bh[0], rel=1e-12)
-        # FP32 GPU and FP64 oracle trajectories agree on the first round
-        assert bh[0] <= rounds[0][0] * 1.002
+        check_hybro_rounds(h, d, rounds, best, br, bh, bt)
     finally:
         h.close()
 
 
-def test_hybro_two_rounds_matches_oracle():
+@pytest.mark.parametrize("n_rounds,iters", [(1, 100), (3, 150)])
+def test_hybro_rounds_match_oracle(n_rounds, iters):
     d = synth.tiny_1k(0)
-    h = Handle(d, tau_stop=-1.0, max_iters=100)
+    h = Handle(d, tau_stop=-1.0, max_iters=iters)
     try:
         bh = np.empty(1); bt = np.empty(1); br = np.empty(1, np.int32)
-        place.place_hybro(h.h, 1, place.PLACE_SHUFFLE_ALL, 0.5, 7, 0.1, bh, bt, br)
-        best, rounds = ohy.run(d, opl.Params(tau_stop=-1.0, max_iters=100), n_rounds=1,
+        place.place_hybro(h.h, n_rounds, place.PLACE_SHUFFLE_ALL, 0.5, 7, 0.1, bh, bt, br)
+        best, rounds = ohy.run(d, opl.Params(tau_stop=-1.0, max_iters=iters), n_rounds=n_rounds,
                                op=ohy.SHUFFLE_ALL, p=0.5, seed=7, tau_target=0.1)
-        assert bh[0] == pytest.approx(rounds[best][0], rel=2e-3)
-        bx = np.empty(d.n_cells, np.float32); by = np.empty(d.n_cells, np.float32)
-        place.place_get_best_positions(h.h, 0, bx, by)
-        hp = owl.hpwl(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, bx, by)
-        assert hp == pytest.approx(bh[0], rel=1e-12)
+        check_hybro_rounds(h, d, rounds, best, br, bh, bt)
     finally:
         h.close()
 
@@ -805,3 +926,53 @@ def test_full_size_2m_stages_tensor_core():
         check_stages(h, x, y, 12.0)
     finally:
         h.close()
+
+
+def test_tuning_candidates_give_identical_results():
+    # The autotuner chooses among variants that compute the same thing: the
+    # scatter's three ways add the same integers; the GEMM tile width, split-K
+    # over two CTAs (each half of the contraction accumulates alone either
+    # way, and the halves are added once) and the big-net cache size change
+    # neither the operations nor their order per output element.  Forced candidates and the tuned choice must therefore
+    # give bit-identical maps and positions over a placement that passes
+    # through the dense, middle and spread phases.
+    d = synth.scaled(20000, 128, seed=2)
+    assert np.max(np.diff(d.net_ptr)) > 256
+    configs = [dict(autotune=0, gemm_bn=128, scatter_mode=0, wa_big_cap=256),
+               dict(autotune=0, gemm_bn=64, scatter_mode=1, wa_big_cap=4096),
+               dict(autotune=0, gemm_bn=128, scatter_mode=2, wa_big_cap=1024),
+               dict(autotune=0, gemm_bn=128, gemm_split=2, scatter_mode=1, wa_big_cap=2048),
+               dict(autotune=1)]
+    ref = None
+    for cfg in configs:
+        h = Handle(d, tau_stop=-1.0, max_iters=1000, **cfg)
+        try:
+            info = h.info
+            assert info.dct_mode == place.PLACE_DCT_BF16X3
+            if cfg.get("autotune"):
+                assert info.autotuned == 1
+                assert all(b in (64, 128) for b in info.gemm_bn)
+                assert 32 <= info.wa_big_cap <= 6144
+                assert 0 < info.scatter_t1 <= info.scatter_t2
+            else:
+                assert info.autotuned == 0 and list(info.gemm_bn) == [cfg["gemm_bn"]] * 4
+                assert list(info.gemm_split) == [cfg.get("gemm_split", 1)] * 4
+                assert info.wa_big_cap == cfg["wa_big_cap"]
+            out = []
+            for n in (5, 60, 300, 300):
+                place.place_step(h.h, n)
+                x, y = h.pos()
+                gm = np.empty(d.nx * d.ny, np.int64)
+                place.place_eval_density(h.h, 0, gm)
+                out.append((x, y, gm, place.place_get_state(h.h, 0).bins_effective))
+        finally:
+            h.close()
+        if ref is None:
+            ref = out
+            # the placement crossed the scatter's phases
+            assert ref[0][3] < 32 and ref[-1][3] > 1024, [r[3] for r in ref]
+            continue
+        for (x, y, gm, _), (rx, ry, rgm, _) in zip(out, ref):
+            np.testing.assert_array_equal(x, rx)
+            np.testing.assert_array_equal(y, ry)
+            np.testing.assert_array_equal(gm, rgm)
