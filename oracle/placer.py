@@ -43,6 +43,13 @@ is accepted.  The overflow stop test applies at every evaluated point.
 Optional density stretching (``stretch``; oracle.density): the field and the
 density gradient come from the stretched cells; the overflow, the stop test
 and gamma keep the exact unstretched map.
+
+Optional filler cells (``fillers``; oracle.fillers): pinless movable cells
+appended after the real movable ones in the optimiser's vectors (positions,
+gradients, preconditioner, every norm).  They enter the density that drives
+the field and the density gradient, never the HPWL, the WA model or the
+overflow.  A reset from new movable positions keeps the fillers where they
+are.
 """
 from __future__ import annotations
 
@@ -52,6 +59,7 @@ import math
 import numpy as np
 
 from . import density as dens
+from . import fillers as fil
 from . import poisson as pois
 from . import wirelength as wlm
 
@@ -108,6 +116,7 @@ class Params:
     constant_gamma: float = 0.0  # > 0: use this gamma every iteration
     max_backtracks: int = 0      # > 0: redo a too-long step at most this often in a row
     stretch: bool = False        # ePlace density stretching for the field
+    fillers: bool = False        # ePlace filler cells in the whitespace
 
 
 class Placer:
@@ -133,33 +142,64 @@ class Placer:
         self.fixed_x = d.x[self.n:].astype(np.float64)
         self.fixed_y = d.y[self.n:].astype(np.float64)
         pc = d.pin_cell.astype(np.int64)
-        self.pins = np.bincount(pc[pc < self.n], minlength=self.n).astype(np.float64)
-        self.area = self.w[:self.n] * self.h[:self.n]
+        pins = np.bincount(pc[pc < self.n], minlength=self.n).astype(np.float64)
+        # the optimiser's cells: the movable cells, then the fillers
+        self.nf = 0
+        fx0 = fy0 = np.zeros(0)
+        wo, ho = self.w[:self.n], self.h[:self.n]
+        Wo, Ho = self.W[:self.n], self.H[:self.n]
+        if self.p.fillers:
+            Wf, Hf = fil.size(self.W, self.H, self.n, d.is_macro)
+            self.nf = fil.count(d.die, self.t, int(np.sum(self.Fmap)), self.mov_area_q, self.F,
+                                Wf, Hf)
+            wf, hf = Wf * 2.0 ** -self.F, Hf * 2.0 ** -self.F
+            fx0, fy0 = fil.start(self.nf, d.die, wf, hf)
+            wo = np.concatenate([wo, np.full(self.nf, wf)])
+            ho = np.concatenate([ho, np.full(self.nf, hf)])
+            Wo = np.concatenate([Wo, np.full(self.nf, Wf, np.int64)])
+            Ho = np.concatenate([Ho, np.full(self.nf, Hf, np.int64)])
+        self.wo, self.ho, self.Wo, self.Ho = wo, ho, Wo, Ho
+        self.pins = np.concatenate([pins, np.zeros(self.nf)])
+        self.area = wo * ho
         self.w_bin = math.sqrt(self.g.bin_w * self.g.bin_h)
         self.dref = self.p.hpwl_ref * d.n_nets * self.w_bin
-        self.reset(d.x[:self.n], d.y[:self.n])
+        self.reset(np.concatenate([d.x[:self.n], fx0]), np.concatenate([d.y[:self.n], fy0]))
 
     # -- helpers -----------------------------------------------------------
     def clamp(self, x, y):
         xl, yl, xh, yh = self.g.die
-        x = np.maximum(xl, np.minimum(x, xh - self.w[:self.n]))
-        y = np.maximum(yl, np.minimum(y, yh - self.h[:self.n]))
+        x = np.maximum(xl, np.minimum(x, xh - self.wo))
+        y = np.maximum(yl, np.minimum(y, yh - self.ho))
         return x, y
 
     def full(self, x, y):
-        return (np.concatenate([x, self.fixed_x]), np.concatenate([y, self.fixed_y]))
+        """All real cells (movable, then fixed) from optimiser or movable
+        vectors; fillers are not cells of the design."""
+        n = self.n
+        return (np.concatenate([x[:n], self.fixed_x]), np.concatenate([y[:n], self.fixed_y]))
 
     def density_map(self, x, y):
+        """Map of the real movable cells: the overflow's."""
+        X = dens.quantize(x[:self.n], self.F)
+        Y = dens.quantize(y[:self.n], self.F)
+        return dens.overlap_map(X, Y, self.W[:self.n], self.H[:self.n], self.g)
+
+    def field_map(self, x, y):
+        """Map that drives the field: the movable cells and the fillers
+        (stretched when ``stretch`` is set)."""
         X = dens.quantize(x, self.F)
         Y = dens.quantize(y, self.F)
-        return dens.overlap_map(X, Y, self.W[:self.n], self.H[:self.n], self.g)
+        if self.p.stretch:
+            Xs, Ys, Ws, Hs, R, _ = dens.stretched(X, Y, self.Wo, self.Ho, self.g)
+            return dens.overlap_map_scaled(Xs, Ys, Ws, Hs, R, self.g)
+        return dens.overlap_map(X, Y, self.Wo, self.Ho, self.g)
 
     def stretched_map(self, x, y):
         """Map of the stretched cells (oracle.density), which drives the field
         when ``stretch`` is set."""
         X = dens.quantize(x, self.F)
         Y = dens.quantize(y, self.F)
-        Xs, Ys, Ws, Hs, R, _ = dens.stretched(X, Y, self.W[:self.n], self.H[:self.n], self.g)
+        Xs, Ys, Ws, Hs, R, _ = dens.stretched(X, Y, self.Wo, self.Ho, self.g)
         return dens.overlap_map_scaled(Xs, Ys, Ws, Hs, R, self.g)
 
     def overflow(self, M):
@@ -180,15 +220,18 @@ class Placer:
         return pois.poisson(rho, self.g.bin_w, self.g.bin_h)
 
     def wirelength(self, x, y, gamma):
+        """WA value and gradient over the optimiser's cells (fillers: 0)."""
         fx, fy = self.full(x, y)
         d = self.d
-        return wlm.wa_wirelength(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, fx, fy,
-                                 gamma, self.n)
+        wl, gx, gy = wlm.wa_wirelength(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, fx, fy,
+                                       gamma, self.n)
+        z = np.zeros(self.nf)
+        return wl, np.concatenate([gx, z]), np.concatenate([gy, z])
 
     def density_grad(self, x, y, ex, ey):
         X = dens.quantize(x, self.F)
         Y = dens.quantize(y, self.F)
-        W, H = self.W[:self.n], self.H[:self.n]
+        W, H = self.Wo, self.Ho
         if self.p.stretch:
             X, Y, W, H, _, wgt = dens.stretched(X, Y, W, H, self.g)
             gx, gy = dens.field_gather(X, Y, W, H, self.g, ex, ey)
@@ -197,9 +240,13 @@ class Placer:
 
     # -- optimiser ------------------------------------------------------------
     def reset(self, x, y):
-        """Restart the optimiser from movable positions (x, y)."""
+        """Restart the optimiser from movable positions (x, y).  Given only
+        the real movable cells, the fillers stay where they are."""
         x = np.asarray(x, np.float64).copy()
         y = np.asarray(y, np.float64).copy()
+        if x.shape[0] == self.n and self.nf:
+            x = np.concatenate([x, self.vx[self.n:]])
+            y = np.concatenate([y, self.vy[self.n:]])
         x, y = self.clamp(x, y)
         self.ux, self.uy = x.copy(), y.copy()
         self.vx, self.vy = x.copy(), y.copy()
@@ -241,7 +288,7 @@ class Placer:
         if tau <= p.tau_stop:
             self.converged = self.stopped = True
             return False
-        _, ex, ey = self.field(self.stretched_map(vx, vy) if p.stretch else M)
+        _, ex, ey = self.field(self.field_map(vx, vy) if (p.stretch or self.nf) else M)
         gdx, gdy = self.density_grad(vx, vy, ex, ey)
         if self.k == 0:
             n1 = np.sum(np.abs(gwx)) + np.sum(np.abs(gwy))
@@ -252,7 +299,7 @@ class Placer:
         gx = (gwx + lam * gdx) / prec
         gy = (gwy + lam * gdy) / prec
         if self.k == 0:
-            gn = math.sqrt((np.sum(gx * gx) + np.sum(gy * gy)) / (2 * self.n))
+            gn = math.sqrt((np.sum(gx * gx) + np.sum(gy * gy)) / (2 * (self.n + self.nf)))
             alpha = p.alpha0 * self.w_bin / gn if gn > 0 else 0.0
         else:
             alpha = lipschitz_step((vx, vy), (self.vpx, self.vpy), (gx, gy),
