@@ -16,7 +16,8 @@ Iteration k at reference point v_k (movable lower-left corners):
     M_k, tau_k = density map and overflow at v_k; stop here if tau_k <= tau_stop
     rho -> (psi, E); gD = field gather at v_k
     k == 0:  lambda = eta * |gWL|_1 / |gD|_1
-    P_i = max(1, pins_i + lambda * area_i)
+    P_i = max(1, pins_i + lambda * k_i * area_i)  (k_i = macro_precond for a
+                                                   movable macro, 1 otherwise)
     g_k = (gWL + lambda gD) / P
     alpha_k = alpha0 * w_bin / rms(g_0)                       (k == 0)
             = |v_k - v_{k-1}|_2 / |g_k - g_{k-1}|_2           (k >= 1)
@@ -117,6 +118,7 @@ class Params:
     max_backtracks: int = 0      # > 0: redo a too-long step at most this often in a row
     stretch: bool = False        # ePlace density stretching for the field
     fillers: bool = False        # ePlace filler cells in the whitespace
+    macro_precond: float = 1.0   # weight of a movable macro's charge in its preconditioner
 
 
 class Placer:
@@ -160,7 +162,11 @@ class Placer:
             Ho = np.concatenate([Ho, np.full(self.nf, Hf, np.int64)])
         self.wo, self.ho, self.Wo, self.Ho = wo, ho, Wo, Ho
         self.pins = np.concatenate([pins, np.zeros(self.nf)])
-        self.area = wo * ho
+        # the charge term of the preconditioner, a movable macro's weighted
+        kappa = np.ones(self.n + self.nf)
+        if d.is_macro is not None:
+            kappa[:self.n][np.asarray(d.is_macro[:self.n]) != 0] = self.p.macro_precond
+        self.area = wo * ho * kappa
         self.w_bin = math.sqrt(self.g.bin_w * self.g.bin_h)
         self.dref = self.p.hpwl_ref * d.n_nets * self.w_bin
         self.reset(np.concatenate([d.x[:self.n], fx0]), np.concatenate([d.y[:self.n], fy0]))

@@ -182,7 +182,8 @@ def _hand_design():
         die=(0.0, 0.0, 8.0, 8.0), nx=2, ny=2, target_density=1.0)
 
 
-def test_first_step_composition_worked_by_hand():
+@pytest.mark.parametrize("kappa", [1.0, 4.0])
+def test_first_step_composition_worked_by_hand(kappa):
     """The placer's first iteration assembled from quantities worked out in
     closed form, none of them through the oracle's own WA, density or Poisson
     code: the two-pin WA gradient d tanh(d / 2g) differentiated, the 2 x 2
@@ -191,10 +192,14 @@ def test_first_step_composition_worked_by_hand():
     max(1, pins_i + lambda area_i), alpha_0 and the first Nesterov step.  A
     preconditioner that counted the pad's pin, dropped lambda area_i or the
     floor at 1, or a step length normalised over n instead of 2n coordinates,
-    fails here."""
+    fails here.  With kappa != 1, cell 2 is a movable macro and its charge in
+    the preconditioner is weighted by kappa."""
     d = _hand_design()
+    if kappa != 1.0:
+        d.is_macro = np.array([0, 0, 1, 0, 0], np.uint8)
     eta, alpha0 = 0.25, 0.05
-    p = pl.Placer(d, pl.Params(tau_stop=-1.0, max_iters=10, lambda_eta=eta, alpha0=alpha0))
+    p = pl.Placer(d, pl.Params(tau_stop=-1.0, max_iters=10, lambda_eta=eta, alpha0=alpha0,
+                               macro_precond=kappa))
     x0, y0 = p.vx.copy(), p.vy.copy()
     assert p.step()
 
@@ -232,7 +237,7 @@ def test_first_step_composition_worked_by_hand():
 
     lam = eta * (np.abs(gwl_x).sum() + np.abs(gwl_y).sum()) / (np.abs(gd_x).sum() + np.abs(gd_y).sum())
     pins = np.array([2.0, 1.0, 0.0, 0.0])
-    P = np.maximum(1.0, pins + lam * area)
+    P = np.maximum(1.0, pins + lam * area * np.array([1.0, 1.0, kappa, 1.0]))
     assert P[3] == 1.0 and P[2] > 1.0 and P[0] > pins[0]   # every branch of the preconditioner
     gx = (gwl_x + lam * gd_x) / P
     gy = (gwl_y + lam * gd_y) / P
