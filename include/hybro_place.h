@@ -110,7 +110,18 @@ typedef struct place_bins { int32_t nx, ny; float target_density; } place_bins;
  * map is floor(overlap R), exact in integers.  The stretched map drives the
  * field and the density gradient, which is scaled by R.  The overflow, the
  * stop test and gamma keep the exact unstretched map.  It costs 8 bytes per
- * bin and copy and 20 bytes per movable cell. */
+ * bin and copy and 20 bytes per movable cell.
+ * Filler cells (fillers = 1; ePlace's whitespace fillers).  Pinless movable
+ * cells that take up the whitespace the target density leaves, so that the
+ * density force holds the real cells together at the target density instead
+ * of spreading them over the die.  Their size is the mean quantised width
+ * and height of the movable non-macro cells, each rounded to a multiple of
+ * 2^-F; their count floor(max(0, t (A_die - A_fixed) - A_mov) / (w_f h_f)),
+ * with A_fixed the fixed area inside the die; their start uniform over the
+ * die from a SplitMix64 stream.  They enter the density that drives the field
+ * and every optimiser norm, never the HPWL, the WA model, the overflow or a
+ * perturbation; a reset keeps them where they are.  place_get_fillers returns
+ * them; place_info.n_fillers counts them. */
 typedef struct place_params {
   int32_t n_copies;       /* K >= 1 */
   float gamma_base;       /* 4 */
@@ -143,6 +154,12 @@ typedef struct place_params {
                              contraction each, on stages with at most half as
                              many tiles as the device has SMs.  Every choice
                              gives the same bits. */
+  int32_t fillers;        /* 0 (default) or 1: filler cells (see below) */
+  float macro_precond;    /* 1 (default): weight of a movable macro's charge in
+                             its preconditioner, max(1, pins_i + k lambda area_i)
+                             with k = macro_precond for macros, 1 otherwise;
+                             above 1 a macro moves in shorter steps than the
+                             standard cells around it */
 } place_params;
 
 /* Read-only facts about a handle. */
@@ -154,6 +171,8 @@ typedef struct place_info {
   int64_t device_bytes;   /* device memory the handle holds */
   int32_t kernels_per_iter; /* this library's kernel launches in one iteration */
   int32_t dct_mode;       /* the spectral path in use: PLACE_DCT_FP32 or _BF16X3 */
+  int32_t n_fillers;      /* filler cells (0 unless params.fillers) */
+  int32_t pad;
   int32_t gemm_bn[4];     /* tile width of each tensor-core GEMM stage */
   int32_t gemm_split[4];  /* CTAs per tile of each stage (split-K when 2) */
   int32_t wa_big_cap;     /* pins of a big net kept in shared memory */
@@ -177,6 +196,17 @@ typedef struct place_state {
                           * density scatter merges the lanes of a warp that hit
                           * the same bin; the map is the same either way. */
 } place_state;
+
+/* One accepted Nesterov iteration of one copy (place_get_history). */
+typedef struct place_iter_record {
+  int32_t iter;        /* k: iterations done before this one since the last reset */
+  int32_t backtracks;  /* steps redone since the last reset, up to this one */
+  double hpwl_wa;      /* HPWL at v_k from the iteration's WA pass (FP32 pins) */
+  double overflow;     /* tau at v_k (exact, Eq. 1's density constraint) */
+  double lambda;       /* the density weight of Eq. 2 for the next iteration */
+  double gamma;        /* Eq. 3's gamma for the next iteration */
+  double alpha;        /* the step length this iteration took */
+} place_iter_record;
 
 void place_default_params(place_params *p);
 
@@ -232,7 +262,9 @@ int place_step_multi(place_t *const *hs, int32_t n, int32_t n_iters, int32_t *co
  * lowest column.  A macro with no free corner stays where it is.  The first
  * WireMask call allocates device scratch of about
  * 8 K (nx + ny + 8 max_nets_per_macro) + 20 K min(nx ny / 256, 304) bytes,
- * freed by place_destroy.  It costs four kernel launches per macro.  A design
+ * freed by place_destroy.  It runs four small kernels per macro, captured
+ * into a CUDA graph on the first call for each copy selection and replayed
+ * by later calls (the graph is freed by place_destroy).  A design
  * without movable macros only resets the optimiser.  EINVAL on an unknown
  * op or, for Shuffle, p outside [0, 1]; ENOMEM if the scratch cannot be
  * allocated. */
@@ -245,10 +277,23 @@ int place_eval_hpwl_overflow(place_t *h, double *hpwl, double *overflow);
 /* Positions of copy `copy`: x, y are [n_cells] host or device buffers. */
 int place_get_positions(place_t *h, int32_t copy, float *x, float *y);
 
+/* Filler positions of copy `copy` (lower-left corners): x, y are host or
+ * device float buffers of at least cap entries (either may be NULL);
+ * min(cap, n_fillers) are written and *n (nullable) receives n_fillers.
+ * Synchronises. */
+int place_get_fillers(place_t *h, int32_t copy, float *x, float *y, int32_t cap, int32_t *n);
+
+/* Set the filler positions of copy `copy` (-1: all copies) from [n_fillers]
+ * host or device arrays, clamp them into the die and reset that copy's
+ * optimiser (as place_set_positions does).  A no-op without fillers. */
+int place_set_fillers(place_t *h, int32_t copy, const float *x, const float *y);
+
 /* Borrowed device pointers to the positions of copy `copy`, valid until
  * place_destroy.  The library keeps each copy's positions interleaved,
  * (x_0, y_0, x_1, y_1, ...), so that every pin costs one 8-byte gather: cell
- * i is (*x)[2 i], (*y)[2 i], for i < n_cells.  Reads must be ordered after
+ * i is (*x)[2 i], (*y)[2 i], for i < n_cells.  With filler cells the library
+ * orders its cells movable, fillers, fixed: fixed cell i (i >= n_movable) is
+ * then at entry i + n_fillers.  Reads must be ordered after
  * the handle's work on its stream; the arrays belong to the library and may
  * not be written (place_set_positions does that). */
 int place_device_views(place_t *h, int32_t copy, float **x, float **y);
@@ -259,6 +304,15 @@ int place_device_views(place_t *h, int32_t copy, float **x, float **y);
 int place_set_positions(place_t *h, int32_t copy, const float *x, const float *y);
 
 int place_get_state(place_t *h, int32_t copy, place_state *out);
+
+/* Per-iteration records of copy `copy` since its last reset (a placement's
+ * convergence: HPWL, overflow, lambda, gamma, step length per iteration).  The
+ * device keeps the last PLACE_HISTORY_CAP records per copy in a ring, written
+ * by the iteration's last kernel; out (host, nullable) receives the last
+ * min(cap, kept) of them, oldest first, and *n (nullable) their number.
+ * Synchronises. */
+#define PLACE_HISTORY_CAP 4096
+int place_get_history(place_t *h, int32_t copy, place_iter_record *out, int32_t cap, int32_t *n);
 
 /* ---- stage-level evaluation at the current positions of one copy --------
  * These run the same kernels as place_step on the copy's reference point
@@ -339,6 +393,16 @@ int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms);
  * untouched.  Synchronises. */
 int place_measure_wa_floor(place_t *h, int32_t reps, float *ms);
 
+/* Failure-path check of the bounded device waits.  Runs the first
+ * tensor-core GEMM stage of copy 0 once with its copy producer idle, so that
+ * no tile ever arrives: the MMA issuer's and the epilogue's waits give up
+ * after about a second each, the kernel frees its tensor memory and raises
+ * the device error flag, and this call returns PLACE_ETIMEOUT (the expected
+ * outcome) after clearing the flag.  Nothing hangs and the handle stays
+ * usable; the next iteration recomputes every stage.  EINVAL on a handle
+ * without the tensor-core path.  Synchronises; takes about two seconds. */
+int place_test_wait_timeout(place_t *h);
+
 /* Density map and overflow of a placement without any device allocation.
  *
  * The paper has no counterpart to this function: it serves callers that
@@ -380,10 +444,12 @@ int place_overflow_noalloc(const float *x, const float *y, const float *w, const
                            int32_t frac_bits, const int64_t *fixed_map, double *overflow,
                            int64_t *map_out, void *stream);
 
-/* Device memory place_create would take for this netlist, bins and
- * parameters (an upper bound; no device work).  Used for admission control. */
-int place_estimate_device_bytes(const place_netlist *nl, const place_bins *bins,
-                                const place_params *params, int64_t *bytes);
+/* Device memory place_create would take for this netlist, die, bins and
+ * parameters (an upper bound; no device work).  Used for admission control.
+ * die may be NULL when params has no filler cells (their count needs it). */
+int place_estimate_device_bytes(const place_netlist *nl, const place_die *die,
+                                const place_bins *bins, const place_params *params,
+                                int64_t *bytes);
 
 /* ---- job server: continuous batching of placement and restart jobs -------
  * Algorithm 1 runs a placement, then perturbed re-placements ("restarts") of

@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
+#include <utility>
 #include <vector>
 
 #include "internal.cuh"
@@ -80,6 +82,89 @@ constexpr int kMaxBigNetBlocks = 8192;  // one block per net above 256 pins, up 
 
 bool is_integer(double v) { return std::floor(v) == v && std::isfinite(v); }
 
+// Fixed-point resolution: the largest F <= 24 with max(|coordinate|, die
+// width, die height) 2^F < 2^30 and total area 2^2F < 2^62 (the extent bound
+// keeps bin-relative coordinates in int32); -1 when none fits.
+int choose_frac_bits(const place_die *die, double total_area) {
+  const double ext = std::max(std::max(std::max(std::fabs(die->xl), std::fabs(die->xh)),
+                                       std::max(std::fabs(die->yl), std::fabs(die->yh))),
+                              std::max(die->xh - die->xl, die->yh - die->yl));
+  for (int f = 24; f >= 0; --f)
+    if (ext * std::ldexp(1.0, f) < std::ldexp(1.0, 30) &&
+        total_area * std::ldexp(1.0, 2 * f) < std::ldexp(1.0, 62))
+      return f;
+  return -1;
+}
+
+// Filler cells (ePlace's whitespace fillers, the density of Eq. 2): pinless
+// movable cells that take up the whitespace the target density leaves.
+//  * size: the mean quantised width and height of the movable non-macro
+//    cells, each rounded to the nearest multiple of 2^-F (ties to even);
+//  * count: floor(max(0, t (A_die - A_fixed) - A_mov) / (w_f h_f)), with
+//    A_fixed the fixed cells' area inside the die (exact in fixed point) and
+//    A_mov the movable cells' quantised area, in float64 in that order;
+//  * start: filler j at (xl + u (xh - xl - w_f), yl + v (yh - yl - h_f))
+//    rounded to float32, u and v the (2j+1)-th and (2j+2)-th SplitMix64
+//    outputs from kFillerSeed as (z >> 11) 2^-53.
+constexpr unsigned long long kFillerSeed = 0x46494C4C45525321ull;  // "FILLERS!"
+struct FillPlan {
+  int Wf = 0, Hf = 0;   // size in units of 2^-F
+  long long n = 0;      // count
+};
+
+FillPlan plan_fillers(const place_netlist *nl, const place_die *die, const place_bins *bins,
+                      int F, unsigned __int128 mov_area_q) {
+  FillPlan fp;
+  const double s = std::ldexp(1.0, F);
+  const int Mv = nl->n_movable, C = nl->n_cells;
+  long long sw = 0, sh = 0, cnt = 0;
+  for (int i = 0; i < Mv; ++i) {
+    if (nl->is_macro && nl->is_macro[i]) continue;
+    sw += (long long)std::nearbyint((double)nl->w[i] * s);
+    sh += (long long)std::nearbyint((double)nl->h[i] * s);
+    ++cnt;
+  }
+  if (cnt == 0) return fp;
+  fp.Wf = std::max(1, (int)std::nearbyint((double)sw / (double)cnt));
+  fp.Hf = std::max(1, (int)std::nearbyint((double)sh / (double)cnt));
+  // fixed area inside the die: each fixed rectangle clipped to the die
+  const long long XL = (long long)(die->xl * s), YL = (long long)(die->yl * s);
+  const long long XH = XL + (long long)std::nearbyint((die->xh - die->xl) * s);
+  const long long YH = YL + (long long)std::nearbyint((die->yh - die->yl) * s);
+  unsigned __int128 fixed_q = 0;
+  for (int i = Mv; i < C; ++i) {
+    const long long X = (long long)std::nearbyint((double)nl->x0[i] * s);
+    const long long Y = (long long)std::nearbyint((double)nl->y0[i] * s);
+    const long long W = (long long)std::nearbyint((double)nl->w[i] * s);
+    const long long H = (long long)std::nearbyint((double)nl->h[i] * s);
+    const long long ox = std::min(X + W, XH) - std::max(X, XL);
+    const long long oy = std::min(Y + H, YH) - std::max(Y, YL);
+    if (ox > 0 && oy > 0) fixed_q += (unsigned __int128)ox * (unsigned __int128)oy;
+  }
+  const double s2 = std::ldexp(1.0, -2 * F);
+  const double a_die = (die->xh - die->xl) * (die->yh - die->yl);
+  const double fill = (double)bins->target_density * (a_die - (double)fixed_q * s2) -
+                      (double)mov_area_q * s2;
+  const double wf = fp.Wf * std::ldexp(1.0, -F), hf = fp.Hf * std::ldexp(1.0, -F);
+  fp.n = fill > 0.0 ? (long long)std::floor(fill / (wf * hf)) : 0;
+  return fp;
+}
+
+void filler_start(long long n, const place_die *die, double wf, double hf, float2 *out) {
+  auto splitmix = [](unsigned long long k) {  // (k+1)-th output from kFillerSeed
+    unsigned long long z = kFillerSeed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  for (long long j = 0; j < n; ++j) {
+    const double u = (double)(splitmix(2 * j) >> 11) * std::ldexp(1.0, -53);
+    const double v = (double)(splitmix(2 * j + 1) >> 11) * std::ldexp(1.0, -53);
+    out[j] = make_float2((float)(die->xl + u * ((die->xh - die->xl) - wf)),
+                         (float)(die->yl + v * ((die->yh - die->yl) - hf)));
+  }
+}
+
 // PLACE_DCT_AUTO: the tensor-core path wherever the grid allows it.
 int resolve_dct_mode(int mode, int nx, int ny) {
   if (mode != PLACE_DCT_AUTO) return mode;
@@ -110,6 +195,9 @@ struct place_t {
   int wm_max_nets = 1;
   void *wm_mem = nullptr;
   WmDev wm{};
+  // one captured graph per (first copy, copies) of a WireMask pass: the pass
+  // is four small kernels per macro, so its launches dominate otherwise
+  std::map<std::pair<int, int>, cudaGraphExec_t> wm_graphs;
   // Hybro bookkeeping (host)
   std::vector<double> best_hpwl, best_tau;
   std::vector<int> best_round;
@@ -144,6 +232,8 @@ void place_default_params(place_params *p) {
   p->gemm_bn = 0;
   p->wa_big_cap = 0;
   p->gemm_split = 0;
+  p->fillers = 0;
+  p->macro_precond = 1.0f;
 }
 
 int place_destroy(place_t *h) {
@@ -156,6 +246,7 @@ int place_destroy(place_t *h) {
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->mem) cudaFreeAsync(h->mem, h->stream);  // stream-ordered: no device-wide sync
+  for (auto &g : h->wm_graphs) cudaGraphExecDestroy(g.second);
   if (h->wm_mem) cudaFreeAsync(h->wm_mem, h->stream);
   delete h;
   return PLACE_OK;
@@ -198,13 +289,15 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.upx = d.prm.max_backtracks > 0 ? a.take<float>(K * Mv) : nullptr;
   d.upy = d.prm.max_backtracks > 0 ? a.take<float>(K * Mv) : nullptr;
   d.gacc = a.take<unsigned long long>(K * std::max<size_t>(Mv, 1));
-  d.M = a.take<unsigned long long>(K * G);
+  d.M = a.take<unsigned long long>(K * (size_t)d.Gm);
   d.Fmap = a.take<long long>(G);
   d.rho = a.take<float>(K * G);
   d.T = a.take<float>(K * 3 * G);
   d.SB = a.take<float>(K * 3 * G);
   d.E = a.take<float>(K * 3 * G);
   d.cs = a.take<CopyState>(K);
+  d.hist_cap = PLACE_HISTORY_CAP;
+  d.hist = a.take<place_iter_record>(K * (size_t)d.hist_cap);
   d.part = a.take<double>(K * S_COUNT * (size_t)d.nb_red);
   d.scal = a.take<double>(K * S_COUNT);
   d.tau_part = a.take<unsigned long long>(K * 2 * (size_t)d.nb_red);
@@ -377,7 +470,7 @@ int enqueue_reset(place_t *h, int c0, int n) {
   Dev &d = h->d;
   cudaStream_t st = h->stream;
   launch_reset(d, c0, n, st);
-  CK(cudaMemsetAsync(d.M + (size_t)c0 * d.G, 0, sizeof(unsigned long long) * d.G * n, st));
+  CK(cudaMemsetAsync(d.M + (size_t)c0 * d.Gm, 0, sizeof(unsigned long long) * d.Gm * n, st));
   launch_scatter(d, c0, n, 1, st);
   launch_density_finish(d, c0, n, FIN_RESET, st);
   CKL();
@@ -396,7 +489,7 @@ void enqueue_iteration(const Dev &d, cudaStream_t st, cudaStream_t st2, cudaEven
   cudaStreamWaitEvent(st2, fork, 0);
   launch_wa(d, 0, K, 0, nullptr, st2);
   cudaEventRecord(join, st2);
-  cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.G * K, st);
+  cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.Gm * K, st);
   launch_scatter(d, 0, K, 0, st);
   launch_density_finish(d, 0, K, FIN_ITER, st);
   launch_spectral(d, 0, K, 0, 0, st);
@@ -421,8 +514,10 @@ int ensure_graph(place_t *h) {
 // Interleaved device positions -> caller's x, y (host or device) through the
 // handle's scratch; synchronises.
 int copy_out_xy(place_t *h, const float2 *src, float *x, float *y) {
-  const int C = h->d.n_cells;
-  launch_unpack_xy(h->d.px_tmp, h->d.py_tmp, src, C, h->stream);
+  const Dev &d = h->d;
+  const int C = d.n_cells - d.n_fill;  // the design's cells: movable, then fixed
+  launch_unpack_xy(d.px_tmp, d.py_tmp, src, d.n_real, h->stream);
+  launch_unpack_xy(d.px_tmp + d.n_real, d.py_tmp + d.n_real, src + d.n_mov, C - d.n_real, h->stream);
   CKL();
   if (x) CK(cudaMemcpyAsync(x, h->d.px_tmp, sizeof(float) * C, cudaMemcpyDefault, h->stream));
   if (y) CK(cudaMemcpyAsync(y, h->d.py_tmp, sizeof(float) * C, cudaMemcpyDefault, h->stream));
@@ -514,6 +609,7 @@ extern "C" {
 
 int place_create(const place_netlist *nl, const place_die *die, const place_bins *bins,
                  const place_params *params, void *stream, place_t **out) {
+  NvtxRange nvtx_("place_create");
   if (out) *out = nullptr;
   if (!nl || !die || !bins || !out) return fail(PLACE_EINVAL, "null argument");
   place_params prm;
@@ -537,6 +633,9 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   if (prm.wa_big_cap != 0 && (prm.wa_big_cap < 32 || prm.wa_big_cap > 6144))
     return fail(PLACE_EINVAL, "wa_big_cap must be 0 or in [32, 6144]");
   if (prm.gemm_split < 0 || prm.gemm_split > 2) return fail(PLACE_EINVAL, "gemm_split must be 0, 1 or 2");
+  if (prm.fillers != 0 && prm.fillers != 1) return fail(PLACE_EINVAL, "fillers must be 0 or 1");
+  if (!(prm.macro_precond > 0.f) || !std::isfinite(prm.macro_precond))
+    return fail(PLACE_EINVAL, "macro_precond must be positive and finite");
   prm.dct_mode = resolve_dct_mode(prm.dct_mode, bins->nx, bins->ny);
   if (prm.dct_mode != PLACE_DCT_FP32 && prm.dct_mode != PLACE_DCT_BF16X3)
     return fail(PLACE_EINVAL, "unknown dct_mode %d", prm.dct_mode);
@@ -561,19 +660,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     total_area += (double)nl->w[i] * (double)nl->h[i];
   }
 
-  // fixed-point resolution: the largest F <= 24 with
-  // max(|coordinate|, die width, die height) 2^F < 2^30 and total area
-  // 2^2F < 2^62 (the extent bound keeps bin-relative coordinates in int32)
-  const double ext = std::max(std::max(std::max(std::fabs(die->xl), std::fabs(die->xh)),
-                                       std::max(std::fabs(die->yl), std::fabs(die->yh))),
-                              std::max(die->xh - die->xl, die->yh - die->yl));
-  int F = -1;
-  for (int f = 24; f >= 0; --f) {
-    if (ext * std::ldexp(1.0, f) < std::ldexp(1.0, 30) && total_area * std::ldexp(1.0, 2 * f) < std::ldexp(1.0, 62)) {
-      F = f;
-      break;
-    }
-  }
+  const int F = choose_frac_bits(die, total_area);
   if (F < 0) return fail(PLACE_ERANGE, "design does not fit the 64-bit fixed-point density range");
   const double s = std::ldexp(1.0, F);
   const double bw = (die->xh - die->xl) / nx, bh = (die->yh - die->yl) / ny;
@@ -639,6 +726,39 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   }
   d.mov_area_q = mov_area_q > 0 ? (double)mov_area_q : 1.0;
 
+  // filler cells; the library's cell order is [movable | fillers | fixed]
+  FillPlan fp;
+  if (prm.fillers) fp = plan_fillers(nl, die, bins, F, mov_area_q);
+  if ((long long)C + fp.n >= (1LL << 30)) {
+    delete h;
+    return fail(PLACE_ERANGE, "too many filler cells (%lld)", fp.n);
+  }
+  const int nf = (int)fp.n;
+  const int Ci = C + nf, Mo = Mv + nf;  // library cells, optimiser cells
+  auto ci = [&](int i) { return i < Mv ? i : i + nf; };  // design cell -> library cell
+  d.n_cells = Ci; d.n_mov = Mo; d.n_real = Mv; d.n_fill = nf;
+  d.Gm = nf ? 2 * d.G : d.G;
+  d.fill_area_q = (double)nf * (double)fp.Wf * (double)fp.Hf;
+  std::vector<float> wi(Ci), hi(Ci);
+  std::vector<int> Wqi(Ci), Hqi(Ci);
+  std::vector<unsigned char> macro(Ci, 0);
+  std::vector<float2> xy0(Ci);
+  for (int i = 0; i < C; ++i) {
+    const int k = ci(i);
+    wi[k] = nl->w[i]; hi[k] = nl->h[i];
+    Wqi[k] = Wq[i]; Hqi[k] = Hq[i];
+    xy0[k] = make_float2(nl->x0[i], nl->y0[i]);
+    if (nl->is_macro) macro[k] = nl->is_macro[i] ? 1 : 0;
+  }
+  {
+    const double wf = fp.Wf * std::ldexp(1.0, -F), hf = fp.Hf * std::ldexp(1.0, -F);
+    filler_start(nf, die, wf, hf, xy0.data() + Mv);
+    for (int j = 0; j < nf; ++j) {
+      wi[Mv + j] = (float)wf; hi[Mv + j] = (float)hf;
+      Wqi[Mv + j] = fp.Wf; Hqi[Mv + j] = fp.Hf;
+    }
+  }
+
   // nets grouped by degree class (stable), pins in the new net order
   std::vector<int> order(E);
   {
@@ -681,7 +801,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
       if (nl->pin_cell[j] < nl->pin_cell[jmin]) jmin = j;
     for (int j = p0; j < p1; ++j, ++q) {
       const int src = j == p0 ? jmin : (j == jmin ? p0 : j);
-      pin_cell[q] = nl->pin_cell[src];
+      pin_cell[q] = ci(nl->pin_cell[src]);
       pin_off[q] = make_float2(nl->pin_dx[src], nl->pin_dy[src]);
     }
     net_ptr[ne + 1] = q;
@@ -722,14 +842,14 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   d.scat_t1 = kScatterMergedBelow;
   d.scat_t2 = kScatterTableBelow;
   d.scat_force = prm.scatter_mode;
-  std::vector<float> npins(std::max(Mv, 1)), area(std::max(Mv, 1));
-  for (int i = 0; i < Mv; ++i) {
-    npins[i] = (float)cell_npins[i];
-    area[i] = nl->w[i] * nl->h[i];
+  // pins and charge per optimiser cell for the preconditioner
+  // max(1, pins_i + lambda area_i); a movable macro's charge is weighted by
+  // macro_precond
+  std::vector<float> npins(std::max(Mo, 1), 0.f), area(std::max(Mo, 1));
+  for (int i = 0; i < Mo; ++i) {
+    if (i < Mv) npins[i] = (float)cell_npins[i];
+    area[i] = (float)((double)wi[i] * (double)hi[i] * (i < Mv && macro[i] ? (double)prm.macro_precond : 1.0));
   }
-  std::vector<unsigned char> macro(C, 0);
-  if (nl->is_macro)
-    for (int i = 0; i < C; ++i) macro[i] = nl->is_macro[i] ? 1 : 0;
   h->n_cand_all = Mv;
   h->n_cand_macro = 0;
   for (int i = 0; i < Mv; ++i) h->n_cand_macro += macro[i];
@@ -759,12 +879,12 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
       h->wm_ptr.push_back((int)h->wm_net.size());
       h->wm_max_nets = std::max(h->wm_max_nets, (int)nets[t].size());
     }
-    for (int i = Mv; i < C; ++i) h->wm_obst.push_back(i);
+    for (int i = Mv; i < C; ++i) h->wm_obst.push_back(ci(i));
     h->wm_obst.insert(h->wm_obst.end(), mo.begin(), mo.end());
   }
 
   // launch plan
-  d.cell_blocks = std::max(1, std::min((Mv + kThreads - 1) / kThreads, kMaxCellBlocks));
+  d.cell_blocks = std::max(1, std::min((Mo + kThreads - 1) / kThreads, kMaxCellBlocks));
   d.bin_blocks = std::max(1, std::min((d.G + kThreads - 1) / kThreads, kMaxCellBlocks));
   d.wa_blocks_total = 0;
   for (int c = 0; c < 5; ++c) {
@@ -785,7 +905,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     d.cg_blocks = std::max(1, std::min(d.cell_blocks, d.sms * cell_grad_blocks_per_sm()));
   }
   int sn = 2;
-  while (sn < C) sn <<= 1;
+  while (sn < Ci) sn <<= 1;
   d.sort_n = sn;
 
   // device memory: one allocation carved into arrays
@@ -813,29 +933,29 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   up(d.net_ptr, net_ptr.data(), sizeof(int) * (E + 1));
   up(d.pin_cell, pin_cell.data(), sizeof(int) * P);
   up(d.pin_off, pin_off.data(), sizeof(float2) * P);
-  up(d.w, nl->w, sizeof(float) * C);
-  up(d.h, nl->h, sizeof(float) * C);
-  up(d.Wq, Wq.data(), sizeof(int) * C);
-  up(d.Hq, Hq.data(), sizeof(int) * C);
-  up(d.npins, npins.data(), sizeof(float) * Mv);
-  up(d.area, area.data(), sizeof(float) * Mv);
-  up(d.is_macro, macro.data(), C);
+  up(d.w, wi.data(), sizeof(float) * Ci);
+  up(d.h, hi.data(), sizeof(float) * Ci);
+  up(d.Wq, Wqi.data(), sizeof(int) * Ci);
+  up(d.Hq, Hqi.data(), sizeof(int) * Ci);
+  up(d.npins, npins.data(), sizeof(float) * Mo);
+  up(d.area, area.data(), sizeof(float) * Mo);
+  up(d.is_macro, macro.data(), Ci);
   if (d.st) {
     // density stretching: along each axis a cell narrower than sqrt(2) bins
     // widens to rint(sqrt(2) BW) about its centre (shift floor((W' - W) / 2));
     // its density scale is R = floor(W H 2^31 / (W' H'))
     const long long ws = (long long)std::nearbyint(std::sqrt(2.0) * (double)d.BW);
     const long long hs = (long long)std::nearbyint(std::sqrt(2.0) * (double)d.BH);
-    std::vector<int4> st(std::max(Mv, 1));
-    std::vector<unsigned int> sR(std::max(Mv, 1));
-    for (int i = 0; i < Mv; ++i) {
-      const long long W2 = std::max<long long>(Wq[i], ws), H2 = std::max<long long>(Hq[i], hs);
-      st[i] = make_int4((int)((W2 - Wq[i]) >> 1), (int)((H2 - Hq[i]) >> 1), (int)W2, (int)H2);
-      const unsigned __int128 num = ((unsigned __int128)((unsigned long long)Wq[i] * (unsigned long long)Hq[i])) << 31;
+    std::vector<int4> st(std::max(Mo, 1));
+    std::vector<unsigned int> sR(std::max(Mo, 1));
+    for (int i = 0; i < Mo; ++i) {
+      const long long W2 = std::max<long long>(Wqi[i], ws), H2 = std::max<long long>(Hqi[i], hs);
+      st[i] = make_int4((int)((W2 - Wqi[i]) >> 1), (int)((H2 - Hqi[i]) >> 1), (int)W2, (int)H2);
+      const unsigned __int128 num = ((unsigned __int128)((unsigned long long)Wqi[i] * (unsigned long long)Hqi[i])) << 31;
       sR[i] = (unsigned int)(num / (unsigned __int128)((unsigned long long)W2 * (unsigned long long)H2));
     }
-    up(d.st, st.data(), sizeof(int4) * Mv);
-    up(d.sR, sR.data(), sizeof(unsigned int) * Mv);
+    up(d.st, st.data(), sizeof(int4) * Mo);
+    up(d.sR, sR.data(), sizeof(unsigned int) * Mo);
   }
   if (d.net_w) up(d.net_w, net_w.data(), sizeof(float) * E);
   {
@@ -854,9 +974,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     up(d.cu, cu.data(), sizeof(float) * nx);
     up(d.cv, cv.data(), sizeof(float) * ny);
   }
-  std::vector<float2> xy0(C);
-  for (int i = 0; i < C; ++i) xy0[i] = make_float2(nl->x0[i], nl->y0[i]);
-  for (int c = 0; c < d.K && rc == PLACE_OK; ++c) up(d.xy + (size_t)c * C, xy0.data(), sizeof(float2) * C);
+  for (int c = 0; c < d.K && rc == PLACE_OK; ++c) up(d.xy + (size_t)c * Ci, xy0.data(), sizeof(float2) * Ci);
   if (rc != PLACE_OK) {
     place_destroy(h);
     return rc;
@@ -872,7 +990,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   ce = cudaMemsetAsync(d.E, 0, sizeof(float) * (size_t)d.K * 3 * d.G, h->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.Fmap, 0, sizeof(long long) * d.G, h->stream);
   if (ce == cudaSuccess)
-    ce = cudaMemsetAsync(d.gacc, 0, sizeof(unsigned long long) * (size_t)d.K * std::max(Mv, 1), h->stream);
+    ce = cudaMemsetAsync(d.gacc, 0, sizeof(unsigned long long) * (size_t)d.K * std::max(Mo, 1), h->stream);
   if (ce == cudaSuccess && wa_prepare(d.wa_big_cap)) ce = cudaErrorInvalidValue;
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.cs, 0, sizeof(CopyState) * d.K, h->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.ctr, 0, sizeof(unsigned int) * d.K * C_COUNT, h->stream);
@@ -885,7 +1003,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     place_destroy(h);
     return rc;
   }
-  launch_scatter_fixed(d, d.xy, Mv, C, reinterpret_cast<unsigned long long *>(d.Fmap), h->stream);
+  launch_scatter_fixed(d, d.xy, Mo, Ci, reinterpret_cast<unsigned long long *>(d.Fmap), h->stream);
   rc = enqueue_reset(h, 0, d.K);
   if (rc == PLACE_OK) {
     ce = cudaStreamSynchronize(h->stream);
@@ -894,6 +1012,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   if (rc == PLACE_OK && prm.autotune) {
     // time the candidates on this design, then put copy 0 and every
     // optimiser back to the start
+    NvtxRange nvtx_tune("autotune");
     TuneOut to{};
     TuneCtx tctx{h, xy0.data()};
     const TuneHooks hooks{encode_tc_maps_cb, time_iters_cb, &tctx};
@@ -904,7 +1023,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     } else {
       h->autotuned = 1;
       h->autotune_ms = to.ms;
-      for (int c = 0; c < d.K && rc == PLACE_OK; ++c) up(d.xy + (size_t)c * C, xy0.data(), sizeof(float2) * C);
+      for (int c = 0; c < d.K && rc == PLACE_OK; ++c) up(d.xy + (size_t)c * Ci, xy0.data(), sizeof(float2) * Ci);
       if (rc == PLACE_OK) rc = enqueue_reset(h, 0, d.K);
       if (rc == PLACE_OK) {
         ce = cudaStreamSynchronize(h->stream);
@@ -923,7 +1042,8 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
 int place_get_info(const place_t *h, place_info *o) {
   if (!h || !o) return fail(PLACE_EINVAL, "null argument");
   const Dev &d = h->d;
-  o->n_cells = d.n_cells; o->n_movable = d.n_mov; o->n_nets = d.n_nets; o->n_pins = d.n_pins;
+  o->n_cells = d.n_cells - d.n_fill; o->n_movable = d.n_real; o->n_nets = d.n_nets; o->n_pins = d.n_pins;
+  o->n_fillers = d.n_fill;
   o->nx = d.nx; o->ny = d.ny; o->n_copies = d.K;
   o->frac_bits = d.F;
   o->bin_w_q = d.BW; o->bin_h_q = d.BH;
@@ -949,6 +1069,7 @@ int place_get_info(const place_t *h, place_info *o) {
 }
 
 int place_step(place_t *h, int32_t n_iters, int32_t *converged) {
+  NvtxRange nvtx_("place_step");
   if (!h) return fail(PLACE_EINVAL, "null handle");
   if (n_iters < 0) return fail(PLACE_EINVAL, "n_iters < 0");
   if (n_iters > 0) {
@@ -967,6 +1088,7 @@ int place_step(place_t *h, int32_t n_iters, int32_t *converged) {
 }
 
 int place_step_multi(place_t *const *hs, int32_t n, int32_t n_iters, int32_t *converged) {
+  NvtxRange nvtx_("place_step_multi");
   if (!hs || n < 1) return fail(PLACE_EINVAL, "need at least one handle");
   if (n_iters < 0) return fail(PLACE_EINVAL, "n_iters < 0");
   for (int i = 0; i < n; ++i)
@@ -991,6 +1113,7 @@ int place_step_multi(place_t *const *hs, int32_t n, int32_t n_iters, int32_t *co
 }
 
 int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms) {
+  NvtxRange nvtx_("place_step_timed");
   if (!h || !stage_ms) return fail(PLACE_EINVAL, "null argument");
   const Dev &d = h->d;
   const int K = d.K;
@@ -1001,7 +1124,7 @@ int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms) {
   int rc = PLACE_OK;
   for (int it = 0; it < n_iters && rc == PLACE_OK; ++it) {
     cudaEventRecord(ev[0], st);
-    cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.G * K, st);
+    cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.Gm * K, st);
     launch_scatter(d, 0, K, 0, st);
     launch_density_finish(d, 0, K, FIN_ITER, st);
     cudaEventRecord(ev[1], st);
@@ -1028,6 +1151,20 @@ int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms) {
   if ((rc = check_dev_err(h))) return rc;
   for (int s = 0; s < PLACE_N_STAGES; ++s) stage_ms[s] += (float)acc[s];
   return PLACE_OK;
+}
+
+int place_test_wait_timeout(place_t *h) {
+  if (!h) return fail(PLACE_EINVAL, "null handle");
+  if (!h->d.tc) return fail(PLACE_EINVAL, "the handle has no tensor-core spectral path");
+  NvtxRange nvtx_("place_test_wait_timeout");
+  launch_spectral_tc_stalled(h->d, h->stream);
+  CKL();
+  CK(cudaStreamSynchronize(h->stream));
+  const int rc = check_dev_err(h);
+  // the kernel ended on its own: clear the flag, the handle stays usable
+  CK(cudaMemsetAsync(h->d.err, 0, sizeof(int), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return rc;
 }
 
 int place_measure_wa_floor(place_t *h, int32_t reps, float *ms) {
@@ -1070,6 +1207,27 @@ int place_get_state(place_t *h, int32_t copy, place_state *o) {
   return PLACE_OK;
 }
 
+int place_get_history(place_t *h, int32_t copy, place_iter_record *out, int32_t cap, int32_t *n) {
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  if (cap < 0) return fail(PLACE_EINVAL, "cap < 0");
+  const Dev &d = h->d;
+  CopyState cs;
+  CK(cudaMemcpyAsync(&cs, d.cs + copy, sizeof cs, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const int kept = std::min(cs.n_hist, d.hist_cap);
+  if (n) *n = kept;
+  const int m = std::min(kept, (int)cap);
+  if (out && m > 0) {
+    // the last m records, oldest first: ring slots (n_hist - m .. n_hist - 1) mod cap
+    std::vector<place_iter_record> ring(d.hist_cap);
+    CK(cudaMemcpy(ring.data(), d.hist + (size_t)copy * d.hist_cap,
+                  sizeof(place_iter_record) * d.hist_cap, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < m; ++i) out[i] = ring[(cs.n_hist - m + i) % d.hist_cap];
+  }
+  return PLACE_OK;
+}
+
 int place_get_stretched_map(place_t *h, int32_t copy, int64_t *map) {
   int rc = check_copy(h, copy, false);
   if (rc) return rc;
@@ -1088,6 +1246,37 @@ int place_get_positions(place_t *h, int32_t copy, float *x, float *y) {
   return copy_out_xy(h, h->d.xy + copy * C, x, y);
 }
 
+int place_get_fillers(place_t *h, int32_t copy, float *x, float *y, int32_t cap, int32_t *n) {
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  if (cap < 0) return fail(PLACE_EINVAL, "cap < 0");
+  const Dev &d = h->d;
+  if (n) *n = d.n_fill;
+  const int m = std::min(cap, d.n_fill);
+  if (m > 0 && (x || y)) {
+    launch_unpack_xy(d.px_tmp, d.py_tmp, d.xy + (size_t)copy * d.n_cells + d.n_real, m, h->stream);
+    CKL();
+    if (x) CK(cudaMemcpyAsync(x, d.px_tmp, sizeof(float) * m, cudaMemcpyDefault, h->stream));
+    if (y) CK(cudaMemcpyAsync(y, d.py_tmp, sizeof(float) * m, cudaMemcpyDefault, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return PLACE_OK;
+}
+
+int place_set_fillers(place_t *h, int32_t copy, const float *x, const float *y) {
+  int rc = check_copy(h, copy, true);
+  if (rc) return rc;
+  const Dev &d = h->d;
+  if (d.n_fill == 0) return PLACE_OK;
+  if (!x || !y) return fail(PLACE_EINVAL, "null positions");
+  const int c0 = copy < 0 ? 0 : copy, n = copy < 0 ? d.K : 1;
+  CK(cudaMemcpyAsync(d.px_tmp, x, sizeof(float) * d.n_fill, cudaMemcpyDefault, h->stream));
+  CK(cudaMemcpyAsync(d.py_tmp, y, sizeof(float) * d.n_fill, cudaMemcpyDefault, h->stream));
+  for (int c = c0; c < c0 + n; ++c)
+    launch_pack_xy(d.xy + (size_t)c * d.n_cells + d.n_real, d.px_tmp, d.py_tmp, d.n_fill, h->stream);
+  return enqueue_reset(h, c0, n);
+}
+
 int place_device_views(place_t *h, int32_t copy, float **x, float **y) {
   int rc = check_copy(h, copy, false);
   if (rc) return rc;
@@ -1102,9 +1291,8 @@ int place_set_positions(place_t *h, int32_t copy, const float *x, const float *y
   int rc = check_copy(h, copy, true);
   if (rc) return rc;
   if (!x || !y) return fail(PLACE_EINVAL, "null positions");
-  const size_t C = h->d.n_cells, Mv = h->d.n_mov;
+  const size_t C = h->d.n_cells, Mv = h->d.n_real;
   int c0 = copy < 0 ? 0 : copy, n = copy < 0 ? h->d.K : 1;
-  (void)C;
   CK(cudaMemcpyAsync(h->d.px_tmp, x, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
   CK(cudaMemcpyAsync(h->d.py_tmp, y, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
   for (int c = c0; c < c0 + n; ++c) launch_pack_xy(h->d.xy + c * C, h->d.px_tmp, h->d.py_tmp, (int)Mv, h->stream);
@@ -1112,6 +1300,7 @@ int place_set_positions(place_t *h, int32_t copy, const float *x, const float *y
 }
 
 int place_eval_wirelength(place_t *h, int32_t copy, float gamma, double *wl, float *gx, float *gy) {
+  NvtxRange nvtx_("place_eval_wirelength");
   int rc = check_copy(h, copy, false);
   if (rc) return rc;
   if (!(gamma > 0.f)) return fail(PLACE_EINVAL, "gamma must be > 0");
@@ -1124,9 +1313,9 @@ int place_eval_wirelength(place_t *h, int32_t copy, float gamma, double *wl, flo
   launch_cell_grad(d, copy, 1, 1, h->stream);
   launch_reduce_slot(d, S_WL, d.wa_blocks_total, copy, 1, h->stream);
   CKL();
-  const size_t Mv = d.n_mov;
-  if (gx) CK(cudaMemcpyAsync(gx, d.gwx + copy * Mv, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
-  if (gy) CK(cudaMemcpyAsync(gy, d.gwy + copy * Mv, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
+  const size_t Mo = d.n_mov, Mv = d.n_real;  // per-copy stride, the design's movable cells
+  if (gx) CK(cudaMemcpyAsync(gx, d.gwx + copy * Mo, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
+  if (gy) CK(cudaMemcpyAsync(gy, d.gwy + copy * Mo, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
   double v = 0;
   CK(cudaMemcpyAsync(&v, d.scal + (size_t)copy * S_COUNT + S_WL, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -1140,7 +1329,7 @@ namespace {
 
 int density_at(place_t *h, int copy) {
   Dev &d = h->d;
-  CK(cudaMemsetAsync(d.M + (size_t)copy * d.G, 0, sizeof(unsigned long long) * d.G, h->stream));
+  CK(cudaMemsetAsync(d.M + (size_t)copy * d.Gm, 0, sizeof(unsigned long long) * d.Gm, h->stream));
   launch_scatter(d, copy, 1, 1, h->stream);
   launch_density_finish(d, copy, 1, FIN_EVAL, h->stream);
   CKL();
@@ -1152,11 +1341,12 @@ int density_at(place_t *h, int copy) {
 extern "C" {
 
 int place_eval_density(place_t *h, int32_t copy, int64_t *map, double *overflow) {
+  NvtxRange nvtx_("place_eval_density");
   int rc = check_copy(h, copy, false);
   if (rc) return rc;
   Dev &d = h->d;
   if ((rc = density_at(h, copy))) return rc;
-  if (map) CK(cudaMemcpyAsync(map, d.M + (size_t)copy * d.G, sizeof(int64_t) * d.G, cudaMemcpyDefault, h->stream));
+  if (map) CK(cudaMemcpyAsync(map, d.M + (size_t)copy * d.Gm, sizeof(int64_t) * d.G, cudaMemcpyDefault, h->stream));
   double s = 0;
   CK(cudaMemcpyAsync(&s, d.scal + (size_t)copy * S_COUNT + S_TAU, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -1172,6 +1362,7 @@ int place_get_fixed_map(place_t *h, int64_t *map) {
 }
 
 int place_eval_field(place_t *h, int32_t copy, float *psi, float *ex, float *ey) {
+  NvtxRange nvtx_("place_eval_field");
   int rc = check_copy(h, copy, false);
   if (rc) return rc;
   Dev &d = h->d;
@@ -1188,6 +1379,7 @@ int place_eval_field(place_t *h, int32_t copy, float *psi, float *ex, float *ey)
 }
 
 int place_eval_density_grad(place_t *h, int32_t copy, float *gx, float *gy) {
+  NvtxRange nvtx_("place_eval_density_grad");
   int rc = check_copy(h, copy, false);
   if (rc) return rc;
   Dev &d = h->d;
@@ -1195,20 +1387,21 @@ int place_eval_density_grad(place_t *h, int32_t copy, float *gx, float *gy) {
   launch_spectral(d, copy, 1, 0, 1, h->stream);
   launch_cell_grad(d, copy, 1, 1, h->stream);
   CKL();
-  const size_t Mv = d.n_mov;
-  if (gx) CK(cudaMemcpyAsync(gx, d.gdx + copy * Mv, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
-  if (gy) CK(cudaMemcpyAsync(gy, d.gdy + copy * Mv, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
+  const size_t Mo = d.n_mov, Mv = d.n_real;  // per-copy stride, the design's movable cells
+  if (gx) CK(cudaMemcpyAsync(gx, d.gdx + copy * Mo, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
+  if (gy) CK(cudaMemcpyAsync(gy, d.gdy + copy * Mo, sizeof(float) * Mv, cudaMemcpyDefault, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return check_dev_err(h);
 }
 
 int place_eval_hpwl_overflow(place_t *h, double *hpwl, double *overflow) {
+  NvtxRange nvtx_("place_eval_hpwl_overflow");
   if (!h) return fail(PLACE_EINVAL, "null handle");
   Dev &d = h->d;
   const int K = d.K;
   launch_hpwl64(d, 0, K, h->stream);
   launch_reduce_slot(d, S_HP64, d.cell_blocks + 2 * std::max(d.cell_blocks / 2, 1), 0, K, h->stream);
-  CK(cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.G * K, h->stream));
+  CK(cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.Gm * K, h->stream));
   launch_scatter(d, 0, K, 1, h->stream);
   launch_density_finish(d, 0, K, FIN_EVAL, h->stream);
   CKL();
@@ -1223,14 +1416,31 @@ int place_eval_hpwl_overflow(place_t *h, double *hpwl, double *overflow) {
 }
 
 int place_perturb(place_t *h, int32_t op, float p, uint64_t seed, int32_t copy) {
+  NvtxRange nvtx_("place_perturb");
   int rc = check_copy(h, copy, true);
   if (rc) return rc;
   if (op == PLACE_WIREMASK) {
     const int c0 = copy < 0 ? 0 : copy, n = copy < 0 ? h->d.K : 1;
     if (!h->wm_order.empty()) {
       if ((rc = ensure_wiremask(h))) return rc;
-      launch_wiremask(h->d, h->wm, h->wm_ptr.data(), c0, n, h->stream);
-      CKL();
+      cudaGraphExec_t &ex = h->wm_graphs[std::make_pair(c0, n)];
+      if (!ex) {
+        // the tables are uploaded on h->stream; the capture stream waits for them
+        CK(cudaEventRecord(h->ev_fork, h->stream));
+        CK(cudaStreamWaitEvent(h->cap, h->ev_fork, 0));
+        CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        launch_wiremask(h->d, h->wm, h->wm_ptr.data(), c0, n, h->cap);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          ex = nullptr;
+          h->wm_graphs.erase(std::make_pair(c0, n));
+          return fail(PLACE_ECUDA, "WireMask graph: %s", cudaGetErrorString(e));
+        }
+      }
+      CK(cudaGraphLaunch(ex, h->stream));
     }
     return enqueue_reset(h, c0, n);
   }
@@ -1254,6 +1464,7 @@ int place_perturb(place_t *h, int32_t op, float p, uint64_t seed, int32_t copy) 
 
 int place_hybro(place_t *h, int32_t n_rounds, int32_t op, float p, uint64_t seed, float tau_target,
                 double *best_hpwl, double *best_overflow, int32_t *best_round) {
+  NvtxRange nvtx_("place_hybro");
   if (!h) return fail(PLACE_EINVAL, "null handle");
   if (n_rounds < 0) return fail(PLACE_EINVAL, "n_rounds < 0");
   Dev &d = h->d;
@@ -1266,6 +1477,7 @@ int place_hybro(place_t *h, int32_t n_rounds, int32_t op, float p, uint64_t seed
   h->round_tau.assign((size_t)K * nrec, 0.0);
   h->n_round_records = 0;
   for (int r = 0; r <= n_rounds; ++r) {
+    NvtxRange nvtx_round("hybro round");
     // place every copy until it stops (converged or max_iters)
     for (;;) {
       int rc = place_step(h, 32, conv.data());
@@ -1335,20 +1547,41 @@ int place_get_hybro_rounds(place_t *h, int32_t copy, double *hpwl, double *overf
 
 }  // extern "C"
 
-extern "C" int place_estimate_device_bytes(const place_netlist *nl, const place_bins *bins,
-                                           const place_params *params, int64_t *bytes) {
+extern "C" int place_estimate_device_bytes(const place_netlist *nl, const place_die *die,
+                                           const place_bins *bins, const place_params *params,
+                                           int64_t *bytes) {
   if (!nl || !bins || !bytes) return fail(PLACE_EINVAL, "null argument");
   place_params prm;
   if (params) prm = *params; else place_default_params(&prm);
   if (nl->n_cells <= 0 || nl->n_pins < 0 || nl->n_nets < 0 || bins->nx <= 0 || bins->ny <= 0 ||
       prm.n_copies < 1)
     return fail(PLACE_EINVAL, "bad sizes");
+  // filler cells: counted exactly as place_create counts them (the die is
+  // needed for that; without it, or without the netlist's arrays, none)
+  long long nf = 0;
+  if (prm.fillers && die && nl->w && nl->h && nl->x0 && nl->y0 && die->xh > die->xl &&
+      die->yh > die->yl) {
+    double total_area = 0.0;
+    for (int i = 0; i < nl->n_cells; ++i) total_area += (double)nl->w[i] * (double)nl->h[i];
+    const int F = choose_frac_bits(die, total_area);
+    if (F >= 0) {
+      const double s = std::ldexp(1.0, F);
+      unsigned __int128 mov_area_q = 0;
+      for (int i = 0; i < nl->n_movable; ++i)
+        mov_area_q += (unsigned __int128)(unsigned long long)std::nearbyint((double)nl->w[i] * s) *
+                      (unsigned __int128)(unsigned long long)std::nearbyint((double)nl->h[i] * s);
+      nf = plan_fillers(nl, die, bins, F, mov_area_q).n;
+    }
+  }
   // the layout of place_create with upper bounds for the sizes that depend on
   // the netlist's contents (pins on movable cells, reduction slots)
   Dev d{};
   d.K = prm.n_copies;
-  d.n_cells = nl->n_cells; d.n_mov = nl->n_movable; d.n_nets = nl->n_nets; d.n_pins = nl->n_pins;
+  d.n_cells = nl->n_cells + (int)nf; d.n_mov = nl->n_movable + (int)nf;
+  d.n_real = nl->n_movable; d.n_fill = (int)nf;
+  d.n_nets = nl->n_nets; d.n_pins = nl->n_pins;
   d.nx = bins->nx; d.ny = bins->ny; d.G = bins->nx * bins->ny;
+  d.Gm = nf ? 2 * d.G : d.G;
   d.has_net_w = nl->net_w ? 1 : 0;
   prm.dct_mode = resolve_dct_mode(prm.dct_mode, bins->nx, bins->ny);
   d.tc = prm.dct_mode == PLACE_DCT_BF16X3 ? 1 : 0;

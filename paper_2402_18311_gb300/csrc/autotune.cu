@@ -232,7 +232,7 @@ int autotune(Dev &d, int max_deg, cudaStream_t st, const TuneHooks &hk, TuneOut 
     std::vector<double> neff(nl);
     std::vector<float> tmode[3];
     for (auto &v : tmode) v.assign(nl, 0.f);
-    const size_t mbytes = sizeof(unsigned long long) * (size_t)d.G;
+    const size_t mbytes = sizeof(unsigned long long) * (size_t)d.Gm;
     const int blocks = std::max(1, std::min((d.n_mov + kThreads - 1) / kThreads, kMaxCellBlocks));
     for (int l = 0; l < nl; ++l) {
       const float width = 0.0004f * std::pow(2.0f, (float)l);  // 0.0004 .. 0.2 of the die

@@ -100,14 +100,17 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
   }
   __syncthreads();
   const float2 *xy = d.xy + (size_t)c * d.n_cells;
-  unsigned long long *M = d.M + (size_t)c * d.G;
+  unsigned long long *M = d.M + (size_t)c * d.Gm;
   const int stride = gridDim.x * blockDim.x;
   const double n_eff = d.cs[c].n_eff;
+  // map index of cell i's bin b: b for a movable cell, G + b for a filler
+  // (the fillers' map follows the movable one)
   const int mode = d.scat_force >= 0 ? d.scat_force
                                      : (n_eff < d.scat_t1 ? SCAT_MERGED
                                                           : (n_eff < d.scat_t2 ? SCAT_TABLE : SCAT_DIRECT));
   if (mode == SCAT_DIRECT) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += stride) {
+      const int mo = i < d.n_real ? 0 : d.G;
       const float2 v = xy[i];
       const QRect32 r = qrect32(v.x, v.y, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW32, d.BH32,
                                 d.nx, d.ny, d.ibw_q, d.ibh_q);
@@ -117,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
         for (int iy = r.iy0; iy <= r.iy1; ++iy) {
           const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
           if (oy == 0) continue;
-          atomicAdd(&M[ix * d.ny + iy], (unsigned long long)((long long)ox * oy));
+          atomicAdd(&M[mo + ix * d.ny + iy], (unsigned long long)((long long)ox * oy));
         }
       }
     }
@@ -125,6 +128,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
   }
   if (mode == SCAT_TABLE) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += stride) {
+      const int mo = i < d.n_real ? 0 : d.G;
       const float2 v = xy[i];
       const QRect32 r = qrect32(v.x, v.y, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW32, d.BH32,
                                 d.nx, d.ny, d.ibw_q, d.ibh_q);
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
         for (int iy = r.iy0; iy <= r.iy1; ++iy) {
           const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
           if (oy == 0) continue;
-          hash_add(keys, vals, M, ix * d.ny + iy, (unsigned long long)((long long)ox * oy));
+          hash_add(keys, vals, M, mo + ix * d.ny + iy, (unsigned long long)((long long)ox * oy));
         }
       }
     }
@@ -145,6 +149,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
   for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < d.n_mov; i0 += stride) {
     const int i = i0 + (threadIdx.x & 31);
     const bool valid = i < d.n_mov;
+    const int mo = i < d.n_real ? 0 : d.G;
     QRect32 r;
     if (valid) {
       const float2 v = xy[i];
@@ -164,7 +169,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
         const int ox = overlap32(r.x0, r.x1, ix, d.BW32);
         const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
         a = (unsigned long long)((long long)ox * oy);
-        if (a != 0ull) b = ix * d.ny + iy;
+        if (a != 0ull) b = mo + ix * d.ny + iy;
       }
       // one full-warp reduction per bin shared by several lanes (a per-group
       // mask would serialise the groups inside every reduction); each
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
           if (ix - r.ix0 <= 1 && iy - r.iy0 <= 1) continue;  // done above
           const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
           if (oy == 0) continue;
-          hash_add(keys, vals, M, ix * d.ny + iy, (unsigned long long)((long long)ox * oy));
+          hash_add(keys, vals, M, mo + ix * d.ny + iy, (unsigned long long)((long long)ox * oy));
         }
       }
     }
@@ -282,11 +287,40 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+// A nonnegative 64-bit integer as FP32 from its two 32-bit halves (two fast
+// conversions and one FMA instead of the multi-instruction 64-bit one; the
+// result may differ from the correctly rounded one in the last bit).
+__device__ __forceinline__ float u64_to_float(unsigned long long v) {
+  return fmaf((float)(unsigned int)(v >> 32), 4294967296.0f, (float)(unsigned int)v);
+}
+
+// Excess contribution of one bin: bins without fixed cells are counted into
+// (m_over, n_over) and closed after the loop; the others are summed exactly
+// in 128 bits.
+__device__ __forceinline__ void bin_excess(const Dev &d, unsigned long long m, long long f, u128 tA,
+                                           u128 &acc, unsigned long long &m_over,
+                                           unsigned int &n_over) {
+  if (f == 0) {
+    if (m > d.tA_floor) {
+      m_over += m;
+      ++n_over;
+    }
+  } else {
+    // excess * 2^s = m 2^s + t_mant F - t_mant A: exact in unsigned 128
+    // bits (below 2^124, and valid when overlapping fixed cells make F > A)
+    u128 lhs = (u128)m << d.t_shift;
+    lhs += (u128)(unsigned long long)d.t_mant * (u128)(unsigned long long)f;
+    if (lhs > tA) acc += lhs - tA;
+  }
+}
+
 // Per bin: exact overflow excess and rho in FP32; the last block of each copy
 // reduces the excess and, by mode, records the overflow as the iteration's
 // tau (with the stop test), as an evaluation result, or as the reset value
 // tau_{-1} that sets the first gamma.  STRETCH: rho comes from the
-// stretched map (density stretching on); the overflow always from M.
+// stretched map (density stretching on); the overflow always from M.  Two
+// bins per thread and step (G is even): 16-byte loads and paired bf16
+// conversions and stores.
 template <bool STRETCH>
 __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, int mode) {
   __shared__ u128 sm[32];
@@ -296,8 +330,10 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
   const int c = copy0 + blockIdx.y;
   CopyState *cs = d.cs + c;
   if (mode == FIN_ITER && cs->stopped) return;
-  const unsigned long long *M = d.M + (size_t)c * d.G;
-  float *rho = d.rho + (size_t)c * d.G;
+  const ulonglong2 *M2 = reinterpret_cast<const ulonglong2 *>(d.M + (size_t)c * d.Gm);
+  // with fillers their map (following M) joins rho and the concentration
+  const ulonglong2 *Mf2 = d.n_fill ? M2 + (d.G >> 1) : nullptr;
+  const longlong2 *F2 = reinterpret_cast<const longlong2 *>(d.Fmap);
   const u128 tA = ((u128)d.tA_hi << 64) | d.tA_lo;  // t_mant * A_bin
   const float inv_a = (float)(1.0 / d.abin_q);
   const float tf = (float)d.t;
@@ -309,32 +345,35 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
   unsigned long long m_over = 0ull;
   unsigned int n_over = 0u;
   float q2 = 0.f;
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < d.G; b += gridDim.x * blockDim.x) {
-    const long long m = (long long)M[b];
-    const float mq = (float)m * inv_a;
-    q2 = fmaf(mq, mq, q2);
-    const long long f = d.Fmap[b];
-    if (f == 0) {
-      if ((unsigned long long)m > d.tA_floor) {
-        m_over += (unsigned long long)m;
-        ++n_over;
-      }
-    } else {
-      // excess * 2^s = m 2^s + t_mant F - t_mant A: exact in unsigned 128
-      // bits (below 2^124, and valid when overlapping fixed cells make F > A)
-      u128 lhs = (u128)(unsigned long long)m << d.t_shift;
-      lhs += (u128)(unsigned long long)d.t_mant * (u128)(unsigned long long)f;
-      if (lhs > tA) acc += lhs - tA;
+  const int G2 = d.G >> 1;
+  for (int b2 = blockIdx.x * blockDim.x + threadIdx.x; b2 < G2; b2 += gridDim.x * blockDim.x) {
+    const ulonglong2 m = M2[b2];
+    const longlong2 f = F2[b2];
+    float mq0 = u64_to_float(m.x) * inv_a, mq1 = u64_to_float(m.y) * inv_a;
+    if (Mf2) {
+      const ulonglong2 mf = Mf2[b2];
+      mq0 = u64_to_float(m.x + mf.x) * inv_a;
+      mq1 = u64_to_float(m.y + mf.y) * inv_a;
     }
-    float mf = mq;
-    if constexpr (STRETCH) mf = (float)(long long)d.Ms[(size_t)c * d.G + b] * inv_a;
-    const float rv = mf + tf * ((float)f * inv_a);
+    q2 = fmaf(mq0, mq0, q2);
+    q2 = fmaf(mq1, mq1, q2);
+    bin_excess(d, m.x, f.x, tA, acc, m_over, n_over);
+    bin_excess(d, m.y, f.y, tA, acc, m_over, n_over);
+    float mf0 = mq0, mf1 = mq1;
+    if constexpr (STRETCH) {
+      const ulonglong2 ms = reinterpret_cast<const ulonglong2 *>(d.Ms + (size_t)c * d.G)[b2];
+      mf0 = u64_to_float(ms.x) * inv_a;
+      mf1 = u64_to_float(ms.y) * inv_a;
+    }
+    const float rv0 = fmaf(tf, u64_to_float((unsigned long long)f.x) * inv_a, mf0);
+    const float rv1 = fmaf(tf, u64_to_float((unsigned long long)f.y) * inv_a, mf1);
     if (d.tc) {
-      const __nv_bfloat16 hi = __float2bfloat16_rn(rv);
-      d.rho_h[(size_t)c * d.G + b] = hi;
-      d.rho_l[(size_t)c * d.G + b] = __float2bfloat16_rn(rv - __bfloat162float(hi));
+      const __nv_bfloat162 hi = __floats2bfloat162_rn(rv0, rv1);
+      const __nv_bfloat162 lo = __floats2bfloat162_rn(rv0 - __low2float(hi), rv1 - __high2float(hi));
+      reinterpret_cast<__nv_bfloat162 *>(d.rho_h + (size_t)c * d.G)[b2] = hi;
+      reinterpret_cast<__nv_bfloat162 *>(d.rho_l + (size_t)c * d.G)[b2] = lo;
     } else {
-      rho[b] = rv;
+      reinterpret_cast<float2 *>(d.rho + (size_t)c * d.G)[b2] = make_float2(rv0, rv1);
     }
   }
   acc += ((u128)m_over << d.t_shift) - (u128)n_over * tA;
@@ -359,7 +398,7 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
   q2 = block_sum_f<kThreads>(q2, smf);
   if (threadIdx.x == 0) {
     const double tau = ldexp(u128_to_double(v), -d.t_shift) / d.mov_area_q;
-    const double s1 = d.mov_area_q / d.abin_q;
+    const double s1 = (d.mov_area_q + d.fill_area_q) / d.abin_q;
     if (mode != FIN_EVAL) cs->n_eff = q2 > 0.f ? s1 * s1 / (double)q2 : 0.0;
     if (mode == FIN_ITER) {
       cs->tau = tau;

@@ -3,11 +3,22 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/hybro_place.h"
 
 namespace hp {
+
+// NVTX range over a scope (header-only NVTX v3: a no-op unless a profiler
+// such as ncu --nvtx is attached).  The C-ABI entry points mark themselves,
+// so a capture can be filtered to one call or one Hybro round.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kThreads = 256;       // block size of the per-cell / per-bin kernels
 constexpr int kRedThreads = 1024;   // block size of the per-copy reducers
@@ -37,6 +48,8 @@ struct CopyState {
   int n_back_total;  // steps redone since reset
   double n_eff;      // effective number of occupied bins of the last density
                      // pass, (sum M)^2 / sum M^2; 0 before the first pass
+  int n_hist;        // iteration records written since reset
+  int pad_;
 };
 
 // Reduction slots (FP64) per copy: each kernel that reduces writes one value
@@ -53,8 +66,13 @@ enum ScatterMode { SCAT_MERGED = 0, SCAT_TABLE = 1, SCAT_DIRECT = 2 };
 enum FinishMode { FIN_ITER = 0, FIN_EVAL = 1, FIN_RESET = 2 };
 
 struct Dev {
-  // sizes
+  // sizes.  With filler cells the library's cell order is [movable | fillers |
+  // fixed]: n_mov counts the optimiser's cells (movable and fillers), n_real
+  // the design's movable cells, n_fill the fillers, and n_cells all three.
   int K, n_cells, n_mov, n_nets, n_pins, nx, ny, G;
+  int n_real, n_fill;
+  int Gm;                     // per-copy stride of M: G, or 2 G with fillers
+                              // (the fillers' map follows the movable one)
   int F;
   float gq, giq;              // 2^Fg, 2^-Fg: fixed-point scale of the WA gradient sums
   long long XL, YL, BW, BH;   // fixed point
@@ -67,7 +85,8 @@ struct Dev {
   unsigned long long tA_floor;      // floor(t_mant * A_bin / 2^t_shift): a bin
                                     // without fixed cells overflows iff M > this
   double abin_q;              // BW * BH
-  double mov_area_q;
+  double mov_area_q;          // the design's movable area (units of 2^-2F): tau's denominator
+  double fill_area_q;         // the fillers' area (units of 2^-2F)
   double die_xl, die_yl, die_xh, die_yh;
   float fxl, fyl, fxh, fyh;
   float fbw, fbh, fibw, fibh;  // bin width/height and their inverses (FP32)
@@ -109,7 +128,7 @@ struct Dev {
   float *upx, *upy;          // [K][n_mov] u_k of the last accepted step (backtracking only)
   unsigned long long *gacc;  // [K][n_mov] WA gradient sums, two int32 fixed-point
                              // values packed as y * 2^32 + x (see add_pin_grad)
-  unsigned long long *M;     // [K][G]
+  unsigned long long *M;     // [K][Gm]: movable-cell map, then (fillers) the fillers' map
   long long *Fmap;           // [G]
   float *rho;                // [K][G]
   float *T;                  // [K][3][G] transform intermediates
@@ -144,6 +163,10 @@ struct Dev {
 
   // Hybro best solutions
   float2 *bxy;               // [K][n_cells]
+
+  // per-iteration records, a ring of hist_cap per copy (place_get_history)
+  place_iter_record *hist;   // [K][hist_cap]
+  int hist_cap;
 
   // perturbation scratch
   unsigned long long *sort_key;  // [2^ceil(log2 n_cells)]
@@ -233,6 +256,7 @@ void launch_pack_xy(float2 *dst, const float *x, const float *y, int n, cudaStre
 void launch_unpack_xy(float *x, float *y, const float2 *src, int n, cudaStream_t st);
 void launch_density_finish(const Dev &d, int copy0, int ncopy, int mode, cudaStream_t st);
 void launch_spectral(const Dev &d, int copy0, int ncopy, int with_psi, int eval, cudaStream_t st);
+void launch_spectral_tc_stalled(const Dev &d, cudaStream_t st);
 void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_override,
                cudaStream_t st);
 void launch_hpwl64(const Dev &d, int copy0, int ncopy, cudaStream_t st);

@@ -319,6 +319,18 @@ __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
   }
   if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_UPDATE, &flag)) return;
   if (threadIdx.x == 0) {
+    // the iteration's record: its HPWL (WA pass) and overflow at v_k, the
+    // step length taken, and the lambda and gamma the next iteration uses
+    place_iter_record r;
+    r.iter = cs->k;
+    r.backtracks = cs->n_back_total;
+    r.hpwl_wa = cs->hpwl;
+    r.overflow = cs->tau;
+    r.lambda = cs->lam;
+    r.gamma = cs->gamma;
+    r.alpha = cs->alpha;
+    d.hist[(size_t)c * d.hist_cap + (cs->n_hist % d.hist_cap)] = r;
+    cs->n_hist += 1;
     cs->k += 1;
     cs->a = cs->a_next;
     cs->parity ^= 1;

@@ -30,7 +30,7 @@ constexpr unsigned int kNotCand = 0x80000000u;
 
 __global__ void k_keys(Dev d, int op, unsigned long long seed) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.sort_n; i += gridDim.x * blockDim.x) {
-    bool cand = i < d.n_mov && (op == PLACE_SHUFFLE_ALL || d.is_macro[i]);
+    bool cand = i < d.n_real && (op == PLACE_SHUFFLE_ALL || d.is_macro[i]);
     if (cand) {
       d.sort_key[i] = splitmix64_at(seed, (unsigned long long)i);
       d.sort_idx[i] = (unsigned int)i;

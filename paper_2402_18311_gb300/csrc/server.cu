@@ -144,7 +144,10 @@ int finish(place_server *s, Job *j) {
   j->state = J_DONE;
   if (j->pending_children > 0) {
     j->keep = true;  // stays resident for its restarts
-    j->result_bytes = (int64_t)sizeof(float2) * j->nl.n_cells;
+    place_info info;
+    if ((rc = place_get_info(j->h, &info))) return rc;
+    // the handle's cells, filler cells included
+    j->result_bytes = (int64_t)sizeof(float2) * (j->nl.n_cells + info.n_fillers);
     // 8 bytes per cell, outside the budget (so that a saved result can never
     // keep a restart from fitting)
     cudaError_t e = cudaMallocAsync(&j->result_xy, j->result_bytes, j->st);
@@ -257,7 +260,7 @@ int place_server_submit(place_server *s, const place_netlist *nl, const place_di
     p->pending_children++;
   }
   int64_t bytes = 0;
-  int rc = place_estimate_device_bytes(nl, bins, &j->prm, &bytes);
+  int rc = place_estimate_device_bytes(nl, die, bins, &j->prm, &bytes);
   if (rc) {
     delete j;
     return rc;
@@ -273,6 +276,7 @@ int place_server_submit(place_server *s, const place_netlist *nl, const place_di
 }
 
 int place_server_run(place_server *s, double timeout_s, double *makespan_s) {
+  hp::NvtxRange nvtx_("place_server_run");
   if (!s) return sfail(PLACE_EINVAL, "null server");
   s->t0 = std::chrono::steady_clock::now();
   size_t remaining = 0;

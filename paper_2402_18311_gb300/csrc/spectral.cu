@@ -173,6 +173,25 @@ void launch_spectral_tc(const Dev &d, int copy0, int ncopy, int with_psi, int ev
   launch_tc_gemm(mp + 12, g, ncopy, d.tc_bn[3], with_psi ? 1 : d.tc_split[3], st);
 }
 
+// The first GEMM stage of copy 0 with its producer idle: no tile ever lands,
+// so the MMA issuer's and the epilogue's bounded waits give up (about a
+// second each) and the kernel raises d.err instead of hanging.
+void launch_spectral_tc_stalled(const Dev &d, cudaStream_t st) {
+  const CUtensorMap *mp = static_cast<const CUtensorMap *>(d.tcm);
+  TcArgs g = {};
+  g.copy0 = 0;
+  g.cs = d.cs;
+  g.eval = 1;
+  g.err = d.err;
+  g.wu = d.wu; g.wv = d.wv; g.cu = d.cu; g.cv = d.cv;
+  g.ws = d.tc_ws;
+  g.ws_ctr = d.tc_ws_ctr;
+  g.no_load = 1;
+  g.M = d.ny; g.N = d.nx; g.K = d.ny; g.nwhich = 1; g.b_per_copy = 1; g.d_per_copy = 3;
+  g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
+  launch_tc_gemm(mp + 0, g, 1, d.tc_bn[0], d.tc_split[0], st);
+}
+
 void launch_spectral(const Dev &d, int copy0, int ncopy, int with_psi, int eval,
                      cudaStream_t st) {
   if (d.tc)

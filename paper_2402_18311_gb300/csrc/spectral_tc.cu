@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0 && lane == 0) {
     // producer
     int issued = 0;
-    for (int kb = 0; kb < nk; ++kb) {
+    for (int kb = 0; kb < (g.no_load ? 0 : nk); ++kb) {
       const int s = kb % STAGES;
       const int round = kb / STAGES;
       if (kb >= STAGES && !mbar_wait(&empty[s], (round - 1) & 1)) {

@@ -25,6 +25,8 @@ struct TcArgs {
   int *err;                    // set to 1 when a bounded wait gives up
   float *ws;                   // split-K: [tiles][2][128][BN] partial halves
   unsigned int *ws_ctr;        // split-K: arrivals per tile (reset by the second)
+  int no_load;                 // 1: the producer issues no copies (failure-path check:
+                               // the consumers' bounded waits give up)
 };
 
 int tc_smem_bytes(int bn);

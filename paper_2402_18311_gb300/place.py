@@ -62,7 +62,8 @@ class place_params(ct.Structure):
                 ("max_iters", ct.c_int32), ("constant_gamma", ct.c_float), ("dct_mode", ct.c_int32),
                 ("max_backtracks", ct.c_int32), ("stretch", ct.c_int32),
                 ("autotune", ct.c_int32), ("scatter_mode", ct.c_int32), ("gemm_bn", ct.c_int32),
-                ("wa_big_cap", ct.c_int32), ("gemm_split", ct.c_int32)]
+                ("wa_big_cap", ct.c_int32), ("gemm_split", ct.c_int32), ("fillers", ct.c_int32),
+                ("macro_precond", ct.c_float)]
 
 
 class place_info(ct.Structure):
@@ -72,6 +73,7 @@ class place_info(ct.Structure):
                 ("bin_w_q", ct.c_int64), ("bin_h_q", ct.c_int64),
                 ("bin_w", ct.c_double), ("bin_h", ct.c_double), ("device_bytes", ct.c_int64),
                 ("kernels_per_iter", ct.c_int32), ("dct_mode", ct.c_int32),
+                ("n_fillers", ct.c_int32), ("pad", ct.c_int32),
                 ("gemm_bn", ct.c_int32 * 4), ("gemm_split", ct.c_int32 * 4),
                 ("wa_big_cap", ct.c_int32), ("autotuned", ct.c_int32),
                 ("scatter_t1", ct.c_double), ("scatter_t2", ct.c_double),
@@ -83,6 +85,15 @@ class place_state(ct.Structure):
                 ("backtracks", ct.c_int32), ("lambda_", ct.c_double), ("gamma", ct.c_double),
                 ("alpha", ct.c_double), ("a", ct.c_double), ("overflow", ct.c_double),
                 ("hpwl_wa", ct.c_double), ("bins_effective", ct.c_double)]
+
+
+class place_iter_record(ct.Structure):
+    _fields_ = [("iter", ct.c_int32), ("backtracks", ct.c_int32), ("hpwl_wa", ct.c_double),
+                ("overflow", ct.c_double), ("lambda_", ct.c_double), ("gamma", ct.c_double),
+                ("alpha", ct.c_double)]
+
+
+PLACE_HISTORY_CAP = 4096
 
 
 class place_job(ct.Structure):
@@ -128,13 +139,18 @@ _SIGS = {
     "place_get_best_positions": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
     "place_step_timed": (ct.c_int, [_VP, ct.c_int32, _VP]),
     "place_measure_wa_floor": (ct.c_int, [_VP, ct.c_int32, ct.POINTER(ct.c_float)]),
+    "place_test_wait_timeout": (ct.c_int, [_VP]),
     "place_get_hybro_rounds": (ct.c_int, [_VP, ct.c_int32, _VP, _VP, ct.c_int32,
                                           ct.POINTER(ct.c_int32)]),
     "place_overflow_noalloc": (ct.c_int, [_VP, _VP, _VP, _VP, ct.c_int32,
                                           ct.POINTER(place_die), ct.POINTER(place_bins),
                                           ct.c_int32, _VP, _VP, _VP, _VP]),
-    "place_estimate_device_bytes": (ct.c_int, [ct.POINTER(place_netlist), ct.POINTER(place_bins),
-                                                ct.POINTER(place_params), ct.POINTER(ct.c_int64)]),
+    "place_estimate_device_bytes": (ct.c_int, [ct.POINTER(place_netlist), ct.POINTER(place_die),
+                                                ct.POINTER(place_bins), ct.POINTER(place_params),
+                                                ct.POINTER(ct.c_int64)]),
+    "place_get_fillers": (ct.c_int, [_VP, ct.c_int32, _VP, _VP, ct.c_int32, ct.POINTER(ct.c_int32)]),
+    "place_get_history": (ct.c_int, [_VP, ct.c_int32, _VP, ct.c_int32, ct.POINTER(ct.c_int32)]),
+    "place_set_fillers": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
     "place_server_create": (ct.c_int, [ct.c_int64, ct.c_int32, ct.c_int32, ct.POINTER(_VP)]),
     "place_server_submit": (ct.c_int, [_VP, ct.POINTER(place_netlist), ct.POINTER(place_die),
                                        ct.POINTER(place_bins), ct.POINTER(place_params),
@@ -365,10 +381,39 @@ def place_overflow_noalloc(x, y, w, h, n_movable, die, bins, frac_bits, fixed_ma
 def place_estimate_device_bytes(design, params=None):
     nl, keep = _netlist(design)
     b = ct.c_int64()
+    die = place_die(*design.die)
     bins = place_bins(design.nx, design.ny, design.target_density)
     prm = params if params is not None else place_default_params()
-    _check(lib().place_estimate_device_bytes(ct.byref(nl), ct.byref(bins), ct.byref(prm), ct.byref(b)))
+    _check(lib().place_estimate_device_bytes(ct.byref(nl), ct.byref(die), ct.byref(bins),
+                                             ct.byref(prm), ct.byref(b)))
     return b.value
+
+
+def place_test_wait_timeout(h):
+    """The C return code (PLACE_ETIMEOUT expected); does not raise."""
+    return lib().place_test_wait_timeout(h)
+
+
+def place_get_history(h, copy, cap=PLACE_HISTORY_CAP):
+    """Per-iteration records (place_iter_record list) of copy ``copy``."""
+    n = ct.c_int32()
+    arr = (place_iter_record * max(int(cap), 1))()
+    _check(lib().place_get_history(h, int(copy), ct.cast(arr, _VP), int(cap), ct.byref(n)))
+    return [arr[i] for i in range(min(n.value, int(cap)))]
+
+
+def place_set_fillers(h, copy, x, y):
+    return _check(lib().place_set_fillers(h, int(copy), _ptr(x), _ptr(y)))
+
+
+def place_get_fillers(h, copy):
+    """(x, y) float32 arrays of copy ``copy``'s filler corners."""
+    n = ct.c_int32()
+    _check(lib().place_get_fillers(h, int(copy), None, None, 0, ct.byref(n)))
+    x = np.empty(n.value, np.float32)
+    y = np.empty(n.value, np.float32)
+    _check(lib().place_get_fillers(h, int(copy), _ptr(x), _ptr(y), n.value, ct.byref(n)))
+    return x, y
 
 
 class Server:

@@ -46,14 +46,15 @@ def test_default_params_match_the_oracle_reading(L):
     assert p.max_iters == o.max_iters
     assert p.max_backtracks == o.max_backtracks == 0
     assert p.dct_mode == place.PLACE_DCT_AUTO and p.autotune == 1 and p.scatter_mode == -1
-    assert p.gemm_bn == 0 and p.wa_big_cap == 0 and p.gemm_split == 0
+    assert p.gemm_bn == 0 and p.wa_big_cap == 0 and p.gemm_split == 0 and p.fillers == 0
+    assert p.macro_precond == o.macro_precond == 1.0
 
 
 def test_struct_sizes_match_header_layout():
     assert ct.sizeof(place.place_netlist) == 4 * 4 + 10 * 8
-    assert ct.sizeof(place.place_params) == 19 * 4
+    assert ct.sizeof(place.place_params) == 21 * 4
     assert ct.sizeof(place.place_state) == 4 * 4 + 7 * 8
-    assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 2 * 4 + 10 * 4 + 3 * 8
+    assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 4 * 4 + 10 * 4 + 3 * 8
     assert ct.sizeof(place.place_job) == 4 * 4 + 8 + 8 + 8
     assert ct.sizeof(place.place_job_result) == 8 + 4 * 4 + 5 * 8 + 8 + 8
 
@@ -135,7 +136,7 @@ def test_create_rejects_bad_params(L):
         place.place_create(d, place.place_default_params(stretch=2))
     assert ei.value.code == place.PLACE_EINVAL and "stretch" in str(ei.value)
     for field, bad in (("autotune", 2), ("scatter_mode", 3), ("gemm_bn", 96), ("wa_big_cap", 16),
-                       ("gemm_split", 3)):
+                       ("gemm_split", 3), ("fillers", 2), ("macro_precond", 0.0)):
         with pytest.raises(place.PlaceError) as ei:
             place.place_create(d, place.place_default_params(**{field: bad}))
         assert ei.value.code == place.PLACE_EINVAL and field in str(ei.value)
@@ -184,3 +185,9 @@ def test_footprint_estimate_grows_with_the_design(L):
     bs = place.place_estimate_device_bytes(big, place.place_default_params(stretch=1))
     extra = 8 * big.nx * big.ny + 20 * big.n_movable
     assert extra <= bs - b <= extra + 768
+    # fillers: the oracle's count of cells more, and a second map per copy
+    from oracle import placer as opl
+    nf = opl.Placer(big, opl.Params(fillers=True)).nf
+    assert nf > 0
+    bf = place.place_estimate_device_bytes(big, place.place_default_params(fillers=1))
+    assert 8 * big.nx * big.ny + 100 * nf <= bf - b <= 8 * big.nx * big.ny + 200 * nf + 8192

@@ -76,3 +76,37 @@ def test_step_multi_equals_separate_steps():
         for h in multi + solo:
             place.place_destroy(h)
         torch.cuda.synchronize()
+
+
+def test_bounded_waits_give_up_and_the_handle_stays_usable():
+    # The tensor-core GEMM's waits on its shared-memory barriers are bounded.
+    # With its copy producer idle no tile ever lands: the waits give up after
+    # about a second, the kernel frees its tensor memory and raises the error
+    # flag, the call reports PLACE_ETIMEOUT, and the handle then places exactly
+    # like a handle that never saw the failure.
+    d = synth.scaled(2000, 128, seed=1)
+    prm = place.place_default_params(tau_stop=-1.0, max_iters=1000)
+    h = place.place_create(d, prm)
+    ref = place.place_create(d, prm)
+    try:
+        assert place.place_get_info(h).dct_mode == place.PLACE_DCT_BF16X3
+        assert place.place_test_wait_timeout(h) == place.PLACE_ETIMEOUT
+        assert "gave up" in place.place_last_error()
+        place.place_step(h, 30)
+        place.place_step(ref, 30)
+        conv = np.zeros(1, np.int32)
+        place.place_step(h, 0, conv)  # reads the error flag: clear
+        x, y = _positions(h, d.n_cells)
+        rx, ry = _positions(ref, d.n_cells)
+        np.testing.assert_array_equal(x, rx)
+        np.testing.assert_array_equal(y, ry)
+    finally:
+        place.place_destroy(h)
+        place.place_destroy(ref)
+    # a handle on the FP32 path has no such wait to test
+    d = synth.tiny_1k(0)
+    h = place.place_create(d, place.place_default_params())
+    try:
+        assert place.place_test_wait_timeout(h) == place.PLACE_EINVAL
+    finally:
+        place.place_destroy(h)
