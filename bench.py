@@ -357,16 +357,14 @@ def _stage_sample(place, h, n=5):
 
 
 def run_full(args, place, torch, d, stream, tau_stop=0.07, max_iters=4000, chunk=100,
-             samples=(5, 155, 305, 505, 805, 1505, 2505), hpwl_ref=1.0):
+             samples=(5, 155, 305, 505, 805, 1205)):
     """A whole placement of the headline workload from its centred start: to
-    overflow <= tau_stop or max_iters iterations.  Reports the average rate
-    over the run, the rate of each chunk of iterations, and per-stage times
-    sampled at several phases (5 iterations each, included in the run).
-    hpwl_ref = 1: with the default 0.1 the lambda schedule of this 2.1M-cell
-    design stalls near overflow 0.92 (its per-iteration HPWL changes exceed
-    the schedule's reference step dref = hpwl_ref n_nets w_bin)."""
-    prm = place.place_default_params(tau_stop=tau_stop, max_iters=max_iters, dct_mode=args.dct,
-                                     hpwl_ref=hpwl_ref)
+    overflow <= tau_stop or max_iters iterations, with the library's default
+    parameters.  Reports the average rate over the run, the rate of each chunk
+    of iterations, and per-stage times sampled at several phases (5
+    iterations each, included in the run)."""
+    prm = place.place_default_params(tau_stop=tau_stop, max_iters=max_iters, dct_mode=args.dct)
+    hpwl_ref = prm.hpwl_ref
     h = place.place_create(d, prm, stream=stream.cuda_stream)
     conv = np.zeros(1, np.int32)
     chunks, stages = [], {}
@@ -403,7 +401,7 @@ def run_full(args, place, torch, d, stream, tau_stop=0.07, max_iters=4000, chunk
     place.place_destroy(h)
     graph_iters = sum(c["iters"] for c in chunks)
     return {"workload": args.workload, "tau_stop": tau_stop, "max_iters": max_iters,
-            "hpwl_ref": hpwl_ref,
+            "hpwl_ref": round(float(hpwl_ref), 6),
             "iterations": int(st.iter), "converged": bool(st.converged),
             "final_overflow": float(tv[0]), "final_hpwl": float(hp[0]),
             "avg_iters_per_s": 1e3 * graph_iters / total_ms if total_ms > 0 else None,

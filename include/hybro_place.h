@@ -127,7 +127,7 @@ typedef struct place_params {
   float gamma_base;       /* 4 */
   float lambda_eta;       /* 1e-3 */
   float alpha0;           /* 0.05 */
-  float hpwl_ref;         /* 0.1 */
+  float hpwl_ref;         /* 0.3 */
   float mu_base, mu_lo, mu_hi; /* 1.1, 0.95, 1.05 */
   float tau_stop;         /* 0.07 */
   int32_t max_iters;      /* 1000 */
@@ -172,7 +172,9 @@ typedef struct place_info {
   int32_t kernels_per_iter; /* this library's kernel launches in one iteration */
   int32_t dct_mode;       /* the spectral path in use: PLACE_DCT_FP32 or _BF16X3 */
   int32_t n_fillers;      /* filler cells (0 unless params.fillers) */
-  int32_t pad;
+  int32_t bounds_checked; /* 1: the library was built with index checks
+                           * (-DPLACE_DEBUG_BOUNDS): a failed check makes the
+                           * next synchronising call return PLACE_EINTERNAL */
   int32_t gemm_bn[4];     /* tile width of each tensor-core GEMM stage */
   int32_t gemm_split[4];  /* CTAs per tile of each stage (split-K when 2) */
   int32_t wa_big_cap;     /* pins of a big net kept in shared memory */

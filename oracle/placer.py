@@ -108,7 +108,7 @@ class Params:
     gamma_base: float = 4.0
     lambda_eta: float = 1e-3
     alpha0: float = 0.05
-    hpwl_ref: float = 0.1
+    hpwl_ref: float = 0.3
     mu_base: float = 1.1
     mu_lo: float = 0.95
     mu_hi: float = 1.05

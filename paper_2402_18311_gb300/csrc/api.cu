@@ -217,7 +217,7 @@ void place_default_params(place_params *p) {
   p->gamma_base = 4.0f;
   p->lambda_eta = 1e-3f;
   p->alpha0 = 0.05f;
-  p->hpwl_ref = 0.1f;
+  p->hpwl_ref = 0.3f;
   p->mu_base = 1.1f;
   p->mu_lo = 0.95f;
   p->mu_hi = 1.05f;
@@ -319,7 +319,8 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.sel_idx = a.take<unsigned int>(d.sort_n);
   d.px_tmp = a.take<float>(C);
   d.py_tmp = a.take<float>(C);
-  d.err = a.take<int>(2);  // [0]: bounded waits gave up; [1]: a sink for measurement kernels
+  d.err = a.take<int>(4);  // [0]: bounded waits gave up; [1]: a sink for measurement kernels;
+                           // [2], [3]: a failed index check (bounds-checking build)
   if (d.tc) {
     const size_t nx2 = (size_t)d.nx * d.nx, ny2 = (size_t)d.ny * d.ny;
     d.rho_h = a.take<__nv_bfloat16>(K * G);
@@ -457,11 +458,36 @@ float time_iters_cb(void *ctx, int n) {
   return cudaGetLastError() == cudaSuccess ? ms : -1.f;
 }
 
-// Device-side error flag (bounded waits that gave up); call after a sync.
+const char *bound_site_name(int site) {
+  switch (site) {
+    case BS_WA_PIN: return "WA: a net's pin range";
+    case BS_WA_CELL: return "WA: a pin's cell";
+    case BS_HPWL_PIN: return "HPWL: a net's pin range";
+    case BS_HPWL_CELL: return "HPWL: a pin's cell";
+    case BS_GRAD_CELL: return "WA: the cell of a pin gradient";
+    case BS_MAP_BIN: return "density scatter: a map entry";
+    case BS_FIELD_BIN: return "cell gradient: a field entry";
+    case BS_TILE_ROW: return "tensor-core GEMM: an output row or column";
+    case BS_WM_NET: return "WireMask: a net or pin";
+    case BS_WM_CELL: return "WireMask: a cell";
+    case BS_WM_BIN: return "WireMask: a bin";
+    case BS_PERM: return "Shuffle: a permutation entry";
+    default: return "unknown site";
+  }
+}
+
+// Device-side error flags, call after a sync: [0] a bounded wait gave up;
+// [2], [3] the first failed index check and its index (bounds-checking build
+// only).  Reported flags are cleared.
 int check_dev_err(place_t *h) {
-  int e = 0;
-  CK(cudaMemcpy(&e, h->d.err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (e) return fail(PLACE_ETIMEOUT, "a device wait gave up (tensor-core pipeline)");
+  int e[4] = {0, 0, 0, 0};
+  CK(cudaMemcpy(e, h->d.err, sizeof e, cudaMemcpyDeviceToHost));
+  if (e[2]) {
+    CK(cudaMemset(h->d.err + 2, 0, 2 * sizeof(int)));
+    return fail(PLACE_EINTERNAL, "index check failed at %s (site %d), index %d", bound_site_name(e[2]),
+                e[2], e[3]);
+  }
+  if (e[0]) return fail(PLACE_ETIMEOUT, "a device wait gave up (tensor-core pipeline)");
   return PLACE_OK;
 }
 
@@ -994,7 +1020,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   if (ce == cudaSuccess && wa_prepare(d.wa_big_cap)) ce = cudaErrorInvalidValue;
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.cs, 0, sizeof(CopyState) * d.K, h->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.ctr, 0, sizeof(unsigned int) * d.K * C_COUNT, h->stream);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(d.err, 0, 2 * sizeof(int), h->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(d.err, 0, 4 * sizeof(int), h->stream);
   if (ce != cudaSuccess) {
     place_destroy(h);
     return fail(PLACE_ECUDA, "memset: %s", cudaGetErrorString(ce));
@@ -1044,6 +1070,11 @@ int place_get_info(const place_t *h, place_info *o) {
   const Dev &d = h->d;
   o->n_cells = d.n_cells - d.n_fill; o->n_movable = d.n_real; o->n_nets = d.n_nets; o->n_pins = d.n_pins;
   o->n_fillers = d.n_fill;
+#ifdef PLACE_DEBUG_BOUNDS
+  o->bounds_checked = 1;
+#else
+  o->bounds_checked = 0;
+#endif
   o->nx = d.nx; o->ny = d.ny; o->n_copies = d.K;
   o->frac_bits = d.F;
   o->bin_w_q = d.BW; o->bin_h_q = d.BH;
@@ -1319,6 +1350,7 @@ int place_eval_wirelength(place_t *h, int32_t copy, float gamma, double *wl, flo
   double v = 0;
   CK(cudaMemcpyAsync(&v, d.scal + (size_t)copy * S_COUNT + S_WL, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if ((rc = check_dev_err(h))) return rc;
   if (wl) *wl = v;
   return PLACE_OK;
 }
@@ -1408,6 +1440,7 @@ int place_eval_hpwl_overflow(place_t *h, double *hpwl, double *overflow) {
   std::vector<double> sc((size_t)K * S_COUNT);
   CK(cudaMemcpyAsync(sc.data(), d.scal, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (int rc = check_dev_err(h)) return rc;
   for (int c = 0; c < K; ++c) {
     if (hpwl) hpwl[c] = sc[(size_t)c * S_COUNT + S_HP64];
     if (overflow) overflow[c] = sc[(size_t)c * S_COUNT + S_TAU];

@@ -6,6 +6,52 @@
 
 namespace hp {
 
+// ---- bounds-checking build ----------------------------------------------
+// Index sites of the bounds-checking build (HP_IN below); names for the
+// error message are in api.cu (bound_site_name).
+enum BoundSite {
+  BS_NONE = 0,
+  BS_WA_PIN,        // a net's CSR pin range in the WA kernels
+  BS_WA_CELL,       // a pin's cell in the WA kernels
+  BS_HPWL_PIN,      // a net's CSR pin range in the exact HPWL kernels
+  BS_HPWL_CELL,     // a pin's cell there
+  BS_GRAD_CELL,     // the cell a pin's gradient is added to
+  BS_MAP_BIN,       // a density-map entry written by a scatter
+  BS_FIELD_BIN,     // a field entry read by the cell-gradient gather
+  BS_TILE_ROW,      // a GEMM output row or column
+  BS_WM_NET,        // WireMask: a net or pin index
+  BS_WM_CELL,       // WireMask: a cell index
+  BS_WM_BIN,        // WireMask: a bin of the mask or the profile
+  BS_PERM,          // a Shuffle permutation or candidate index
+  BS_NOALLOC_BIN,   // place_overflow_noalloc: a map entry
+  BS_COUNT
+};
+
+// Built with -DPLACE_DEBUG_BOUNDS, HP_IN(err, i, n, site) tests 0 <= i < n for
+// an index about to be used (a CSR offset, a cell, a bin, a tile row); a failed test records the first failing site and its index in
+// err[2] and err[3] (the host reports them as PLACE_EINTERNAL) and yields
+// false, and the caller then skips the access or uses index 0 instead.  In
+// the normal build HP_IN is the constant true and its arguments are not
+// evaluated.  The sites are the BoundSite values.
+#ifdef PLACE_DEBUG_BOUNDS
+static __device__ __noinline__ void bound_fail(int *err, int site, long long i) {
+  if (atomicCAS(err + 2, 0, site) == 0)
+    atomicExch(err + 3, (int)(i < -2147483647LL ? -2147483647LL : (i > 2147483647LL ? 2147483647LL : i)));
+}
+#define HP_IN(err, i, n, site)                                              \
+  (((long long)(i) >= 0 && (long long)(i) < (long long)(n))                 \
+       ? true                                                               \
+       : (::hp::bound_fail((err), (site), (long long)(i)), false))
+#else
+#define HP_IN(err, i, n, site) true
+#endif
+// An index that fails HP_IN is replaced by 0 (a valid element) so that the
+// code after it needs no second branch.
+#define HP_FIX(err, var, n, site) \
+  do {                            \
+    if (!HP_IN(err, var, n, site)) (var) = 0; \
+  } while (0)
+
 __device__ __forceinline__ long long floordiv_ll(long long a, long long b) {
   long long q = a / b;
   if ((a % b != 0) && ((a < 0) != (b < 0))) --q;

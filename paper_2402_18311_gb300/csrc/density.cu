@@ -18,10 +18,12 @@ namespace hp {
 constexpr int kHash = 2048;  // shared-memory aggregation table entries
 
 // Adds one (bin, area) contribution to the block's shared-memory table, or to
-// the global map when its slot is taken (bounded linear probing).
+// the global map when its slot is taken (bounded linear probing).  lim: the
+// map's length (checked in the bounds-checking build only).
 __device__ __forceinline__ void hash_add(int *keys, unsigned long long *vals,
                                          unsigned long long *M, int b,
-                                         unsigned long long a) {
+                                         unsigned long long a, int *err, int lim) {
+  if (!HP_IN(err, b, lim, BS_MAP_BIN)) return;
   unsigned int hsh = ((unsigned int)b * 2654435761u) >> (32 - 11);
 #pragma unroll 1
   for (int probe = 0; probe < 2; ++probe) {
@@ -120,7 +122,9 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
         for (int iy = r.iy0; iy <= r.iy1; ++iy) {
           const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
           if (oy == 0) continue;
-          atomicAdd(&M[mo + ix * d.ny + iy], (unsigned long long)((long long)ox * oy));
+          const int b = mo + ix * d.ny + iy;
+          if (HP_IN(d.err, b, d.Gm, BS_MAP_BIN))
+            atomicAdd(&M[b], (unsigned long long)((long long)ox * oy));
         }
       }
     }
@@ -138,7 +142,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
         for (int iy = r.iy0; iy <= r.iy1; ++iy) {
           const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
           if (oy == 0) continue;
-          hash_add(keys, vals, M, mo + ix * d.ny + iy, (unsigned long long)((long long)ox * oy));
+          hash_add(keys, vals, M, mo + ix * d.ny + iy, (unsigned long long)((long long)ox * oy),
+                   d.err, d.Gm);
         }
       }
     }
@@ -183,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
       if (__popc(groups) > kMaxMergeGroups) {
         // many small groups: one reduction per group would cost more than
         // the few same-address conflicts of adding every term to the table
-        if (b >= 0) hash_add(keys, vals, M, b, a);
+        if (b >= 0) hash_add(keys, vals, M, b, a, d.err, d.Gm);
         continue;
       }
       unsigned long long tot = a;
@@ -198,8 +203,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
       }
       if (lead) {
         if (shared)
-          hash_add(keys, vals, M, b, tot);
-        else
+          hash_add(keys, vals, M, b, tot, d.err, d.Gm);
+        else if (HP_IN(d.err, b, d.Gm, BS_MAP_BIN))
           atomicAdd(&M[b], tot);
       }
     }
@@ -212,7 +217,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
           if (ix - r.ix0 <= 1 && iy - r.iy0 <= 1) continue;  // done above
           const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
           if (oy == 0) continue;
-          hash_add(keys, vals, M, mo + ix * d.ny + iy, (unsigned long long)((long long)ox * oy));
+          hash_add(keys, vals, M, mo + ix * d.ny + iy, (unsigned long long)((long long)ox * oy),
+                   d.err, d.Gm);
         }
       }
     }
@@ -257,7 +263,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_stretch(Dev d, int copy0, 
         if (oy == 0) continue;
         const unsigned long long ov = (unsigned long long)((long long)ox * oy);
         const unsigned long long t = (ov >> 31) * R + (((ov & 0x7fffffffull) * R) >> 31);
-        if (t) hash_add(keys, vals, M, ix * d.ny + iy, t);
+        if (t) hash_add(keys, vals, M, ix * d.ny + iy, t, d.err, d.G);
       }
     }
   }
@@ -281,7 +287,9 @@ __global__ void __launch_bounds__(kThreads)
       for (int iy = r.iy0; iy <= r.iy1; ++iy) {
         const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
         if (oy == 0) continue;
-        atomicAdd(&out[ix * d.ny + iy], (unsigned long long)((long long)ox * oy));
+        const int b = ix * d.ny + iy;
+        if (HP_IN(d.err, b, d.G, BS_MAP_BIN))
+          atomicAdd(&out[b], (unsigned long long)((long long)ox * oy));
       }
     }
   }

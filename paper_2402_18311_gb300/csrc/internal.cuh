@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "../../include/hybro_place.h"
+#include "common.cuh"
 
 namespace hp {
 
@@ -159,7 +160,8 @@ struct Dev {
   float *tc_ws;                     // split-K partial halves (stages with tc_split_ok)
   unsigned int *tc_ws_ctr;          // split-K arrivals per tile
   int tc_ws_tiles;                  // tiles the split-K workspace holds
-  int *err;                         // [2]: device error flag (bounded waits), measurement sink
+  int *err;                         // [4]: bounded waits gave up; measurement sink; failed
+                                    // index check (site, index) of the bounds-checking build
 
   // Hybro best solutions
   float2 *bxy;               // [K][n_cells]
@@ -214,6 +216,7 @@ struct WmDev {
 __device__ __forceinline__ void add_pin_grad(const Dev &d, unsigned long long *acc, int cell,
                                              float gx, float gy) {
   if (cell >= d.n_mov) return;  // fixed cells take no gradient
+  if (!HP_IN(d.err, cell, d.n_mov, BS_GRAD_CELL)) return;
   const long long qx = __float2int_rn(gx * d.gq), qy = __float2int_rn(gy * d.gq);
   atomicAdd(acc + cell, (unsigned long long)(qy * 4294967296LL + qx));
 }

@@ -46,6 +46,7 @@ struct NoAllocScratch {
   unsigned long long area_lo, area_hi;  // exact sum of W H over the cells (128 bits)
   unsigned int counter;                 // last-block counter of the finish pass
   int bad;                              // a cell size outside [1, 2^31) units
+  int dbg[4];                           // failed index check (bounds-checking build)
 };
 
 static __device__ __align__(256) NoAllocScratch g_scratch;
@@ -101,7 +102,9 @@ __global__ void __launch_bounds__(kNaThreads)
       for (int iy = r.iy0; iy <= r.iy1; ++iy) {
         long long oy = overlap1(r.Y, r.H, g.YL + (long long)iy * g.BH, g.BH);
         if (oy == 0) continue;
-        atomicAdd(&s->map[(size_t)ix * g.ny + iy], (unsigned long long)(ox * oy));
+        const long long b = (long long)ix * g.ny + iy;
+        if (!HP_IN(s->dbg, b, (long long)g.nx * g.ny, BS_NOALLOC_BIN)) continue;
+        atomicAdd(&s->map[b], (unsigned long long)(ox * oy));
       }
     }
   }
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(kNaThreads)
     // beyond 2^62 (or with a rejected cell) the map itself is not trusted
     const unsigned long long lo = *(volatile unsigned long long *)&s->area_lo;
     const unsigned long long hi = *(volatile unsigned long long *)&s->area_hi;
-    const int bad = *(volatile int *)&s->bad;
+    const int bad = *(volatile int *)&s->bad || *(volatile int *)&s->dbg[2];
     if (bad || hi != 0 || lo >= (1ull << 62)) {
       *overflow = __longlong_as_double(0x7ff8000000000000LL);  // quiet NaN
     } else {

@@ -165,6 +165,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_cell_grad(Dev d, int copy0, int
       const float ox1 = ix0 + 1 < d.nx ? fmaxf(rx1 - d.fbw, 0.f) : 0.f;
       const float oy1 = iy0 + 1 < d.ny ? fmaxf(ry1 - d.fbh, 0.f) : 0.f;
       const size_t b0 = (size_t)ix0 * d.ny + iy0;
+      if (!HP_IN(d.err, (long long)b0 + (ox1 > 0.f ? d.ny : 0) + (oy1 > 0.f ? 1 : 0), d.G,
+                 BS_FIELD_BIN))
+        continue;
       const float e00x = ex[b0], e00y = ey[b0];
       const float e01x = oy1 > 0.f ? ex[b0 + 1] : 0.f, e01y = oy1 > 0.f ? ey[b0 + 1] : 0.f;
       const float e10x = ox1 > 0.f ? ex[b0 + d.ny] : 0.f, e10y = ox1 > 0.f ? ey[b0 + d.ny] : 0.f;
@@ -181,6 +184,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_cell_grad(Dev d, int copy0, int
           const float oy = fminf(ry1, (float)(ky + 1) * d.fbh) - fmaxf(ry, (float)ky * d.fbh);
           if (!(oy > 0.f)) continue;
           const float a = ox * oy;
+          if (!HP_IN(d.err, (long long)ix * d.ny + iy, d.G, BS_FIELD_BIN)) continue;
           dx = fmaf(-a, exr[iy], dx);
           dy = fmaf(-a, eyr[iy], dy);
         }

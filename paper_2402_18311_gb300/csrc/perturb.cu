@@ -81,8 +81,10 @@ __global__ void k_bitonic_u32(unsigned int *v, int n, int j, int k) {
 __global__ void k_shuffle_compute(Dev d, int copy, int k) {
   const float2 *xy = d.xy + (size_t)copy * d.n_cells;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
-    const int r = (int)d.sort_idx[j];  // receiver (key order)
-    const int s = (int)d.sel_idx[j];   // donor (index order)
+    int r = (int)d.sort_idx[j];  // receiver (key order)
+    int s = (int)d.sel_idx[j];   // donor (index order)
+    HP_FIX(d.err, r, d.n_real, BS_PERM);
+    HP_FIX(d.err, s, d.n_real, BS_PERM);
     const float2 ps = xy[s];
     double cx = (double)ps.x + 0.5 * (double)d.w[s];
     double cy = (double)ps.y + 0.5 * (double)d.h[s];
@@ -99,6 +101,7 @@ __global__ void k_shuffle_apply(Dev d, int copy, int k) {
   float2 *xy = d.xy + (size_t)copy * d.n_cells;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
     const int r = (int)d.sort_idx[j];
+    if (!HP_IN(d.err, r, d.n_real, BS_PERM)) continue;
     xy[r] = make_float2(d.px_tmp[j], d.py_tmp[j]);
   }
 }

@@ -293,6 +293,12 @@ __global__ void __launch_bounds__(128, 1)
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
   float *ws_row = nullptr, *ws_other = nullptr;
   bool run = have;
+#ifdef PLACE_DEBUG_BOUNDS
+  // the output rows and columns of this warp (run stays warp-uniform: the
+  // TMEM loads below are warp-collective)
+  run = run && __all_sync(0xffffffffu, HP_IN(g.err, m, g.M, BS_TILE_ROW) &&
+                                           HP_IN(g.err, n0 + BN - 1, g.N, BS_TILE_ROW));
+#endif
   if constexpr (SPLIT == 2) {
     // publish this half, then the second of the pair to arrive finishes
     const int tile = (z * (int)gridDim.y / SPLIT + mt) * (int)gridDim.x + blockIdx.x;

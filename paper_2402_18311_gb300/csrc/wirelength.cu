@@ -79,12 +79,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int
     const int p0 = d.net_ptr[e], p1 = d.net_ptr[e + 1];
     const int deg = p1 - p0;
     if (deg <= 0) continue;
+    if (!HP_IN(d.err, p0, d.n_pins, BS_WA_PIN) || !HP_IN(d.err, p1, d.n_pins + 1, BS_WA_PIN) ||
+        !HP_IN(d.err, deg, D + 1, BS_WA_PIN))
+      continue;
     int cell[D];
     float2 off[D], pos[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       if (k < deg) {
         cell[k] = d.pin_cell[p0 + k];
+        HP_FIX(d.err, cell[k], d.n_cells, BS_WA_CELL);
         off[k] = d.pin_off[p0 + k];
       }
     }
@@ -171,6 +175,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_wa_group(Dev d, int copy0, i
     if (valid) {
       p0 = d.net_ptr[e];
       p1 = d.net_ptr[e + 1];
+      if (!HP_IN(d.err, p0, d.n_pins + 1, BS_WA_PIN) || !HP_IN(d.err, p1, d.n_pins + 1, BS_WA_PIN) ||
+          !HP_IN(d.err, p1 - p0, G * PPL + 1, BS_WA_PIN))
+        p0 = p1 = 0;
     }
     const float wn = (valid && d.net_w) ? d.net_w[e] : 1.0f;
     // all of the net's loads in flight together; coordinates relative to the
@@ -182,12 +189,15 @@ __global__ void __launch_bounds__(kThreads, MINB) k_wa_group(Dev d, int copy0, i
     for (int k = 0; k < PPL; ++k) {
       const int j = p0 + lane + k * G;
       cl[k] = j < p1 ? d.pin_cell[j] : -1;
+      if (cl[k] >= 0) HP_FIX(d.err, cl[k], d.n_cells, BS_WA_CELL);
       of[k] = j < p1 ? d.pin_off[j] : make_float2(0.f, 0.f);
     }
     float2 r0 = make_float2(0.f, 0.f), o0 = make_float2(0.f, 0.f);
     if (p1 > p0) {
       o0 = d.pin_off[p0];
-      r0 = xy[d.pin_cell[p0]];
+      int c0 = d.pin_cell[p0];
+      HP_FIX(d.err, c0, d.n_cells, BS_WA_CELL);
+      r0 = xy[c0];
     }
 #pragma unroll
     for (int k = 0; k < PPL; ++k) v[k] = cl[k] >= 0 ? xy[cl[k]] : make_float2(0.f, 0.f);
@@ -296,15 +306,23 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
   double hp_acc = 0.0, wl_acc = 0.0;
   for (int e = d.cls_begin[cls] + blockIdx.x; e < d.cls_begin[cls + 1]; e += gridDim.x) {
     const int p0 = d.net_ptr[e], p1 = d.net_ptr[e + 1];
+    // (every thread of the block tests the same net, so a skip is uniform)
+    if (!HP_IN(d.err, p0, d.n_pins, BS_WA_PIN) || !HP_IN(d.err, p1, d.n_pins + 1, BS_WA_PIN) ||
+        !HP_IN(d.err, p1 - p0, 1 << 30, BS_WA_PIN))
+      continue;
     const float wn = d.net_w ? d.net_w[e] : 1.0f;
     const float2 o0 = d.pin_off[p0];
-    const float2 v0 = xy[d.pin_cell[p0]];
+    int c0 = d.pin_cell[p0];
+    HP_FIX(d.err, c0, d.n_cells, BS_WA_CELL);
+    const float2 v0 = xy[c0];
     const float rx = v0.x, ry = v0.y, rdx = o0.x, rdy = o0.y;
     float ext[4] = {-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};  // max x, -min x, max y, -min y
 #pragma unroll 4
     for (int j = p0 + threadIdx.x; j < p1; j += kBigNet) {
       const float2 o = d.pin_off[j];
-      const float2 v = xy[d.pin_cell[j]];
+      int cj = d.pin_cell[j];
+      HP_FIX(d.err, cj, d.n_cells, BS_WA_CELL);
+      const float2 v = xy[cj];
       const float px = (v.x - rx) + (o.x - rdx), py = (v.y - ry) + (o.y - rdy);
       if (j - p0 < cap) { spx[j - p0] = px; spy[j - p0] = py; }
       ext[0] = fmaxf(ext[0], px); ext[1] = fmaxf(ext[1], -px);
@@ -320,7 +338,9 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
         px = spx[j - p0]; py = spy[j - p0];
       } else {
         const float2 o = d.pin_off[j];
-        const float2 v = xy[d.pin_cell[j]];
+        int cj = d.pin_cell[j];
+        HP_FIX(d.err, cj, d.n_cells, BS_WA_CELL);
+        const float2 v = xy[cj];
         px = (v.x - rx) + (o.x - rdx); py = (v.y - ry) + (o.y - rdy);
       }
       float a = __expf((px - mxx) * ig), b = __expf((mnx - px) * ig);
@@ -334,7 +354,8 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
 #pragma unroll 4
     for (int j = p0 + threadIdx.x; j < p1; j += kBigNet) {
       float px, py;
-      const int cj = d.pin_cell[j];
+      int cj = d.pin_cell[j];
+      HP_FIX(d.err, cj, d.n_cells, BS_WA_CELL);
       if (j - p0 < cap) {
         px = spx[j - p0]; py = spy[j - p0];
       } else {
@@ -378,11 +399,15 @@ __global__ void __launch_bounds__(kThreads) k_hpwl64(Dev d, int copy0, int e_beg
     if (e < e_end) {
       p0 = d.net_ptr[e];
       p1 = d.net_ptr[e + 1];
+      if (!HP_IN(d.err, p0, d.n_pins + 1, BS_HPWL_PIN) || !HP_IN(d.err, p1, d.n_pins + 1, BS_HPWL_PIN))
+        p0 = p1 = 0;
     }
     double mxx = -1e300, mnx = 1e300, mxy = -1e300, mny = 1e300;
     for (int j = p0 + lane; j < p1; j += G) {
       const float2 o = d.pin_off[j];
-      const float2 v = xy[d.pin_cell[j]];
+      int cj = d.pin_cell[j];
+      HP_FIX(d.err, cj, d.n_cells, BS_HPWL_CELL);
+      const float2 v = xy[cj];
       double px = (double)v.x + (double)o.x, py = (double)v.y + (double)o.y;
       mxx = fmax(mxx, px); mnx = fmin(mnx, px);
       mxy = fmax(mxy, py); mny = fmin(mny, py);
@@ -476,11 +501,15 @@ __global__ void __launch_bounds__(kThreads) k_hpwl64_big(Dev d, int copy0, int e
   const float2 *xy = d.xy + (size_t)c * d.n_cells;
   double acc = 0.0;
   for (int e = e_begin + blockIdx.x; e < e_end; e += gridDim.x) {
-    const int p0 = d.net_ptr[e], p1 = d.net_ptr[e + 1];
+    int p0 = d.net_ptr[e], p1 = d.net_ptr[e + 1];
+    if (!HP_IN(d.err, p0, d.n_pins + 1, BS_HPWL_PIN) || !HP_IN(d.err, p1, d.n_pins + 1, BS_HPWL_PIN))
+      p0 = p1 = 0;
     double v[4] = {-1e300, -1e300, -1e300, -1e300};  // max x, -min x, max y, -min y
     for (int j = p0 + threadIdx.x; j < p1; j += kThreads) {
       const float2 o = d.pin_off[j];
-      const float2 q = xy[d.pin_cell[j]];
+      int cj = d.pin_cell[j];
+      HP_FIX(d.err, cj, d.n_cells, BS_HPWL_CELL);
+      const float2 q = xy[cj];
       const double px = (double)q.x + (double)o.x, py = (double)q.y + (double)o.y;
       v[0] = fmax(v[0], px); v[1] = fmax(v[1], -px);
       v[2] = fmax(v[2], py); v[3] = fmax(v[3], -py);

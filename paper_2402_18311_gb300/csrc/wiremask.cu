@@ -132,11 +132,15 @@ __global__ void __launch_bounds__(kWmThreads) k_wm_nets(Dev d, WmDev w, int t, i
   const int s = blockIdx.x * (kWmThreads / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (s >= nn) return;  // the whole warp leaves together
-  const int e = w.mnet[w.mptr[t] + s];
+  if (!HP_IN(d.err, s, w.max_nets, BS_WM_NET)) return;
+  int e = w.mnet[w.mptr[t] + s];
+  HP_FIX(d.err, e, d.n_nets, BS_WM_NET);
   double v[8] = {INFINITY, -INFINITY, INFINITY, -INFINITY,
                  INFINITY, -INFINITY, INFINITY, -INFINITY};
   for (int j = d.net_ptr[e] + lane; j < d.net_ptr[e + 1]; j += 32) {
-    const int cj = d.pin_cell[j];
+    if (!HP_IN(d.err, j, d.n_pins, BS_WM_NET)) break;
+    int cj = d.pin_cell[j];
+    HP_FIX(d.err, cj, d.n_cells, BS_WM_CELL);
     const float2 o = d.pin_off[j];
     if (cj == m) {
       v[4] = fmin(v[4], (double)o.x); v[5] = fmax(v[5], (double)o.x);
@@ -197,7 +201,8 @@ __global__ void __launch_bounds__(kWmThreads) k_wm_select(Dev d, WmDev w, int t,
   __shared__ int4 so[kWmThreads];  // blocked columns [x, y], rows [z, w]
   const int c = copy0 + blockIdx.y;
   const float2 *xy = d.xy + (size_t)c * d.n_cells;
-  const int m = w.order[t];
+  int m = w.order[t];
+  HP_FIX(d.err, m, d.n_cells, BS_WM_CELL);
   const double mw = (double)d.w[m], mh = (double)d.h[m];
   const float2 pm = xy[m];
   const int nob = w.n_fixed + t;
@@ -206,7 +211,8 @@ __global__ void __launch_bounds__(kWmThreads) k_wm_select(Dev d, WmDev w, int t,
   const double *fx = w.fx + (size_t)blockIdx.y * d.nx, *fy = w.fy + (size_t)blockIdx.y * d.ny;
   auto stage = [&](int o0) {
     if (o0 + (int)threadIdx.x < nob) {
-      const int oc = w.obst[o0 + threadIdx.x];
+      int oc = w.obst[o0 + threadIdx.x];
+      HP_FIX(d.err, oc, d.n_cells, BS_WM_CELL);
       const float2 p = xy[oc];
       const int2 rx = blocked_range(d.die_xl, bx, d.nx, mw, (double)p.x,
                                     __dadd_rn((double)p.x, (double)d.w[oc]));
@@ -270,9 +276,10 @@ __global__ void __launch_bounds__(kWmThreads) k_wm_apply(Dev d, WmDev w, int t, 
     if (better(v, best)) best = v;
   }
   best = block_best(best);
-  if (threadIdx.x == 0 && best.idx >= 0) {
+  if (threadIdx.x == 0 && best.idx >= 0 && HP_IN(d.err, best.idx, d.nx * d.ny, BS_WM_BIN)) {
     const int j = best.idx / d.nx, i = best.idx - j * d.nx;
-    const int m = w.order[t];
+    int m = w.order[t];
+    HP_FIX(d.err, m, d.n_cells, BS_WM_CELL);
     d.xy[(size_t)c * d.n_cells + m] =
         make_float2((float)wm_corner(d.die_xl, d.die_xh, d.nx, i),
                     (float)wm_corner(d.die_yl, d.die_yh, d.ny, j));

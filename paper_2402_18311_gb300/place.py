@@ -15,6 +15,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhybro_place.so")
+# the same library built with index checks in its kernels (-DPLACE_DEBUG_BOUNDS);
+# loaded instead of LIB_PATH when HYBRO_PLACE_BOUNDS=1 is set before the first call
+BOUNDS_LIB_PATH = os.path.join(HERE, "libhybro_place_bounds.so")
 
 PLACE_OK = 0
 PLACE_EINVAL = -1
@@ -73,7 +76,7 @@ class place_info(ct.Structure):
                 ("bin_w_q", ct.c_int64), ("bin_h_q", ct.c_int64),
                 ("bin_w", ct.c_double), ("bin_h", ct.c_double), ("device_bytes", ct.c_int64),
                 ("kernels_per_iter", ct.c_int32), ("dct_mode", ct.c_int32),
-                ("n_fillers", ct.c_int32), ("pad", ct.c_int32),
+                ("n_fillers", ct.c_int32), ("bounds_checked", ct.c_int32),
                 ("gemm_bn", ct.c_int32 * 4), ("gemm_split", ct.c_int32 * 4),
                 ("wa_big_cap", ct.c_int32), ("autotuned", ct.c_int32),
                 ("scatter_t1", ct.c_double), ("scatter_t2", ct.c_double),
@@ -165,14 +168,21 @@ _SIGS = {
 _lib = None
 
 
+def lib_path():
+    """The library this process loads: the bounds-checking build when the
+    environment variable HYBRO_PLACE_BOUNDS is 1, else the normal one."""
+    return BOUNDS_LIB_PATH if os.environ.get("HYBRO_PLACE_BOUNDS") == "1" else LIB_PATH
+
+
 def lib():
     """Load the library (once).  Raises if it has not been built."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
                                "paper_2402_18311_gb300.build.build()")
-        L = ct.CDLL(LIB_PATH)
+        L = ct.CDLL(path)
         for name, (res, args) in _SIGS.items():
             f = getattr(L, name)
             f.restype = res

@@ -36,6 +36,17 @@ def test_every_declared_symbol_is_exported(L):
     assert sorted(place.exported_symbols()) == names
 
 
+def test_bounds_checked_build_exports_every_declared_symbol(L):
+    # the -DPLACE_DEBUG_BOUNDS twin of the library (loaded by the binding when
+    # HYBRO_PLACE_BOUNDS=1) exports the same entry points
+    if not os.path.exists(place.BOUNDS_LIB_PATH):
+        from paper_2402_18311_gb300 import build
+        build.build(variant="bounds")
+    Lb = ct.CDLL(place.BOUNDS_LIB_PATH)
+    for n in declared():
+        assert hasattr(Lb, n), n
+
+
 def test_default_params_match_the_oracle_reading(L):
     p = place.place_default_params()
     o = opl.Params()
