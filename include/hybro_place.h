@@ -160,6 +160,10 @@ typedef struct place_params {
                              with k = macro_precond for macros, 1 otherwise;
                              above 1 a macro moves in shorter steps than the
                              standard cells around it */
+  int32_t wa_streams;     /* 0 (default): automatic; 1, 2 or 3: the WA degree
+                             classes run as a chain on one graph branch, or
+                             split over two or three branches that run side by
+                             side (integer gradient sums: the same bits) */
 } place_params;
 
 /* Read-only facts about a handle. */
@@ -181,6 +185,8 @@ typedef struct place_info {
   int32_t autotuned;      /* 1: the choices here came from timing (or its cache) */
   double scatter_t1, scatter_t2; /* effective-bin thresholds of the scatter's ways */
   double autotune_ms;     /* host time the tuning took at create (0 on a cache hit) */
+  int32_t wa_streams;     /* graph branches the WA classes run on (1..3) */
+  int32_t reserved;
 } place_info;
 
 /* Optimiser scalars of one copy after its last iteration. */
@@ -315,6 +321,25 @@ int place_get_state(place_t *h, int32_t copy, place_state *out);
  * Synchronises. */
 #define PLACE_HISTORY_CAP 4096
 int place_get_history(place_t *h, int32_t copy, place_iter_record *out, int32_t cap, int32_t *n);
+
+/* Checkpoint of one copy's optimiser state, for pausing a placement and
+ * resuming it on this handle or on a new handle of the same design, grid and
+ * parameters: the positions u and v (fillers included), the previous
+ * reference point, both gradient buffers and the raw gradients, the pending
+ * WA sums, the backtracking arrays when on, the scalars (lambda, step length,
+ * momentum, gamma, overflow, iteration count, stop flags) and the history
+ * ring.  A placement resumed from it continues bit for bit as if it had not
+ * been interrupted (the kernels are deterministic).
+ * place_checkpoint_bytes: the size of one copy's checkpoint.
+ * place_checkpoint_save: writes it to the host buffer buf of cap bytes
+ *   (PLACE_EINVAL when smaller).
+ * place_checkpoint_load: replaces copy `copy`'s state; PLACE_EINVAL when the
+ *   buffer is short or its header (sizes, grid, fixed-point resolution, the
+ *   lambda schedule's reference step, the knobs that add arrays) differs from
+ *   this handle's.  Both synchronise. */
+int place_checkpoint_bytes(const place_t *h, int64_t *bytes);
+int place_checkpoint_save(place_t *h, int32_t copy, void *buf, int64_t cap);
+int place_checkpoint_load(place_t *h, int32_t copy, const void *buf, int64_t bytes);
 
 /* ---- stage-level evaluation at the current positions of one copy --------
  * These run the same kernels as place_step on the copy's reference point
@@ -478,11 +503,19 @@ typedef struct place_job {
   uint64_t seed;     /* restart: SplitMix64 seed */
   int64_t parent;    /* restart: id of an earlier job of the same design */
   double arrival_s;  /* not admitted before this many seconds into place_server_run */
+  double max_seconds; /* > 0: wall-clock budget from admission; the job is stopped at the
+                       * first chunk boundary past it (status PLACE_JOB_EXPIRED); 0: none */
 } place_job;
+
+/* place_job_result.status */
+#define PLACE_JOB_FINISHED 0  /* stopped by its stop test or max_iters */
+#define PLACE_JOB_CANCELLED 1 /* place_server_cancel (or its parent's); a job cancelled
+                               * before admission has no positions: NaN HPWL, hash 0 */
+#define PLACE_JOB_EXPIRED 2   /* ran past max_seconds */
 
 typedef struct place_job_result {
   int64_t id;
-  int32_t kind, iterations, converged, pad;
+  int32_t kind, iterations, converged, status; /* status: PLACE_JOB_* */
   double arrival_s, admit_s, done_s; /* seconds since place_server_run started */
   double hpwl, overflow;             /* exact FP64 HPWL (Eq. 1) and overflow at the end */
   int64_t device_bytes;
@@ -508,6 +541,12 @@ int place_server_submit(place_server *s, const place_netlist *nl, const place_di
 /* Run until every queued job has finished (or timeout_s > 0 elapses:
  * PLACE_ETIMEOUT).  *makespan_s (nullable) receives the wall time. */
 int place_server_run(place_server *s, double timeout_s, double *makespan_s);
+
+/* Cancel job `id`: a queued job is never admitted (nor are its restarts); an
+ * active one stops at its next chunk boundary, its in-flight kernels left to
+ * finish.  May be called from another thread while place_server_run runs (it
+ * only sets a flag that the run loop reads). */
+int place_server_cancel(place_server *s, int64_t id);
 
 /* Results of the finished jobs in submission order; *n receives their count
  * (out may be NULL to query it). */

@@ -182,8 +182,10 @@ struct place_t {
   Dev d{};
   cudaStream_t stream = nullptr;     // caller's stream
   cudaStream_t cap = nullptr;        // private stream used for graph capture
-  cudaStream_t cap2 = nullptr;       // second captured stream: wirelength branch
+  cudaStream_t cap2 = nullptr;       // captured streams of the wirelength branches
+  cudaStream_t cap3 = nullptr, cap4 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_join2 = nullptr, ev_join3 = nullptr;
   void *mem = nullptr;
   size_t mem_bytes = 0;
   cudaGraph_t graph = nullptr;
@@ -232,6 +234,7 @@ void place_default_params(place_params *p) {
   p->gemm_bn = 0;
   p->wa_big_cap = 0;
   p->gemm_split = 0;
+  p->wa_streams = 0;
   p->fillers = 0;
   p->macro_precond = 1.0f;
 }
@@ -243,8 +246,12 @@ int place_destroy(place_t *h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->cap2) cudaStreamDestroy(h->cap2);
+  if (h->cap3) cudaStreamDestroy(h->cap3);
+  if (h->cap4) cudaStreamDestroy(h->cap4);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_join2) cudaEventDestroy(h->ev_join2);
+  if (h->ev_join3) cudaEventDestroy(h->ev_join3);
   if (h->mem) cudaFreeAsync(h->mem, h->stream);  // stream-ordered: no device-wide sync
   for (auto &g : h->wm_graphs) cudaGraphExecDestroy(g.second);
   if (h->wm_mem) cudaFreeAsync(h->wm_mem, h->stream);
@@ -505,21 +512,22 @@ int enqueue_reset(place_t *h, int c0, int n) {
 
 // One Nesterov iteration of every copy (the graph body).  The wirelength
 // kernels depend only on the positions and on gamma_k (from the previous
-// iteration's overflow), so they run on a second stream beside the density
-// scatter and the tensor-core Poisson solve and join before the per-cell
-// gradient.
-void enqueue_iteration(const Dev &d, cudaStream_t st, cudaStream_t st2, cudaEvent_t fork,
-                       cudaEvent_t join) {
+// iteration's overflow), so they run on their own branches (d.wa_streams of
+// them) beside the density scatter and the tensor-core Poisson solve, and
+// join before the per-cell gradient.
+void enqueue_iteration(const Dev &d, cudaStream_t st, const cudaStream_t *wst, cudaEvent_t fork,
+                       const cudaEvent_t *join) {
   const int K = d.K;
+  const int nb = std::max(1, std::min(d.wa_streams, kMaxWaStreams));
   cudaEventRecord(fork, st);
-  cudaStreamWaitEvent(st2, fork, 0);
-  launch_wa(d, 0, K, 0, nullptr, st2);
-  cudaEventRecord(join, st2);
+  for (int b = 0; b < nb; ++b) cudaStreamWaitEvent(wst[b], fork, 0);
+  launch_wa_branches(d, 0, K, wst);
+  for (int b = 0; b < nb; ++b) cudaEventRecord(join[b], wst[b]);
   cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.Gm * K, st);
   launch_scatter(d, 0, K, 0, st);
   launch_density_finish(d, 0, K, FIN_ITER, st);
   launch_spectral(d, 0, K, 0, 0, st);
-  cudaStreamWaitEvent(st, join, 0);
+  for (int b = 0; b < nb; ++b) cudaStreamWaitEvent(st, join[b], 0);
   launch_cell_grad(d, 0, K, 0, st);
   launch_precond0(d, 0, K, st);
   launch_update(d, 0, K, st);
@@ -528,7 +536,9 @@ void enqueue_iteration(const Dev &d, cudaStream_t st, cudaStream_t st2, cudaEven
 int ensure_graph(place_t *h) {
   if (h->exec) return PLACE_OK;
   CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-  enqueue_iteration(h->d, h->cap, h->cap2, h->ev_fork, h->ev_join);
+  const cudaStream_t wst[kMaxWaStreams] = {h->cap2, h->cap3, h->cap4};
+  const cudaEvent_t joins[kMaxWaStreams] = {h->ev_join, h->ev_join2, h->ev_join3};
+  enqueue_iteration(h->d, h->cap, wst, h->ev_fork, joins);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap, &g);
   if (e != cudaSuccess) return fail(PLACE_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
@@ -659,6 +669,8 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   if (prm.wa_big_cap != 0 && (prm.wa_big_cap < 32 || prm.wa_big_cap > 6144))
     return fail(PLACE_EINVAL, "wa_big_cap must be 0 or in [32, 6144]");
   if (prm.gemm_split < 0 || prm.gemm_split > 2) return fail(PLACE_EINVAL, "gemm_split must be 0, 1 or 2");
+  if (prm.wa_streams < 0 || prm.wa_streams > kMaxWaStreams)
+    return fail(PLACE_EINVAL, "wa_streams must be 0, 1, 2 or 3");
   if (prm.fillers != 0 && prm.fillers != 1) return fail(PLACE_EINVAL, "fillers must be 0 or 1");
   if (!(prm.macro_precond > 0.f) || !std::isfinite(prm.macro_precond))
     return fail(PLACE_EINVAL, "macro_precond must be positive and finite");
@@ -865,6 +877,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   int max_deg = 0;
   for (int e = 0; e < E; ++e) max_deg = std::max(max_deg, net_ptr[e + 1] - net_ptr[e]);
   d.wa_big_cap = prm.wa_big_cap ? prm.wa_big_cap : std::min(std::max(max_deg, 1), kBigCapMax);
+  d.wa_streams = prm.wa_streams ? prm.wa_streams : 1;  // fixed rule: one chain
   d.scat_t1 = kScatterMergedBelow;
   d.scat_t2 = kScatterTableBelow;
   d.scat_force = prm.scatter_mode;
@@ -1007,8 +1020,12 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   }
   cudaError_t ce = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
   if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&h->cap2, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&h->cap3, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&h->cap4, cudaStreamNonBlocking);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&h->ev_join3, cudaEventDisableTiming);
   if (ce != cudaSuccess) {
     place_destroy(h);
     return fail(PLACE_ECUDA, "stream create: %s", cudaGetErrorString(ce));
@@ -1096,6 +1113,8 @@ int place_get_info(const place_t *h, place_info *o) {
   o->scatter_t1 = d.scat_t1;
   o->scatter_t2 = d.scat_t2;
   o->autotune_ms = h->autotune_ms;
+  o->wa_streams = d.wa_streams;
+  o->reserved = 0;
   return PLACE_OK;
 }
 
@@ -1257,6 +1276,130 @@ int place_get_history(place_t *h, int32_t copy, place_iter_record *out, int32_t 
     for (int i = 0; i < m; ++i) out[i] = ring[(cs.n_hist - m + i) % d.hist_cap];
   }
   return PLACE_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Checkpoint layout: a header, the copy's CopyState, then its arrays in the
+// order of ckpt_arrays (each padded to 8 bytes), then the history ring.
+struct CkptHeader {
+  char magic[8];                 // "HYBROCK1"
+  int32_t version;               // 1
+  int32_t n_cells, n_mov, n_real, n_fill, n_nets, n_pins, nx, ny, frac_bits, hist_cap;
+  int32_t has_up;                // backtracking arrays present
+  int32_t state_bytes;           // sizeof(CopyState)
+  double dref, w_bin;            // the schedule's reference step and bin size
+};
+
+struct CkptArray {
+  void *dev;
+  size_t bytes;
+};
+
+std::vector<CkptArray> ckpt_arrays(const Dev &d, int c) {
+  const size_t C = d.n_cells, Mo = d.n_mov;
+  std::vector<CkptArray> v = {
+      {d.xy + c * C, sizeof(float2) * C},
+      {d.ux + c * Mo, sizeof(float) * Mo}, {d.uy + c * Mo, sizeof(float) * Mo},
+      {d.vpx + c * Mo, sizeof(float) * Mo}, {d.vpy + c * Mo, sizeof(float) * Mo},
+      {d.gx[0] + c * Mo, sizeof(float) * Mo}, {d.gy[0] + c * Mo, sizeof(float) * Mo},
+      {d.gx[1] + c * Mo, sizeof(float) * Mo}, {d.gy[1] + c * Mo, sizeof(float) * Mo},
+      {d.gwx + c * Mo, sizeof(float) * Mo}, {d.gwy + c * Mo, sizeof(float) * Mo},
+      {d.gdx + c * Mo, sizeof(float) * Mo}, {d.gdy + c * Mo, sizeof(float) * Mo},
+      {d.gacc + c * Mo, sizeof(unsigned long long) * Mo},
+      {d.hist + (size_t)c * d.hist_cap, sizeof(place_iter_record) * d.hist_cap}};
+  if (d.upx) {
+    v.push_back({d.upx + c * Mo, sizeof(float) * Mo});
+    v.push_back({d.upy + c * Mo, sizeof(float) * Mo});
+  }
+  return v;
+}
+
+size_t pad8(size_t n) { return (n + 7) & ~size_t(7); }
+
+CkptHeader ckpt_header(const Dev &d) {
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof hd);
+  std::memcpy(hd.magic, "HYBROCK1", 8);
+  hd.version = 1;
+  hd.n_cells = d.n_cells; hd.n_mov = d.n_mov; hd.n_real = d.n_real; hd.n_fill = d.n_fill;
+  hd.n_nets = d.n_nets; hd.n_pins = d.n_pins; hd.nx = d.nx; hd.ny = d.ny;
+  hd.frac_bits = d.F; hd.hist_cap = d.hist_cap;
+  hd.has_up = d.upx ? 1 : 0;
+  hd.state_bytes = (int32_t)sizeof(CopyState);
+  hd.dref = d.dref; hd.w_bin = d.w_bin;
+  return hd;
+}
+
+size_t ckpt_bytes(const Dev &d) {
+  size_t n = pad8(sizeof(CkptHeader)) + pad8(sizeof(CopyState));
+  for (const CkptArray &a : ckpt_arrays(d, 0)) n += pad8(a.bytes);
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int place_checkpoint_bytes(const place_t *h, int64_t *bytes) {
+  if (!h) return fail(PLACE_EINVAL, "null handle");
+  if (!bytes) return fail(PLACE_EINVAL, "null output");
+  *bytes = (int64_t)ckpt_bytes(h->d);
+  return PLACE_OK;
+}
+
+int place_checkpoint_save(place_t *h, int32_t copy, void *buf, int64_t cap) {
+  NvtxRange nvtx_("place_checkpoint_save");
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  const Dev &d = h->d;
+  if (!buf) return fail(PLACE_EINVAL, "null buffer");
+  if (cap < (int64_t)ckpt_bytes(d))
+    return fail(PLACE_EINVAL, "buffer of %lld bytes, the checkpoint needs %lld", (long long)cap,
+                (long long)ckpt_bytes(d));
+  unsigned char *p = static_cast<unsigned char *>(buf);
+  const CkptHeader hd = ckpt_header(d);
+  std::memcpy(p, &hd, sizeof hd);
+  p += pad8(sizeof hd);
+  CK(cudaMemcpyAsync(p, d.cs + copy, sizeof(CopyState), cudaMemcpyDeviceToHost, h->stream));
+  p += pad8(sizeof(CopyState));
+  for (const CkptArray &a : ckpt_arrays(d, copy)) {
+    CK(cudaMemcpyAsync(p, a.dev, a.bytes, cudaMemcpyDeviceToHost, h->stream));
+    p += pad8(a.bytes);
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return check_dev_err(h);
+}
+
+int place_checkpoint_load(place_t *h, int32_t copy, const void *buf, int64_t bytes) {
+  NvtxRange nvtx_("place_checkpoint_load");
+  int rc = check_copy(h, copy, false);
+  if (rc) return rc;
+  const Dev &d = h->d;
+  if (!buf) return fail(PLACE_EINVAL, "null buffer");
+  if (bytes < (int64_t)ckpt_bytes(d))
+    return fail(PLACE_EINVAL, "checkpoint of %lld bytes, this handle's needs %lld",
+                (long long)bytes, (long long)ckpt_bytes(d));
+  const unsigned char *p = static_cast<const unsigned char *>(buf);
+  CkptHeader got;
+  std::memcpy(&got, p, sizeof got);
+  const CkptHeader want = ckpt_header(d);
+  if (std::memcmp(&got, &want, sizeof got) != 0)
+    return fail(PLACE_EINVAL, "the checkpoint was taken on a handle of another design, grid or "
+                "parameters (header mismatch)");
+  p += pad8(sizeof got);
+  // the copy's queued work ends before its state is replaced
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpyAsync(d.cs + copy, p, sizeof(CopyState), cudaMemcpyHostToDevice, h->stream));
+  p += pad8(sizeof(CopyState));
+  for (const CkptArray &a : ckpt_arrays(d, copy)) {
+    CK(cudaMemcpyAsync(a.dev, p, a.bytes, cudaMemcpyHostToDevice, h->stream));
+    p += pad8(a.bytes);
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return check_dev_err(h);
 }
 
 int place_get_stretched_map(place_t *h, int32_t copy, int64_t *map) {

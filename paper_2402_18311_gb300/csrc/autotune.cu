@@ -8,8 +8,11 @@
 //    would leave SMs idle) and whether a stage with few tiles splits its
 //    contraction over two CTAs per tile;
 //  * how many pins of a net above 256 pins the big-net WA kernel keeps in
-//    shared memory (more pins cached, fewer blocks resident per SM).
-//  Both run beside other kernels of the iteration (the wirelength branch and
+//    shared memory (more pins cached, fewer blocks resident per SM);
+//  * on how many graph branches the WA degree classes run (one chain, or two
+//    or three chains side by side, so that the tails of the classes with few
+//    long blocks overlap the classes with many short ones).
+//  These run beside other kernels of the iteration (the wirelength branch and
 //  the density/spectral branch share the GPU), so they are timed as whole
 //  iterations of the captured graph, every candidate from the same start;
 //  * the two effective-bin thresholds at which the density scatter switches
@@ -37,11 +40,12 @@ namespace hp {
 namespace {
 
 struct Key {
-  int nx, ny, K, tc, lg_mov, lg_pins, lg_deg, stretch, gemm_bn, gemm_split, cap, scat;
+  int nx, ny, K, tc, lg_mov, lg_pins, lg_deg, stretch, gemm_bn, gemm_split, cap, scat, wa_streams;
   bool operator<(const Key &o) const {
     return std::tie(nx, ny, K, tc, lg_mov, lg_pins, lg_deg, stretch, gemm_bn, gemm_split, cap,
-                    scat) < std::tie(o.nx, o.ny, o.K, o.tc, o.lg_mov, o.lg_pins, o.lg_deg,
-                                     o.stretch, o.gemm_bn, o.gemm_split, o.cap, o.scat);
+                    scat, wa_streams) <
+           std::tie(o.nx, o.ny, o.K, o.tc, o.lg_mov, o.lg_pins, o.lg_deg, o.stretch, o.gemm_bn,
+                    o.gemm_split, o.cap, o.scat, o.wa_streams);
   }
 };
 
@@ -127,8 +131,10 @@ struct Timer {
 
 int autotune(Dev &d, int max_deg, cudaStream_t st, const TuneHooks &hk, TuneOut *out) {
   const auto t0 = std::chrono::steady_clock::now();
-  const Key key{d.nx, d.ny, d.K, d.tc, lg2(d.n_mov), lg2(d.n_pins), lg2(max_deg), d.prm.stretch,
-                d.prm.gemm_bn, d.prm.gemm_split, d.prm.wa_big_cap, d.prm.scatter_mode};
+  const Key key{d.nx,           d.ny,           d.K,           d.tc,
+                lg2(d.n_mov),   lg2(d.n_pins),  lg2(max_deg),  d.prm.stretch,
+                d.prm.gemm_bn,  d.prm.gemm_split, d.prm.wa_big_cap, d.prm.scatter_mode,
+                d.prm.wa_streams};
   {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find(key);
@@ -141,6 +147,7 @@ int autotune(Dev &d, int max_deg, cudaStream_t st, const TuneHooks &hk, TuneOut 
         d.tc_split[s] = out->split[s];
       }
       d.wa_big_cap = out->cap;
+      d.wa_streams = out->wa_streams;
       d.scat_t1 = out->t1;
       d.scat_t2 = out->t2;
       return d.tc ? hk.encode_maps(hk.ctx) : 0;
@@ -225,6 +232,24 @@ int autotune(Dev &d, int max_deg, cudaStream_t st, const TuneHooks &hk, TuneOut 
     d.wa_big_cap = best_c;
   }
 
+  // 2b. graph branches of the WA classes, the same way
+  if (d.prm.wa_streams == 0 && d.n_cls > 1) {
+    const int rule = d.wa_streams;
+    float best_t = 1e30f;
+    int best_n = rule;
+    const int cand[3] = {rule, rule == 2 ? 1 : 2, rule == 3 ? 1 : 3};
+    for (int i = 0; i < 3; ++i) {
+      d.wa_streams = cand[i];
+      const float t = time_graph(hk);
+      if (t < 0.f) return PLACE_ECUDA;
+      if (i == 0 || t < best_t * (1.f - kTuneMargin)) {
+        best_t = t;
+        best_n = cand[i];
+      }
+    }
+    d.wa_streams = best_n;
+  }
+
   // 3. the scatter's thresholds, from clouds of increasing width (the
   // scatter's cost depends on the phase, which one start cannot show)
   if (d.prm.scatter_mode < 0 && d.n_mov > 0) {
@@ -284,6 +309,7 @@ int autotune(Dev &d, int max_deg, cudaStream_t st, const TuneHooks &hk, TuneOut 
     out->split[s] = d.tc_split[s];
   }
   out->cap = d.wa_big_cap;
+  out->wa_streams = d.wa_streams;
   out->t1 = d.scat_t1;
   out->t2 = d.scat_t2;
   out->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

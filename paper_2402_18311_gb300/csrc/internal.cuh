@@ -184,6 +184,7 @@ struct Dev {
   int wa_block_base[8];       // slot offset of the class's blocks
   int wa_blocks_total;
   int wa_big_cap;             // pins of a > 256-pin net kept in shared memory
+  int wa_streams;             // graph branches of the WA classes (1..3, wa_branch_of)
   // density scatter: SCAT_MERGED below n_eff scat_t1, SCAT_TABLE below scat_t2,
   // SCAT_DIRECT above; scat_force >= 0 forces one way (tuning)
   double scat_t1, scat_t2;
@@ -262,6 +263,11 @@ void launch_spectral(const Dev &d, int copy0, int ncopy, int with_psi, int eval,
 void launch_spectral_tc_stalled(const Dev &d, cudaStream_t st);
 void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_override,
                cudaStream_t st);
+// The WA classes of an iteration on d.wa_streams branches: branch b's classes
+// run in sequence on st[b] (st[0..wa_streams-1]); every branch must already
+// follow the positions' producer.
+void launch_wa_branches(const Dev &d, int copy0, int ncopy, const cudaStream_t *st);
+constexpr int kMaxWaStreams = 3;
 void launch_hpwl64(const Dev &d, int copy0, int ncopy, cudaStream_t st);
 int wa_prepare(int cap);
 void launch_wa_floor(const Dev &d, int copy0, int ncopy, cudaStream_t st);
@@ -277,6 +283,7 @@ struct TuneOut {
   int bn[4];
   int split[4];
   int cap;
+  int wa_streams;
   double t1, t2;
   double ms;     // host time spent
   int cached;    // 1: taken from the process-wide cache

@@ -13,14 +13,25 @@
 //
 // A restart job (the perturbation step of Algorithm 1) perturbs the converged result of its
 // parent and re-optimises it.  When a job with pending restarts finishes, its
-// converged positions are saved in a device buffer and its handle stays
-// resident; the first restart admitted adopts the handle (no new allocation,
-// no netlist upload), later ones create a handle and start from the saved
-// positions.  Every job fits the budget alone, and the handles of active jobs
+// converged positions are saved in a device buffer; if a pending restart has
+// the same parameters, the handle stays resident and the first such restart
+// admitted adopts it (no new allocation, no netlist upload), the others create
+// a handle and start from the saved positions.  Every job fits the budget alone, and the handles of active jobs
 // are freed when they finish, so admission always makes progress.
+//
+// Failure handling on the host: a job may carry a wall-clock budget
+// (max_seconds from admission), and any job may be cancelled
+// (place_server_cancel, also from another thread while the server runs).  An
+// active job is stopped at the first chunk boundary past its budget or after
+// its cancellation, so no kernel of it is ever interrupted; its result then
+// carries the status PLACE_JOB_EXPIRED or PLACE_JOB_CANCELLED.  A queued job
+// that is cancelled is never admitted, and neither are the restarts of a
+// cancelled job.  The restarts of an expired job start from its positions.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <cmath>
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
@@ -70,6 +81,7 @@ struct Job {
   int64_t result_bytes = 0;
   double admit_s = 0, done_s = 0;
   place_job_result res{};
+  std::atomic<int> cancel{0};  // set by place_server_cancel, read by the run loop
 };
 
 }  // namespace
@@ -100,6 +112,20 @@ Job *find(place_server *s, int64_t id) {
   return nullptr;
 }
 
+// A restart may take over its parent's handle only if it would have created
+// the same one: the handle's parameters are fixed at create.
+bool same_params(const place_params &a, const place_params &b) {
+  return std::memcmp(&a, &b, sizeof a) == 0;
+}
+
+bool a_child_adopts(place_server *s, const Job *parent) {
+  for (const Job *c : s->jobs)
+    if (c->state == J_QUEUED && c->spec.kind == PLACE_JOB_RESTART && c->spec.parent == parent->id &&
+        same_params(c->prm, parent->prm))
+      return true;
+  return false;
+}
+
 void release(place_server *s, Job *j) {
   if (j->result_xy) {
     cudaFreeAsync(j->result_xy, j->st);
@@ -120,7 +146,7 @@ void release(place_server *s, Job *j) {
 }
 
 // Result of a finished job: exact HPWL/overflow and a hash of the positions.
-int finish(place_server *s, Job *j) {
+int finish(place_server *s, Job *j, int status = PLACE_JOB_FINISHED) {
   double hp = 0, tau = 0;
   int rc = place_eval_hpwl_overflow(j->h, &hp, &tau);
   if (rc) return rc;
@@ -141,9 +167,10 @@ int finish(place_server *s, Job *j) {
   r.overflow = tau;
   r.device_bytes = j->footprint;
   r.position_hash = fnv1a(y.data(), y.size() * 4, fnv1a(x.data(), x.size() * 4));
+  r.status = status;
   j->state = J_DONE;
   if (j->pending_children > 0) {
-    j->keep = true;  // stays resident for its restarts
+    j->keep = a_child_adopts(s, j);  // stays resident for a restart to adopt
     place_info info;
     if ((rc = place_get_info(j->h, &info))) return rc;
     // the handle's cells, filler cells included
@@ -156,15 +183,26 @@ int finish(place_server *s, Job *j) {
     if (cudaStreamSynchronize(j->st) != cudaSuccess) return sfail(PLACE_ECUDA, "saving a result");
     if (j->ev) cudaEventDestroy(j->ev);
     j->ev = nullptr;
+    if (!j->keep) {
+      // no restart can adopt the handle: free it now, keep the saved positions
+      float2 *saved = j->result_xy;
+      j->result_xy = nullptr;
+      release(s, j);
+      j->result_xy = saved;
+    }
   } else {
     release(s, j);
   }
   return PLACE_OK;
 }
 
-// A restart no longer needs its parent's saved positions.
+// A restart no longer needs its parent's saved positions.  after: the stream
+// of the restart's copy of them (nullptr: no copy was made; then every
+// stream is drained before the buffer is freed, as other restarts may still
+// be copying from it).
 void drop_child(place_server *s, Job *parent, cudaStream_t after) {
   if (--parent->pending_children > 0) return;
+  if (!after && parent->result_xy) cudaDeviceSynchronize();
   if (parent->result_xy) {
     cudaFreeAsync(parent->result_xy, after);  // after the child's copy
     parent->result_xy = nullptr;
@@ -180,7 +218,7 @@ int admit(place_server *s, Job *j) {
   Job *parent = j->spec.kind == PLACE_JOB_RESTART ? find(s, j->spec.parent) : nullptr;
   cudaError_t e;
   int rc;
-  if (parent && parent->keep) {
+  if (parent && parent->keep && same_params(parent->prm, j->prm)) {
     // take over the parent's resident handle and stream
     j->h = parent->h;
     j->st = parent->st;
@@ -216,6 +254,30 @@ int admit(place_server *s, Job *j) {
   return PLACE_OK;
 }
 
+// A job that ends without running (cancelled while queued, or a restart of
+// a cancelled job): its result has no positions.
+void cancel_queued(place_server *s, Job *j) {
+  if (j->spec.kind == PLACE_JOB_RESTART) {
+    Job *p = find(s, j->spec.parent);
+    if (p) drop_child(s, p, nullptr);
+  }
+  j->state = J_DONE;
+  place_job_result &r = j->res;
+  r = place_job_result{};
+  r.id = j->id;
+  r.kind = j->spec.kind;
+  r.status = PLACE_JOB_CANCELLED;
+  r.arrival_s = j->spec.arrival_s;
+  r.admit_s = r.done_s = now_s(s);
+  r.hpwl = r.overflow = std::nan("");
+}
+
+bool parent_cancelled(place_server *s, const Job *j) {
+  if (j->spec.kind != PLACE_JOB_RESTART) return false;
+  const Job *p = find(s, j->spec.parent);
+  return p && p->state == J_DONE && p->res.status == PLACE_JOB_CANCELLED;
+}
+
 }  // namespace
 
 extern "C" {
@@ -240,6 +302,7 @@ int place_server_submit(place_server *s, const place_netlist *nl, const place_di
   if (!s || !nl || !die || !bins || !job) return sfail(PLACE_EINVAL, "null argument");
   if (job->kind != PLACE_JOB_PLACE && job->kind != PLACE_JOB_RESTART)
     return sfail(PLACE_EINVAL, "unknown job kind %d", job->kind);
+  if (!(job->max_seconds >= 0.0)) return sfail(PLACE_EINVAL, "max_seconds must be >= 0");
   Job *j = new Job();
   j->id = (int64_t)s->jobs.size();
   j->spec = *job;
@@ -286,6 +349,13 @@ int place_server_run(place_server *s, double timeout_s, double *makespan_s) {
     const double now = now_s(s);
     if (timeout_s > 0 && now > timeout_s) return sfail(PLACE_ETIMEOUT, "server run timed out");
     bool progress = false;
+    // queued jobs that will never run: cancelled, or restarts of a cancelled job
+    for (Job *j : s->jobs) {
+      if (j->state != J_QUEUED || !(j->cancel.load() || parent_cancelled(s, j))) continue;
+      cancel_queued(s, j);
+      --remaining;
+      progress = true;
+    }
     // advance or retire active jobs whose chunk has completed
     for (Job *j : s->jobs) {
       if (j->state != J_ACTIVE || !j->in_flight) continue;
@@ -294,8 +364,21 @@ int place_server_run(place_server *s, double timeout_s, double *makespan_s) {
       if (q != cudaSuccess) return sfail(PLACE_ECUDA, "job %lld: %s", (long long)j->id, cudaGetErrorString(q));
       progress = true;
       j->in_flight = false;
-      if (*j->flags) {
-        int rc = finish(s, j);
+      const int status = j->cancel.load() ? PLACE_JOB_CANCELLED
+                         : (j->spec.max_seconds > 0 && now - j->admit_s > j->spec.max_seconds)
+                             ? PLACE_JOB_EXPIRED
+                             : PLACE_JOB_FINISHED;
+      if (*j->flags || status != PLACE_JOB_FINISHED) {
+        if (status == PLACE_JOB_CANCELLED) {
+          // its restarts will not run: release the claims they hold on it
+          for (Job *c : s->jobs)
+            if (c->state == J_QUEUED && c->spec.kind == PLACE_JOB_RESTART && c->spec.parent == j->id) {
+              c->cancel.store(1);
+              cancel_queued(s, c);
+              --remaining;
+            }
+        }
+        int rc = finish(s, j, status);
         if (rc) return rc;
         --active;
         --remaining;
@@ -312,7 +395,8 @@ int place_server_run(place_server *s, double timeout_s, double *makespan_s) {
       if (j->spec.kind == PLACE_JOB_RESTART) {
         Job *p = find(s, j->spec.parent);
         if (!p || p->state != J_DONE) continue;
-        if (!p->keep && s->used + j->footprint > s->budget) continue;  // adopting needs no memory
+        const bool adopts = p->keep && same_params(p->prm, j->prm);  // adopting needs no memory
+        if (!adopts && s->used + j->footprint > s->budget) continue;
       } else if (s->used + j->footprint > s->budget) {
         continue;
       }
@@ -325,6 +409,14 @@ int place_server_run(place_server *s, double timeout_s, double *makespan_s) {
     if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
   if (makespan_s) *makespan_s = now_s(s);
+  return PLACE_OK;
+}
+
+int place_server_cancel(place_server *s, int64_t id) {
+  if (!s) return sfail(PLACE_EINVAL, "null server");
+  Job *j = find(s, id);
+  if (!j) return sfail(PLACE_EINVAL, "no job %lld", (long long)id);
+  j->cancel.store(1);
   return PLACE_OK;
 }
 

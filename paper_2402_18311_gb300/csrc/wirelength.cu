@@ -474,6 +474,24 @@ void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_
   }
 }
 
+// Branch of each degree class (thread, 4-lane, 16-lane, warp, big) for 1, 2
+// and 3 branches.  Two: the short nets beside the long ones; three: the
+// thread class alone, the group classes, the warp and big-net classes (whose
+// few long blocks then overlap the others' many short ones).
+constexpr int kWaBranch[3][5] = {{0, 0, 0, 0, 0}, {0, 0, 1, 1, 1}, {0, 1, 1, 2, 2}};
+
+void launch_wa_branches(const Dev &d, int copy0, int ncopy, const cudaStream_t *st) {
+  const int nb = d.wa_streams < 1 ? 1 : (d.wa_streams > kMaxWaStreams ? kMaxWaStreams : d.wa_streams);
+  int launched[kMaxWaStreams] = {0, 0, 0};
+  for (int cls = 0; cls < d.n_cls; ++cls) {
+    if (d.wa_blocks[cls] == 0) continue;
+    const int b = kWaBranch[nb - 1][cls < 5 ? cls : 4];
+    // the first class of a branch follows the branch's fork; the others
+    // follow a WA kernel and launch programmatically
+    launch_wa_one(d, cls, copy0, ncopy, 0, nullptr, launched[b]++ > 0, st[b]);
+  }
+}
+
 void launch_wa_class(const Dev &d, int cls, int copy0, int ncopy, int eval, cudaStream_t st) {
   if (cls >= 0 && cls < d.n_cls && d.wa_blocks[cls] > 0)
     launch_wa_one(d, cls, copy0, ncopy, eval, nullptr, false, st);

@@ -66,7 +66,7 @@ class place_params(ct.Structure):
                 ("max_backtracks", ct.c_int32), ("stretch", ct.c_int32),
                 ("autotune", ct.c_int32), ("scatter_mode", ct.c_int32), ("gemm_bn", ct.c_int32),
                 ("wa_big_cap", ct.c_int32), ("gemm_split", ct.c_int32), ("fillers", ct.c_int32),
-                ("macro_precond", ct.c_float)]
+                ("macro_precond", ct.c_float), ("wa_streams", ct.c_int32)]
 
 
 class place_info(ct.Structure):
@@ -80,7 +80,7 @@ class place_info(ct.Structure):
                 ("gemm_bn", ct.c_int32 * 4), ("gemm_split", ct.c_int32 * 4),
                 ("wa_big_cap", ct.c_int32), ("autotuned", ct.c_int32),
                 ("scatter_t1", ct.c_double), ("scatter_t2", ct.c_double),
-                ("autotune_ms", ct.c_double)]
+                ("autotune_ms", ct.c_double), ("wa_streams", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class place_state(ct.Structure):
@@ -101,12 +101,13 @@ PLACE_HISTORY_CAP = 4096
 
 class place_job(ct.Structure):
     _fields_ = [("kind", ct.c_int32), ("op", ct.c_int32), ("p", ct.c_float), ("pad", ct.c_int32),
-                ("seed", ct.c_uint64), ("parent", ct.c_int64), ("arrival_s", ct.c_double)]
+                ("seed", ct.c_uint64), ("parent", ct.c_int64), ("arrival_s", ct.c_double),
+                ("max_seconds", ct.c_double)]
 
 
 class place_job_result(ct.Structure):
     _fields_ = [("id", ct.c_int64), ("kind", ct.c_int32), ("iterations", ct.c_int32),
-                ("converged", ct.c_int32), ("pad", ct.c_int32), ("arrival_s", ct.c_double),
+                ("converged", ct.c_int32), ("status", ct.c_int32), ("arrival_s", ct.c_double),
                 ("admit_s", ct.c_double), ("done_s", ct.c_double), ("hpwl", ct.c_double),
                 ("overflow", ct.c_double), ("device_bytes", ct.c_int64),
                 ("position_hash", ct.c_uint64)]
@@ -114,6 +115,9 @@ class place_job_result(ct.Structure):
 
 PLACE_JOB_PLACE = 0
 PLACE_JOB_RESTART = 1
+PLACE_JOB_FINISHED = 0
+PLACE_JOB_CANCELLED = 1
+PLACE_JOB_EXPIRED = 2
 
 _VP = ct.c_void_p
 _SIGS = {
@@ -154,11 +158,15 @@ _SIGS = {
     "place_get_fillers": (ct.c_int, [_VP, ct.c_int32, _VP, _VP, ct.c_int32, ct.POINTER(ct.c_int32)]),
     "place_get_history": (ct.c_int, [_VP, ct.c_int32, _VP, ct.c_int32, ct.POINTER(ct.c_int32)]),
     "place_set_fillers": (ct.c_int, [_VP, ct.c_int32, _VP, _VP]),
+    "place_checkpoint_bytes": (ct.c_int, [_VP, ct.POINTER(ct.c_int64)]),
+    "place_checkpoint_save": (ct.c_int, [_VP, ct.c_int32, _VP, ct.c_int64]),
+    "place_checkpoint_load": (ct.c_int, [_VP, ct.c_int32, _VP, ct.c_int64]),
     "place_server_create": (ct.c_int, [ct.c_int64, ct.c_int32, ct.c_int32, ct.POINTER(_VP)]),
     "place_server_submit": (ct.c_int, [_VP, ct.POINTER(place_netlist), ct.POINTER(place_die),
                                        ct.POINTER(place_bins), ct.POINTER(place_params),
                                        ct.POINTER(place_job), ct.POINTER(ct.c_int64)]),
     "place_server_run": (ct.c_int, [_VP, ct.c_double, ct.POINTER(ct.c_double)]),
+    "place_server_cancel": (ct.c_int, [_VP, ct.c_int64]),
     "place_server_results": (ct.c_int, [_VP, _VP, ct.c_int32, ct.POINTER(ct.c_int32)]),
     "place_server_stats": (ct.c_int, [_VP, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int32)]),
     "place_server_destroy": (ct.c_int, [_VP]),
@@ -416,6 +424,24 @@ def place_set_fillers(h, copy, x, y):
     return _check(lib().place_set_fillers(h, int(copy), _ptr(x), _ptr(y)))
 
 
+def place_checkpoint_bytes(h):
+    n = ct.c_int64()
+    _check(lib().place_checkpoint_bytes(h, ct.byref(n)))
+    return n.value
+
+
+def place_checkpoint_save(h, copy):
+    """Copy ``copy``'s optimiser state as a uint8 numpy array."""
+    buf = np.empty(place_checkpoint_bytes(h), np.uint8)
+    _check(lib().place_checkpoint_save(h, int(copy), _ptr(buf), buf.size))
+    return buf
+
+
+def place_checkpoint_load(h, copy, buf):
+    buf = np.ascontiguousarray(buf, np.uint8)
+    return _check(lib().place_checkpoint_load(h, int(copy), _ptr(buf), buf.size))
+
+
 def place_get_fillers(h, copy):
     """(x, y) float32 arrays of copy ``copy``'s filler corners."""
     n = ct.c_int32()
@@ -437,12 +463,12 @@ class Server:
         self._keep = []
 
     def submit(self, design, params=None, kind=PLACE_JOB_PLACE, arrival_s=0.0, parent=-1,
-               op=PLACE_SHUFFLE_ALL, p=0.5, seed=0):
+               op=PLACE_SHUFFLE_ALL, p=0.5, seed=0, max_seconds=0.0):
         nl, keep = _netlist(design)
         die = place_die(*design.die)
         bins = place_bins(design.nx, design.ny, design.target_density)
         prm = params if params is not None else place_default_params()
-        job = place_job(kind, op, p, 0, seed, parent, arrival_s)
+        job = place_job(kind, op, p, 0, seed, parent, arrival_s, max_seconds)
         jid = ct.c_int64()
         _check(lib().place_server_submit(self.h, ct.byref(nl), ct.byref(die), ct.byref(bins),
                                          ct.byref(prm), ct.byref(job), ct.byref(jid)))
@@ -453,6 +479,9 @@ class Server:
         m = ct.c_double()
         _check(lib().place_server_run(self.h, float(timeout_s), ct.byref(m)))
         return m.value
+
+    def cancel(self, job_id):
+        return _check(lib().place_server_cancel(self.h, int(job_id)))
 
     def results(self):
         n = ct.c_int32()

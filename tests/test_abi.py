@@ -58,15 +58,16 @@ def test_default_params_match_the_oracle_reading(L):
     assert p.max_backtracks == o.max_backtracks == 0
     assert p.dct_mode == place.PLACE_DCT_AUTO and p.autotune == 1 and p.scatter_mode == -1
     assert p.gemm_bn == 0 and p.wa_big_cap == 0 and p.gemm_split == 0 and p.fillers == 0
+    assert p.wa_streams == 0
     assert p.macro_precond == o.macro_precond == 1.0
 
 
 def test_struct_sizes_match_header_layout():
     assert ct.sizeof(place.place_netlist) == 4 * 4 + 10 * 8
-    assert ct.sizeof(place.place_params) == 21 * 4
+    assert ct.sizeof(place.place_params) == 22 * 4
     assert ct.sizeof(place.place_state) == 4 * 4 + 7 * 8
-    assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 4 * 4 + 10 * 4 + 3 * 8
-    assert ct.sizeof(place.place_job) == 4 * 4 + 8 + 8 + 8
+    assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 4 * 4 + 10 * 4 + 3 * 8 + 2 * 4
+    assert ct.sizeof(place.place_job) == 4 * 4 + 8 + 8 + 8 + 8
     assert ct.sizeof(place.place_job_result) == 8 + 4 * 4 + 5 * 8 + 8 + 8
 
 
@@ -147,7 +148,8 @@ def test_create_rejects_bad_params(L):
         place.place_create(d, place.place_default_params(stretch=2))
     assert ei.value.code == place.PLACE_EINVAL and "stretch" in str(ei.value)
     for field, bad in (("autotune", 2), ("scatter_mode", 3), ("gemm_bn", 96), ("wa_big_cap", 16),
-                       ("gemm_split", 3), ("fillers", 2), ("macro_precond", 0.0)):
+                       ("gemm_split", 3), ("fillers", 2), ("macro_precond", 0.0),
+                       ("wa_streams", 4)):
         with pytest.raises(place.PlaceError) as ei:
             place.place_create(d, place.place_default_params(**{field: bad}))
         assert ei.value.code == place.PLACE_EINVAL and field in str(ei.value)
@@ -164,6 +166,11 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.place_step_multi(arr, 2, 1, None) == place.PLACE_EINVAL
     x, y = ct.c_void_p(), ct.c_void_p()
     assert L.place_device_views(None, 0, ct.byref(x), ct.byref(y)) == place.PLACE_EINVAL
+    n = ct.c_int64()
+    assert L.place_checkpoint_bytes(None, ct.byref(n)) == place.PLACE_EINVAL
+    buf = (ct.c_uint8 * 64)()
+    assert L.place_checkpoint_save(None, 0, buf, 64) == place.PLACE_EINVAL
+    assert L.place_checkpoint_load(None, 0, buf, 64) == place.PLACE_EINVAL
     assert L.place_destroy(None) == place.PLACE_OK
     assert b"null" in L.place_last_error()
 
@@ -177,6 +184,30 @@ def test_server_rejects_bad_arguments_on_host(L):
         with pytest.raises(place.PlaceError) as ei:
             s.submit(d, kind=place.PLACE_JOB_RESTART, parent=5)
         assert ei.value.code == place.PLACE_EINVAL
+    finally:
+        s.close()
+
+
+def test_server_cancels_queued_jobs_and_their_restarts_on_host(L):
+    # failure handling on the host, no GPU: a job cancelled before it runs is
+    # never admitted, nor are its restarts; a negative budget is rejected
+    s = place.Server(1 << 30, 2)
+    try:
+        d = _design()
+        with pytest.raises(place.PlaceError):
+            s.submit(d, max_seconds=-1.0)
+        a = s.submit(d)
+        r1 = s.submit(d, kind=place.PLACE_JOB_RESTART, parent=a, seed=1)
+        r2 = s.submit(d, kind=place.PLACE_JOB_RESTART, parent=a, seed=2)
+        s.cancel(a)
+        with pytest.raises(place.PlaceError):
+            s.cancel(99)
+        s.run()
+        res = s.results()
+        assert [r.id for r in res] == [a, r1, r2]
+        for r in res:
+            assert r.status == place.PLACE_JOB_CANCELLED
+            assert r.iterations == 0 and r.position_hash == 0 and np.isnan(r.hpwl)
     finally:
         s.close()
 

@@ -1,5 +1,6 @@
 """Host-visible API calls beyond the parity path: borrowed device views of the
-positions and stepping several handles at once."""
+positions, stepping several handles at once, checkpoint and resume, and the
+bounded waits' failure path."""
 import numpy as np
 import pytest
 
@@ -110,3 +111,76 @@ def test_bounded_waits_give_up_and_the_handle_stays_usable():
         assert place.place_test_wait_timeout(h) == place.PLACE_EINVAL
     finally:
         place.place_destroy(h)
+
+
+def _resume_case(d, prm, first, rest, copy=0):
+    """Run first + rest iterations straight, and first, checkpoint, rest on a
+    new handle from the checkpoint: positions, state and history agree bit
+    for bit."""
+    a = place.place_create(d, prm)
+    b = place.place_create(d, prm)
+    try:
+        place.place_step(a, first)
+        buf = place.place_checkpoint_save(a, copy)
+        assert buf.size == place.place_checkpoint_bytes(a)
+        place.place_step(a, rest)
+        place.place_checkpoint_load(b, copy, buf)
+        place.place_step(b, rest)
+        n = d.n_cells
+        xa = np.empty(n, np.float32); ya = np.empty(n, np.float32)
+        xb = np.empty(n, np.float32); yb = np.empty(n, np.float32)
+        place.place_get_positions(a, copy, xa, ya)
+        place.place_get_positions(b, copy, xb, yb)
+        np.testing.assert_array_equal(xa, xb)
+        np.testing.assert_array_equal(ya, yb)
+        sa, sb = place.place_get_state(a, copy), place.place_get_state(b, copy)
+        for f in ("iter", "converged", "stopped", "backtracks", "lambda_", "gamma", "alpha", "a",
+                  "overflow", "hpwl_wa", "bins_effective"):
+            assert getattr(sa, f) == getattr(sb, f), f
+        ha = [(r.iter, r.hpwl_wa, r.overflow, r.lambda_) for r in place.place_get_history(a, copy)]
+        hb = [(r.iter, r.hpwl_wa, r.overflow, r.lambda_) for r in place.place_get_history(b, copy)]
+        assert ha == hb and len(ha) > 0
+        if place.place_get_info(a).n_fillers:
+            fa, fb = place.place_get_fillers(a, copy), place.place_get_fillers(b, copy)
+            np.testing.assert_array_equal(fa[0], fb[0])
+            np.testing.assert_array_equal(fa[1], fb[1])
+        return sa
+    finally:
+        place.place_destroy(a)
+        place.place_destroy(b)
+
+
+def test_checkpoint_resume_is_bit_exact_fp32_path():
+    d = synth.tiny_1k(0)
+    st = _resume_case(d, place.place_default_params(tau_stop=-1.0, max_iters=10 ** 6), 90, 110)
+    assert st.iter == 200
+
+
+def test_checkpoint_resume_is_bit_exact_tensor_core_path_with_knobs():
+    # BF16x3 spectral path, fillers, backtracking: every array the knobs add
+    d = synth.scaled(20000, 128, seed=2)
+    prm = place.place_default_params(tau_stop=-1.0, max_iters=10 ** 6, fillers=1,
+                                     max_backtracks=2, n_copies=2)
+    _resume_case(d, prm, 75, 80, copy=1)
+
+
+def test_checkpoint_rejects_another_design_and_short_buffers():
+    d1, d2 = synth.tiny_1k(0), synth.tiny_1k(1)
+    prm = place.place_default_params(tau_stop=-1.0, max_iters=100)
+    a = place.place_create(d1, prm)
+    try:
+        buf = place.place_checkpoint_save(a, 0)
+        with pytest.raises(place.PlaceError):
+            place.place_checkpoint_load(a, 0, buf[:-8])
+        with pytest.raises(place.PlaceError):
+            place.place_checkpoint_load(a, 1, buf)  # one copy only
+        other = place.place_create(d2, place.place_default_params(tau_stop=-1.0, max_iters=100,
+                                                                   hpwl_ref=0.5))
+        try:
+            with pytest.raises(place.PlaceError):
+                place.place_checkpoint_load(other, 0, buf)  # another lambda reference step
+        finally:
+            place.place_destroy(other)
+        place.place_checkpoint_load(a, 0, buf)  # its own checkpoint loads
+    finally:
+        place.place_destroy(a)

@@ -141,3 +141,64 @@ def test_wiremask_restart_job_equals_plain_handle_run():
             assert r.hpwl == hp[0] and r.overflow == tv[0], phase
     finally:
         place.place_destroy(h)
+
+
+def _alone(d, prm):
+    s = place.Server(8 << 30, 1, iters_per_tick=16)
+    try:
+        s.submit(d, prm)
+        s.run(timeout_s=300)
+        return s.results()[0]
+    finally:
+        s.close()
+
+
+def test_a_job_past_its_wall_clock_budget_expires_at_a_chunk_boundary():
+    ds = designs()
+    endless = place.place_default_params(tau_stop=-1.0, max_iters=10 ** 6,
+                                         dct_mode=place.PLACE_DCT_BF16X3)
+    s = place.Server(8 << 30, 4, iters_per_tick=16)
+    try:
+        a = s.submit(ds[0], params())
+        b = s.submit(ds[1], endless, max_seconds=1e-6)  # over budget after its first chunk
+        rb = s.submit(ds[1], params(), kind=place.PLACE_JOB_RESTART, parent=b, seed=5)
+        s.run(timeout_s=300)
+        res = {r.id: r for r in s.results()}
+    finally:
+        s.close()
+    assert res[b].status == place.PLACE_JOB_EXPIRED and res[b].iterations == 16
+    assert np.isfinite(res[b].hpwl) and res[b].position_hash != 0
+    # the others run to their stop test, and the restart starts from b's positions
+    assert res[a].status == res[rb].status == place.PLACE_JOB_FINISHED
+    assert res[rb].converged == 1
+    ra = _alone(ds[0], params())
+    assert (res[a].position_hash, res[a].iterations) == (ra.position_hash, ra.iterations)
+
+
+def test_cancelling_a_running_job_stops_it_and_leaves_the_others_alone():
+    import threading
+    import time
+    ds = designs()
+    endless = place.place_default_params(tau_stop=-1.0, max_iters=10 ** 6,
+                                         dct_mode=place.PLACE_DCT_BF16X3)
+    s = place.Server(8 << 30, 4, iters_per_tick=16)
+    try:
+        a = s.submit(ds[0], params())
+        b = s.submit(ds[1], endless)
+        rb = s.submit(ds[1], params(), kind=place.PLACE_JOB_RESTART, parent=b, seed=5)
+        err = []
+        t = threading.Thread(target=lambda: err.append(s.run(timeout_s=300)))
+        t.start()
+        time.sleep(1.0)
+        s.cancel(b)  # from this thread while the server runs in the other
+        t.join(timeout=300)
+        assert not t.is_alive()
+        res = {r.id: r for r in s.results()}
+    finally:
+        s.close()
+    assert res[b].status == place.PLACE_JOB_CANCELLED
+    assert 0 < res[b].iterations < 10 ** 6 and res[b].iterations % 16 == 0
+    assert res[rb].status == place.PLACE_JOB_CANCELLED and res[rb].iterations == 0
+    assert res[a].status == place.PLACE_JOB_FINISHED
+    ra = _alone(ds[0], params())
+    assert (res[a].position_hash, res[a].iterations) == (ra.position_hash, ra.iterations)
