@@ -346,7 +346,8 @@ def tuning(info):
     return {"autotuned": bool(info.autotuned), "autotune_ms": info.autotune_ms,
             "gemm_bn": list(info.gemm_bn), "gemm_split": list(info.gemm_split),
             "wa_big_cap": info.wa_big_cap, "wa_streams": info.wa_streams,
-            "scatter_thresholds": [info.scatter_t1, info.scatter_t2]}
+            "scatter_thresholds": [info.scatter_t1, info.scatter_t2],
+            "scatter_sorted_from": info.scatter_ts if info.scatter_ts < 1e300 else None}
 
 
 def _stage_sample(place, h, n=5):
