@@ -143,10 +143,8 @@ typedef struct place_params {
   int32_t scatter_mode;   /* -1 (default): the density scatter picks per copy and
                              pass, from the previous pass's effective number of
                              occupied bins, between merging a warp's shared bins,
-                             a shared-memory table, direct atomics, and the
-                             table over the cells in tile order (an order
-                             rebuilt every 8 iterations); 0..3 force one of
-                             them.  All give the same map. */
+                             a shared-memory table and direct atomics; 0, 1, 2
+                             force one of them.  All give the same map. */
   int32_t gemm_bn;        /* 0 (default): automatic; 64 or 128: tile width of
                              every tensor-core GEMM stage of the spectral solve */
   int32_t wa_big_cap;     /* 0 (default): automatic; 32..6144: pins of a net of
@@ -189,8 +187,6 @@ typedef struct place_info {
   double autotune_ms;     /* host time the tuning took at create (0 on a cache hit) */
   int32_t wa_streams;     /* graph branches the WA classes run on (1..3) */
   int32_t reserved;
-  double scatter_ts;      /* effective bins from which the scatter takes the
-                           * table over cells in tile order (1e300: never) */
 } place_info;
 
 /* Optimiser scalars of one copy after its last iteration. */

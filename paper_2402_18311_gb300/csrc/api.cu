@@ -78,9 +78,6 @@ constexpr int kBigCapMax = 3072;
 // atomics above (the autotuner replaces them by measured crossovers)
 constexpr double kScatterMergedBelow = 32.0;
 constexpr double kScatterTableBelow = 1024.0;
-// ... and the sorted way from this many on (a cell order rebuilt every
-// kSortEvery iterations; the autotuner measures its own crossover)
-constexpr double kScatterSortedFrom = 4096.0;
 constexpr int kMaxBigNetBlocks = 8192;  // one block per net above 256 pins, up to this many
 
 bool is_integer(double v) { return std::floor(v) == v && std::isfinite(v); }
@@ -193,11 +190,6 @@ struct place_t {
   size_t mem_bytes = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  // the same iteration preceded by the rebuild of the sorted scatter's cell
-  // order, launched instead of `exec` every kSortEvery iterations
-  cudaGraph_t graph_sort = nullptr;
-  cudaGraphExec_t exec_sort = nullptr;
-  unsigned long long n_launch = 0;
   CUtensorMap maps[16];              // tensor maps of the tcgen05 spectral path
   int n_cand_all = 0, n_cand_macro = 0;
   // WireMask: host tables built at create, device copy made on first use
@@ -252,8 +244,6 @@ int place_destroy(place_t *h) {
   cudaStreamSynchronize(h->stream);  // no work of this handle may still run
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
-  if (h->exec_sort) cudaGraphExecDestroy(h->exec_sort);
-  if (h->graph_sort) cudaGraphDestroy(h->graph_sort);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->cap2) cudaStreamDestroy(h->cap2);
   if (h->cap3) cudaStreamDestroy(h->cap3);
@@ -306,12 +296,6 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.upx = d.prm.max_backtracks > 0 ? a.take<float>(K * Mv) : nullptr;
   d.upy = d.prm.max_backtracks > 0 ? a.take<float>(K * Mv) : nullptr;
   d.gacc = a.take<unsigned long long>(K * std::max<size_t>(Mv, 1));
-  // the sorted scatter's cell order (8 x 8-bin tiles; fillers sort after)
-  d.s_nty = (d.ny + (1 << kSortTileShift) - 1) >> kSortTileShift;
-  d.s_ntiles = ((d.nx + (1 << kSortTileShift) - 1) >> kSortTileShift) * d.s_nty;
-  d.s_nkeys = d.s_ntiles * (d.n_fill > 0 ? 2 : 1);
-  d.sperm = a.take<int>(K * std::max<size_t>(Mv, 1));
-  d.scnt = a.take<unsigned int>(K * (size_t)d.s_nkeys);
   d.M = a.take<unsigned long long>(K * (size_t)d.Gm);
   d.Fmap = a.take<long long>(G);
   d.rho = a.take<float>(K * G);
@@ -441,13 +425,9 @@ int encode_tc_maps_cb(void *ctx) { return encode_tc_maps(static_cast<TuneCtx *>(
 void drop_graph(place_t *h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
-  if (h->exec_sort) cudaGraphExecDestroy(h->exec_sort);
-  if (h->graph_sort) cudaGraphDestroy(h->graph_sort);
-  h->exec = h->exec_sort = nullptr;
-  h->graph = h->graph_sort = nullptr;
+  h->exec = nullptr;
+  h->graph = nullptr;
 }
-
-int launch_iter(place_t *h, cudaStream_t st);
 
 int enqueue_reset(place_t *h, int c0, int n);
 int ensure_graph(place_t *h);
@@ -467,16 +447,15 @@ float time_iters_cb(void *ctx, int n) {
   if (enqueue_reset(h, 0, d.K)) return -1.f;
   drop_graph(h);
   if (ensure_graph(h)) return -1.f;
-  h->n_launch = 0;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
   if (cudaEventCreate(&e1) != cudaSuccess) {
     cudaEventDestroy(e0);
     return -1.f;
   }
-  for (int i = 0; i < 2; ++i) launch_iter(h, h->stream);
+  for (int i = 0; i < 2; ++i) cudaGraphLaunch(h->exec, h->stream);
   cudaEventRecord(e0, h->stream);
-  for (int i = 0; i < n; ++i) launch_iter(h, h->stream);
+  for (int i = 0; i < n; ++i) cudaGraphLaunch(h->exec, h->stream);
   cudaEventRecord(e1, h->stream);
   float ms = -1.f;
   if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
@@ -537,15 +516,13 @@ int enqueue_reset(place_t *h, int c0, int n) {
 // them) beside the density scatter and the tensor-core Poisson solve, and
 // join before the per-cell gradient.
 void enqueue_iteration(const Dev &d, cudaStream_t st, const cudaStream_t *wst, cudaEvent_t fork,
-                       const cudaEvent_t *join, bool sort) {
+                       const cudaEvent_t *join) {
   const int K = d.K;
   const int nb = std::max(1, std::min(d.wa_streams, kMaxWaStreams));
   cudaEventRecord(fork, st);
   for (int b = 0; b < nb; ++b) cudaStreamWaitEvent(wst[b], fork, 0);
   launch_wa_branches(d, 0, K, wst);
   for (int b = 0; b < nb; ++b) cudaEventRecord(join[b], wst[b]);
-  // the sorted scatter's cell order, beside the WA branches
-  if (sort) launch_cell_sort(d, 0, K, d.scat_force == SCAT_SORTED, st);
   cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.Gm * K, st);
   launch_scatter(d, 0, K, 0, st);
   launch_density_finish(d, 0, K, FIN_ITER, st);
@@ -556,37 +533,17 @@ void enqueue_iteration(const Dev &d, cudaStream_t st, const cudaStream_t *wst, c
   launch_update(d, 0, K, st);
 }
 
-// The sorted way can run: forced, or below a reachable threshold.
-bool uses_sorted_scatter(const Dev &d) {
-  return d.scat_force == SCAT_SORTED || (d.scat_force < 0 && d.scat_ts < 1e300);
-}
-
-int capture_iteration(place_t *h, bool sort, cudaGraph_t *graph, cudaGraphExec_t *exec) {
+int ensure_graph(place_t *h) {
+  if (h->exec) return PLACE_OK;
   CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
   const cudaStream_t wst[kMaxWaStreams] = {h->cap2, h->cap3, h->cap4};
   const cudaEvent_t joins[kMaxWaStreams] = {h->ev_join, h->ev_join2, h->ev_join3};
-  enqueue_iteration(h->d, h->cap, wst, h->ev_fork, joins, sort);
+  enqueue_iteration(h->d, h->cap, wst, h->ev_fork, joins);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap, &g);
   if (e != cudaSuccess) return fail(PLACE_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
-  *graph = g;
-  CK(cudaGraphInstantiate(exec, g, 0));
-  return PLACE_OK;
-}
-
-int ensure_graph(place_t *h) {
-  if (h->exec) return PLACE_OK;
-  int rc = capture_iteration(h, false, &h->graph, &h->exec);
-  if (rc == PLACE_OK && uses_sorted_scatter(h->d))
-    rc = capture_iteration(h, true, &h->graph_sort, &h->exec_sort);
-  return rc;
-}
-
-// One iteration of every copy: the captured graph, every kSortEvery-th time
-// the one that first rebuilds the sorted scatter's cell order.
-int launch_iter(place_t *h, cudaStream_t st) {
-  const bool sort = h->exec_sort && (h->n_launch++ % kSortEvery) == 0;
-  CK(cudaGraphLaunch(sort ? h->exec_sort : h->exec, st));
+  h->graph = g;
+  CK(cudaGraphInstantiate(&h->exec, g, 0));
   return PLACE_OK;
 }
 
@@ -705,8 +662,8 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     return fail(PLACE_EINVAL, "max_backtracks must be in [0, 64]");
   if (prm.stretch != 0 && prm.stretch != 1) return fail(PLACE_EINVAL, "stretch must be 0 or 1");
   if (prm.autotune != 0 && prm.autotune != 1) return fail(PLACE_EINVAL, "autotune must be 0 or 1");
-  if (prm.scatter_mode < -1 || prm.scatter_mode > 3)
-    return fail(PLACE_EINVAL, "scatter_mode must be -1, 0, 1, 2 or 3");
+  if (prm.scatter_mode < -1 || prm.scatter_mode > 2)
+    return fail(PLACE_EINVAL, "scatter_mode must be -1, 0, 1 or 2");
   if (prm.gemm_bn != 0 && prm.gemm_bn != 64 && prm.gemm_bn != 128)
     return fail(PLACE_EINVAL, "gemm_bn must be 0, 64 or 128");
   if (prm.wa_big_cap != 0 && (prm.wa_big_cap < 32 || prm.wa_big_cap > 6144))
@@ -923,7 +880,6 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   d.wa_streams = prm.wa_streams ? prm.wa_streams : 1;  // fixed rule: one chain
   d.scat_t1 = kScatterMergedBelow;
   d.scat_t2 = kScatterTableBelow;
-  d.scat_ts = kScatterSortedFrom;
   d.scat_force = prm.scatter_mode;
   // pins and charge per optimiser cell for the preconditioner
   // max(1, pins_i + lambda area_i); a movable macro's charge is weighted by
@@ -1079,10 +1035,6 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   if (ce == cudaSuccess)
     ce = cudaMemsetAsync(d.gacc, 0, sizeof(unsigned long long) * (size_t)d.K * std::max(Mo, 1), h->stream);
   if (ce == cudaSuccess && wa_prepare(d.wa_big_cap)) ce = cudaErrorInvalidValue;
-  if (ce == cudaSuccess) {
-    launch_sort_identity(d, h->stream);  // any order is valid; this one until the first sort
-    ce = cudaGetLastError();
-  }
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.cs, 0, sizeof(CopyState) * d.K, h->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.ctr, 0, sizeof(unsigned int) * d.K * C_COUNT, h->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(d.err, 0, 4 * sizeof(int), h->stream);
@@ -1163,7 +1115,6 @@ int place_get_info(const place_t *h, place_info *o) {
   o->autotune_ms = h->autotune_ms;
   o->wa_streams = d.wa_streams;
   o->reserved = 0;
-  o->scatter_ts = d.scat_ts;
   return PLACE_OK;
 }
 
@@ -1174,8 +1125,7 @@ int place_step(place_t *h, int32_t n_iters, int32_t *converged) {
   if (n_iters > 0) {
     int rc = ensure_graph(h);
     if (rc) return rc;
-    for (int i = 0; i < n_iters; ++i)
-      if ((rc = launch_iter(h, h->stream))) return rc;
+    for (int i = 0; i < n_iters; ++i) CK(cudaGraphLaunch(h->exec, h->stream));
   }
   if (converged) {
     std::vector<CopyState> cs(h->d.K);
@@ -1224,9 +1174,6 @@ int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms) {
   int rc = PLACE_OK;
   for (int it = 0; it < n_iters && rc == PLACE_OK; ++it) {
     cudaEventRecord(ev[0], st);
-    // the density stage includes the sorted scatter's order rebuild when due
-    if (uses_sorted_scatter(d) && (h->n_launch++ % kSortEvery) == 0)
-      launch_cell_sort(d, 0, K, d.scat_force == SCAT_SORTED, st);
     cudaMemsetAsync(d.M, 0, sizeof(unsigned long long) * (size_t)d.Gm * K, st);
     launch_scatter(d, 0, K, 0, st);
     launch_density_finish(d, 0, K, FIN_ITER, st);
@@ -1835,8 +1782,7 @@ int step_async(place_t *h, int n, int *stopped_host, cudaEvent_t ev) {
   if (n > 0) {
     int rc = ensure_graph(h);
     if (rc) return rc;
-    for (int i = 0; i < n; ++i)
-      if ((rc = launch_iter(h, h->stream))) return rc;
+    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(h->exec, h->stream));
   }
   for (int c = 0; c < h->d.K; ++c)
     CK(cudaMemcpyAsync(stopped_host + c, &h->d.cs[c].stopped, sizeof(int), cudaMemcpyDeviceToHost,

@@ -15,10 +15,9 @@
 //  These run beside other kernels of the iteration (the wirelength branch and
 //  the density/spectral branch share the GPU), so they are timed as whole
 //  iterations of the captured graph, every candidate from the same start;
-//  * the effective-bin thresholds at which the density scatter switches
-//    from merging a warp's shared bins to the shared-memory table, from the
-//    table to direct atomics, and to the table over cells in tile order (the
-//    order's rebuild, every kSortEvery iterations, is charged to it).  The scatter's cost depends on how
+//  * the two effective-bin thresholds at which the density scatter switches
+//    from merging a warp's shared bins to the shared-memory table and from
+//    the table to direct atomics.  The scatter's cost depends on how
 //    concentrated the cells are, which changes during a placement, so the
 //    three ways are timed on centred Gaussian clouds of the design's own cells
 //    at widths that span the phases of a placement, and the thresholds are
@@ -151,7 +150,6 @@ int autotune(Dev &d, int max_deg, cudaStream_t st, const TuneHooks &hk, TuneOut 
       d.wa_streams = out->wa_streams;
       d.scat_t1 = out->t1;
       d.scat_t2 = out->t2;
-      d.scat_ts = out->ts;
       return d.tc ? hk.encode_maps(hk.ctx) : 0;
     }
   }
@@ -257,7 +255,7 @@ int autotune(Dev &d, int max_deg, cudaStream_t st, const TuneHooks &hk, TuneOut 
   if (d.prm.scatter_mode < 0 && d.n_mov > 0) {
     constexpr int nl = 10;
     std::vector<double> neff(nl);
-    std::vector<float> tmode[4];
+    std::vector<float> tmode[3];
     for (auto &v : tmode) v.assign(nl, 0.f);
     const size_t mbytes = sizeof(unsigned long long) * (size_t)d.Gm;
     const int blocks = std::max(1, std::min((d.n_mov + kThreads - 1) / kThreads, kMaxCellBlocks));
@@ -284,14 +282,6 @@ int autotune(Dev &d, int max_deg, cudaStream_t st, const TuneHooks &hk, TuneOut 
         if (t < 0.f) return PLACE_ECUDA;
         tmode[m][l] = t;
       }
-      // the sorted way: the scatter over the cloud in tile order, plus its
-      // share of one rebuild of that order
-      const float tsort = tm.best(2, [&] { launch_cell_sort(d, 0, 1, 1, st); }, [] {});
-      d.scat_force = SCAT_SORTED;
-      const float t = tm.best(3, [&] { launch_scatter_main(d, 0, 1, 1, st); },
-                              [&] { cudaMemsetAsync(d.M, 0, mbytes, st); });
-      if (t < 0.f || tsort < 0.f) return PLACE_ECUDA;
-      tmode[SCAT_SORTED][l] = t + tsort / kSortEvery;
     }
     d.scat_force = -1;
     // where one way stops being slower than another: the zero of their time
@@ -311,14 +301,6 @@ int autotune(Dev &d, int max_deg, cudaStream_t st, const TuneHooks &hk, TuneOut 
     const double t2 = crossing(SCAT_TABLE, SCAT_DIRECT);
     d.scat_t1 = std::min(t1, t2);
     d.scat_t2 = t2;
-    // the sorted way from the widest cloud on from which it beats the way the
-    // thresholds above pick there, in every wider cloud too (by the margin)
-    d.scat_ts = 1e300;
-    for (int l = nl - 1; l >= 0; --l) {
-      const int m = neff[l] < d.scat_t1 ? SCAT_MERGED : (neff[l] < d.scat_t2 ? SCAT_TABLE : SCAT_DIRECT);
-      if (!(tmode[SCAT_SORTED][l] < tmode[m][l] * (1.f - kTuneMargin))) break;
-      d.scat_ts = l > 0 ? std::sqrt(neff[l - 1] * neff[l]) : 0.5 * neff[0];
-    }
   }
 
   out->cached = 0;
@@ -330,7 +312,6 @@ int autotune(Dev &d, int max_deg, cudaStream_t st, const TuneHooks &hk, TuneOut 
   out->wa_streams = d.wa_streams;
   out->t1 = d.scat_t1;
   out->t2 = d.scat_t2;
-  out->ts = d.scat_ts;
   out->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   std::lock_guard<std::mutex> lk(g_mu);
   g_cache[key] = *out;

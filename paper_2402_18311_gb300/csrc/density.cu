@@ -108,9 +108,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
   // map index of cell i's bin b: b for a movable cell, G + b for a filler
   // (the fillers' map follows the movable one)
   const int mode = d.scat_force >= 0 ? d.scat_force
-                   : n_eff >= d.scat_ts ? SCAT_SORTED
-                   : (n_eff < d.scat_t1 ? SCAT_MERGED
-                                        : (n_eff < d.scat_t2 ? SCAT_TABLE : SCAT_DIRECT));
+                                     : (n_eff < d.scat_t1 ? SCAT_MERGED
+                                                          : (n_eff < d.scat_t2 ? SCAT_TABLE : SCAT_DIRECT));
   if (mode == SCAT_DIRECT) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += stride) {
       const int mo = i < d.n_real ? 0 : d.G;
@@ -131,32 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(Dev d, int copy0, int eval
     }
     return;
   }
-  if (mode == SCAT_SORTED) {
-    // a contiguous run of the sorted order per block: its cells lie in a few
-    // neighbouring tiles, so most of their terms meet in the block's table
-    // and the flush adds one 64-bit value per distinct bin
-    const int *perm = d.sperm + (size_t)c * d.n_mov;
-    const int chunk = (d.n_mov + gridDim.x - 1) / gridDim.x;
-    const int j1 = min(d.n_mov, (blockIdx.x + 1) * chunk);
-    for (int j = blockIdx.x * chunk + threadIdx.x; j < j1; j += blockDim.x) {
-      int i = perm[j];
-      HP_FIX(d.err, i, d.n_mov, BS_PERM);
-      const int mo = i < d.n_real ? 0 : d.G;
-      const float2 v = xy[i];
-      const QRect32 r = qrect32(v.x, v.y, d.Wq[i], d.Hq[i], d.scale, d.XL, d.YL, d.BW32, d.BH32,
-                                d.nx, d.ny, d.ibw_q, d.ibh_q);
-      for (int ix = r.ix0; ix <= r.ix1; ++ix) {
-        const int ox = overlap32(r.x0, r.x1, ix, d.BW32);
-        if (ox == 0) continue;
-        for (int iy = r.iy0; iy <= r.iy1; ++iy) {
-          const int oy = overlap32(r.y0, r.y1, iy, d.BH32);
-          if (oy == 0) continue;
-          hash_add(keys, vals, M, mo + ix * d.ny + iy, (unsigned long long)((long long)ox * oy),
-                   d.err, d.Gm);
-        }
-      }
-    }
-  } else if (mode == SCAT_TABLE) {
+  if (mode == SCAT_TABLE) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += stride) {
       const int mo = i < d.n_real ? 0 : d.G;
       const float2 v = xy[i];
@@ -446,109 +420,6 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
     }
     d.ctr[(size_t)c * C_COUNT + C_FINISH] = 0u;
   }
-}
-
-// ---- the sorted scatter's cell order --------------------------------------
-// A counting sort of the cells by tile: count per tile, exclusive scan, place.
-// Lanes of a warp with the same tile are merged (one atomic per tile and
-// warp).  The order within a tile depends on the atomics' order, which does
-// not matter: every order adds the same integers to the map.
-
-__device__ __forceinline__ int sort_key(const Dev &d, float2 v, int i) {
-  const int ix = min(max((int)floorf((v.x - d.fxl) * d.fibw), 0), d.nx - 1) >> kSortTileShift;
-  const int iy = min(max((int)floorf((v.y - d.fyl) * d.fibh), 0), d.ny - 1) >> kSortTileShift;
-  return (i < d.n_real ? 0 : d.s_ntiles) + ix * d.s_nty + iy;
-}
-
-// A copy is sorted from half the sorted way's threshold on, so that its
-// order is at most kSortEvery iterations old when the way takes over.
-__device__ __forceinline__ bool sort_this_copy(const Dev &d, int c, int force) {
-  return force || (!d.cs[c].stopped && d.cs[c].n_eff >= 0.5 * d.scat_ts);
-}
-
-__global__ void __launch_bounds__(kThreads) k_sort_count(Dev d, int copy0, int force) {
-  const int c = copy0 + blockIdx.y;
-  if (!sort_this_copy(d, c, force)) return;
-  const float2 *xy = d.xy + (size_t)c * d.n_cells;
-  unsigned int *cnt = d.scnt + (size_t)c * d.s_nkeys;
-  const int lane = threadIdx.x & 31;
-  for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < d.n_mov;
-       i0 += gridDim.x * blockDim.x) {
-    const int i = i0 + lane;
-    const int key = i < d.n_mov ? sort_key(d, xy[i], i) : -1;
-    const unsigned int mask = __match_any_sync(0xffffffffu, key);
-    if (key >= 0 && lane == __ffs(mask) - 1 && HP_IN(d.err, key, d.s_nkeys, BS_PERM))
-      atomicAdd(&cnt[key], (unsigned int)__popc(mask));
-  }
-}
-
-// In-place exclusive scan of one copy's counters, one block per copy.
-__global__ void __launch_bounds__(1024) k_sort_scan(Dev d, int copy0, int force) {
-  __shared__ unsigned int part[1024];
-  const int c = copy0 + blockIdx.x;
-  if (!sort_this_copy(d, c, force)) return;
-  unsigned int *cnt = d.scnt + (size_t)c * d.s_nkeys;
-  const int per = (d.s_nkeys + 1023) / 1024;
-  const int k0 = threadIdx.x * per, k1 = min(k0 + per, d.s_nkeys);
-  unsigned int s = 0;
-  for (int k = k0; k < k1; ++k) s += cnt[k];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the thread sums
-    const unsigned int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
-  }
-  unsigned int run = part[threadIdx.x] - s;
-  for (int k = k0; k < k1; ++k) {
-    const unsigned int n = cnt[k];
-    cnt[k] = run;
-    run += n;
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) k_sort_place(Dev d, int copy0, int force) {
-  const int c = copy0 + blockIdx.y;
-  if (!sort_this_copy(d, c, force)) return;
-  const float2 *xy = d.xy + (size_t)c * d.n_cells;
-  unsigned int *cnt = d.scnt + (size_t)c * d.s_nkeys;
-  int *perm = d.sperm + (size_t)c * d.n_mov;
-  const int lane = threadIdx.x & 31;
-  for (int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < d.n_mov;
-       i0 += gridDim.x * blockDim.x) {
-    const int i = i0 + lane;
-    const int key = i < d.n_mov ? sort_key(d, xy[i], i) : -1;
-    const unsigned int mask = __match_any_sync(0xffffffffu, key);
-    const int lead = __ffs(mask) - 1;
-    unsigned int base = 0;
-    if (key >= 0 && lane == lead && HP_IN(d.err, key, d.s_nkeys, BS_PERM))
-      base = atomicAdd(&cnt[key], (unsigned int)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, lead);
-    const unsigned int pos = base + (unsigned int)__popc(mask & ((1u << lane) - 1u));
-    if (key >= 0 && HP_IN(d.err, pos, d.n_mov, BS_PERM)) perm[pos] = i;
-  }
-}
-
-__global__ void k_sort_identity(Dev d) {
-  for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < (size_t)d.K * d.n_mov;
-       j += (size_t)gridDim.x * blockDim.x)
-    d.sperm[j] = (int)(j % (size_t)d.n_mov);
-}
-
-void launch_cell_sort(const Dev &d, int copy0, int ncopy, int force, cudaStream_t st) {
-  if (!d.sperm || d.n_mov == 0) return;
-  cudaMemsetAsync(d.scnt + (size_t)copy0 * d.s_nkeys, 0,
-                  sizeof(unsigned int) * (size_t)d.s_nkeys * ncopy, st);
-  const dim3 grid(d.cell_blocks, ncopy);
-  k_sort_count<<<grid, kThreads, 0, st>>>(d, copy0, force);
-  k_sort_scan<<<ncopy, 1024, 0, st>>>(d, copy0, force);
-  k_sort_place<<<grid, kThreads, 0, st>>>(d, copy0, force);
-}
-
-void launch_sort_identity(const Dev &d, cudaStream_t st) {
-  if (!d.sperm || d.n_mov == 0) return;
-  k_sort_identity<<<1024, kThreads, 0, st>>>(d);
 }
 
 void launch_scatter_main(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st) {

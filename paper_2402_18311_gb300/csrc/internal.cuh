@@ -61,12 +61,7 @@ enum Slot { S_TAU = 0, S_HPWL, S_WL, S_GW1, S_GD1, S_DG2, S_DV2, S_G2, S_HP64, S
 enum Counter { C_FINISH = 0, C_CELL, C_PRE0, C_UPDATE, C_COUNT };
 
 // The density scatter's ways of adding overlaps to the map (density.cu).
-enum ScatterMode { SCAT_MERGED = 0, SCAT_TABLE = 1, SCAT_DIRECT = 2, SCAT_SORTED = 3 };
-
-// The sorted scatter's cell order: cells grouped by the 8 x 8-bin tile of
-// their lower-left bin, rebuilt every kSortEvery iterations.
-constexpr int kSortTileShift = 3;
-constexpr int kSortEvery = 8;
+enum ScatterMode { SCAT_MERGED = 0, SCAT_TABLE = 1, SCAT_DIRECT = 2 };
 
 // What the density-finish kernel does with the overflow it reduces.
 enum FinishMode { FIN_ITER = 0, FIN_EVAL = 1, FIN_RESET = 2 };
@@ -191,14 +186,9 @@ struct Dev {
   int wa_big_cap;             // pins of a > 256-pin net kept in shared memory
   int wa_streams;             // graph branches of the WA classes (1..3, wa_branch_of)
   // density scatter: SCAT_MERGED below n_eff scat_t1, SCAT_TABLE below scat_t2,
-  // SCAT_DIRECT above, SCAT_SORTED from scat_ts on (it overrides the other
-  // two); scat_force >= 0 forces one way (tuning)
-  double scat_t1, scat_t2, scat_ts;
+  // SCAT_DIRECT above; scat_force >= 0 forces one way (tuning)
+  double scat_t1, scat_t2;
   int scat_force;
-  // the sorted way's cell order per copy and its tile counters
-  int *sperm;                // [K][n_mov]
-  unsigned int *scnt;        // [K][s_nkeys]
-  int s_nty, s_ntiles, s_nkeys;  // tiles per column, per map, keys (fillers: two maps)
 };
 
 // WireMask tables (built at create) and scratch (allocated on first use).
@@ -283,11 +273,6 @@ int wa_prepare(int cap);
 void launch_wa_floor(const Dev &d, int copy0, int ncopy, cudaStream_t st);
 void launch_wa_class(const Dev &d, int cls, int copy0, int ncopy, int eval, cudaStream_t st);
 void launch_scatter_main(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
-// Rebuild the sorted scatter's cell order of copies [copy0, copy0 + ncopy)
-// whose last density pass reached scat_ts effective bins (all of them when
-// force != 0).
-void launch_cell_sort(const Dev &d, int copy0, int ncopy, int force, cudaStream_t st);
-void launch_sort_identity(const Dev &d, cudaStream_t st);
 
 // Create-time tuning (autotune.cu).  Chooses, for the knobs the caller left
 // automatic, the tensor-core GEMM tile width, the big-net shared-memory cap
@@ -299,7 +284,7 @@ struct TuneOut {
   int split[4];
   int cap;
   int wa_streams;
-  double t1, t2, ts;
+  double t1, t2;
   double ms;     // host time spent
   int cached;    // 1: taken from the process-wide cache
 };

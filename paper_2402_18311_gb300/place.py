@@ -80,8 +80,7 @@ class place_info(ct.Structure):
                 ("gemm_bn", ct.c_int32 * 4), ("gemm_split", ct.c_int32 * 4),
                 ("wa_big_cap", ct.c_int32), ("autotuned", ct.c_int32),
                 ("scatter_t1", ct.c_double), ("scatter_t2", ct.c_double),
-                ("autotune_ms", ct.c_double), ("wa_streams", ct.c_int32), ("reserved", ct.c_int32),
-                ("scatter_ts", ct.c_double)]
+                ("autotune_ms", ct.c_double), ("wa_streams", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class place_state(ct.Structure):

@@ -66,7 +66,7 @@ def test_struct_sizes_match_header_layout():
     assert ct.sizeof(place.place_netlist) == 4 * 4 + 10 * 8
     assert ct.sizeof(place.place_params) == 22 * 4
     assert ct.sizeof(place.place_state) == 4 * 4 + 7 * 8
-    assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 4 * 4 + 10 * 4 + 3 * 8 + 2 * 4 + 8
+    assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 4 * 4 + 10 * 4 + 3 * 8 + 2 * 4
     assert ct.sizeof(place.place_job) == 4 * 4 + 8 + 8 + 8 + 8
     assert ct.sizeof(place.place_job_result) == 8 + 4 * 4 + 5 * 8 + 8 + 8
 
@@ -147,7 +147,7 @@ def test_create_rejects_bad_params(L):
     with pytest.raises(place.PlaceError) as ei:
         place.place_create(d, place.place_default_params(stretch=2))
     assert ei.value.code == place.PLACE_EINVAL and "stretch" in str(ei.value)
-    for field, bad in (("autotune", 2), ("scatter_mode", 4), ("gemm_bn", 96), ("wa_big_cap", 16),
+    for field, bad in (("autotune", 2), ("scatter_mode", 3), ("gemm_bn", 96), ("wa_big_cap", 16),
                        ("gemm_split", 3), ("fillers", 2), ("macro_precond", 0.0),
                        ("wa_streams", 4)):
         with pytest.raises(place.PlaceError) as ei:

@@ -806,16 +806,14 @@ def test_stages_scaled_20k_with_big_nets():
         h.close()
 
 
-@pytest.mark.parametrize("mode", [-1, 0, 1, 2, 3])
+@pytest.mark.parametrize("mode", [-1, 0, 1, 2])
 def test_density_map_bit_exact_on_every_scatter_path(mode):
-    # Four ways to build the map (chosen per pass from the previous pass's
+    # Three ways to build the map (chosen per pass from the previous pass's
     # effective number of occupied bins, (sum M)^2 / sum M^2, or forced):
-    # warp match/reduce plus a shared-memory table, the table alone, direct
-    # atomics, and the table over the cells in tile order (that order is
-    # rebuilt every 8 iterations by a counting sort; a stale or a fresh one
-    # must give the same map).  Each must give the oracle's map bit for bit,
-    # on two concentrated clusters far apart, on the centred start and while
-    # the placement spreads.
+    # warp match/reduce plus a shared-memory table, the table alone, and
+    # direct atomics.  Each must give the oracle's map bit for bit, on two
+    # concentrated clusters far apart, on the centred start and while the
+    # placement spreads.
     d = synth.scaled(20000, 128, seed=2)
     h = Handle(d, tau_stop=-1.0, max_iters=5000, scatter_mode=mode, autotune=0)
     n = d.n_movable
@@ -845,7 +843,7 @@ def test_density_map_bit_exact_on_every_scatter_path(mode):
         M = check_map(x2, y2)
         assert n_eff_of(M) < 256
         assert place.place_get_state(h.h, 0).bins_effective == pytest.approx(n_eff_of(M), rel=1e-3)
-        place.place_step(h.h, 9)  # the sorted way's order rebuilt on the clusters
+        place.place_step(h.h, 9)
         check_map(*h.pos())
         # the centred start (concentrated), then spreading until direct atomics
         place.place_set_positions(h.h, 0, x, y)
@@ -992,8 +990,7 @@ def test_tuning_candidates_give_identical_results():
     # scatter's three ways add the same integers; the GEMM tile width, split-K
     # over two CTAs (each half of the contraction accumulates alone either
     # way, and the halves are added once) and the big-net cache size change
-    # neither the operations nor their order per output element; the sorted
-    # way adds the same integers in another order; the WA
+    # neither the operations nor their order per output element; the WA
     # classes on one, two or three graph branches add the same integer
     # gradient sums.  Forced candidates and the tuned choice must therefore
     # give bit-identical maps and positions over a placement that passes
@@ -1005,7 +1002,6 @@ def test_tuning_candidates_give_identical_results():
                dict(autotune=0, gemm_bn=128, scatter_mode=2, wa_big_cap=1024, wa_streams=3),
                dict(autotune=0, gemm_bn=128, gemm_split=2, scatter_mode=1, wa_big_cap=2048,
                     wa_streams=1),
-               dict(autotune=0, gemm_bn=128, scatter_mode=3, wa_big_cap=3072, wa_streams=1),
                dict(autotune=1)]
     ref = None
     for cfg in configs:
