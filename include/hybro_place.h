@@ -430,6 +430,15 @@ int place_measure_wa_floor(place_t *h, int32_t reps, float *ms);
  * without the tensor-core path.  Synchronises; takes about two seconds. */
 int place_test_wait_timeout(place_t *h);
 
+/* Failure-path check of the index checks of the bounds-checking build
+ * (place_info.bounds_checked): one thread tests the index n_cells against
+ * the cell count, as a kernel would before a position gather, and touches
+ * no memory with it.  The check fails, so this call returns PLACE_EINTERNAL
+ * (the expected outcome) with the site and the index in place_last_error(),
+ * and the flag is cleared.  EINVAL in the normal build, which has no index
+ * checks.  Synchronises. */
+int place_test_bounds_check(place_t *h);
+
 /* Density map and overflow of a placement without any device allocation.
  *
  * The paper has no counterpart to this function: it serves callers that

@@ -1217,6 +1217,19 @@ int place_test_wait_timeout(place_t *h) {
   return rc;
 }
 
+int place_test_bounds_check(place_t *h) {
+  if (!h) return fail(PLACE_EINVAL, "null handle");
+#ifndef PLACE_DEBUG_BOUNDS
+  return fail(PLACE_EINVAL, "this library was built without index checks");
+#else
+  NvtxRange nvtx_("place_test_bounds_check");
+  launch_test_bounds(h->d, h->stream);
+  CKL();
+  CK(cudaStreamSynchronize(h->stream));
+  return check_dev_err(h);  // reports and clears the failed check
+#endif
+}
+
 int place_measure_wa_floor(place_t *h, int32_t reps, float *ms) {
   if (!h || !ms) return fail(PLACE_EINVAL, "null argument");
   if (reps < 1) return fail(PLACE_EINVAL, "reps < 1");

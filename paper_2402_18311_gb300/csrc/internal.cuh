@@ -261,6 +261,7 @@ void launch_unpack_xy(float *x, float *y, const float2 *src, int n, cudaStream_t
 void launch_density_finish(const Dev &d, int copy0, int ncopy, int mode, cudaStream_t st);
 void launch_spectral(const Dev &d, int copy0, int ncopy, int with_psi, int eval, cudaStream_t st);
 void launch_spectral_tc_stalled(const Dev &d, cudaStream_t st);
+void launch_test_bounds(const Dev &d, cudaStream_t st);
 void launch_wa(const Dev &d, int copy0, int ncopy, int eval, const float *gamma_override,
                cudaStream_t st);
 // The WA classes of an iteration on d.wa_streams branches: branch b's classes

@@ -443,6 +443,15 @@ void launch_cell_grad(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t
   else
     launch_pdl(k_cell_grad<false>, dim3(d.cg_blocks, ncopy), dim3(kThreads), 0, st, d, copy0, eval);
 }
+// One failing index check and no access (place_test_bounds_check).
+__global__ void k_test_bounds(Dev d) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const long long i = d.n_cells;  // one past the last cell
+    if (HP_IN(d.err, i, d.n_cells, BS_WA_CELL)) d.err[1] = 0;  // (reached only when it passes)
+  }
+}
+void launch_test_bounds(const Dev &d, cudaStream_t st) { k_test_bounds<<<1, 32, 0, st>>>(d); }
+
 int cell_grad_blocks_per_sm() {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cell_grad<false>, kThreads, 0) != cudaSuccess || n < 1)

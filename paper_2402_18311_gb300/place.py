@@ -147,6 +147,7 @@ _SIGS = {
     "place_step_timed": (ct.c_int, [_VP, ct.c_int32, _VP]),
     "place_measure_wa_floor": (ct.c_int, [_VP, ct.c_int32, ct.POINTER(ct.c_float)]),
     "place_test_wait_timeout": (ct.c_int, [_VP]),
+    "place_test_bounds_check": (ct.c_int, [_VP]),
     "place_get_hybro_rounds": (ct.c_int, [_VP, ct.c_int32, _VP, _VP, ct.c_int32,
                                           ct.POINTER(ct.c_int32)]),
     "place_overflow_noalloc": (ct.c_int, [_VP, _VP, _VP, _VP, ct.c_int32,
@@ -405,6 +406,12 @@ def place_estimate_device_bytes(design, params=None):
     _check(lib().place_estimate_device_bytes(ct.byref(nl), ct.byref(die), ct.byref(bins),
                                              ct.byref(prm), ct.byref(b)))
     return b.value
+
+
+def place_test_bounds_check(h):
+    """The C return code (PLACE_EINTERNAL expected in the bounds-checking
+    build, PLACE_EINVAL in the normal one); does not raise."""
+    return lib().place_test_bounds_check(h)
 
 
 def place_test_wait_timeout(h):

@@ -61,6 +61,14 @@ for mode in (-1, 0, 1, 2):
     evals(f"tiny_scatter{mode}", h, d)
     place.place_destroy(h)
 
+# the failure path: a check that fails (no access is made with the index)
+h = place.place_create(d, place.place_default_params(tau_stop=-1.0, max_iters=10**6))
+rc = place.place_test_bounds_check(h)
+msg = place.place_last_error()
+place.place_step(h, 5)  # the handle stays usable; the flag was cleared
+failpath = {"rc": rc, "msg": msg}
+place.place_destroy(h)
+
 # mixed-size: Shuffle (macros), WireMask, Hybro rounds, knobs
 d = synth.mixed_size_1k(0)
 h = place.place_create(d, place.place_default_params(tau_stop=0.1, max_iters=400, n_copies=2,
@@ -104,7 +112,7 @@ mp = torch.zeros(d.nx * d.ny, dtype=torch.int64, device="cuda")
 place.place_overflow_noalloc(x, y, w, hh, n, d.die, (d.nx, d.ny, d.target_density), 8, None, ov, mp)
 torch.cuda.synchronize()
 out["noalloc"] = {"tau": float(ov.item()), "map": hsh(mp.cpu().numpy())}
-print(json.dumps({"checked": checked, "out": out}))
+print(json.dumps({"checked": checked, "out": out, "failpath": failpath}))
 """
 
 
@@ -125,5 +133,9 @@ def test_bounds_checked_build_passes_and_matches_the_normal_build():
     ref = _run(False)
     assert all(v == 1 for v in chk["checked"]), chk["checked"]
     assert all(v == 0 for v in ref["checked"]), ref["checked"]
+    # a failing check is reported with its site and index, and only there
+    assert chk["failpath"]["rc"] == place.PLACE_EINTERNAL, chk["failpath"]
+    assert "WA: a pin's cell" in chk["failpath"]["msg"]
+    assert ref["failpath"]["rc"] == place.PLACE_EINVAL
     for k, v in ref["out"].items():
         assert chk["out"][k] == v, k
