@@ -364,8 +364,11 @@ int place_server_run(place_server *s, double timeout_s, double *makespan_s) {
       if (q != cudaSuccess) return sfail(PLACE_ECUDA, "job %lld: %s", (long long)j->id, cudaGetErrorString(q));
       progress = true;
       j->in_flight = false;
+      // a job that stopped by itself in this chunk counts as finished even
+      // when its budget ran out with it
       const int status = j->cancel.load() ? PLACE_JOB_CANCELLED
-                         : (j->spec.max_seconds > 0 && now - j->admit_s > j->spec.max_seconds)
+                         : (!*j->flags && j->spec.max_seconds > 0 &&
+                            now - j->admit_s > j->spec.max_seconds)
                              ? PLACE_JOB_EXPIRED
                              : PLACE_JOB_FINISHED;
       if (*j->flags || status != PLACE_JOB_FINISHED) {
