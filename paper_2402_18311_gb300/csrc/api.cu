@@ -70,6 +70,10 @@ int degree_class(int deg) {
   return 4;
 }
 constexpr int kNetsPerBlock[4] = {256, 64, 16, 8};
+// degree up to which a group class's net runs on half its lanes (4-lane class:
+// 2 lanes for up to 8 pins; 16-lane class: 8 lanes for up to 32 pins; the
+// warp class is not split)
+constexpr int kGroupHalfDeg[4] = {0, 8, 32, 256};
 // pins of a big net kept in shared memory: 3072 (24 KB) is the most that
 // still lets eight 256-thread blocks share an SM; longer nets re-gather the rest
 constexpr int kBigCapMax = 3072;
@@ -821,9 +825,29 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
       for (int j = nl->net_ptr[e]; j < nl->net_ptr[e + 1]; ++j) m = std::min(m, nl->pin_cell[j]);
       min_cell[e] = m;
     }
-    for (int c = 0; c < 4; ++c)
+    // the one-thread class by degree first, so that a warp's nets have one
+    // degree (2-pin nets take a closed form, 3- and 4-pin nets their own
+    // unrolled path) and only the warps at the two boundaries mix them
+    std::stable_sort(order.begin() + d.cls_begin[0], order.begin() + d.cls_begin[1],
+                     [&](int a, int b) {
+                       return deg(a) != deg(b) ? deg(a) < deg(b) : min_cell[a] < min_cell[b];
+                     });
+    // the group classes in two sub-ranges, each by lowest cell: the nets of
+    // up to half the class's lane slots first (they run on half the lanes)
+    for (int c = 1; c < 4; ++c) {
+      const int half = kGroupHalfDeg[c];
       std::stable_sort(order.begin() + d.cls_begin[c], order.begin() + d.cls_begin[c + 1],
-                       [&](int a, int b) { return min_cell[a] < min_cell[b]; });
+                       [&](int a, int b) {
+                         const bool ha = deg(a) > half, hb = deg(b) > half;
+                         return ha != hb ? hb : min_cell[a] < min_cell[b];
+                       });
+    }
+    for (int c = 0; c < 8; ++c) d.cls_split[c] = c < 6 ? d.cls_begin[std::min(c + 1, 5)] : 0;
+    for (int c = 1; c < 4; ++c) {
+      int e = d.cls_begin[c];
+      while (e < d.cls_begin[c + 1] && deg(order[e]) <= kGroupHalfDeg[c]) ++e;
+      d.cls_split[c] = e;
+    }
   }
   std::vector<int> net_ptr(E + 1), pin_cell(P);
   std::vector<float2> pin_off(P);

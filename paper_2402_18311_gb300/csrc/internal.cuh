@@ -179,6 +179,7 @@ struct Dev {
 
   // WA launch plan: nets [cls_begin[c], cls_begin[c+1]) belong to class c
   int cls_begin[8];
+  int cls_split[8];           // the group classes' second sub-range (nets on more lanes)
   int n_cls;
   int wa_blocks[8];           // blocks per class per copy
   int wa_block_base[8];       // slot offset of the class's blocks

@@ -56,32 +56,11 @@ __device__ __forceinline__ float copy_gamma(const Dev &d, int c, const float *ov
   return ovr ? *ovr : (float)d.cs[c].gamma;
 }
 
-// Nets of at most D pins: one thread per net, pins held in registers, no
-// shuffles (most nets of a netlist have 2 or 3 pins).
+// One net of deg <= D pins on one thread, pins held in registers, no shuffles.
 template <int D>
-__global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int cls, int eval,
-                                                            const float *gamma_ovr) {
-  __shared__ float2 sm[32];
-  pdl_wait();
-  const int c = copy0 + blockIdx.y;
-  if (!eval && d.cs[c].stopped) return;
-  const float g = copy_gamma(d, c, gamma_ovr);
-  const float ig = 1.0f / g;
-  const float2 *xy = d.xy + (size_t)c * d.n_cells;
-  unsigned long long *ga = d.gacc + (size_t)c * d.n_mov;
-  const int e_end = d.cls_begin[cls + 1];
-  // each thread sums its few nets in FP32; the block sum is compensated (the
-  // HPWL sum drives the lambda schedule through differences of consecutive
-  // iterations)
-  float hp_acc = 0.f, wl_acc = 0.f;
-  for (int e = d.cls_begin[cls] + blockIdx.x * blockDim.x + threadIdx.x; e < e_end;
-       e += gridDim.x * blockDim.x) {
-    const int p0 = d.net_ptr[e], p1 = d.net_ptr[e + 1];
-    const int deg = p1 - p0;
-    if (deg <= 0) continue;
-    if (!HP_IN(d.err, p0, d.n_pins, BS_WA_PIN) || !HP_IN(d.err, p1, d.n_pins + 1, BS_WA_PIN) ||
-        !HP_IN(d.err, deg, D + 1, BS_WA_PIN))
-      continue;
+__device__ __forceinline__ void wa_net_small(const Dev &d, const float2 *xy, unsigned long long *ga,
+                                             int e, int p0, int deg, float ig, float &hp_acc,
+                                             float &wl_acc) {
     int cell[D];
     float2 off[D], pos[D];
 #pragma unroll
@@ -140,6 +119,75 @@ __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int
     }
     hp_acc += wn * ((mxx - mnx) + (mxy - mny));
     wl_acc += wn * (((mxx - mnx) + (rxp - rxm)) + ((mxy - mny) + (ryp - rym)));
+}
+
+// One 2-pin net in closed form.  Per axis, with d the second pin's
+// coordinate relative to the first, Eq. 3 reduces to
+//   WL = |d| tanh(|d| / 2g),  dWL/dp_1 = -dWL/dp_0 = sign(d) (th + (|d|/2g)(1 - th^2)),
+// th = tanh(|d|/2g) = (1 - t)/(1 + t) with t = exp(-|d|/g): one exponential
+// per axis instead of eight.  For |d| << g the difference 1 - t loses
+// relative digits, but the value and the gradient it feeds are then of
+// order |d|/g, far below the other terms of the sums they enter.
+__device__ __forceinline__ void wa_axis_2pin(float dd, float ig, float &wl, float &gr) {
+  const float ad = fabsf(dd);
+  const float t = __expf(-ad * ig);
+  const float th = (1.f - t) / (1.f + t);
+  wl = ad * th;
+  gr = copysignf(fmaf(0.5f * ad * ig, 1.f - th * th, th), dd);
+}
+
+__device__ __forceinline__ void wa_net_2pin(const Dev &d, const float2 *xy, unsigned long long *ga,
+                                            int e, int p0, float ig, float &hp_acc, float &wl_acc) {
+  int c0 = d.pin_cell[p0], c1 = d.pin_cell[p0 + 1];
+  HP_FIX(d.err, c0, d.n_cells, BS_WA_CELL);
+  HP_FIX(d.err, c1, d.n_cells, BS_WA_CELL);
+  const float2 o0 = d.pin_off[p0], o1 = d.pin_off[p0 + 1];
+  const float2 v0 = xy[c0], v1 = xy[c1];
+  const float dx = (v1.x - v0.x) + (o1.x - o0.x), dy = (v1.y - v0.y) + (o1.y - o0.y);
+  float wx, gx, wy, gy;
+  wa_axis_2pin(dx, ig, wx, gx);
+  wa_axis_2pin(dy, ig, wy, gy);
+  const float wn = d.net_w ? d.net_w[e] : 1.0f;
+  add_pin_grad(d, ga, c0, -gx * wn, -gy * wn);
+  add_pin_grad(d, ga, c1, gx * wn, gy * wn);
+  hp_acc += wn * (fabsf(dx) + fabsf(dy));
+  wl_acc += wn * (wx + wy);
+}
+
+// Nets of at most D pins: one thread per net.  The class is ordered by
+// degree, so a warp's nets share one path: the closed form for 2 pins, the
+// unrolled general form for 3 and for 4 (most nets of a netlist have 2 or 3
+// pins).
+template <int D>
+__global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int cls, int eval,
+                                                            const float *gamma_ovr) {
+  __shared__ float2 sm[32];
+  pdl_wait();
+  const int c = copy0 + blockIdx.y;
+  if (!eval && d.cs[c].stopped) return;
+  const float g = copy_gamma(d, c, gamma_ovr);
+  const float ig = 1.0f / g;
+  const float2 *xy = d.xy + (size_t)c * d.n_cells;
+  unsigned long long *ga = d.gacc + (size_t)c * d.n_mov;
+  const int e_end = d.cls_begin[cls + 1];
+  // each thread sums its few nets in FP32; the block sum is compensated (the
+  // HPWL sum drives the lambda schedule through differences of consecutive
+  // iterations)
+  float hp_acc = 0.f, wl_acc = 0.f;
+  for (int e = d.cls_begin[cls] + blockIdx.x * blockDim.x + threadIdx.x; e < e_end;
+       e += gridDim.x * blockDim.x) {
+    const int p0 = d.net_ptr[e], p1 = d.net_ptr[e + 1];
+    const int deg = p1 - p0;
+    if (deg <= 0) continue;
+    if (!HP_IN(d.err, p0, d.n_pins, BS_WA_PIN) || !HP_IN(d.err, p1, d.n_pins + 1, BS_WA_PIN) ||
+        !HP_IN(d.err, deg, D + 1, BS_WA_PIN))
+      continue;
+    if (deg == 2)
+      wa_net_2pin(d, xy, ga, e, p0, ig, hp_acc, wl_acc);
+    else if (deg == 3)
+      wa_net_small<3>(d, xy, ga, e, p0, deg, ig, hp_acc, wl_acc);
+    else
+      wa_net_small<D>(d, xy, ga, e, p0, deg, ig, hp_acc, wl_acc);
   }
   const double rh = block_sum_fc<kThreads>(hp_acc, sm);
   const double rw = block_sum_fc<kThreads>(wl_acc, sm);
@@ -150,27 +198,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int
   }
 }
 
-// Nets of at most G * PPL pins: G lanes per net, each lane holding up to PPL
-// of the net's pins in registers, so every pin is gathered once.  MINB
-// resident blocks per SM bound the registers (no spills at the chosen values).
-template <int G, int PPL, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) k_wa_group(Dev d, int copy0, int cls, int eval,
-                                                        const float *gamma_ovr) {
-  __shared__ float2 sm[32];
-  pdl_wait();
-  const int c = copy0 + blockIdx.y;
-  if (!eval && d.cs[c].stopped) return;
-  const float g = copy_gamma(d, c, gamma_ovr);
-  const float ig = 1.0f / g;
-  const float2 *xy = d.xy + (size_t)c * d.n_cells;
-  unsigned long long *ga = d.gacc + (size_t)c * d.n_mov;
-  constexpr int NPB = kThreads / G;
-  const int lane = threadIdx.x % G;
-  const int e_end = d.cls_begin[cls + 1];
-  float hp_acc = 0.f, wl_acc = 0.f;
-  for (int base = d.cls_begin[cls] + blockIdx.x * NPB; base < e_end; base += gridDim.x * NPB) {
-    const int e = base + threadIdx.x / G;
-    const bool valid = e < e_end;
+// One net of at most G * PPL pins on G lanes (lane = this thread's lane in
+// its group), each lane holding up to PPL of the net's pins in registers, so
+// every pin is gathered once.  valid: the group has a net (all G lanes of a
+// group agree).
+template <int G, int PPL>
+__device__ __forceinline__ void wa_group_net(const Dev &d, const float2 *xy, unsigned long long *ga,
+                                             int e, bool valid, int lane, float ig, float &hp_acc,
+                                             float &wl_acc) {
     int p0 = 0, p1 = 0;
     if (valid) {
       p0 = d.net_ptr[e];
@@ -246,6 +281,40 @@ __global__ void __launch_bounds__(kThreads, MINB) k_wa_group(Dev d, int copy0, i
         hp_acc += wn * ((mxx - mnx) + (mxy - mny));
         wl_acc += wn * (((mxx - mnx) + (rxp - rxm)) + ((mxy - mny) + (ryp - rym)));
       }
+    }
+  }
+
+// Nets of a degree class in two sub-ranges, the class ordered so that the
+// nets of at most GL * PPL pins come first (up to d.cls_split[cls]): those
+// on GL lanes each, the rest on G lanes.  A warp takes 32 / GL or 32 / G
+// consecutive nets of one sub-range, so the choice is warp-uniform and no
+// lane slot is spent on the short nets' empty halves.  MINB resident blocks
+// per SM bound the registers (no spills at the chosen values).
+template <int G, int GL, int PPL, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_wa_group(Dev d, int copy0, int cls, int eval,
+                                                        const float *gamma_ovr) {
+  __shared__ float2 sm[32];
+  pdl_wait();
+  const int c = copy0 + blockIdx.y;
+  if (!eval && d.cs[c].stopped) return;
+  const float g = copy_gamma(d, c, gamma_ovr);
+  const float ig = 1.0f / g;
+  const float2 *xy = d.xy + (size_t)c * d.n_cells;
+  unsigned long long *ga = d.gacc + (size_t)c * d.n_mov;
+  const int e_beg = d.cls_begin[cls], e_mid = d.cls_split[cls], e_end = d.cls_begin[cls + 1];
+  constexpr int NL = 32 / GL, NH = 32 / G;  // nets per warp task in each sub-range
+  const int tlo = (e_mid - e_beg + NL - 1) / NL;
+  const int tall = tlo + (e_end - e_mid + NH - 1) / NH;
+  const int wl = threadIdx.x & 31;
+  const int nwarps = gridDim.x * (kThreads / 32);
+  float hp_acc = 0.f, wl_acc = 0.f;
+  for (int t = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); t < tall; t += nwarps) {
+    if (t < tlo) {
+      const int e = e_beg + t * NL + wl / GL;
+      wa_group_net<GL, PPL>(d, xy, ga, e, e < e_mid, wl % GL, ig, hp_acc, wl_acc);
+    } else {
+      const int e = e_mid + (t - tlo) * NH + wl / G;
+      wa_group_net<G, PPL>(d, xy, ga, e, e < e_end, wl % G, ig, hp_acc, wl_acc);
     }
   }
   const double rh = block_sum_fc<kThreads>(hp_acc, sm);
@@ -440,16 +509,16 @@ static void launch_wa_one(const Dev &d, int cls, int copy0, int ncopy, int eval,
       else k_wa_thread<4><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
       break;
     case 1:
-      if (pdl) launch_pdl(k_wa_group<4, 4, 6>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
-      else k_wa_group<4, 4, 6><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
+      if (pdl) launch_pdl(k_wa_group<4, 2, 4, 5>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
+      else k_wa_group<4, 2, 4, 5><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
       break;
     case 2:
-      if (pdl) launch_pdl(k_wa_group<16, 4, 6>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
-      else k_wa_group<16, 4, 6><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
+      if (pdl) launch_pdl(k_wa_group<16, 8, 4, 5>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
+      else k_wa_group<16, 8, 4, 5><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
       break;
     case 3:
-      if (pdl) launch_pdl(k_wa_group<32, 8, 1>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
-      else k_wa_group<32, 8, 1><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
+      if (pdl) launch_pdl(k_wa_group<32, 32, 8, 1>, grid, blk, 0, st, d, copy0, cls, eval, gamma_ovr);
+      else k_wa_group<32, 32, 8, 1><<<grid, kThreads, 0, st>>>(d, copy0, cls, eval, gamma_ovr);
       break;
     default: {
       const size_t sm = 2 * sizeof(float) * d.wa_big_cap;
