@@ -825,9 +825,9 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
       for (int j = nl->net_ptr[e]; j < nl->net_ptr[e + 1]; ++j) m = std::min(m, nl->pin_cell[j]);
       min_cell[e] = m;
     }
-    // the one-thread class by degree first, so that a warp's nets have one
-    // degree (2-pin nets take a closed form, 3- and 4-pin nets their own
-    // unrolled path) and only the warps at the two boundaries mix them
+    // the one-thread class by degree first, so that a warp's nets take one
+    // path (2-pin nets a closed form) and only the warps at the boundaries
+    // mix them
     std::stable_sort(order.begin() + d.cls_begin[0], order.begin() + d.cls_begin[1],
                      [&](int a, int b) {
                        return deg(a) != deg(b) ? deg(a) < deg(b) : min_cell[a] < min_cell[b];

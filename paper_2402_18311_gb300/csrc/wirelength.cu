@@ -56,6 +56,38 @@ __device__ __forceinline__ float copy_gamma(const Dev &d, int c, const float *ov
   return ovr ? *ovr : (float)d.cs[c].gamma;
 }
 
+// The arithmetic of Eq. 3 per pin and per net, every operation written with
+// its rounding (no multiply-add left for the compiler to contract or not), so
+// that every build of the library computes the same bits.
+//   sums:     S+ += a, T+ += (p - m+) a, S- += b, T- += (p - m-) b
+//   gradient: (a/S+)(1 + (p - m+ - R+)/g) - (b/S-)(1 - (p - m- - R-)/g)
+__device__ __forceinline__ void wa_sums(float p, float mx, float mn, float ig, float &sp, float &tp,
+                                        float &sm, float &tm) {
+  const float dp = __fsub_rn(p, mx), dm = __fsub_rn(p, mn);
+  const float a = __expf(__fmul_rn(dp, ig)), b = __expf(__fmul_rn(__fsub_rn(mn, p), ig));
+  sp = __fadd_rn(sp, a);
+  tp = __fmaf_rn(dp, a, tp);
+  sm = __fadd_rn(sm, b);
+  tm = __fmaf_rn(dm, b, tm);
+}
+__device__ __forceinline__ float wa_grad(float p, float mx, float mn, float ig, float isp, float ism,
+                                         float rp, float rm) {
+  const float dp = __fsub_rn(p, mx), dm = __fsub_rn(p, mn);
+  const float a = __expf(__fmul_rn(dp, ig)), b = __expf(__fmul_rn(__fsub_rn(mn, p), ig));
+  const float fp = __fmaf_rn(__fsub_rn(dp, rp), ig, 1.f);
+  const float fm = __fmaf_rn(-__fsub_rn(dm, rm), ig, 1.f);
+  return __fmaf_rn(__fmul_rn(a, isp), fp, -__fmul_rn(__fmul_rn(b, ism), fm));
+}
+// a net's HPWL (its pin extents) and WA value, weighted, into the thread's sums
+__device__ __forceinline__ void wa_net_sums(float wn, float mxx, float mnx, float mxy, float mny,
+                                            float rxp, float rxm, float ryp, float rym,
+                                            float &hp_acc, float &wl_acc) {
+  const float ex = __fsub_rn(mxx, mnx), ey = __fsub_rn(mxy, mny);
+  hp_acc = __fmaf_rn(wn, __fadd_rn(ex, ey), hp_acc);
+  wl_acc = __fmaf_rn(wn, __fadd_rn(__fadd_rn(ex, __fsub_rn(rxp, rxm)), __fadd_rn(ey, __fsub_rn(ryp, rym))),
+                     wl_acc);
+}
+
 // One net of deg <= D pins on one thread, pins held in registers, no shuffles.
 template <int D>
 __device__ __forceinline__ void wa_net_small(const Dev &d, const float2 *xy, unsigned long long *ga,
@@ -96,10 +128,8 @@ __device__ __forceinline__ void wa_net_small(const Dev &d, const float2 *xy, uns
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       if (k < deg) {
-        float a = __expf((px[k] - mxx) * ig), b = __expf((mnx - px[k]) * ig);
-        sxp += a; txp += (px[k] - mxx) * a; sxm += b; txm += (px[k] - mnx) * b;
-        a = __expf((py[k] - mxy) * ig); b = __expf((mny - py[k]) * ig);
-        syp += a; typ += (py[k] - mxy) * a; sym += b; tym += (py[k] - mny) * b;
+        wa_sums(px[k], mxx, mnx, ig, sxp, txp, sxm, txm);
+        wa_sums(py[k], mxy, mny, ig, syp, typ, sym, tym);
       }
     }
     const float wn = d.net_w ? d.net_w[e] : 1.0f;
@@ -108,17 +138,12 @@ __device__ __forceinline__ void wa_net_small(const Dev &d, const float2 *xy, uns
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       if (k < deg) {
-        float a = __expf((px[k] - mxx) * ig), b = __expf((mnx - px[k]) * ig);
-        const float gx = a * isxp * (1.f + (px[k] - mxx - rxp) * ig) -
-                         b * isxm * (1.f - (px[k] - mnx - rxm) * ig);
-        a = __expf((py[k] - mxy) * ig); b = __expf((mny - py[k]) * ig);
-        const float gy = a * isyp * (1.f + (py[k] - mxy - ryp) * ig) -
-                         b * isym * (1.f - (py[k] - mny - rym) * ig);
-        add_pin_grad(d, ga, cell[k], gx * wn, gy * wn);
+        const float gx = wa_grad(px[k], mxx, mnx, ig, isxp, isxm, rxp, rxm);
+        const float gy = wa_grad(py[k], mxy, mny, ig, isyp, isym, ryp, rym);
+        add_pin_grad(d, ga, cell[k], __fmul_rn(gx, wn), __fmul_rn(gy, wn));
       }
     }
-    hp_acc += wn * ((mxx - mnx) + (mxy - mny));
-    wl_acc += wn * (((mxx - mnx) + (rxp - rxm)) + ((mxy - mny) + (ryp - rym)));
+    wa_net_sums(wn, mxx, mnx, mxy, mny, rxp, rxm, ryp, rym, hp_acc, wl_acc);
 }
 
 // One 2-pin net in closed form.  Per axis, with d the second pin's
@@ -128,12 +153,15 @@ __device__ __forceinline__ void wa_net_small(const Dev &d, const float2 *xy, uns
 // per axis instead of eight.  For |d| << g the difference 1 - t loses
 // relative digits, but the value and the gradient it feeds are then of
 // order |d|/g, far below the other terms of the sums they enter.
+// Every operation is written with its rounding (no contraction left to the
+// compiler), so the result is the same in every build of the library.
 __device__ __forceinline__ void wa_axis_2pin(float dd, float ig, float &wl, float &gr) {
   const float ad = fabsf(dd);
-  const float t = __expf(-ad * ig);
-  const float th = (1.f - t) / (1.f + t);
-  wl = ad * th;
-  gr = copysignf(fmaf(0.5f * ad * ig, 1.f - th * th, th), dd);
+  const float u = __fmul_rn(ad, ig);
+  const float t = __expf(-u);
+  const float th = __fdiv_rn(__fsub_rn(1.f, t), __fadd_rn(1.f, t));
+  wl = __fmul_rn(ad, th);
+  gr = copysignf(__fmaf_rn(__fmul_rn(0.5f, u), __fmaf_rn(-th, th, 1.f), th), dd);
 }
 
 __device__ __forceinline__ void wa_net_2pin(const Dev &d, const float2 *xy, unsigned long long *ga,
@@ -148,16 +176,17 @@ __device__ __forceinline__ void wa_net_2pin(const Dev &d, const float2 *xy, unsi
   wa_axis_2pin(dx, ig, wx, gx);
   wa_axis_2pin(dy, ig, wy, gy);
   const float wn = d.net_w ? d.net_w[e] : 1.0f;
-  add_pin_grad(d, ga, c0, -gx * wn, -gy * wn);
-  add_pin_grad(d, ga, c1, gx * wn, gy * wn);
-  hp_acc += wn * (fabsf(dx) + fabsf(dy));
-  wl_acc += wn * (wx + wy);
+  const float gxw = __fmul_rn(gx, wn), gyw = __fmul_rn(gy, wn);
+  add_pin_grad(d, ga, c0, -gxw, -gyw);
+  add_pin_grad(d, ga, c1, gxw, gyw);
+  hp_acc = __fmaf_rn(wn, __fadd_rn(fabsf(dx), fabsf(dy)), hp_acc);
+  wl_acc = __fmaf_rn(wn, __fadd_rn(wx, wy), wl_acc);
 }
 
 // Nets of at most D pins: one thread per net.  The class is ordered by
-// degree, so a warp's nets share one path: the closed form for 2 pins, the
-// unrolled general form for 3 and for 4 (most nets of a netlist have 2 or 3
-// pins).
+// degree, so a warp's nets share one path: the closed form for 2 pins (most
+// nets of a netlist), the unrolled general form otherwise (a third path for
+// 3-pin nets made the kernel spill and was slower).
 template <int D>
 __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int cls, int eval,
                                                             const float *gamma_ovr) {
@@ -184,8 +213,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_wa_thread(Dev d, int copy0, int
       continue;
     if (deg == 2)
       wa_net_2pin(d, xy, ga, e, p0, ig, hp_acc, wl_acc);
-    else if (deg == 3)
-      wa_net_small<3>(d, xy, ga, e, p0, deg, ig, hp_acc, wl_acc);
     else
       wa_net_small<D>(d, xy, ga, e, p0, deg, ig, hp_acc, wl_acc);
   }
@@ -254,10 +281,8 @@ __device__ __forceinline__ void wa_group_net(const Dev &d, const float2 *xy, uns
 #pragma unroll
     for (int k = 0; k < PPL; ++k) {
       if (cl[k] >= 0) {
-        float a = __expf((px[k] - mxx) * ig), b = __expf((mnx - px[k]) * ig);
-        sxp += a; txp += (px[k] - mxx) * a; sxm += b; txm += (px[k] - mnx) * b;
-        a = __expf((py[k] - mxy) * ig); b = __expf((mny - py[k]) * ig);
-        syp += a; typ += (py[k] - mxy) * a; sym += b; tym += (py[k] - mny) * b;
+        wa_sums(px[k], mxx, mnx, ig, sxp, txp, sxm, txm);
+        wa_sums(py[k], mxy, mny, ig, syp, typ, sym, tym);
       }
     }
     sxp = gsum<G>(sxp); txp = gsum<G>(txp); sxm = gsum<G>(sxm); txm = gsum<G>(txm);
@@ -268,19 +293,12 @@ __device__ __forceinline__ void wa_group_net(const Dev &d, const float2 *xy, uns
 #pragma unroll
       for (int k = 0; k < PPL; ++k) {
         if (cl[k] >= 0) {
-          float a = __expf((px[k] - mxx) * ig), b = __expf((mnx - px[k]) * ig);
-          const float gx = a * isxp * (1.f + (px[k] - mxx - rxp) * ig) -
-                           b * isxm * (1.f - (px[k] - mnx - rxm) * ig);
-          a = __expf((py[k] - mxy) * ig); b = __expf((mny - py[k]) * ig);
-          const float gy = a * isyp * (1.f + (py[k] - mxy - ryp) * ig) -
-                           b * isym * (1.f - (py[k] - mny - rym) * ig);
-          add_pin_grad(d, ga, cl[k], gx * wn, gy * wn);
+          const float gx = wa_grad(px[k], mxx, mnx, ig, isxp, isxm, rxp, rxm);
+          const float gy = wa_grad(py[k], mxy, mny, ig, isyp, isym, ryp, rym);
+          add_pin_grad(d, ga, cl[k], __fmul_rn(gx, wn), __fmul_rn(gy, wn));
         }
       }
-      if (lane == 0) {
-        hp_acc += wn * ((mxx - mnx) + (mxy - mny));
-        wl_acc += wn * (((mxx - mnx) + (rxp - rxm)) + ((mxy - mny) + (ryp - rym)));
-      }
+      if (lane == 0) wa_net_sums(wn, mxx, mnx, mxy, mny, rxp, rxm, ryp, rym, hp_acc, wl_acc);
     }
   }
 
@@ -412,10 +430,8 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
         const float2 v = xy[cj];
         px = (v.x - rx) + (o.x - rdx); py = (v.y - ry) + (o.y - rdy);
       }
-      float a = __expf((px - mxx) * ig), b = __expf((mnx - px) * ig);
-      s[0] += a; s[1] += (px - mxx) * a; s[2] += b; s[3] += (px - mnx) * b;
-      a = __expf((py - mxy) * ig); b = __expf((mny - py) * ig);
-      s[4] += a; s[5] += (py - mxy) * a; s[6] += b; s[7] += (py - mny) * b;
+      wa_sums(px, mxx, mnx, ig, s[0], s[1], s[2], s[3]);
+      wa_sums(py, mxy, mny, ig, s[4], s[5], s[6], s[7]);
     }
     block_all<8, false>(s, sm);
     const float isxp = 1.f / s[0], isxm = 1.f / s[2], isyp = 1.f / s[4], isym = 1.f / s[6];
@@ -432,11 +448,9 @@ __global__ void __launch_bounds__(kBigNet) k_wa_big(Dev d, int copy0, int cls, i
         const float2 v = xy[cj];
         px = (v.x - rx) + (o.x - rdx); py = (v.y - ry) + (o.y - rdy);
       }
-      float a = __expf((px - mxx) * ig), b = __expf((mnx - px) * ig);
-      const float gx = a * isxp * (1.f + (px - mxx - rxp) * ig) - b * isxm * (1.f - (px - mnx - rxm) * ig);
-      a = __expf((py - mxy) * ig); b = __expf((mny - py) * ig);
-      const float gy = a * isyp * (1.f + (py - mxy - ryp) * ig) - b * isym * (1.f - (py - mny - rym) * ig);
-      add_pin_grad(d, ga, cj, gx * wn, gy * wn);
+      const float gx = wa_grad(px, mxx, mnx, ig, isxp, isxm, rxp, rxm);
+      const float gy = wa_grad(py, mxy, mny, ig, isyp, isym, ryp, rym);
+      add_pin_grad(d, ga, cj, __fmul_rn(gx, wn), __fmul_rn(gy, wn));
     }
     hp_acc += wn * ((mxx - mnx) + (mxy - mny));
     wl_acc += wn * (((mxx - mnx) + (rxp - rxm)) + ((mxy - mny) + (ryp - rym)));

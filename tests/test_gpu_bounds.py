@@ -1,6 +1,9 @@
 """The bounds-checking build (``-DPLACE_DEBUG_BOUNDS``, in its place for
 compute-sanitizer): every index check in the kernels passes on the library's
-workloads, and the results are bit-identical to those of the normal build.
+workloads, and the results are bit-identical to those of the normal build
+(the kernels write their floating-point arithmetic with explicit rounding
+where a multiply-add could be contracted either way, so both builds compute
+the same bits).
 
 Each build runs in a child process (the binding loads one library per
 process), through the same script; the script raises on any non-zero return
