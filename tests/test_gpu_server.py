@@ -202,3 +202,30 @@ def test_cancelling_a_running_job_stops_it_and_leaves_the_others_alone():
     assert res[a].status == place.PLACE_JOB_FINISHED
     ra = _alone(ds[0], params())
     assert (res[a].position_hash, res[a].iterations) == (ra.position_hash, ra.iterations)
+
+
+def test_cancelling_one_restart_of_a_resident_parent_leaves_the_other_alone():
+    # the parent's handle stays resident for a restart with its parameters;
+    # one of its two restarts is cancelled while queued, the other adopts the
+    # handle and gives the result it gives without the cancelled one
+    ds = designs()
+
+    def trace(cancel):
+        s = place.Server(8 << 30, 1, iters_per_tick=16)
+        try:
+            a = s.submit(ds[0], params())
+            r1 = s.submit(ds[0], params(), kind=place.PLACE_JOB_RESTART, parent=a, seed=3)
+            r2 = s.submit(ds[0], params(), kind=place.PLACE_JOB_RESTART, parent=a, seed=4)
+            if cancel:
+                s.cancel(r1)
+            s.run(timeout_s=300)
+            return {r.id: r for r in s.results()}, (a, r1, r2)
+        finally:
+            s.close()
+
+    full, (a, r1, r2) = trace(False)
+    part, _ = trace(True)
+    assert part[r1].status == place.PLACE_JOB_CANCELLED and part[r1].iterations == 0
+    for j in (a, r2):
+        assert part[j].status == place.PLACE_JOB_FINISHED
+        assert (part[j].position_hash, part[j].iterations) == (full[j].position_hash, full[j].iterations)
