@@ -374,6 +374,7 @@ def run_full(args, place, torch, d, stream, tau_stop=0.07, max_iters=4000, chunk
     h = place.place_create(d, prm, stream=stream.cuda_stream)
     conv = np.zeros(1, np.int32)
     chunks, stages = [], {}
+    scatter_floor = None
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     done, total_ms = 0, 0.0
     torch.cuda.synchronize()
@@ -381,6 +382,11 @@ def run_full(args, place, torch, d, stream, tau_stop=0.07, max_iters=4000, chunk
         nxt = min([k for k in samples if k >= done] + [max_iters])
         if nxt == done:  # a stage sample here
             stages[str(done)] = _stage_sample(place, h)
+            if done == samples[-1]:
+                # the scatter against its floor (same loads, one 64-bit
+                # reduction per covered bin) once the cells have spread
+                sc, fl = place.place_measure_scatter_floor(h, 10)
+                scatter_floor = {"iteration": done, "scatter_ms": sc, "floor_ms": fl}
             done += 5
             place.place_step(h, 0, conv)
             if conv[0]:
@@ -415,7 +421,7 @@ def run_full(args, place, torch, d, stream, tau_stop=0.07, max_iters=4000, chunk
             "note": "graph-launched iterations timed with CUDA events chunk by chunk; the "
                     "stage samples (place_step_timed, 5 iterations each) are part of the run "
                     "but not of the average",
-            "chunks": chunks, "stage_ms_at_iteration": stages}
+            "chunks": chunks, "stage_ms_at_iteration": stages, "scatter_floor": scatter_floor}
 
 
 def run_configs(args, place, torch):

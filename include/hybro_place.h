@@ -420,6 +420,16 @@ int place_step_timed(place_t *h, int32_t n_iters, float *stage_ms);
  * untouched.  Synchronises. */
 int place_measure_wa_floor(place_t *h, int32_t reps, float *ms);
 
+/* The density scatter against its floor at the current positions (all
+ * copies): *ms_scatter receives the mean device time of the scatter as an
+ * iteration runs it (the way each copy's last density pass chose), and
+ * *ms_floor that of a kernel that makes only the same loads (position and
+ * size per movable cell) and one 64-bit reduction into each bin the cell
+ * covers, none of the exact overlap arithmetic.  Both use the density map as
+ * scratch and leave it cleared (the next density pass rebuilds it).
+ * Synchronises. */
+int place_measure_scatter_floor(place_t *h, int32_t reps, float *ms_scatter, float *ms_floor);
+
 /* Failure-path check of the bounded device waits.  Runs the first
  * tensor-core GEMM stage of copy 0 once with its copy producer idle, so that
  * no tile ever arrives: the MMA issuer's and the epilogue's waits give up

@@ -1241,6 +1241,50 @@ int place_test_wait_timeout(place_t *h) {
   return rc;
 }
 
+int place_measure_scatter_floor(place_t *h, int32_t reps, float *ms_scatter, float *ms_floor) {
+  if (!h || !ms_scatter || !ms_floor) return fail(PLACE_EINVAL, "null argument");
+  if (reps < 1) return fail(PLACE_EINVAL, "reps < 1");
+  NvtxRange nvtx_("place_measure_scatter_floor");
+  const Dev &d = h->d;
+  cudaStream_t st = h->stream;
+  const size_t mbytes = sizeof(unsigned long long) * (size_t)d.Gm * d.K;
+  cudaEvent_t ev[4];
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  // the scatter as the iteration runs it (the way its copies' last pass
+  // chose), then the floor kernel, each after a cleared map
+  cudaMemsetAsync(d.M, 0, mbytes, st);
+  launch_scatter_main(d, 0, d.K, 1, st);  // warm-up
+  cudaMemsetAsync(d.M, 0, mbytes, st);
+  launch_scatter_floor(d, 0, d.K, st);
+  float t[2] = {0.f, 0.f};
+  cudaError_t e = cudaSuccess;
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+    cudaMemsetAsync(d.M, 0, mbytes, st);
+    cudaEventRecord(ev[0], st);
+    launch_scatter_main(d, 0, d.K, 1, st);
+    cudaEventRecord(ev[1], st);
+    cudaMemsetAsync(d.M, 0, mbytes, st);
+    cudaEventRecord(ev[2], st);
+    launch_scatter_floor(d, 0, d.K, st);
+    cudaEventRecord(ev[3], st);
+    e = cudaEventSynchronize(ev[3]);
+    float a = 0.f, b = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[2], ev[3]);
+    t[0] += a;
+    t[1] += b;
+  }
+  // the map is scratch here: the next density pass clears and rebuilds it
+  cudaMemsetAsync(d.M, 0, mbytes, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  for (auto &x : ev) cudaEventDestroy(x);
+  if (e != cudaSuccess) return fail(PLACE_ECUDA, "scatter floor: %s", cudaGetErrorString(e));
+  CKL();
+  *ms_scatter = t[0] / reps;
+  *ms_floor = t[1] / reps;
+  return check_dev_err(h);
+}
+
 int place_test_bounds_check(place_t *h) {
   if (!h) return fail(PLACE_EINVAL, "null handle");
 #ifndef PLACE_DEBUG_BOUNDS

@@ -422,6 +422,36 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
   }
 }
 
+// Floor of the scatter's memory work at the current positions: per movable
+// cell the same loads (position and quantised size) and one 64-bit reduction
+// into each bin the cell covers (the bins from an FP32 estimate of its
+// corners), none of the exact rectangle arithmetic.  It adds into the map,
+// which the caller clears.
+__global__ void __launch_bounds__(kThreads) k_scatter_floor(Dev d, int copy0) {
+  const int c = copy0 + blockIdx.y;
+  const float2 *xy = d.xy + (size_t)c * d.n_cells;
+  unsigned long long *M = d.M + (size_t)c * d.Gm;
+  const float is = 1.f / d.scale;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
+    const int mo = i < d.n_real ? 0 : d.G;
+    const float2 v = xy[i];
+    const float w = (float)d.Wq[i] * is, h = (float)d.Hq[i] * is;
+    const int ix0 = min(max((int)floorf((v.x - d.fxl) * d.fibw), 0), d.nx - 1);
+    const int ix1 = min(max((int)floorf((v.x + w - d.fxl) * d.fibw), 0), d.nx - 1);
+    const int iy0 = min(max((int)floorf((v.y - d.fyl) * d.fibh), 0), d.ny - 1);
+    const int iy1 = min(max((int)floorf((v.y + h - d.fyl) * d.fibh), 0), d.ny - 1);
+    for (int ix = ix0; ix <= ix1; ++ix)
+      for (int iy = iy0; iy <= iy1; ++iy) {
+        const int b = mo + ix * d.ny + iy;
+        if (HP_IN(d.err, b, d.Gm, BS_MAP_BIN)) atomicAdd(&M[b], 1ull);
+      }
+  }
+}
+
+void launch_scatter_floor(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
+  k_scatter_floor<<<dim3(d.cell_blocks, ncopy), kThreads, 0, st>>>(d, copy0);
+}
+
 void launch_scatter_main(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st) {
   k_scatter<<<dim3(d.cell_blocks, ncopy), kThreads, 0, st>>>(d, copy0, eval);
 }

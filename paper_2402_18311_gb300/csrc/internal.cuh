@@ -275,6 +275,7 @@ int wa_prepare(int cap);
 void launch_wa_floor(const Dev &d, int copy0, int ncopy, cudaStream_t st);
 void launch_wa_class(const Dev &d, int cls, int copy0, int ncopy, int eval, cudaStream_t st);
 void launch_scatter_main(const Dev &d, int copy0, int ncopy, int eval, cudaStream_t st);
+void launch_scatter_floor(const Dev &d, int copy0, int ncopy, cudaStream_t st);
 
 // Create-time tuning (autotune.cu).  Chooses, for the knobs the caller left
 // automatic, the tensor-core GEMM tile width, the big-net shared-memory cap

@@ -148,6 +148,8 @@ _SIGS = {
     "place_measure_wa_floor": (ct.c_int, [_VP, ct.c_int32, ct.POINTER(ct.c_float)]),
     "place_test_wait_timeout": (ct.c_int, [_VP]),
     "place_test_bounds_check": (ct.c_int, [_VP]),
+    "place_measure_scatter_floor": (ct.c_int, [_VP, ct.c_int32, ct.POINTER(ct.c_float),
+                                               ct.POINTER(ct.c_float)]),
     "place_get_hybro_rounds": (ct.c_int, [_VP, ct.c_int32, _VP, _VP, ct.c_int32,
                                           ct.POINTER(ct.c_int32)]),
     "place_overflow_noalloc": (ct.c_int, [_VP, _VP, _VP, _VP, ct.c_int32,
@@ -366,6 +368,13 @@ def place_measure_wa_floor(h, reps=10):
     ms = ct.c_float()
     _check(lib().place_measure_wa_floor(h, int(reps), ct.byref(ms)))
     return ms.value
+
+
+def place_measure_scatter_floor(h, reps=10):
+    """(scatter ms, floor ms) at the current positions (see the header)."""
+    a, b = ct.c_float(), ct.c_float()
+    _check(lib().place_measure_scatter_floor(h, int(reps), ct.byref(a), ct.byref(b)))
+    return a.value, b.value
 
 
 def place_get_hybro_rounds(h, copy):

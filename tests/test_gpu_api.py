@@ -184,3 +184,20 @@ def test_checkpoint_rejects_another_design_and_short_buffers():
         place.place_checkpoint_load(a, 0, buf)  # its own checkpoint loads
     finally:
         place.place_destroy(a)
+
+
+def test_scatter_floor_measurement_leaves_the_map_to_the_next_pass():
+    d = synth.scaled(20000, 128, seed=2)
+    h = place.place_create(d, place.place_default_params(tau_stop=-1.0, max_iters=10 ** 6))
+    try:
+        place.place_step(h, 300)
+        m0 = np.empty(d.nx * d.ny, np.int64)
+        place.place_eval_density(h, 0, m0)
+        t_scatter, t_floor = place.place_measure_scatter_floor(h, 5)
+        assert t_scatter > 0 and t_floor > 0
+        m1 = np.empty(d.nx * d.ny, np.int64)
+        place.place_eval_density(h, 0, m1)
+        np.testing.assert_array_equal(m0, m1)
+        place.place_step(h, 5)  # and the placement goes on
+    finally:
+        place.place_destroy(h)
