@@ -948,7 +948,6 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
 
   // launch plan
   d.cell_blocks = std::max(1, std::min((Mo + kThreads - 1) / kThreads, kMaxCellBlocks));
-  d.bin_blocks = std::max(1, std::min((d.G + kThreads - 1) / kThreads, kMaxCellBlocks));
   d.wa_blocks_total = 0;
   for (int c = 0; c < 5; ++c) {
     int n = d.cls_begin[c + 1] - d.cls_begin[c];
@@ -958,7 +957,6 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     d.wa_block_base[c] = d.wa_blocks_total;
     d.wa_blocks_total += nb;
   }
-  d.nb_red = std::max(std::max(2 * d.cell_blocks + 2, d.bin_blocks), std::max(d.wa_blocks_total, 1));
   {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -967,6 +965,12 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     // the cell-gradient kernel runs as one resident wave (grid-stride)
     d.cg_blocks = std::max(1, std::min(d.cell_blocks, d.sms * cell_grad_blocks_per_sm()));
   }
+  // four blocks per SM: more bins per thread amortise the per-block exact
+  // reductions of the density finish (measured on the 2.1M-cell design:
+  // 0.0816 -> 0.0783 ms for the density stage at iteration 5 against 1216
+  // blocks; 304 blocks were in between)
+  d.bin_blocks = std::max(1, std::min((d.G + kThreads - 1) / kThreads, 4 * std::max(d.sms, 1)));
+  d.nb_red = std::max(std::max(2 * d.cell_blocks + 2, d.bin_blocks), std::max(d.wa_blocks_total, 1));
   int sn = 2;
   while (sn < Ci) sn <<= 1;
   d.sort_n = sn;
