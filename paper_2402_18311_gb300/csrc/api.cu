@@ -338,8 +338,8 @@ void layout(Dev &d, Arena &a, int n_copies) {
     d.rho_l = a.take<__nv_bfloat16>(K * G);
     d.T_h = a.take<__nv_bfloat16>(K * 3 * G);
     d.T_l = a.take<__nv_bfloat16>(K * 3 * G);
-    d.SB_h = a.take<__nv_bfloat16>(K * 3 * G);
-    d.SB_l = a.take<__nv_bfloat16>(K * 3 * G);
+    d.SB_h = a.take<__nv_bfloat16>(K * G);
+    d.SB_l = a.take<__nv_bfloat16>(K * G);
     d.A1h = a.take<__nv_bfloat16>(ny2);
     d.A1l = a.take<__nv_bfloat16>(ny2);
     d.A2h = a.take<__nv_bfloat16>(nx2);
@@ -376,7 +376,9 @@ int setup_tc(place_t *h) {
   launch_split_bf16(d.Cn, d.A1h, d.A1l, ny2, st);
   launch_split_bf16(d.Cm, d.A2h, d.A2l, nx2, st);
   launch_split_bf16(d.CTn, d.A3h, d.A3l, ny2, st);
-  launch_split_bf16(d.STn, d.A3h + ny2, d.A3l + ny2, ny2, st);
+  // S_N with column v scaled by w_v: stage 3's y field from the one
+  // coefficient field of stage 2
+  launch_split_bf16_colscale(d.STn, d.wv, d.A3h + ny2, d.A3l + ny2, d.ny, d.ny, st);
   launch_split_bf16(d.CTn, d.A3h + 2 * ny2, d.A3l + 2 * ny2, ny2, st);
   launch_split_bf16(d.STm, d.A4h, d.A4l, nx2, st);
   launch_split_bf16(d.CTm, d.A4h + nx2, d.A4l + nx2, nx2, st);
@@ -407,7 +409,7 @@ int encode_tc_maps(place_t *h) {
       {d.A2h, nx, nx, 1, 128}, {d.A2l, nx, nx, 1, 128},
       {d.T_h, nx, ny, 3 * K, d.tc_bn[1]}, {d.T_l, nx, ny, 3 * K, d.tc_bn[1]},
       {d.A3h, ny, ny, 3, 128}, {d.A3l, ny, ny, 3, 128},
-      {d.SB_h, ny, nx, 3 * K, d.tc_bn[2]}, {d.SB_l, ny, nx, 3 * K, d.tc_bn[2]},
+      {d.SB_h, ny, nx, K, d.tc_bn[2]}, {d.SB_l, ny, nx, K, d.tc_bn[2]},
       {d.A4h, nx, nx, 3, 128}, {d.A4l, nx, nx, 3, 128},
       {d.T_h, nx, ny, 3 * K, d.tc_bn[3]}, {d.T_l, nx, ny, 3 * K, d.tc_bn[3]}};
   for (int i = 0; i < 16; ++i) {

@@ -140,6 +140,10 @@ void launch_spectral_fp32(const Dev &d, int copy0, int ncopy, int with_psi, int 
 }
 
 // Tensor-core chain (BF16x3): rho_hl -> T_hl[0] -> SB_hl -> T_hl[w] -> E[w].
+// Stage 2 writes one coefficient field, B = a / (w_u^2 + w_v^2); stage 3
+// reads it for every field w: its y matrix holds S_N with column v scaled by
+// w_v, and its x output's columns u are scaled by w_u, which gives the field
+// coefficients w_u B and w_v B of the FP32 chain above (psi takes B as is).
 void launch_spectral_tc(const Dev &d, int copy0, int ncopy, int with_psi, int eval,
                         cudaStream_t st) {
   const CUtensorMap *mp = static_cast<const CUtensorMap *>(d.tcm);
@@ -157,18 +161,20 @@ void launch_spectral_tc(const Dev &d, int copy0, int ncopy, int with_psi, int ev
   g.M = d.ny; g.N = d.nx; g.K = d.ny; g.nwhich = 1; g.b_per_copy = 1; g.d_per_copy = 3;
   g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
   launch_tc_gemm(mp + 0, g, ncopy, d.tc_bn[0], d.tc_split[0], st);
-  // G2: SB = spectral(Cm T[0]^T)   (nx x ny, K = nx)
-  g.M = d.nx; g.N = d.ny; g.K = d.nx; g.b_per_copy = 3; g.d_per_copy = 3;
+  // G2: SB = spectral(Cm T[0]^T)   (nx x ny, K = nx), one field per copy
+  g.M = d.nx; g.N = d.ny; g.K = d.nx; g.b_per_copy = 3; g.d_per_copy = 1;
   g.epi = TC_EPI_SPECTRAL; g.Dh = d.SB_h; g.Dl = d.SB_l;
   launch_tc_gemm(mp + 4, g, ncopy, d.tc_bn[1], d.tc_split[1], st);
-  // G3: T[w] = An_w SB[w]^T   (ny x nx, K = ny)
+  // G3: T[w] = An_w SB^T   (ny x nx, K = ny), the x output scaled by w_u
   g.M = d.ny; g.N = d.nx; g.K = d.ny; g.nwhich = nw;
+  g.b_per_copy = 1; g.b_shared = 1; g.d_per_copy = 3; g.col_scale = d.wu;
   g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
   // with psi the last two stages have a third field: more tiles than the
   // split-K workspace holds, so one CTA per tile (the same bits)
   launch_tc_gemm(mp + 8, g, ncopy, d.tc_bn[2], with_psi ? 1 : d.tc_split[2], st);
   // G4: E[w] = Am_w T[w]^T   (nx x ny, K = nx)
   g.M = d.nx; g.N = d.ny; g.K = d.nx;
+  g.b_per_copy = 3; g.b_shared = 0; g.col_scale = nullptr;
   g.epi = TC_EPI_F32; g.Df = d.E; g.Dh = g.Dl = nullptr;
   launch_tc_gemm(mp + 12, g, ncopy, d.tc_bn[3], with_psi ? 1 : d.tc_split[3], st);
 }

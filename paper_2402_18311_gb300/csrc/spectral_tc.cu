@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(128, 1)
   if (!g.eval && g.cs[c].stopped) return;
   const int mt = blockIdx.y / SPLIT, ks = blockIdx.y % SPLIT;
   const int m0 = mt * BM, n0 = blockIdx.x * BN;
-  const int bz = c * g.b_per_copy + which;  // batch index of B
+  const int bz = c * g.b_per_copy + (g.b_shared ? 0 : which);  // batch index of B
   const int dz = c * g.d_per_copy + which;  // batch index of D
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int TCOLS = SPLIT == 1 ? 2 * BN : BN;  // TMEM columns: one accumulator per half here
@@ -363,26 +363,28 @@ __global__ void __launch_bounds__(128, 1)
                 make_uint4(__float_as_uint(v[4 * i + 4]), __float_as_uint(v[4 * i + 5]),
                            __float_as_uint(v[4 * i + 6]), __float_as_uint(v[4 * i + 7])));
       } else if (g.epi == TC_EPI_SPLIT) {
+        if (g.col_scale && which == 0) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = __fmul_rn(v[i], g.col_scale[n + i]);
+        }
         split_store(g.Dh + o, g.Dl + o, v);
       } else {
-        // spectral weights: a_uv = acc c_u c_v/(M N); (Bx, By, Bpsi) = a (w_u, w_v, 1)/(w_u^2 + w_v^2)
+        // spectral weights: a_uv = acc c_u c_v/(M N) and the one field
+        // B_uv = a_uv / (w_u^2 + w_v^2), the potential's coefficients; the
+        // field coefficients w_u B and w_v B are formed by the next stage (w_u
+        // scales its x output's columns, w_v its y matrix's columns)
         const size_t G = (size_t)g.M * g.N;
         const size_t ob = (size_t)c * g.d_per_copy * G + (size_t)m * g.N + n;
         const float cu = g.cu[m], wu = g.wu[m], wu2 = wu * wu;
-        float bx[32], by[32], bp[32];
+        float bp[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float wv = s_wv[cc + i];
           // fast reciprocal (2 ulp), far below the BF16x3 error of the solve
           const float inv = (m == 0 && n + i == 0) ? 0.f : __fdividef(1.f, fmaf(wv, wv, wu2));
-          const float a = v[i] * cu * s_cv[cc + i] * inv;
-          bx[i] = a * wu;
-          by[i] = a * wv;
-          bp[i] = a;
+          bp[i] = v[i] * cu * s_cv[cc + i] * inv;
         }
-        split_store(g.Dh + ob, g.Dl + ob, bx);
-        split_store(g.Dh + ob + G, g.Dl + ob + G, by);
-        if (g.with_psi) split_store(g.Dh + ob + 2 * G, g.Dl + ob + 2 * G, bp);
+        split_store(g.Dh + ob, g.Dl + ob, bp);
       }
     }
   }
@@ -429,6 +431,24 @@ int tc_prepare() {
 }
 
 // FP32 -> (bf16 hi, bf16 lo) for the static transform matrices.
+__global__ void k_split_bf16_colscale(const float *src, const float *w, __nv_bfloat16 *hi,
+                                      __nv_bfloat16 *lo, int rows, int cols) {
+  const size_t n = (size_t)rows * cols;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float v = __fmul_rn(src[i], w[i % cols]);
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+void launch_split_bf16_colscale(const float *src, const float *w, __nv_bfloat16 *hi,
+                                __nv_bfloat16 *lo, int rows, int cols, cudaStream_t st) {
+  size_t b = ((size_t)rows * cols + 255) / 256;
+  int blocks = (int)(b < 4096 ? (b < 1 ? 1 : b) : 4096);
+  k_split_bf16_colscale<<<blocks, 256, 0, st>>>(src, w, hi, lo, rows, cols);
+}
+
 __global__ void k_split_bf16(const float *src, __nv_bfloat16 *hi, __nv_bfloat16 *lo, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x) {

@@ -16,6 +16,9 @@ struct TcArgs {
   int M, N, K;                 // D is M x N per batch; contraction over K
   int nwhich, copy0;
   int b_per_copy, d_per_copy;  // batch slots per copy in B and in D
+  int b_shared;                // 1: every `which` reads the copy's one B (batch c * b_per_copy)
+  const float *col_scale;      // TC_EPI_SPLIT: the which == 0 output's columns n are scaled
+                               // by col_scale[n] (nullptr: none)
   int epi, with_psi;
   float *Df;                   // TC_EPI_F32 output
   __nv_bfloat16 *Dh, *Dl;      // split outputs
@@ -35,6 +38,10 @@ void launch_tc_gemm(const CUtensorMap *maps4, const TcArgs &g, int ncopy, int bn
                     cudaStream_t st);
 void launch_split_bf16(const float *src, __nv_bfloat16 *hi, __nv_bfloat16 *lo, size_t n,
                        cudaStream_t st);
+// The same for a rows x cols row-major matrix whose column j is first scaled
+// by w[j] (one FP32 product per element).
+void launch_split_bf16_colscale(const float *src, const float *w, __nv_bfloat16 *hi,
+                                __nv_bfloat16 *lo, int rows, int cols, cudaStream_t st);
 // 3D bf16 tensor map {K, rows, batch} with a {64, box_rows, 1} box and
 // 128-byte swizzle; returns 0 on success.
 int make_map_bf16_3d(CUtensorMap *map, const void *base, int K, int rows, int batch, int box_rows);
