@@ -164,6 +164,12 @@ typedef struct place_params {
                              classes run as a chain on one graph branch, or
                              split over two or three branches that run side by
                              side (integer gradient sums: the same bits) */
+  int32_t dct_fold;       /* 1 (default): on the BF16x3 path with both grid sides
+                             multiples of 256, every transform is split into its
+                             even and odd frequencies (the first step of a fast
+                             cosine transform), which halves the tensor-core
+                             work of the solve; 0: the plain GEMMs.  Both solve
+                             the same Poisson equation (to rounding). */
 } place_params;
 
 /* Read-only facts about a handle. */
@@ -186,7 +192,7 @@ typedef struct place_info {
   double scatter_t1, scatter_t2; /* effective-bin thresholds of the scatter's ways */
   double autotune_ms;     /* host time the tuning took at create (0 on a cache hit) */
   int32_t wa_streams;     /* graph branches the WA classes run on (1..3) */
-  int32_t reserved;
+  int32_t dct_fold;       /* 1: the solve runs the even/odd split (params.dct_fold) */
 } place_info;
 
 /* Optimiser scalars of one copy after its last iteration. */

@@ -175,6 +175,13 @@ int resolve_dct_mode(int mode, int nx, int ny) {
   return (nx % 128 == 0 && ny % 128 == 0) ? PLACE_DCT_BF16X3 : PLACE_DCT_FP32;
 }
 
+// The even/odd split of the tensor-core solve: each half of a side must
+// hold whole 128-row tiles (and each half of a contraction whole pairs of
+// 64-element K-blocks), so both sides are multiples of 256.
+int use_fold(int tc, int fold, int nx, int ny) {
+  return (tc && fold && nx % 256 == 0 && ny % 256 == 0) ? 1 : 0;
+}
+
 }  // namespace
 
 namespace hp {
@@ -241,6 +248,7 @@ void place_default_params(place_params *p) {
   p->wa_streams = 0;
   p->fillers = 0;
   p->macro_precond = 1.0f;
+  p->dct_fold = 1;
 }
 
 int place_destroy(place_t *h) {
@@ -348,12 +356,21 @@ void layout(Dev &d, Arena &a, int n_copies) {
     d.A3l = a.take<__nv_bfloat16>(3 * ny2);
     d.A4h = a.take<__nv_bfloat16>(3 * nx2);
     d.A4l = a.take<__nv_bfloat16>(3 * nx2);
+    if (d.bfly) {
+      d.wu_p = a.take<float>(d.nx);
+      d.cu_p = a.take<float>(d.nx);
+      d.wv_p = a.take<float>(d.ny);
+      d.cv_p = a.take<float>(d.ny);
+    }
     // split-K workspace: two 128 x 128 FP32 halves per tile of the largest
     // stage that may split (a stage with at most half as many 128-wide tiles
     // as the device has SMs)
     const int sms = d.sms > 0 ? d.sms : 152;
     const size_t t1 = (size_t)(d.nx / 128) * (d.ny / 128) * K;
-    const size_t tiles[4] = {t1, t1, 2 * t1, 2 * t1};
+    // the inverse stages have two fields; with the even/odd split they
+    // cover half the rows of each
+    const size_t t3 = d.bfly ? t1 : 2 * t1;
+    const size_t tiles[4] = {t1, t1, t3, t3};
     size_t ws_tiles = 0;
     for (int s = 0; s < 4; ++s) {
       d.tc_split_ok[s] = 2 * tiles[s] <= (size_t)sms ? 1 : 0;
@@ -373,6 +390,7 @@ int setup_tc(place_t *h) {
   Dev &d = h->d;
   cudaStream_t st = h->stream;
   const size_t nx2 = (size_t)d.nx * d.nx, ny2 = (size_t)d.ny * d.ny;
+  if (!d.bfly) {  // the even/odd split's operands were built at create
   launch_split_bf16(d.Cn, d.A1h, d.A1l, ny2, st);
   launch_split_bf16(d.Cm, d.A2h, d.A2l, nx2, st);
   launch_split_bf16(d.CTn, d.A3h, d.A3l, ny2, st);
@@ -383,13 +401,14 @@ int setup_tc(place_t *h) {
   launch_split_bf16(d.STm, d.A4h, d.A4l, nx2, st);
   launch_split_bf16(d.CTm, d.A4h + nx2, d.A4l + nx2, nx2, st);
   launch_split_bf16(d.CTm, d.A4h + 2 * nx2, d.A4l + 2 * nx2, nx2, st);
+  }
   CKL();
   const int nx = d.nx, ny = d.ny, K = d.K;
   // tile width per stage, unless forced or tuned: 128; 64 only for grids so
   // small that 128-wide tiles would occupy under a quarter of the SMs
   const int sms = d.sms;
-  const int tiles128[4] = {(nx / 128) * (ny / 128) * K, (ny / 128) * (nx / 128) * K,
-                           (nx / 128) * (ny / 128) * 2 * K, (ny / 128) * (nx / 128) * 2 * K};
+  const int t3 = (nx / 128) * (ny / 128) * (d.bfly ? 1 : 2) * K;  // two fields; half the rows
+  const int tiles128[4] = {(nx / 128) * (ny / 128) * K, (ny / 128) * (nx / 128) * K, t3, t3};
   for (int s = 0; s < 4; ++s) {
     d.tc_bn[s] = d.prm.gemm_bn ? d.prm.gemm_bn : (tiles128[s] * 4 <= sms ? 64 : 128);
     d.tc_split[s] = (d.prm.gemm_split == 2 && d.tc_split_ok[s] && d.tc_bn[s] == 128) ? 2 : 1;
@@ -403,14 +422,17 @@ int setup_tc(place_t *h) {
 int encode_tc_maps(place_t *h) {
   Dev &d = h->d;
   const int nx = d.nx, ny = d.ny, K = d.K;
+  // the even/odd split: forward A matrices with half the contraction,
+  // inverse ones with half the rows, stage 1's B tile in two mirrored halves
+  const int f = d.bfly ? 2 : 1;
   struct M { const void *p; int k, rows, batch, box; } spec[16] = {
-      {d.A1h, ny, ny, 1, 128}, {d.A1l, ny, ny, 1, 128},
-      {d.rho_h, ny, nx, K, d.tc_bn[0]}, {d.rho_l, ny, nx, K, d.tc_bn[0]},
-      {d.A2h, nx, nx, 1, 128}, {d.A2l, nx, nx, 1, 128},
+      {d.A1h, ny / f, ny, 1, 128}, {d.A1l, ny / f, ny, 1, 128},
+      {d.rho_h, ny, nx, K, d.tc_bn[0] / f}, {d.rho_l, ny, nx, K, d.tc_bn[0] / f},
+      {d.A2h, nx / f, nx, 1, 128}, {d.A2l, nx / f, nx, 1, 128},
       {d.T_h, nx, ny, 3 * K, d.tc_bn[1]}, {d.T_l, nx, ny, 3 * K, d.tc_bn[1]},
-      {d.A3h, ny, ny, 3, 128}, {d.A3l, ny, ny, 3, 128},
+      {d.A3h, ny, ny / f, 3, 128}, {d.A3l, ny, ny / f, 3, 128},
       {d.SB_h, ny, nx, K, d.tc_bn[2]}, {d.SB_l, ny, nx, K, d.tc_bn[2]},
-      {d.A4h, nx, nx, 3, 128}, {d.A4l, nx, nx, 3, 128},
+      {d.A4h, nx, nx / f, 3, 128}, {d.A4l, nx, nx / f, 3, 128},
       {d.T_h, nx, ny, 3 * K, d.tc_bn[3]}, {d.T_l, nx, ny, 3 * K, d.tc_bn[3]}};
   for (int i = 0; i < 16; ++i) {
     int r = make_map_bf16_3d(&h->maps[i], spec[i].p, spec[i].k, spec[i].rows, spec[i].batch, spec[i].box);
@@ -645,6 +667,99 @@ void host_dct_tables(int n, double h, std::vector<float> &C, std::vector<float> 
   }
 }
 
+// Frequency order of the even/odd split: position p < n/2 holds frequency
+// 2p, position n/2 + p frequency 2p + 1.
+inline int fold_freq(int p, int n) { return p < n / 2 ? 2 * p : 2 * (p - n / 2) + 1; }
+
+// FP32 -> bf16, rounding to nearest even (finite values), and the bf16 pair
+// (hi, lo) of x with hi = bf16(x), lo = bf16(x - hi), as the device splits.
+inline uint16_t host_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+inline void host_split(float v, uint16_t &hi, uint16_t &lo) {
+  hi = host_bf16(v);
+  const uint32_t hu = (uint32_t)hi << 16;
+  float hf;
+  std::memcpy(&hf, &hu, 4);
+  lo = host_bf16(v - hf);
+}
+
+// The operands of the four stages with the even/odd split (the tensor
+// maps' shapes in encode_tc_maps):
+//   A1 [ny][ny/2]: row p = Cn row fold_freq(p), columns y < ny/2 (the forward
+//     transform of rho's even/odd halves; the odd rows read the second half)
+//   A2 [nx][nx/2]: the same for Cm
+//   A3 [3][ny/2][ny]: rows y < ny/2 of the three inverse y matrices (CT,
+//     S diag(w_v), CT), columns in the split frequency order
+//   A4 [3][nx/2][nx]: rows x < nx/2 of S, CT, CT along x, the same order
+// and wu, wv, cu, cv in that order.  Values are the FP32 tables' (the y
+// field's products rounded once to FP32, as the device split does).
+int upload_fold_tables(Dev &d, cudaStream_t st, const std::vector<float> &Cn,
+                       const std::vector<float> &CTn, const std::vector<float> &STn,
+                       const std::vector<float> &Cm, const std::vector<float> &CTm,
+                       const std::vector<float> &STm, const std::vector<float> &wu,
+                       const std::vector<float> &wv, const std::vector<float> &cu,
+                       const std::vector<float> &cv) {
+  const int nx = d.nx, ny = d.ny;
+  std::vector<uint16_t> hi, lo;
+  auto put = [&](__nv_bfloat16 *dh, __nv_bfloat16 *dl) -> int {
+    if (cudaMemcpyAsync(dh, hi.data(), 2 * hi.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dl, lo.data(), 2 * lo.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return fail(PLACE_ECUDA, "upload of the transform matrices failed");
+    return PLACE_OK;
+  };
+  // forward: [n][n/2] rows in the split order
+  auto fwd = [&](const std::vector<float> &C, int n) {
+    hi.assign((size_t)n * (n / 2), 0);
+    lo = hi;
+    for (int p = 0; p < n; ++p)
+      for (int i = 0; i < n / 2; ++i) {
+        const size_t o = (size_t)p * (n / 2) + i;
+        host_split(C[(size_t)fold_freq(p, n) * n + i], hi[o], lo[o]);
+      }
+  };
+  // inverse: [3][n/2][n] from three [i][k] matrices (w: column scale or null)
+  auto inv = [&](const std::vector<float> *M3[3], const std::vector<float> *w3[3], int n) {
+    hi.assign((size_t)3 * (n / 2) * n, 0);
+    lo = hi;
+    for (int w = 0; w < 3; ++w)
+      for (int i = 0; i < n / 2; ++i)
+        for (int p = 0; p < n; ++p) {
+          const int k = fold_freq(p, n);
+          float v = (*M3[w])[(size_t)i * n + k];
+          if (w3[w]) v = (float)((double)v * (double)(*w3[w])[k]);
+          const size_t o = ((size_t)w * (n / 2) + i) * n + p;
+          host_split(v, hi[o], lo[o]);
+        }
+  };
+  int rc;
+  fwd(Cn, ny);
+  if ((rc = put(d.A1h, d.A1l))) return rc;
+  fwd(Cm, nx);
+  if ((rc = put(d.A2h, d.A2l))) return rc;
+  const std::vector<float> *m3[3] = {&CTn, &STn, &CTn}, *w3[3] = {nullptr, &wv, nullptr};
+  inv(m3, w3, ny);
+  if ((rc = put(d.A3h, d.A3l))) return rc;
+  const std::vector<float> *m4[3] = {&STm, &CTm, &CTm}, *w4[3] = {nullptr, nullptr, nullptr};
+  inv(m4, w4, nx);
+  if ((rc = put(d.A4h, d.A4l))) return rc;
+  std::vector<float> t(std::max(nx, ny));
+  auto perm = [&](float *dst, const std::vector<float> &src, int n) -> int {
+    for (int p = 0; p < n; ++p) t[p] = src[fold_freq(p, n)];
+    if (cudaMemcpy(dst, t.data(), sizeof(float) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(PLACE_ECUDA, "upload of the frequency tables failed");
+    return PLACE_OK;
+  };
+  if ((rc = perm(d.wu_p, wu, nx)) || (rc = perm(d.cu_p, cu, nx)) || (rc = perm(d.wv_p, wv, ny)) ||
+      (rc = perm(d.cv_p, cv, ny)))
+    return rc;
+  return PLACE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -677,6 +792,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   if (prm.gemm_split < 0 || prm.gemm_split > 2) return fail(PLACE_EINVAL, "gemm_split must be 0, 1 or 2");
   if (prm.wa_streams < 0 || prm.wa_streams > kMaxWaStreams)
     return fail(PLACE_EINVAL, "wa_streams must be 0, 1, 2 or 3");
+  if (prm.dct_fold != 0 && prm.dct_fold != 1) return fail(PLACE_EINVAL, "dct_fold must be 0 or 1");
   if (prm.fillers != 0 && prm.fillers != 1) return fail(PLACE_EINVAL, "fillers must be 0 or 1");
   if (!(prm.macro_precond > 0.f) || !std::isfinite(prm.macro_precond))
     return fail(PLACE_EINVAL, "macro_precond must be positive and finite");
@@ -754,6 +870,7 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   d.prm = prm;
   d.has_net_w = nl->net_w ? 1 : 0;
   d.tc = prm.dct_mode == PLACE_DCT_BF16X3 ? 1 : 0;
+  d.bfly = use_fold(d.tc, prm.dct_fold, bins->nx, bins->ny);
   h->stream = (cudaStream_t)stream;
 
   // quantised sizes and movable area
@@ -1042,6 +1159,8 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
     up(d.wv, wv.data(), sizeof(float) * ny);
     up(d.cu, cu.data(), sizeof(float) * nx);
     up(d.cv, cv.data(), sizeof(float) * ny);
+    if (rc == PLACE_OK && d.bfly)
+      rc = upload_fold_tables(d, h->stream, Cn, CTn, STn, Cm, CTm, STm, wu, wv, cu, cv);
   }
   for (int c = 0; c < d.K && rc == PLACE_OK; ++c) up(d.xy + (size_t)c * Ci, xy0.data(), sizeof(float2) * Ci);
   if (rc != PLACE_OK) {
@@ -1144,7 +1263,7 @@ int place_get_info(const place_t *h, place_info *o) {
   o->scatter_t2 = d.scat_t2;
   o->autotune_ms = h->autotune_ms;
   o->wa_streams = d.wa_streams;
-  o->reserved = 0;
+  o->dct_fold = d.bfly;
   return PLACE_OK;
 }
 
@@ -1848,6 +1967,7 @@ extern "C" int place_estimate_device_bytes(const place_netlist *nl, const place_
   d.has_net_w = nl->net_w ? 1 : 0;
   prm.dct_mode = resolve_dct_mode(prm.dct_mode, bins->nx, bins->ny);
   d.tc = prm.dct_mode == PLACE_DCT_BF16X3 ? 1 : 0;
+  d.bfly = use_fold(d.tc, prm.dct_fold, bins->nx, bins->ny);
   d.prm = prm;
   const int cb = std::max(1, std::min((d.n_mov + kThreads - 1) / kThreads, kMaxCellBlocks));
   const int bb = std::max(1, std::min((d.G + kThreads - 1) / kThreads, kMaxCellBlocks));

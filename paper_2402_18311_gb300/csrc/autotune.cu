@@ -40,12 +40,13 @@ namespace hp {
 namespace {
 
 struct Key {
-  int nx, ny, K, tc, lg_mov, lg_pins, lg_deg, stretch, gemm_bn, gemm_split, cap, scat, wa_streams;
+  int nx, ny, K, tc, lg_mov, lg_pins, lg_deg, stretch, gemm_bn, gemm_split, cap, scat, wa_streams,
+      fold;
   bool operator<(const Key &o) const {
     return std::tie(nx, ny, K, tc, lg_mov, lg_pins, lg_deg, stretch, gemm_bn, gemm_split, cap,
-                    scat, wa_streams) <
+                    scat, wa_streams, fold) <
            std::tie(o.nx, o.ny, o.K, o.tc, o.lg_mov, o.lg_pins, o.lg_deg, o.stretch, o.gemm_bn,
-                    o.gemm_split, o.cap, o.scat, o.wa_streams);
+                    o.gemm_split, o.cap, o.scat, o.wa_streams, o.fold);
   }
 };
 
@@ -134,7 +135,7 @@ int autotune(Dev &d, int max_deg, cudaStream_t st, const TuneHooks &hk, TuneOut 
   const Key key{d.nx,           d.ny,           d.K,           d.tc,
                 lg2(d.n_mov),   lg2(d.n_pins),  lg2(max_deg),  d.prm.stretch,
                 d.prm.gemm_bn,  d.prm.gemm_split, d.prm.wa_big_cap, d.prm.scatter_mode,
-                d.prm.wa_streams};
+                d.prm.wa_streams, d.bfly};
   {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find(key);
@@ -163,8 +164,9 @@ int autotune(Dev &d, int max_deg, cudaStream_t st, const TuneHooks &hk, TuneOut 
     // tile width per stage, and split-K on the stages with few tiles (the
     // first two, or all four, where the workspace allows it)
     struct Cand { int bn[4], split[4]; };
-    const Cand all[5] = {{{128, 128, 128, 128}, {1, 1, 1, 1}}, {{128, 128, 128, 128}, {2, 2, 1, 1}},
-                         {{128, 128, 128, 128}, {2, 2, 2, 2}}, {{64, 64, 128, 128}, {1, 1, 1, 1}},
+    const Cand all[7] = {{{128, 128, 128, 128}, {1, 1, 1, 1}}, {{128, 128, 128, 128}, {2, 2, 1, 1}},
+                         {{128, 128, 128, 128}, {1, 1, 2, 2}}, {{128, 128, 128, 128}, {2, 2, 2, 2}},
+                         {{64, 64, 128, 128}, {1, 1, 1, 1}}, {{128, 128, 64, 64}, {1, 1, 1, 1}},
                          {{64, 64, 64, 64}, {1, 1, 1, 1}}};
     std::vector<Cand> cand;
     for (const Cand &c0 : all) {

@@ -322,14 +322,54 @@ __device__ __forceinline__ void bin_excess(const Dev &d, unsigned long long m, l
   }
 }
 
+// One pair of bins (2 b2, 2 b2 + 1): their excess into the sums and rho.
+template <bool STRETCH>
+__device__ __forceinline__ float2 finish_pair(const Dev &d, int c, int b2, const ulonglong2 *M2,
+                                              const ulonglong2 *Mf2, const longlong2 *F2,
+                                              u128 tA, float inv_a, float tf, u128 &acc,
+                                              unsigned long long &m_over, unsigned int &n_over,
+                                              float &q2) {
+  const ulonglong2 m = M2[b2];
+  const longlong2 f = F2[b2];
+  float mq0 = u64_to_float(m.x) * inv_a, mq1 = u64_to_float(m.y) * inv_a;
+  if (Mf2) {
+    const ulonglong2 mf = Mf2[b2];
+    mq0 = u64_to_float(m.x + mf.x) * inv_a;
+    mq1 = u64_to_float(m.y + mf.y) * inv_a;
+  }
+  q2 = fmaf(mq0, mq0, q2);
+  q2 = fmaf(mq1, mq1, q2);
+  bin_excess(d, m.x, f.x, tA, acc, m_over, n_over);
+  bin_excess(d, m.y, f.y, tA, acc, m_over, n_over);
+  float mf0 = mq0, mf1 = mq1;
+  if constexpr (STRETCH) {
+    const ulonglong2 ms = reinterpret_cast<const ulonglong2 *>(d.Ms + (size_t)c * d.G)[b2];
+    mf0 = u64_to_float(ms.x) * inv_a;
+    mf1 = u64_to_float(ms.y) * inv_a;
+  }
+  return make_float2(fmaf(tf, u64_to_float((unsigned long long)f.x) * inv_a, mf0),
+                     fmaf(tf, u64_to_float((unsigned long long)f.y) * inv_a, mf1));
+}
+
+__device__ __forceinline__ void store_bf16_pair(__nv_bfloat16 *hp, __nv_bfloat16 *lp, size_t b2,
+                                                float v0, float v1) {
+  const __nv_bfloat162 hi = __floats2bfloat162_rn(v0, v1);
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(v0 - __low2float(hi), v1 - __high2float(hi));
+  reinterpret_cast<__nv_bfloat162 *>(hp)[b2] = hi;
+  reinterpret_cast<__nv_bfloat162 *>(lp)[b2] = lo;
+}
+
 // Per bin: exact overflow excess and rho in FP32; the last block of each copy
 // reduces the excess and, by mode, records the overflow as the iteration's
 // tau (with the stop test), as an evaluation result, or as the reset value
 // tau_{-1} that sets the first gamma.  STRETCH: rho comes from the
 // stretched map (density stretching on); the overflow always from M.  Two
 // bins per thread and step (G is even): 16-byte loads and paired bf16
-// conversions and stores.
-template <bool STRETCH>
+// conversions and stores.  FOLD (the even/odd split of the tensor-core
+// solve): four bins per step, (x, y), (x, y+1) and their mirrors
+// (x, ny-1-y), (x, ny-2-y), and rho leaves as the sums rho_y + rho_{ny-1-y}
+// at y and the differences at ny/2 + y (y < ny/2).
+template <bool STRETCH, bool FOLD>
 __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, int mode) {
   __shared__ u128 sm[32];
   __shared__ float smf[32];
@@ -353,35 +393,30 @@ __global__ void __launch_bounds__(kThreads) k_density_finish(Dev d, int copy0, i
   unsigned long long m_over = 0ull;
   unsigned int n_over = 0u;
   float q2 = 0.f;
-  const int G2 = d.G >> 1;
-  for (int b2 = blockIdx.x * blockDim.x + threadIdx.x; b2 < G2; b2 += gridDim.x * blockDim.x) {
-    const ulonglong2 m = M2[b2];
-    const longlong2 f = F2[b2];
-    float mq0 = u64_to_float(m.x) * inv_a, mq1 = u64_to_float(m.y) * inv_a;
-    if (Mf2) {
-      const ulonglong2 mf = Mf2[b2];
-      mq0 = u64_to_float(m.x + mf.x) * inv_a;
-      mq1 = u64_to_float(m.y + mf.y) * inv_a;
+  if constexpr (FOLD) {
+    __nv_bfloat16 *rh = d.rho_h + (size_t)c * d.G, *rl = d.rho_l + (size_t)c * d.G;
+    const int q4 = d.ny >> 2, nq = d.G >> 2, hy = d.ny >> 1;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nq; t += gridDim.x * blockDim.x) {
+      const int x = t / q4, y = 2 * (t - x * q4);  // y even, below ny/2
+      const int row = x * d.ny;
+      const float2 a = finish_pair<STRETCH>(d, c, (row + y) >> 1, M2, Mf2, F2, tA, inv_a, tf, acc,
+                                            m_over, n_over, q2);
+      // bins ny-2-y and ny-1-y
+      const float2 b = finish_pair<STRETCH>(d, c, (row + d.ny - 2 - y) >> 1, M2, Mf2, F2, tA,
+                                            inv_a, tf, acc, m_over, n_over, q2);
+      store_bf16_pair(rh, rl, (size_t)(row + y) >> 1, __fadd_rn(a.x, b.y), __fadd_rn(a.y, b.x));
+      store_bf16_pair(rh, rl, (size_t)(row + hy + y) >> 1, __fsub_rn(a.x, b.y),
+                      __fsub_rn(a.y, b.x));
     }
-    q2 = fmaf(mq0, mq0, q2);
-    q2 = fmaf(mq1, mq1, q2);
-    bin_excess(d, m.x, f.x, tA, acc, m_over, n_over);
-    bin_excess(d, m.y, f.y, tA, acc, m_over, n_over);
-    float mf0 = mq0, mf1 = mq1;
-    if constexpr (STRETCH) {
-      const ulonglong2 ms = reinterpret_cast<const ulonglong2 *>(d.Ms + (size_t)c * d.G)[b2];
-      mf0 = u64_to_float(ms.x) * inv_a;
-      mf1 = u64_to_float(ms.y) * inv_a;
-    }
-    const float rv0 = fmaf(tf, u64_to_float((unsigned long long)f.x) * inv_a, mf0);
-    const float rv1 = fmaf(tf, u64_to_float((unsigned long long)f.y) * inv_a, mf1);
-    if (d.tc) {
-      const __nv_bfloat162 hi = __floats2bfloat162_rn(rv0, rv1);
-      const __nv_bfloat162 lo = __floats2bfloat162_rn(rv0 - __low2float(hi), rv1 - __high2float(hi));
-      reinterpret_cast<__nv_bfloat162 *>(d.rho_h + (size_t)c * d.G)[b2] = hi;
-      reinterpret_cast<__nv_bfloat162 *>(d.rho_l + (size_t)c * d.G)[b2] = lo;
-    } else {
-      reinterpret_cast<float2 *>(d.rho + (size_t)c * d.G)[b2] = make_float2(rv0, rv1);
+  } else {
+    const int G2 = d.G >> 1;
+    for (int b2 = blockIdx.x * blockDim.x + threadIdx.x; b2 < G2; b2 += gridDim.x * blockDim.x) {
+      const float2 rv = finish_pair<STRETCH>(d, c, b2, M2, Mf2, F2, tA, inv_a, tf, acc, m_over,
+                                             n_over, q2);
+      if (d.tc)
+        store_bf16_pair(d.rho_h + (size_t)c * d.G, d.rho_l + (size_t)c * d.G, b2, rv.x, rv.y);
+      else
+        reinterpret_cast<float2 *>(d.rho + (size_t)c * d.G)[b2] = rv;
     }
   }
   acc += ((u128)m_over << d.t_shift) - (u128)n_over * tA;
@@ -475,10 +510,14 @@ void launch_scatter_fixed(const Dev &d, const float2 *xy, int n0, int n1,
 
 void launch_density_finish(const Dev &d, int copy0, int ncopy, int mode, cudaStream_t st) {
   dim3 grid(d.bin_blocks, ncopy);
-  if (d.Ms)
-    launch_pdl(k_density_finish<true>, grid, dim3(kThreads), 0, st, d, copy0, mode);
+  if (d.Ms && d.bfly)
+    launch_pdl(k_density_finish<true, true>, grid, dim3(kThreads), 0, st, d, copy0, mode);
+  else if (d.Ms)
+    launch_pdl(k_density_finish<true, false>, grid, dim3(kThreads), 0, st, d, copy0, mode);
+  else if (d.bfly)
+    launch_pdl(k_density_finish<false, true>, grid, dim3(kThreads), 0, st, d, copy0, mode);
   else
-    launch_pdl(k_density_finish<false>, grid, dim3(kThreads), 0, st, d, copy0, mode);
+    launch_pdl(k_density_finish<false, false>, grid, dim3(kThreads), 0, st, d, copy0, mode);
 }
 
 }  // namespace hp

@@ -153,6 +153,9 @@ struct Dev {
   __nv_bfloat16 *T_h, *T_l;         // [K][3][G]
   __nv_bfloat16 *SB_h, *SB_l;       // [K][3][G]
   __nv_bfloat16 *A1h, *A1l, *A2h, *A2l, *A3h, *A3l, *A4h, *A4l;
+  int bfly;                         // the even/odd split of every transform (spectral.cu)
+  float *wu_p, *wv_p, *cu_p, *cv_p; // with it: wu, wv, cu, cv in the frequency order of the
+                                    // split (the even frequencies, then the odd ones)
   const void *tcm;                  // host array of 16 CUtensorMap (4 per GEMM stage)
   int tc_bn[4];                     // tile width N (64 or 128) of each GEMM stage
   int tc_split[4];                  // 1, or 2: split-K over two CTAs (tile width 128 only)

@@ -144,39 +144,88 @@ void launch_spectral_fp32(const Dev &d, int copy0, int ncopy, int with_psi, int 
 // reads it for every field w: its y matrix holds S_N with column v scaled by
 // w_v, and its x output's columns u are scaled by w_u, which gives the field
 // coefficients w_u B and w_v B of the FP32 chain above (psi takes B as is).
-void launch_spectral_tc(const Dev &d, int copy0, int ncopy, int with_psi, int eval,
-                        cudaStream_t st) {
-  const CUtensorMap *mp = static_cast<const CUtensorMap *>(d.tcm);
-  TcArgs g = {};
+//
+// Even/odd split (d.bfly; both sides multiples of 256).  With
+// c_k(i) = cos(pi k (i + 1/2) / L) and s_k(i) = sin(pi k (i + 1/2) / L),
+// c_k(L-1-i) = (-1)^k c_k(i) and s_k(L-1-i) = (-1)^(k+1) s_k(i).  So a
+// forward cosine transform needs, for its even frequencies, only the sums
+// x_i + x_{L-1-i} and, for its odd ones, only the differences (i < L/2):
+// half the contraction.  An inverse transform gives, with E_i and O_i its
+// sums over the even and over the odd frequencies (i < L/2),
+// x_i = E_i + O_i and x_{L-1-i} = +-(E_i - O_i) (+ for cosines, - for
+// sines): half the rows, each contracted over all frequencies.  Frequencies
+// are kept in the order 0, 2, 4, ..., 1, 3, 5, ... between the stages, so
+// the even and odd halves are the two halves of every contraction:
+//   rho' = rho's y-halves (sums, differences)     (density finish)
+//   stage 1: T' rows in that order; its epilogue writes the x-halves of T
+//            (each CTA holds columns x and nx-1-x)
+//   stage 2: forward along x on T', the coefficient field in that order
+//   stage 3: inverse along y (rows y < ny/2 and their mirrors)
+//   stage 4: inverse along x: the field in natural order
+// Every stage does half the tensor-core work of the plain chain.
+namespace {
+
+void stage_args(const Dev &d, int stage, int with_psi, TcArgs &g) {
+  const int f = d.bfly;
+  g.b_koff = g.fold = g.mirror = 0;
+  if (stage == 0) {
+    // G1: T[0] = Cn rho^T   (ny x nx, K = ny)
+    g.M = d.ny; g.N = d.nx; g.K = f ? d.ny / 2 : d.ny; g.nwhich = 1;
+    g.b_per_copy = 1; g.b_shared = 0; g.d_per_copy = 3; g.col_scale = nullptr;
+    g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
+    g.b_koff = f ? d.ny / 2 : 0;
+    g.fold = f;
+  } else if (stage == 1) {
+    // G2: SB = spectral(Cm T[0]^T)   (nx x ny, K = nx), one field per copy
+    g.M = d.nx; g.N = d.ny; g.K = f ? d.nx / 2 : d.nx; g.nwhich = 1;
+    g.b_per_copy = 3; g.b_shared = 0; g.d_per_copy = 1; g.col_scale = nullptr;
+    g.epi = TC_EPI_SPECTRAL; g.Dh = d.SB_h; g.Dl = d.SB_l;
+    g.b_koff = f ? d.nx / 2 : 0;
+  } else if (stage == 2) {
+    // G3: T[w] = An_w SB^T   (ny x nx, K = ny), the x output scaled by w_u
+    g.M = d.ny; g.N = d.nx; g.K = d.ny; g.nwhich = with_psi ? 3 : 2;
+    g.b_per_copy = 1; g.b_shared = 1; g.d_per_copy = 3; g.col_scale = f ? d.wu_p : d.wu;
+    g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
+    g.mirror = f;
+    g.msign[0] = 1.f; g.msign[1] = -1.f; g.msign[2] = 1.f;  // y: cos, sin, cos
+  } else {
+    // G4: E[w] = Am_w T[w]^T   (nx x ny, K = nx)
+    g.M = d.nx; g.N = d.ny; g.K = d.nx; g.nwhich = with_psi ? 3 : 2;
+    g.b_per_copy = 3; g.b_shared = 0; g.d_per_copy = 3; g.col_scale = nullptr;
+    g.epi = TC_EPI_F32; g.Df = d.E; g.Dh = g.Dl = nullptr;
+    g.mirror = f;
+    g.msign[0] = -1.f; g.msign[1] = 1.f; g.msign[2] = 1.f;  // x: sin, cos, cos
+  }
+}
+
+void base_args(const Dev &d, int copy0, int eval, int with_psi, TcArgs &g) {
+  g = TcArgs{};
   g.copy0 = copy0;
   g.cs = d.cs;
   g.eval = eval;
   g.err = d.err;
-  g.wu = d.wu; g.wv = d.wv; g.cu = d.cu; g.cv = d.cv;
+  const bool f = d.bfly != 0;
+  g.wu = f ? d.wu_p : d.wu; g.wv = f ? d.wv_p : d.wv;
+  g.cu = f ? d.cu_p : d.cu; g.cv = f ? d.cv_p : d.cv;
   g.with_psi = with_psi;
   g.ws = d.tc_ws;
   g.ws_ctr = d.tc_ws_ctr;
-  const int nw = with_psi ? 3 : 2;
-  // G1: T[0] = Cn rho^T   (ny x nx, K = ny)
-  g.M = d.ny; g.N = d.nx; g.K = d.ny; g.nwhich = 1; g.b_per_copy = 1; g.d_per_copy = 3;
-  g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
-  launch_tc_gemm(mp + 0, g, ncopy, d.tc_bn[0], d.tc_split[0], st);
-  // G2: SB = spectral(Cm T[0]^T)   (nx x ny, K = nx), one field per copy
-  g.M = d.nx; g.N = d.ny; g.K = d.nx; g.b_per_copy = 3; g.d_per_copy = 1;
-  g.epi = TC_EPI_SPECTRAL; g.Dh = d.SB_h; g.Dl = d.SB_l;
-  launch_tc_gemm(mp + 4, g, ncopy, d.tc_bn[1], d.tc_split[1], st);
-  // G3: T[w] = An_w SB^T   (ny x nx, K = ny), the x output scaled by w_u
-  g.M = d.ny; g.N = d.nx; g.K = d.ny; g.nwhich = nw;
-  g.b_per_copy = 1; g.b_shared = 1; g.d_per_copy = 3; g.col_scale = d.wu;
-  g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
-  // with psi the last two stages have a third field: more tiles than the
-  // split-K workspace holds, so one CTA per tile (the same bits)
-  launch_tc_gemm(mp + 8, g, ncopy, d.tc_bn[2], with_psi ? 1 : d.tc_split[2], st);
-  // G4: E[w] = Am_w T[w]^T   (nx x ny, K = nx)
-  g.M = d.nx; g.N = d.ny; g.K = d.nx;
-  g.b_per_copy = 3; g.b_shared = 0; g.col_scale = nullptr;
-  g.epi = TC_EPI_F32; g.Df = d.E; g.Dh = g.Dl = nullptr;
-  launch_tc_gemm(mp + 12, g, ncopy, d.tc_bn[3], with_psi ? 1 : d.tc_split[3], st);
+}
+
+}  // namespace
+
+void launch_spectral_tc(const Dev &d, int copy0, int ncopy, int with_psi, int eval,
+                        cudaStream_t st) {
+  const CUtensorMap *mp = static_cast<const CUtensorMap *>(d.tcm);
+  TcArgs g;
+  base_args(d, copy0, eval, with_psi, g);
+  for (int s = 0; s < 4; ++s) {
+    stage_args(d, s, with_psi, g);
+    // with psi the last two stages have a third field: more tiles than the
+    // split-K workspace holds, so one CTA per tile (the same bits)
+    const int split = (with_psi && s >= 2) ? 1 : d.tc_split[s];
+    launch_tc_gemm(mp + 4 * s, g, ncopy, d.tc_bn[s], split, st);
+  }
 }
 
 // The first GEMM stage of copy 0 with its producer idle: no tile ever lands,
@@ -184,17 +233,10 @@ void launch_spectral_tc(const Dev &d, int copy0, int ncopy, int with_psi, int ev
 // second each) and the kernel raises d.err instead of hanging.
 void launch_spectral_tc_stalled(const Dev &d, cudaStream_t st) {
   const CUtensorMap *mp = static_cast<const CUtensorMap *>(d.tcm);
-  TcArgs g = {};
-  g.copy0 = 0;
-  g.cs = d.cs;
-  g.eval = 1;
-  g.err = d.err;
-  g.wu = d.wu; g.wv = d.wv; g.cu = d.cu; g.cv = d.cv;
-  g.ws = d.tc_ws;
-  g.ws_ctr = d.tc_ws_ctr;
+  TcArgs g;
+  base_args(d, 0, 1, 0, g);
   g.no_load = 1;
-  g.M = d.ny; g.N = d.nx; g.K = d.ny; g.nwhich = 1; g.b_per_copy = 1; g.d_per_copy = 3;
-  g.epi = TC_EPI_SPLIT; g.Dh = d.T_h; g.Dl = d.T_l;
+  stage_args(d, 0, 0, g);
   launch_tc_gemm(mp + 0, g, 1, d.tc_bn[0], d.tc_split[0], st);
 }
 

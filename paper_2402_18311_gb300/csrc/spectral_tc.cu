@@ -12,12 +12,12 @@
 // Kernel layout: one 128 x BN output tile per CTA of 4 warps.  Warp 0 (one
 // lane) streams K-blocks of 64 elements of A_hi, A_lo, B_hi, B_lo into a
 // 3-stage shared-memory ring with TMA (128-byte swizzle); warp 1 (one lane)
-// issues tcgen05.mma (M=128, N=BN, K=16) into a TMEM accumulator and frees
-// each stage with tcgen05.commit; then all four warps read the accumulator
+// issues tcgen05.mma (M=128, N=BN, K=16) into TMEM accumulators and frees
+// each stage with tcgen05.commit; then all four warps read the accumulators
 // with tcgen05.ld and run the fused epilogue (plain FP32 store, bf16 split,
-// or the spectral weights of the Poisson solve).  Every wait on an mbarrier
-// gives up after about a second of clock cycles and raises an error flag
-// instead of hanging.
+// the spectral weights of the Poisson solve, or the even/odd combinations
+// of spectral.cu).  Every wait on an mbarrier gives up after about a second
+// of clock cycles and raises an error flag instead of hanging.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -114,6 +114,24 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                : "memory");
 }
 
+// 32 columns of this warp's 32 TMEM lanes; tmem_wait() makes them valid.
+__device__ __forceinline__ void tmem_ld32_nw(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -135,6 +153,52 @@ __device__ __forceinline__ void st_v8(void *p, uint4 a, uint4 b) {
                : "memory");
 }
 
+// The two K halves of 32 accumulator columns from cc: with SPLIT = 1 both
+// are this CTA's (TMEM columns cc and BN + cc), with SPLIT = 2 one is this
+// CTA's (half ks) and the other the partner's, from the workspace.
+template <int BN, int SPLIT>
+__device__ __forceinline__ void acc_halves(uint32_t trow, int cc, const float *ws_other, int ks,
+                                           float (&h0)[32], float (&h1)[32]) {
+  uint32_t r[32];
+  if constexpr (SPLIT == 1) {
+    // both halves in flight before one wait
+    uint32_t r2[32];
+    tmem_ld32_nw(trow + (uint32_t)cc, r);
+    tmem_ld32_nw(trow + (uint32_t)(BN + cc), r2);
+    tmem_wait();
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      h0[i] = __uint_as_float(r[i]);
+      h1[i] = __uint_as_float(r2[i]);
+    }
+  } else {
+    tmem_ld32(trow + (uint32_t)cc, r);
+    const float4 *src = reinterpret_cast<const float4 *>(ws_other + cc);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float4 q = __ldcg(src + i);
+      const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float own = __uint_as_float(r[4 * i + j]);
+        h0[4 * i + j] = ks == 0 ? own : qv[j];
+        h1[4 * i + j] = ks == 0 ? qv[j] : own;
+      }
+    }
+  }
+}
+
+// Their sum: the tile's 32 output values (addition is commutative, so the
+// split and unsplit kernels give the same bits).
+template <int BN, int SPLIT>
+__device__ __forceinline__ void acc_sum(uint32_t trow, int cc, const float *ws_other, int ks,
+                                        float (&v)[32]) {
+  float h1[32];
+  acc_halves<BN, SPLIT>(trow, cc, ws_other, ks, v, h1);
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __fadd_rn(v[i], h1[i]);
+}
+
 __device__ __forceinline__ void split_store(__nv_bfloat16 *hi, __nv_bfloat16 *lo, const float *v) {
   // 32 consecutive values -> 32 bf16 hi and 32 bf16 lo (64 bytes each)
   __align__(16) __nv_bfloat16 h[32];
@@ -150,6 +214,29 @@ __device__ __forceinline__ void split_store(__nv_bfloat16 *hi, __nv_bfloat16 *lo
   for (int i = 0; i < 4; i += 2) {
     st_v8(dh + i, sh[i], sh[i + 1]);
     st_v8(dl + i, sl[i], sl[i + 1]);
+  }
+}
+
+// 32 consecutive FP32 outputs at element o of the output (column n of the
+// row): stored as they are (TC_EPI_F32) or as a bf16 pair (TC_EPI_SPLIT,
+// the which == 0 output scaled by col_scale[n] first).
+__device__ __forceinline__ void store_out(const TcArgs &g, int which, size_t o, int n,
+                                          float (&v)[32]) {
+  if (g.epi == TC_EPI_F32) {
+    uint4 *dst = reinterpret_cast<uint4 *>(g.Df + o);
+#pragma unroll
+    for (int i = 0; i < 8; i += 2)
+      st_v8(dst + i,
+            make_uint4(__float_as_uint(v[4 * i]), __float_as_uint(v[4 * i + 1]),
+                       __float_as_uint(v[4 * i + 2]), __float_as_uint(v[4 * i + 3])),
+            make_uint4(__float_as_uint(v[4 * i + 4]), __float_as_uint(v[4 * i + 5]),
+                       __float_as_uint(v[4 * i + 6]), __float_as_uint(v[4 * i + 7])));
+  } else {
+    if (g.col_scale && which == 0) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = __fmul_rn(v[i], g.col_scale[n + i]);
+    }
+    split_store(g.Dh + o, g.Dl + o, v);
   }
 }
 
@@ -171,7 +258,6 @@ __global__ void __launch_bounds__(128, 1)
                 const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
                 TcArgs g) {
   extern __shared__ unsigned char smem_raw[];
-  pdl_wait();
   const int z = blockIdx.z;
   const int which = z % g.nwhich;
   const int c = g.copy0 + z / g.nwhich;
@@ -224,7 +310,26 @@ __global__ void __launch_bounds__(128, 1)
   const int nhalf = g.K / BKE / 2;  // K-blocks per half (K is a multiple of 128)
   const int kb0 = ks * nhalf;       // this CTA's first K-block
   const int nk = SPLIT == 1 ? 2 * nhalf : nhalf;
+  const bool fold = g.fold != 0, mirror = g.mirror != 0;
+  // forward even/odd split: the odd-frequency rows read the second half of B
+  const int kxb = (g.b_koff && m0 >= g.M / 2) ? g.b_koff : 0;
 
+  // Programmatic launch: everything up to here, and the loads of the
+  // constant operand A into the first ring stages, overlaps the end of the
+  // kernel before (which lets this one launch once its epilogue starts);
+  // B and every output wait for it to complete.  The copy's stopped flag
+  // and the tables read above are written by earlier kernels only.
+  const int npre = g.no_load ? 0 : (nk < STAGES ? nk : STAGES);
+  if (warp == 0 && lane == 0) {
+    for (int kb = 0; kb < npre; ++kb) {
+      unsigned char *st = tiles + kb * STAGE_BYTES;
+      const int kx = (kb0 + kb) * BKE;
+      mbar_expect_tx(&full[kb], STAGE_BYTES);
+      tma_load_3d(st, &mAh, &full[kb], kx, m0, which);
+      tma_load_3d(st + TILE_A, &mAl, &full[kb], kx, m0, which);
+    }
+  }
+  pdl_wait();
   if (warp == 0 && lane == 0) {
     // producer
     int issued = 0;
@@ -238,11 +343,24 @@ __global__ void __launch_bounds__(128, 1)
       if (*(volatile int *)abort_flag) break;
       unsigned char *st = tiles + s * STAGE_BYTES;
       const int kx = (kb0 + kb) * BKE;
-      mbar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_3d(st, &mAh, &full[s], kx, m0, which);
-      tma_load_3d(st + TILE_A, &mAl, &full[s], kx, m0, which);
-      tma_load_3d(st + 2 * TILE_A, &mBh, &full[s], kx, n0, bz);
-      tma_load_3d(st + 2 * TILE_A + TILE_B, &mBl, &full[s], kx, n0, bz);
+      if (kb >= npre) {
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        tma_load_3d(st, &mAh, &full[s], kx, m0, which);
+        tma_load_3d(st + TILE_A, &mAl, &full[s], kx, m0, which);
+      }
+      if (fold) {
+        // two half-height boxes (the map's box is BN/2 rows): rows from
+        // f BN/2 and their mirrors, stacked in the order of a full box
+        constexpr int HB = BN / 2;
+        const int r0 = blockIdx.x * HB, r1 = g.N - (blockIdx.x + 1) * HB;
+        tma_load_3d(st + 2 * TILE_A, &mBh, &full[s], kxb + kx, r0, bz);
+        tma_load_3d(st + 2 * TILE_A + HB * BKE * 2, &mBh, &full[s], kxb + kx, r1, bz);
+        tma_load_3d(st + 2 * TILE_A + TILE_B, &mBl, &full[s], kxb + kx, r0, bz);
+        tma_load_3d(st + 2 * TILE_A + TILE_B + HB * BKE * 2, &mBl, &full[s], kxb + kx, r1, bz);
+      } else {
+        tma_load_3d(st + 2 * TILE_A, &mBh, &full[s], kxb + kx, n0, bz);
+        tma_load_3d(st + 2 * TILE_A + TILE_B, &mBl, &full[s], kxb + kx, n0, bz);
+      }
       issued = kb + 1;
     }
     // make sure no copy is still landing in shared memory when the CTA ends
@@ -286,6 +404,7 @@ __global__ void __launch_bounds__(128, 1)
   // epilogue: TMEM lanes 32*warp .. +31 hold rows m0 + 32*warp + lane
   // the tcgen05.ld below is warp-collective: decide per warp
   const bool have = __all_sync(0xffffffffu, mbar_wait(done, 0)) != 0;
+  asm volatile("griddepcontrol.launch_dependents;");  // the next kernel may launch
   if (!have) *abort_flag = 1;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncwarp();
@@ -327,47 +446,52 @@ __global__ void __launch_bounds__(128, 1)
     run = have && *(volatile int *)last_flag != 0;
     if (run) __threadfence();
   }
-  if (run) {
+  if (run && fold) {
+    // forward even/odd split of the next stage's contraction: column j
+    // (n = f BN/2 + j) pairs with column BN-1-j (its mirror N-1-n)
+#pragma unroll 1
+    for (int cc = 0; cc < BN / 2; cc += 32) {
+      float va[32], vb[32], vd[32];
+      acc_sum<BN, SPLIT>(trow, cc, ws_other, ks, va);
+      acc_sum<BN, SPLIT>(trow, BN - 32 - cc, ws_other, ks, vb);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float b = vb[31 - i];
+        vd[i] = __fsub_rn(va[i], b);
+        va[i] = __fadd_rn(va[i], b);
+      }
+      const size_t o = (size_t)dz * g.M * g.N + (size_t)m * g.N + blockIdx.x * (BN / 2) + cc;
+      split_store(g.Dh + o, g.Dl + o, va);
+      split_store(g.Dh + o + g.N / 2, g.Dl + o + g.N / 2, vd);
+    }
+  } else if (run && mirror) {
+    // inverse even/odd split: E (first K half) and O (second K half) give
+    // rows m and M-1-m
+    const float sg = g.msign[which];
+    const size_t o0 = (size_t)dz * g.M * g.N + (size_t)m * g.N + n0;
+    const size_t o1 = (size_t)dz * g.M * g.N + (size_t)(g.M - 1 - m) * g.N + n0;
+#pragma unroll 1
+    for (int cc = 0; cc < BN; cc += 32) {
+      float ve[32], vo[32];
+      acc_halves<BN, SPLIT>(trow, cc, ws_other, ks, ve, vo);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float e = ve[i], od = vo[i];
+        ve[i] = __fadd_rn(e, od);
+        vo[i] = sg > 0.f ? __fsub_rn(e, od) : __fsub_rn(od, e);
+      }
+      store_out(g, which, o0 + cc, n0 + cc, ve);
+      store_out(g, which, o1 + cc, n0 + cc, vo);
+    }
+  } else if (run) {
 #pragma unroll 1
     for (int cc = 0; cc < BN; cc += 32) {
       float v[32];
-      {
-        uint32_t r[32];
-        tmem_ld32(trow + (uint32_t)cc, r);
-        if constexpr (SPLIT == 1) {
-          uint32_t r2[32];
-          tmem_ld32(trow + (uint32_t)(BN + cc), r2);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = __fadd_rn(__uint_as_float(r[i]), __uint_as_float(r2[i]));
-        } else {
-          const float4 *src = reinterpret_cast<const float4 *>(ws_other + cc);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float4 q = __ldcg(src + i);
-            v[4 * i] = __fadd_rn(__uint_as_float(r[4 * i]), q.x);
-            v[4 * i + 1] = __fadd_rn(__uint_as_float(r[4 * i + 1]), q.y);
-            v[4 * i + 2] = __fadd_rn(__uint_as_float(r[4 * i + 2]), q.z);
-            v[4 * i + 3] = __fadd_rn(__uint_as_float(r[4 * i + 3]), q.w);
-          }
-        }
-      }
+      acc_sum<BN, SPLIT>(trow, cc, ws_other, ks, v);
       const int n = n0 + cc;
       const size_t o = (size_t)dz * g.M * g.N + (size_t)m * g.N + n;
-      if (g.epi == TC_EPI_F32) {
-        uint4 *dst = reinterpret_cast<uint4 *>(g.Df + o);
-#pragma unroll
-        for (int i = 0; i < 8; i += 2)
-          st_v8(dst + i,
-                make_uint4(__float_as_uint(v[4 * i]), __float_as_uint(v[4 * i + 1]),
-                           __float_as_uint(v[4 * i + 2]), __float_as_uint(v[4 * i + 3])),
-                make_uint4(__float_as_uint(v[4 * i + 4]), __float_as_uint(v[4 * i + 5]),
-                           __float_as_uint(v[4 * i + 6]), __float_as_uint(v[4 * i + 7])));
-      } else if (g.epi == TC_EPI_SPLIT) {
-        if (g.col_scale && which == 0) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = __fmul_rn(v[i], g.col_scale[n + i]);
-        }
-        split_store(g.Dh + o, g.Dl + o, v);
+      if (g.epi != TC_EPI_SPECTRAL) {
+        store_out(g, which, o, n, v);
       } else {
         // spectral weights: a_uv = acc c_u c_v/(M N) and the one field
         // B_uv = a_uv / (w_u^2 + w_v^2), the potential's coefficients; the
@@ -405,7 +529,9 @@ int tc_smem_bytes(int bn) {
 // (bn = 128 only): two CTAs per tile, one half of K each.
 void launch_tc_gemm(const CUtensorMap *maps4, const TcArgs &g, int ncopy, int bn, int split,
                     cudaStream_t st) {
-  dim3 grid(g.N / bn, (g.M / BM) * (split == 2 ? 2 : 1), g.nwhich * ncopy);
+  // with mirror the grid covers the first half of the rows
+  const int mrows = g.mirror ? g.M / 2 : g.M;
+  dim3 grid(g.N / bn, (mrows / BM) * (split == 2 ? 2 : 1), g.nwhich * ncopy);
   if (bn == 64)
     launch_pdl(k_umma_gemm<64, 2, 1>, grid, dim3(128), Cfg<64, 2>::SMEM_BYTES, st, maps4[0],
                maps4[1], maps4[2], maps4[3], g);

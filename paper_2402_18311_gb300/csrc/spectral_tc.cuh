@@ -30,6 +30,21 @@ struct TcArgs {
   unsigned int *ws_ctr;        // split-K: arrivals per tile (reset by the second)
   int no_load;                 // 1: the producer issues no copies (failure-path check:
                                // the consumers' bounded waits give up)
+  // Even/odd split of a length-L transform (L a multiple of 256; see
+  // spectral.cu): with x'_i = x_i + x_{L-1-i} and x''_i = x_i - x_{L-1-i}
+  // (i < L/2) the forward cosine transform's even frequencies need only x'
+  // and its odd ones only x''; an inverse transform's outputs i and L-1-i
+  // share the sums E_i over the even frequencies and O_i over the odd ones.
+  int b_koff;                  // forward: K is the half length; output rows m >= M/2 (the odd
+                               // frequencies) read B from K offset b_koff (x''), the others
+                               // from 0 (x'); 0: off
+  int fold;                    // TC_EPI_SPLIT: the CTA's B tile is rows [f BN/2, (f+1) BN/2)
+                               // and their mirrors N-1-n (f = tile column), and the epilogue
+                               // writes the split pair (x', x'') of its N/2-wide halves
+  int mirror;                  // inverse: the grid covers rows m < M/2; the two K halves
+                               // (even, odd frequencies) give E and O, row m gets E + O and
+                               // row M-1-m gets msign[which] (E - O)
+  float msign[3];
 };
 
 int tc_smem_bytes(int bn);

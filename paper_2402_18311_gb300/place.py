@@ -66,7 +66,8 @@ class place_params(ct.Structure):
                 ("max_backtracks", ct.c_int32), ("stretch", ct.c_int32),
                 ("autotune", ct.c_int32), ("scatter_mode", ct.c_int32), ("gemm_bn", ct.c_int32),
                 ("wa_big_cap", ct.c_int32), ("gemm_split", ct.c_int32), ("fillers", ct.c_int32),
-                ("macro_precond", ct.c_float), ("wa_streams", ct.c_int32)]
+                ("macro_precond", ct.c_float), ("wa_streams", ct.c_int32),
+                ("dct_fold", ct.c_int32)]
 
 
 class place_info(ct.Structure):
@@ -80,7 +81,7 @@ class place_info(ct.Structure):
                 ("gemm_bn", ct.c_int32 * 4), ("gemm_split", ct.c_int32 * 4),
                 ("wa_big_cap", ct.c_int32), ("autotuned", ct.c_int32),
                 ("scatter_t1", ct.c_double), ("scatter_t2", ct.c_double),
-                ("autotune_ms", ct.c_double), ("wa_streams", ct.c_int32), ("reserved", ct.c_int32)]
+                ("autotune_ms", ct.c_double), ("wa_streams", ct.c_int32), ("dct_fold", ct.c_int32)]
 
 
 class place_state(ct.Structure):

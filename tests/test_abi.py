@@ -58,13 +58,13 @@ def test_default_params_match_the_oracle_reading(L):
     assert p.max_backtracks == o.max_backtracks == 0
     assert p.dct_mode == place.PLACE_DCT_AUTO and p.autotune == 1 and p.scatter_mode == -1
     assert p.gemm_bn == 0 and p.wa_big_cap == 0 and p.gemm_split == 0 and p.fillers == 0
-    assert p.wa_streams == 0
+    assert p.wa_streams == 0 and p.dct_fold == 1
     assert p.macro_precond == o.macro_precond == 1.0
 
 
 def test_struct_sizes_match_header_layout():
     assert ct.sizeof(place.place_netlist) == 4 * 4 + 10 * 8
-    assert ct.sizeof(place.place_params) == 22 * 4
+    assert ct.sizeof(place.place_params) == 23 * 4
     assert ct.sizeof(place.place_state) == 4 * 4 + 7 * 8
     assert ct.sizeof(place.place_info) == 8 * 4 + 2 * 8 + 2 * 8 + 8 + 4 * 4 + 10 * 4 + 3 * 8 + 2 * 4
     assert ct.sizeof(place.place_job) == 4 * 4 + 8 + 8 + 8 + 8
@@ -149,7 +149,7 @@ def test_create_rejects_bad_params(L):
     assert ei.value.code == place.PLACE_EINVAL and "stretch" in str(ei.value)
     for field, bad in (("autotune", 2), ("scatter_mode", 3), ("gemm_bn", 96), ("wa_big_cap", 16),
                        ("gemm_split", 3), ("fillers", 2), ("macro_precond", 0.0),
-                       ("wa_streams", 4)):
+                       ("wa_streams", 4), ("dct_fold", 2)):
         with pytest.raises(place.PlaceError) as ei:
             place.place_create(d, place.place_default_params(**{field: bad}))
         assert ei.value.code == place.PLACE_EINVAL and field in str(ei.value)

@@ -1285,3 +1285,128 @@ def test_tensor_core_field_error_at_512_bins():
         assert rel_l2(psi, opsi.ravel()) < 1e-4
     finally:
         h.close()
+
+
+# --- the even/odd split of the transforms (dct_fold, grids of 256-multiples)
+
+
+def _fold_design(nx, ny, die=None, n=8000, seed=21):
+    die = die or (0, 0, 2 * nx, 2 * ny)
+    return synth.make_design(n_movable=n, die=die, nx=nx, ny=ny, n_nets=int(n * 1.1), n_pads=16,
+                             target_density=0.9, seed=seed, name=f"fold_{nx}x{ny}")
+
+
+@pytest.mark.parametrize("nx,ny,die", [(256, 256, None), (512, 256, (-512, -256, 512, 256)),
+                                       (256, 512, (1000, 3000, 1512, 4024))])
+def test_fold_stages_match_oracle(nx, ny, die):
+    # every stage through the split solve, square and non-square (the two
+    # axes' splits are told apart), at the start and once spread
+    d = _fold_design(nx, ny, die)
+    h = Handle(d, tau_stop=-1.0, max_iters=1000)
+    try:
+        assert h.info.dct_mode == place.PLACE_DCT_BF16X3 and h.info.dct_fold == 1
+        x, y = h.pos()
+        check_stages(h, x, y, 2.0)
+        x, y = spread(h, 150)
+        check_stages(h, x, y, 2.0)
+    finally:
+        h.close()
+
+
+def test_fold_only_where_the_grid_allows():
+    # both sides multiples of 256 and the tensor-core path; dct_fold = 0 turns it off
+    cases = [((128, 128), {}, 0), ((384, 256), {}, 0), ((256, 256), {}, 1),
+             ((256, 256), {"dct_fold": 0}, 0), ((256, 256), {"dct_mode": place.PLACE_DCT_FP32}, 0)]
+    for (nx, ny), kw, want in cases:
+        h = Handle(_fold_design(nx, ny, n=2000), tau_stop=-1.0, **kw)
+        try:
+            assert h.info.dct_fold == want, (nx, ny, kw)
+        finally:
+            h.close()
+
+
+def test_fold_matches_the_plain_gemms():
+    # the split and the plain chain solve the same equation: fields within
+    # 1e-5 of each other (each is within ~1e-5 of the FP64 solution), and
+    # the same 100-iteration trajectory (HPWL 2e-5, overflow 1e-5, the
+    # bounds of the tensor-core vs FP32 comparison)
+    d = _fold_design(256, 256, n=20000, seed=3)
+    out = []
+    for fold in (0, 1):
+        h = Handle(d, tau_stop=-1.0, max_iters=1000, dct_fold=fold)
+        try:
+            assert h.info.dct_fold == fold
+            G = d.nx * d.ny
+            f = [np.empty(G, np.float32) for _ in range(3)]
+            place.place_eval_field(h.h, 0, *f)
+            place.place_step(h.h, 100)
+            hp = np.empty(1); tv = np.empty(1)
+            place.place_eval_hpwl_overflow(h.h, hp, tv)
+            out.append((f, hp[0], tv[0]))
+        finally:
+            h.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        assert rel_l2(b, a) < 1e-5
+    assert out[1][1] == pytest.approx(out[0][1], rel=2e-5)
+    assert out[1][2] == pytest.approx(out[0][2], abs=1e-5)
+
+
+def test_fold_tuning_candidates_give_identical_results():
+    # the split's variants (tile width, split-K of the forward stages' half
+    # contraction and of the inverse stages' even and odd sums) and the tuned
+    # choice: bit-identical positions and maps
+    d = _fold_design(256, 256, n=20000, seed=2)
+    configs = [dict(autotune=0, gemm_bn=128), dict(autotune=0, gemm_bn=64),
+               dict(autotune=0, gemm_bn=128, gemm_split=2), dict(autotune=1)]
+    ref = None
+    for cfg in configs:
+        h = Handle(d, tau_stop=-1.0, max_iters=1000, **cfg)
+        try:
+            assert h.info.dct_fold == 1
+            if not cfg.get("autotune"):
+                assert list(h.info.gemm_bn) == [cfg["gemm_bn"]] * 4
+                assert list(h.info.gemm_split) == [cfg.get("gemm_split", 1)] * 4
+            out = []
+            for n in (5, 100, 200):
+                place.place_step(h.h, n)
+                x, y = h.pos()
+                gm = np.empty(d.nx * d.ny, np.int64)
+                place.place_eval_density(h.h, 0, gm)
+                out.append((x, y, gm))
+        finally:
+            h.close()
+        if ref is None:
+            ref = out
+            continue
+        for (x, y, gm), (rx, ry, rgm) in zip(out, ref):
+            np.testing.assert_array_equal(x, rx)
+            np.testing.assert_array_equal(y, ry)
+            np.testing.assert_array_equal(gm, rgm)
+
+
+def test_fold_batched_copies_equal_solo_runs():
+    # the copies' batch coordinate through the split solve
+    d = _fold_design(256, 256, n=6000, seed=4)
+    K = 3
+    hb = Handle(d, tau_stop=-1.0, max_iters=300, n_copies=K)
+    try:
+        assert hb.info.dct_fold == 1
+        place.place_step(hb.h, 40)
+        base_x, base_y = hb.pos(0)
+        place.place_set_positions(hb.h, -1, base_x, base_y)
+        place.place_perturb(hb.h, place.PLACE_SHUFFLE_ALL, 0.5, 7, -1)
+        place.place_step(hb.h, 50)
+        finals = [hb.pos(c) for c in range(K)]
+    finally:
+        hb.close()
+    for c in range(K):
+        hs = Handle(d, tau_stop=-1.0, max_iters=300)
+        try:
+            place.place_set_positions(hs.h, 0, base_x, base_y)
+            place.place_perturb(hs.h, place.PLACE_SHUFFLE_ALL, 0.5, 7 + c, 0)
+            place.place_step(hs.h, 50)
+            sx, sy = hs.pos()
+        finally:
+            hs.close()
+        np.testing.assert_array_equal(finals[c][0], sx)
+        np.testing.assert_array_equal(finals[c][1], sy)
