@@ -56,3 +56,15 @@ def test_serving_trace_is_reproducible_and_follows_its_recipe():
 def test_cpu_model_names_something():
     m = bench.cpu_model()
     assert isinstance(m, str) and m
+
+
+def test_spectral_pipe_flops_count_products_and_the_even_odd_split():
+    from types import SimpleNamespace as NS
+    d = NS(n_movable=10, n_cells=12, n_pins=40, n_nets=9, nx=1024, ny=512)
+    n3 = 2 * 512 * 512 * 1024 + 2 * 1024 * 1024 * 512   # one 2D transform's two GEMMs
+    plain = bench.algorithmic(d, NS(dct_mode=0, dct_fold=0))["spectral"]
+    assert plain["flops"] == 2.0 * n3 * 1.5 == plain["flops_pipe"]     # three transforms
+    bf = bench.algorithmic(d, NS(dct_mode=1, dct_fold=0))["spectral"]
+    assert bf["flops_pipe"] == 3 * bf["flops"]                           # BF16x3
+    fold = bench.algorithmic(d, NS(dct_mode=1, dct_fold=1))["spectral"]
+    assert fold["flops"] == bf["flops"] and fold["flops_pipe"] == 1.5 * fold["flops"]
