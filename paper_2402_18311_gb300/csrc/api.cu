@@ -284,29 +284,23 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.pin_off = a.take<float2>(P);
   d.w = a.take<float>(C);
   d.h = a.take<float>(C);
+  d.wh = a.take<float2>(C);
   d.Wq = a.take<int>(C);
   d.Hq = a.take<int>(C);
-  d.npins = a.take<float>(Mv);
-  d.area = a.take<float>(Mv);
+  d.pa = a.take<float2>(Mv);
   d.is_macro = a.take<unsigned char>(C);
   d.st = d.prm.stretch ? a.take<int4>(std::max<size_t>(Mv, 1)) : nullptr;
   d.sR = d.prm.stretch ? a.take<unsigned int>(std::max<size_t>(Mv, 1)) : nullptr;
   d.Ms = d.prm.stretch ? a.take<unsigned long long>(K * G) : nullptr;
   d.xy = a.take<float2>(K * C);
-  d.ux = a.take<float>(K * Mv);
-  d.uy = a.take<float>(K * Mv);
-  d.vpx = a.take<float>(K * Mv);
-  d.vpy = a.take<float>(K * Mv);
-  for (int q = 0; q < 2; ++q) {
-    d.gx[q] = a.take<float>(K * Mv);
-    d.gy[q] = a.take<float>(K * Mv);
-  }
+  d.u = a.take<float2>(K * Mv);
+  d.vp = a.take<float2>(K * Mv);
+  for (int q = 0; q < 2; ++q) d.g[q] = a.take<float2>(K * Mv);
   d.gwx = a.take<float>(K * Mv);
   d.gwy = a.take<float>(K * Mv);
   d.gdx = a.take<float>(K * Mv);
   d.gdy = a.take<float>(K * Mv);
-  d.upx = d.prm.max_backtracks > 0 ? a.take<float>(K * Mv) : nullptr;
-  d.upy = d.prm.max_backtracks > 0 ? a.take<float>(K * Mv) : nullptr;
+  d.up = d.prm.max_backtracks > 0 ? a.take<float2>(K * Mv) : nullptr;
   d.gacc = a.take<unsigned long long>(K * std::max<size_t>(Mv, 1));
   d.M = a.take<unsigned long long>(K * (size_t)d.Gm);
   d.Fmap = a.take<long long>(G);
@@ -1123,8 +1117,13 @@ int place_create(const place_netlist *nl, const place_die *die, const place_bins
   up(d.h, hi.data(), sizeof(float) * Ci);
   up(d.Wq, Wqi.data(), sizeof(int) * Ci);
   up(d.Hq, Hqi.data(), sizeof(int) * Ci);
-  up(d.npins, npins.data(), sizeof(float) * Mo);
-  up(d.area, area.data(), sizeof(float) * Mo);
+  {
+    std::vector<float2> whv(std::max(Ci, 1)), pav(std::max(Mo, 1));
+    for (int i = 0; i < Ci; ++i) whv[i] = make_float2(wi[i], hi[i]);
+    for (int i = 0; i < Mo; ++i) pav[i] = make_float2(npins[i], area[i]);
+    up(d.wh, whv.data(), sizeof(float2) * Ci);
+    up(d.pa, pav.data(), sizeof(float2) * Mo);
+  }
   up(d.is_macro, macro.data(), Ci);
   if (d.st) {
     // density stretching: along each axis a cell narrower than sqrt(2) bins
@@ -1251,7 +1250,7 @@ int place_get_info(const place_t *h, place_info *o) {
   for (int c = 0; c < d.n_cls; ++c) wa += d.wa_blocks[c] > 0;
   // scatter, finish, 4 GEMMs, WA classes, cell grad, precond0, update; the
   // stretched scatter with density stretching, the step redo with backtracking
-  o->kernels_per_iter = 2 + 4 + wa + 3 + (d.Ms ? 1 : 0) + (d.upx ? 1 : 0);
+  o->kernels_per_iter = 2 + 4 + wa + 3 + (d.Ms ? 1 : 0) + (d.up ? 1 : 0);
   o->dct_mode = d.tc ? PLACE_DCT_BF16X3 : PLACE_DCT_FP32;
   for (int s = 0; s < 4; ++s) {
     o->gemm_bn[s] = d.tc ? d.tc_bn[s] : 0;
@@ -1492,7 +1491,7 @@ namespace {
 // order of ckpt_arrays (each padded to 8 bytes), then the history ring.
 struct CkptHeader {
   char magic[8];                 // "HYBROCK1"
-  int32_t version;               // 1
+  int32_t version;               // 2: the per-cell (x, y) pairs of u, v_prev and g interleaved
   int32_t n_cells, n_mov, n_real, n_fill, n_nets, n_pins, nx, ny, frac_bits, hist_cap;
   int32_t has_up;                // backtracking arrays present
   int32_t state_bytes;           // sizeof(CopyState)
@@ -1508,18 +1507,13 @@ std::vector<CkptArray> ckpt_arrays(const Dev &d, int c) {
   const size_t C = d.n_cells, Mo = d.n_mov;
   std::vector<CkptArray> v = {
       {d.xy + c * C, sizeof(float2) * C},
-      {d.ux + c * Mo, sizeof(float) * Mo}, {d.uy + c * Mo, sizeof(float) * Mo},
-      {d.vpx + c * Mo, sizeof(float) * Mo}, {d.vpy + c * Mo, sizeof(float) * Mo},
-      {d.gx[0] + c * Mo, sizeof(float) * Mo}, {d.gy[0] + c * Mo, sizeof(float) * Mo},
-      {d.gx[1] + c * Mo, sizeof(float) * Mo}, {d.gy[1] + c * Mo, sizeof(float) * Mo},
+      {d.u + c * Mo, sizeof(float2) * Mo}, {d.vp + c * Mo, sizeof(float2) * Mo},
+      {d.g[0] + c * Mo, sizeof(float2) * Mo}, {d.g[1] + c * Mo, sizeof(float2) * Mo},
       {d.gwx + c * Mo, sizeof(float) * Mo}, {d.gwy + c * Mo, sizeof(float) * Mo},
       {d.gdx + c * Mo, sizeof(float) * Mo}, {d.gdy + c * Mo, sizeof(float) * Mo},
       {d.gacc + c * Mo, sizeof(unsigned long long) * Mo},
       {d.hist + (size_t)c * d.hist_cap, sizeof(place_iter_record) * d.hist_cap}};
-  if (d.upx) {
-    v.push_back({d.upx + c * Mo, sizeof(float) * Mo});
-    v.push_back({d.upy + c * Mo, sizeof(float) * Mo});
-  }
+  if (d.up) v.push_back({d.up + c * Mo, sizeof(float2) * Mo});
   return v;
 }
 
@@ -1529,11 +1523,11 @@ CkptHeader ckpt_header(const Dev &d) {
   CkptHeader hd;
   std::memset(&hd, 0, sizeof hd);
   std::memcpy(hd.magic, "HYBROCK1", 8);
-  hd.version = 1;
+  hd.version = 2;
   hd.n_cells = d.n_cells; hd.n_mov = d.n_mov; hd.n_real = d.n_real; hd.n_fill = d.n_fill;
   hd.n_nets = d.n_nets; hd.n_pins = d.n_pins; hd.nx = d.nx; hd.ny = d.ny;
   hd.frac_bits = d.F; hd.hist_cap = d.hist_cap;
-  hd.has_up = d.upx ? 1 : 0;
+  hd.has_up = d.up ? 1 : 0;
   hd.state_bytes = (int32_t)sizeof(CopyState);
   hd.dref = d.dref; hd.w_bin = d.w_bin;
   return hd;

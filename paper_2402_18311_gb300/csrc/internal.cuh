@@ -108,9 +108,9 @@ struct Dev {
   float *net_w;      // [n_nets] or nullptr
   int has_net_w;
   float *w, *h;      // [n_cells]
+  float2 *wh;        // [n_cells] (w, h) interleaved, for the per-cell optimiser kernels
   int *Wq, *Hq;      // [n_cells] quantised sizes
-  float *npins;      // [n_mov] pin count per movable cell
-  float *area;       // [n_mov]
+  float2 *pa;        // [n_mov] (pin count, charge area) per movable cell: the preconditioner's terms
   unsigned char *is_macro;  // [n_cells]
   // density stretching (null when off): per movable cell {x shift, y shift,
   // stretched W, stretched H} in fixed point, the density scale R (2^31 = 1),
@@ -122,11 +122,12 @@ struct Dev {
 
   // per-copy state
   float2 *xy;                // [K][n_cells] reference positions v, interleaved (fixed part replicated)
-  float *ux, *uy;            // [K][n_mov]
-  float *vpx, *vpy;          // [K][n_mov]
-  float *gx[2], *gy[2];      // [K][n_mov] preconditioned gradient, by parity
+  // per-cell (x, y) pairs are interleaved: one 8-byte access per cell
+  float2 *u;                 // [K][n_mov] u_k
+  float2 *vp;                // [K][n_mov] v_{k-1}
+  float2 *g[2];              // [K][n_mov] preconditioned gradient, by parity
   float *gwx, *gwy, *gdx, *gdy;  // [K][n_mov] raw gradients
-  float *upx, *upy;          // [K][n_mov] u_k of the last accepted step (backtracking only)
+  float2 *up;                // [K][n_mov] u_k of the last accepted step (backtracking only)
   unsigned long long *gacc;  // [K][n_mov] WA gradient sums, two int32 fixed-point
                              // values packed as y * 2^32 + x (see add_pin_grad)
   unsigned long long *M;     // [K][Gm]: movable-cell map, then (fillers) the fillers' map

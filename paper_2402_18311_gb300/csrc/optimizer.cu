@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_cell_grad(Dev d, int copy0, int
   unsigned long long *ga = d.gacc + cm;
   const float *ex = d.E + (size_t)c * 3 * d.G, *ey = ex + d.G;
   float n1 = 0.f, d1 = 0.f, dg2 = 0.f, dv2 = 0.f;
-  const float *gxo = d.gx[par ^ 1] + cm, *gyo = d.gy[par ^ 1] + cm;
+  const float2 *wh = d.wh, *pa = d.pa, *go = d.g[par ^ 1] + cm, *vp = d.vp + cm;
   // every load of the next cell is issued while this cell's field gather is
   // in flight (the gather depends on the position): two cells' loads per
   // thread in flight, at 80 registers and three blocks per SM (measured on
@@ -122,28 +122,25 @@ __global__ void __launch_bounds__(kThreads, 3) k_cell_grad(Dev d, int copy0, int
   // position prefetched, or of 40 registers, were slower)
   const int stride = gridDim.x * blockDim.x;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  float2 vnext = i < d.n_mov ? xy[i] : make_float2(0.f, 0.f);
-  float wnext = i < d.n_mov ? d.w[i] : 0.f, hnext = i < d.n_mov ? d.h[i] : 0.f;
+  const float2 zero2 = make_float2(0.f, 0.f);
+  float2 vnext = i < d.n_mov ? xy[i] : zero2, whn = i < d.n_mov ? wh[i] : zero2;
   unsigned long long gsn = i < d.n_mov ? ga[i] : 0ull;
-  float npn = 0.f, arn = 0.f, gxpn = 0.f, gypn = 0.f, vpxn = 0.f, vpyn = 0.f;
+  float2 pan = zero2, gon = zero2, vpn = zero2;
   if (full && i < d.n_mov) {
-    npn = d.npins[i]; arn = d.area[i]; gxpn = gxo[i]; gypn = gyo[i];
-    vpxn = d.vpx[cm + i]; vpyn = d.vpy[cm + i];
+    pan = pa[i]; gon = go[i]; vpn = vp[i];
   }
   for (; i < d.n_mov; i += stride) {
     const unsigned long long gs = gsn;
     const float2 vi = vnext;
-    const float wi = wnext, hi = hnext;
-    const float np = npn, ar = arn, gxp = gxpn, gyp = gypn, vpx = vpxn, vpy = vpyn;
+    const float wi = whn.x, hi = whn.y;
+    const float np = pan.x, ar = pan.y, gxp = gon.x, gyp = gon.y, vpx = vpn.x, vpy = vpn.y;
     const int in = i + stride;
     if (in < d.n_mov) {
       vnext = xy[in];
-      wnext = d.w[in];
-      hnext = d.h[in];
+      whn = wh[in];
       gsn = ga[in];
       if (full) {
-        npn = d.npins[in]; arn = d.area[in]; gxpn = gxo[in]; gypn = gyo[in];
-        vpxn = d.vpx[cm + in]; vpyn = d.vpy[cm + in];
+        pan = pa[in]; gon = go[in]; vpn = vp[in];
       }
     }
     ga[i] = 0ull;
@@ -213,8 +210,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_cell_grad(Dev d, int copy0, int
     if (full) {
       const float rP = 1.f / fmaxf(1.f, np + lam * ar);
       const float gx = (sx + lam * dx) * rP, gy = (sy + lam * dy) * rP;
-      d.gx[par][cm + i] = gx;
-      d.gy[par][cm + i] = gy;
+      d.g[par][cm + i] = make_float2(gx, gy);
       const float ax = gx - gxp, ay = gy - gyp;
       dg2 += ax * ax + ay * ay;
       const float bx = xi - vpx, by = yi - vpy;
@@ -280,11 +276,11 @@ __global__ void __launch_bounds__(kThreads) k_precond0(Dev d, int copy0) {
   const size_t cm = (size_t)c * d.n_mov;
   float g2 = 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
-    float P = fmaxf(1.f, d.npins[i] + lam * d.area[i]);
+    const float2 q = d.pa[i];
+    float P = fmaxf(1.f, q.x + lam * q.y);
     float gx = (d.gwx[cm + i] + lam * d.gdx[cm + i]) / P;
     float gy = (d.gwy[cm + i] + lam * d.gdy[cm + i]) / P;
-    d.gx[par][cm + i] = gx;
-    d.gy[par][cm + i] = gy;
+    d.g[par][cm + i] = make_float2(gx, gy);
     g2 += gx * gx + gy * gy;
   }
   const double r = block_sum_fc<kThreads>(g2, smc);
@@ -315,20 +311,19 @@ __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
   const int par = cs->parity;
   const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
-    const float xh = d.fxh - d.w[i], yh = d.fyh - d.h[i];
+    const float2 s = d.wh[i];
+    const float xh = d.fxh - s.x, yh = d.fyh - s.y;
     const float2 v = d.xy[cn + i];
     const float vx = v.x, vy = v.y;
-    const float ux = d.ux[cm + i], uy = d.uy[cm + i];
-    float nux = fmaxf(d.fxl, fminf(vx - alpha * d.gx[par][cm + i], xh));
-    float nuy = fmaxf(d.fyl, fminf(vy - alpha * d.gy[par][cm + i], yh));
+    const float2 u = d.u[cm + i], g = d.g[par][cm + i];
+    const float ux = u.x, uy = u.y;
+    float nux = fmaxf(d.fxl, fminf(vx - alpha * g.x, xh));
+    float nuy = fmaxf(d.fyl, fminf(vy - alpha * g.y, yh));
     float nvx = fmaxf(d.fxl, fminf(nux + coef * (nux - ux), xh));
     float nvy = fmaxf(d.fyl, fminf(nuy + coef * (nuy - uy), yh));
-    d.vpx[cm + i] = vx; d.vpy[cm + i] = vy;
-    if constexpr (KEEP_U) {
-      d.upx[cm + i] = ux;
-      d.upy[cm + i] = uy;
-    }
-    d.ux[cm + i] = nux; d.uy[cm + i] = nuy;
+    d.vp[cm + i] = v;
+    if constexpr (KEEP_U) d.up[cm + i] = u;
+    d.u[cm + i] = make_float2(nux, nuy);
     d.xy[cn + i] = make_float2(nvx, nvy);
   }
   if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_UPDATE, &flag)) return;
@@ -365,14 +360,15 @@ __global__ void __launch_bounds__(kThreads) k_redo_step(Dev d, int copy0) {
   const float alpha = (float)cs->alpha, coef = (float)cs->coef;
   const int par = cs->parity;
   const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
-  const float *gxo = d.gx[par ^ 1] + cm, *gyo = d.gy[par ^ 1] + cm;
+  const float2 *go = d.g[par ^ 1] + cm;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
-    const float xh = d.fxh - d.w[i], yh = d.fyh - d.h[i];
-    const float vx = d.vpx[cm + i], vy = d.vpy[cm + i];
-    const float ux = d.upx[cm + i], uy = d.upy[cm + i];
-    const float nux = fmaxf(d.fxl, fminf(vx - alpha * gxo[i], xh));
-    const float nuy = fmaxf(d.fyl, fminf(vy - alpha * gyo[i], yh));
-    d.ux[cm + i] = nux; d.uy[cm + i] = nuy;
+    const float2 s = d.wh[i];
+    const float xh = d.fxh - s.x, yh = d.fyh - s.y;
+    const float2 v = d.vp[cm + i], u = d.up[cm + i], g = go[i];
+    const float vx = v.x, vy = v.y, ux = u.x, uy = u.y;
+    const float nux = fmaxf(d.fxl, fminf(vx - alpha * g.x, xh));
+    const float nuy = fmaxf(d.fyl, fminf(vy - alpha * g.y, yh));
+    d.u[cm + i] = make_float2(nux, nuy);
     d.xy[cn + i] = make_float2(fmaxf(d.fxl, fminf(nux + coef * (nux - ux), xh)),
                                fmaxf(d.fyl, fminf(nuy + coef * (nuy - uy), yh)));
   }
@@ -393,7 +389,7 @@ __global__ void __launch_bounds__(kThreads) k_reset(Dev d, int copy0) {
     float vx = fmaxf(d.fxl, fminf(v.x, d.fxh - d.w[i]));
     float vy = fmaxf(d.fyl, fminf(v.y, d.fyh - d.h[i]));
     d.xy[cn + i] = make_float2(vx, vy);
-    d.ux[cm + i] = vx; d.uy[cm + i] = vy;
+    d.u[cm + i] = make_float2(vx, vy);
     d.gacc[cm + i] = 0ull;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -463,7 +459,7 @@ void launch_precond0(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
 }
 void launch_update(const Dev &d, int copy0, int ncopy, cudaStream_t st) {
   const dim3 grid(d.cell_blocks, ncopy);
-  if (d.upx) {
+  if (d.up) {
     launch_pdl(k_update<true>, grid, dim3(kThreads), 0, st, d, copy0);
     launch_pdl(k_redo_step, grid, dim3(kThreads), 0, st, d, copy0);
   } else {

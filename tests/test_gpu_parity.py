@@ -1031,8 +1031,12 @@ def test_tuning_candidates_give_identical_results():
             h.close()
         if ref is None:
             ref = out
-            # the placement crossed the scatter's phases
-            assert ref[0][3] < 32 and ref[-1][3] > 1024, [r[3] for r in ref]
+            # the placement crossed the scatter's phases: dense at the start,
+            # spread at some sampled point (n_eff need not grow monotonically
+            # on this small design: it falls again late in the placement, by
+            # an amount that depends on the chaotic trajectory)
+            ne = [r[3] for r in ref]
+            assert ne[0] < 32 and max(ne) > 1024, ne
             continue
         for (x, y, gm, _), (rx, ry, rgm, _) in zip(out, ref):
             np.testing.assert_array_equal(x, rx)
