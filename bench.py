@@ -172,11 +172,12 @@ def algorithmic(d, info):
         # (accumulated in L2 by 64-bit reductions, written once)
         "wirelength": {"bytes": 12 * P + 4 * E + 8 * n_all + 8 * C},
         # per cell: gradient sum read 8 + cleared 8, position 8, sizes 8,
-        # field 8, pins/area 8, previous gradient 8, previous position 8,
-        # gradient written 8 (the raw gradients are written only at k = 0)
-        "cellgrad": {"bytes": 72 * C},
-        # read w, h 8, v 8, u 8, g 8; write v_prev 8, u 8, v 8 per cell
-        "update": {"bytes": 56 * C},
+        # field 8, pins/area 8, previous gradient 8, gradient written 8 (the
+        # raw gradients are written only at k = 0)
+        "cellgrad": {"bytes": 64 * C},
+        # read w, h 8, v 8, u 8, g 8; write u 8, v 8 per cell (the step norm
+        # |v_{k+1} - v_k| is reduced here, so v_k is not stored)
+        "update": {"bytes": 48 * C},
     }
 
 

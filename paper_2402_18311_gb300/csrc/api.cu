@@ -294,7 +294,9 @@ void layout(Dev &d, Arena &a, int n_copies) {
   d.Ms = d.prm.stretch ? a.take<unsigned long long>(K * G) : nullptr;
   d.xy = a.take<float2>(K * C);
   d.u = a.take<float2>(K * Mv);
-  d.vp = a.take<float2>(K * Mv);
+  // v_{k-1} is kept only for backtracking (the redone step starts there);
+  // otherwise k_update reduces |v_{k+1} - v_k| itself
+  d.vp = d.prm.max_backtracks > 0 ? a.take<float2>(K * Mv) : nullptr;
   for (int q = 0; q < 2; ++q) d.g[q] = a.take<float2>(K * Mv);
   d.gwx = a.take<float>(K * Mv);
   d.gwy = a.take<float>(K * Mv);
@@ -1491,8 +1493,9 @@ namespace {
 // order of ckpt_arrays (each padded to 8 bytes), then the history ring.
 struct CkptHeader {
   char magic[8];                 // "HYBROCK1"
-  int32_t version;               // 2: the per-cell (x, y) pairs of u, v_prev and g interleaved
+  int32_t version;               // 3: (x, y) pairs interleaved; the step-norm partials
   int32_t n_cells, n_mov, n_real, n_fill, n_nets, n_pins, nx, ny, frac_bits, hist_cap;
+  int32_t norm_blocks;           // step-norm partials saved (blocks of the update kernel)
   int32_t has_up;                // backtracking arrays present
   int32_t state_bytes;           // sizeof(CopyState)
   double dref, w_bin;            // the schedule's reference step and bin size
@@ -1507,13 +1510,18 @@ std::vector<CkptArray> ckpt_arrays(const Dev &d, int c) {
   const size_t C = d.n_cells, Mo = d.n_mov;
   std::vector<CkptArray> v = {
       {d.xy + c * C, sizeof(float2) * C},
-      {d.u + c * Mo, sizeof(float2) * Mo}, {d.vp + c * Mo, sizeof(float2) * Mo},
+      {d.u + c * Mo, sizeof(float2) * Mo},
       {d.g[0] + c * Mo, sizeof(float2) * Mo}, {d.g[1] + c * Mo, sizeof(float2) * Mo},
+      // the last step's |v_k - v_{k-1}|^2 partials (one per update block)
+      {d.part + ((size_t)c * S_COUNT + S_DV2) * d.nb_red, sizeof(double) * d.cell_blocks},
       {d.gwx + c * Mo, sizeof(float) * Mo}, {d.gwy + c * Mo, sizeof(float) * Mo},
       {d.gdx + c * Mo, sizeof(float) * Mo}, {d.gdy + c * Mo, sizeof(float) * Mo},
       {d.gacc + c * Mo, sizeof(unsigned long long) * Mo},
       {d.hist + (size_t)c * d.hist_cap, sizeof(place_iter_record) * d.hist_cap}};
-  if (d.up) v.push_back({d.up + c * Mo, sizeof(float2) * Mo});
+  if (d.up) {
+    v.push_back({d.vp + c * Mo, sizeof(float2) * Mo});
+    v.push_back({d.up + c * Mo, sizeof(float2) * Mo});
+  }
   return v;
 }
 
@@ -1523,7 +1531,8 @@ CkptHeader ckpt_header(const Dev &d) {
   CkptHeader hd;
   std::memset(&hd, 0, sizeof hd);
   std::memcpy(hd.magic, "HYBROCK1", 8);
-  hd.version = 2;
+  hd.version = 3;
+  hd.norm_blocks = d.cell_blocks;
   hd.n_cells = d.n_cells; hd.n_mov = d.n_mov; hd.n_real = d.n_real; hd.n_fill = d.n_fill;
   hd.n_nets = d.n_nets; hd.n_pins = d.n_pins; hd.nx = d.nx; hd.ny = d.ny;
   hd.frac_bits = d.F; hd.hist_cap = d.hist_cap;

@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_cell_grad(Dev d, int copy0, int
   const float2 *xy = d.xy + cn;
   unsigned long long *ga = d.gacc + cm;
   const float *ex = d.E + (size_t)c * 3 * d.G, *ey = ex + d.G;
-  float n1 = 0.f, d1 = 0.f, dg2 = 0.f, dv2 = 0.f;
-  const float2 *wh = d.wh, *pa = d.pa, *go = d.g[par ^ 1] + cm, *vp = d.vp + cm;
+  float n1 = 0.f, d1 = 0.f, dg2 = 0.f;
+  const float2 *wh = d.wh, *pa = d.pa, *go = d.g[par ^ 1] + cm;
   // every load of the next cell is issued while this cell's field gather is
   // in flight (the gather depends on the position): two cells' loads per
   // thread in flight, at 80 registers and three blocks per SM (measured on
@@ -125,22 +125,22 @@ __global__ void __launch_bounds__(kThreads, 3) k_cell_grad(Dev d, int copy0, int
   const float2 zero2 = make_float2(0.f, 0.f);
   float2 vnext = i < d.n_mov ? xy[i] : zero2, whn = i < d.n_mov ? wh[i] : zero2;
   unsigned long long gsn = i < d.n_mov ? ga[i] : 0ull;
-  float2 pan = zero2, gon = zero2, vpn = zero2;
+  float2 pan = zero2, gon = zero2;
   if (full && i < d.n_mov) {
-    pan = pa[i]; gon = go[i]; vpn = vp[i];
+    pan = pa[i]; gon = go[i];
   }
   for (; i < d.n_mov; i += stride) {
     const unsigned long long gs = gsn;
     const float2 vi = vnext;
     const float wi = whn.x, hi = whn.y;
-    const float np = pan.x, ar = pan.y, gxp = gon.x, gyp = gon.y, vpx = vpn.x, vpy = vpn.y;
+    const float np = pan.x, ar = pan.y, gxp = gon.x, gyp = gon.y;
     const int in = i + stride;
     if (in < d.n_mov) {
       vnext = xy[in];
       whn = wh[in];
       gsn = ga[in];
       if (full) {
-        pan = pa[in]; gon = go[in]; vpn = vp[in];
+        pan = pa[in]; gon = go[in];
       }
     }
     ga[i] = 0ull;
@@ -213,8 +213,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_cell_grad(Dev d, int copy0, int
       d.g[par][cm + i] = make_float2(gx, gy);
       const float ax = gx - gxp, ay = gy - gyp;
       dg2 += ax * ax + ay * ay;
-      const float bx = xi - vpx, by = yi - vpy;
-      dv2 += bx * bx + by * by;
     }
   }
   // per-thread sums in FP32 (a few cells each), compensated block sums:
@@ -222,22 +220,23 @@ __global__ void __launch_bounds__(kThreads, 3) k_cell_grad(Dev d, int copy0, int
   const double r0 = block_sum_fc<kThreads>(n1, smc);
   const double r1 = block_sum_fc<kThreads>(d1, smc);
   const double r2 = block_sum_fc<kThreads>(dg2, smc);
-  const double r3 = block_sum_fc<kThreads>(dv2, smc);
   if (threadIdx.x == 0) {
     part_ptr(d, c, S_GW1)[blockIdx.x] = r0;
     part_ptr(d, c, S_GD1)[blockIdx.x] = r1;
     part_ptr(d, c, S_DG2)[blockIdx.x] = r2;
-    part_ptr(d, c, S_DV2)[blockIdx.x] = r3;
   }
   if (eval) return;
   if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_CELL, &flag)) return;
   const int wa_slots[2] = {S_HPWL, S_WL};
-  const int cg_slots[4] = {S_GW1, S_GD1, S_DG2, S_DV2};
-  double wa_sum[2], cg_sum[4];
+  const int cg_slots[3] = {S_GW1, S_GD1, S_DG2};
+  double wa_sum[2], cg_sum[3];
   sum_slots<kThreads, 2>(d, c, wa_slots, d.wa_blocks_total, wa_sum, smd);
-  sum_slots<kThreads, 4>(d, c, cg_slots, gridDim.x, cg_sum, smd);
+  sum_slots<kThreads, 3>(d, c, cg_slots, gridDim.x, cg_sum, smd);
+  // |v_k - v_{k-1}|^2: the partials of the step that led here (k_update or
+  // k_redo_step, one per block of their grid)
+  const double s4 = k > 0 ? sum_slot<kThreads>(d, c, S_DV2, d.cell_blocks, smd) : 0.0;
   const double hp = wa_sum[0], wl = wa_sum[1];
-  const double s1 = cg_sum[0], s2 = cg_sum[1], s3 = cg_sum[2], s4 = cg_sum[3];
+  const double s1 = cg_sum[0], s2 = cg_sum[1], s3 = cg_sum[2];
   if (threadIdx.x == 0) {
     cs->hpwl = hp;
     cs->wl = wl;
@@ -300,6 +299,7 @@ __global__ void __launch_bounds__(kThreads) k_precond0(Dev d, int copy0) {
 template <bool KEEP_U>
 __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
   __shared__ int flag;
+  __shared__ float2 smc[32];
   pdl_wait();
   const int c = copy0 + blockIdx.y;
   CopyState *cs = d.cs + c;
@@ -310,6 +310,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
   const float alpha = (float)cs->alpha, coef = (float)cs->coef;
   const int par = cs->parity;
   const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
+  float dv2 = 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
     const float2 s = d.wh[i];
     const float xh = d.fxh - s.x, yh = d.fyh - s.y;
@@ -321,11 +322,19 @@ __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
     float nuy = fmaxf(d.fyl, fminf(vy - alpha * g.y, yh));
     float nvx = fmaxf(d.fxl, fminf(nux + coef * (nux - ux), xh));
     float nvy = fmaxf(d.fyl, fminf(nuy + coef * (nuy - uy), yh));
-    d.vp[cm + i] = v;
-    if constexpr (KEEP_U) d.up[cm + i] = u;
+    if constexpr (KEEP_U) {  // a rejected next step restarts from v_k and u_k
+      d.vp[cm + i] = v;
+      d.up[cm + i] = u;
+    }
     d.u[cm + i] = make_float2(nux, nuy);
     d.xy[cn + i] = make_float2(nvx, nvy);
+    const float bx = nvx - vx, by = nvy - vy;
+    dv2 += bx * bx + by * by;
   }
+  // |v_{k+1} - v_k|^2 per block, for the next iteration's step length: the
+  // update knows both points, so v_k need not be stored and read back
+  const double r = block_sum_fc<kThreads>(dv2, smc);
+  if (threadIdx.x == 0) part_ptr(d, c, S_DV2)[blockIdx.x] = r;
   if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_UPDATE, &flag)) return;
   if (threadIdx.x == 0) {
     // the iteration's record: its HPWL (WA pass) and overflow at v_k, the
@@ -353,6 +362,7 @@ __global__ void __launch_bounds__(kThreads) k_update(Dev d, int copy0) {
 // buffer parity stay.  Launched after k_update on handles with backtracking.
 __global__ void __launch_bounds__(kThreads) k_redo_step(Dev d, int copy0) {
   __shared__ int flag;
+  __shared__ float2 smc[32];
   pdl_wait();
   const int c = copy0 + blockIdx.y;
   CopyState *cs = d.cs + c;
@@ -361,6 +371,7 @@ __global__ void __launch_bounds__(kThreads) k_redo_step(Dev d, int copy0) {
   const int par = cs->parity;
   const size_t cn = (size_t)c * d.n_cells, cm = (size_t)c * d.n_mov;
   const float2 *go = d.g[par ^ 1] + cm;
+  float dv2 = 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_mov; i += gridDim.x * blockDim.x) {
     const float2 s = d.wh[i];
     const float xh = d.fxh - s.x, yh = d.fyh - s.y;
@@ -369,9 +380,14 @@ __global__ void __launch_bounds__(kThreads) k_redo_step(Dev d, int copy0) {
     const float nux = fmaxf(d.fxl, fminf(vx - alpha * g.x, xh));
     const float nuy = fmaxf(d.fyl, fminf(vy - alpha * g.y, yh));
     d.u[cm + i] = make_float2(nux, nuy);
-    d.xy[cn + i] = make_float2(fmaxf(d.fxl, fminf(nux + coef * (nux - ux), xh)),
-                               fmaxf(d.fyl, fminf(nuy + coef * (nuy - uy), yh)));
+    const float nvx = fmaxf(d.fxl, fminf(nux + coef * (nux - ux), xh));
+    const float nvy = fmaxf(d.fyl, fminf(nuy + coef * (nuy - uy), yh));
+    d.xy[cn + i] = make_float2(nvx, nvy);
+    const float bx = nvx - vx, by = nvy - vy;
+    dv2 += bx * bx + by * by;
   }
+  const double r = block_sum_fc<kThreads>(dv2, smc);  // the redone step's |v_k - v_{k-1}|^2
+  if (threadIdx.x == 0) part_ptr(d, c, S_DV2)[blockIdx.x] = r;
   if (!arrive_last(d.ctr + (size_t)c * C_COUNT + C_UPDATE, &flag)) return;
   if (threadIdx.x == 0) {
     cs->reject = 0;
