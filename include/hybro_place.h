@@ -179,7 +179,8 @@ typedef struct place_info {
   int64_t bin_w_q, bin_h_q; /* bin size in units of 2^-F */
   double bin_w, bin_h;
   int64_t device_bytes;   /* device memory the handle holds */
-  int32_t kernels_per_iter; /* this library's kernel launches in one iteration */
+  int32_t kernels_per_iter; /* this library's kernel launches in one iteration (the first
+                              iteration after a reset adds one: k_precond0) */
   int32_t dct_mode;       /* the spectral path in use: PLACE_DCT_FP32 or _BF16X3 */
   int32_t n_fillers;      /* filler cells (0 unless params.fillers) */
   int32_t bounds_checked; /* 1: the library was built with index checks

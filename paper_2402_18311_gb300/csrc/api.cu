@@ -201,6 +201,12 @@ struct place_t {
   size_t mem_bytes = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // the same iteration with the k = 0 preconditioning pass (k_precond0),
+  // launched for the first iteration after a reset of any copy; `exec`
+  // leaves that pass out, where it would only find every copy past k = 0
+  cudaGraph_t graph0 = nullptr;
+  cudaGraphExec_t exec0 = nullptr;
+  bool k0_pending = true;
   CUtensorMap maps[16];              // tensor maps of the tcgen05 spectral path
   int n_cand_all = 0, n_cand_macro = 0;
   // WireMask: host tables built at create, device copy made on first use
@@ -256,6 +262,8 @@ int place_destroy(place_t *h) {
   cudaStreamSynchronize(h->stream);  // no work of this handle may still run
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->exec0) cudaGraphExecDestroy(h->exec0);
+  if (h->graph0) cudaGraphDestroy(h->graph0);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->cap2) cudaStreamDestroy(h->cap2);
   if (h->cap3) cudaStreamDestroy(h->cap3);
@@ -449,12 +457,15 @@ int encode_tc_maps_cb(void *ctx) { return encode_tc_maps(static_cast<TuneCtx *>(
 void drop_graph(place_t *h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
-  h->exec = nullptr;
-  h->graph = nullptr;
+  if (h->exec0) cudaGraphExecDestroy(h->exec0);
+  if (h->graph0) cudaGraphDestroy(h->graph0);
+  h->exec = h->exec0 = nullptr;
+  h->graph = h->graph0 = nullptr;
 }
 
 int enqueue_reset(place_t *h, int c0, int n);
 int ensure_graph(place_t *h);
+cudaError_t launch_iter(place_t *h);
 
 // Every copy back at the start, a graph captured for the current device
 // state, two warm-up iterations, then n timed ones: ms per iteration
@@ -477,9 +488,9 @@ float time_iters_cb(void *ctx, int n) {
     cudaEventDestroy(e0);
     return -1.f;
   }
-  for (int i = 0; i < 2; ++i) cudaGraphLaunch(h->exec, h->stream);
+  for (int i = 0; i < 2; ++i) launch_iter(h);
   cudaEventRecord(e0, h->stream);
-  for (int i = 0; i < n; ++i) cudaGraphLaunch(h->exec, h->stream);
+  for (int i = 0; i < n; ++i) launch_iter(h);
   cudaEventRecord(e1, h->stream);
   float ms = -1.f;
   if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
@@ -526,6 +537,7 @@ int check_dev_err(place_t *h) {
 int enqueue_reset(place_t *h, int c0, int n) {
   Dev &d = h->d;
   cudaStream_t st = h->stream;
+  h->k0_pending = true;  // the next iteration preconditions these copies' first step
   launch_reset(d, c0, n, st);
   CK(cudaMemsetAsync(d.M + (size_t)c0 * d.Gm, 0, sizeof(unsigned long long) * d.Gm * n, st));
   launch_scatter(d, c0, n, 1, st);
@@ -540,7 +552,7 @@ int enqueue_reset(place_t *h, int c0, int n) {
 // them) beside the density scatter and the tensor-core Poisson solve, and
 // join before the per-cell gradient.
 void enqueue_iteration(const Dev &d, cudaStream_t st, const cudaStream_t *wst, cudaEvent_t fork,
-                       const cudaEvent_t *join) {
+                       const cudaEvent_t *join, bool with_precond0) {
   const int K = d.K;
   const int nb = std::max(1, std::min(d.wa_streams, kMaxWaStreams));
   cudaEventRecord(fork, st);
@@ -553,22 +565,37 @@ void enqueue_iteration(const Dev &d, cudaStream_t st, const cudaStream_t *wst, c
   launch_spectral(d, 0, K, 0, 0, st);
   for (int b = 0; b < nb; ++b) cudaStreamWaitEvent(st, join[b], 0);
   launch_cell_grad(d, 0, K, 0, st);
-  launch_precond0(d, 0, K, st);
+  if (with_precond0) launch_precond0(d, 0, K, st);
   launch_update(d, 0, K, st);
 }
 
 int ensure_graph(place_t *h) {
-  if (h->exec) return PLACE_OK;
-  CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  if (h->exec && h->exec0) return PLACE_OK;
+  drop_graph(h);
   const cudaStream_t wst[kMaxWaStreams] = {h->cap2, h->cap3, h->cap4};
   const cudaEvent_t joins[kMaxWaStreams] = {h->ev_join, h->ev_join2, h->ev_join3};
-  enqueue_iteration(h->d, h->cap, wst, h->ev_fork, joins);
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamEndCapture(h->cap, &g);
-  if (e != cudaSuccess) return fail(PLACE_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
-  h->graph = g;
-  CK(cudaGraphInstantiate(&h->exec, g, 0));
+  for (int with0 = 0; with0 < 2; ++with0) {
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    enqueue_iteration(h->d, h->cap, wst, h->ev_fork, joins, with0 != 0);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    if (e != cudaSuccess) return fail(PLACE_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    (with0 ? h->graph0 : h->graph) = g;
+    CK(cudaGraphInstantiate(with0 ? &h->exec0 : &h->exec, g, 0));
+  }
   return PLACE_OK;
+}
+
+// One iteration of every copy: the graph with the k = 0 preconditioning pass
+// when a reset since the last iteration may have left a copy at k = 0, the
+// one without it otherwise (the two compute the same: the pass does nothing
+// for a copy past k = 0).  ensure_graph must have succeeded.
+cudaError_t launch_iter(place_t *h) {
+  if (h->k0_pending) {
+    h->k0_pending = false;
+    return cudaGraphLaunch(h->exec0, h->stream);
+  }
+  return cudaGraphLaunch(h->exec, h->stream);
 }
 
 // Interleaved device positions -> caller's x, y (host or device) through the
@@ -1252,7 +1279,8 @@ int place_get_info(const place_t *h, place_info *o) {
   for (int c = 0; c < d.n_cls; ++c) wa += d.wa_blocks[c] > 0;
   // scatter, finish, 4 GEMMs, WA classes, cell grad, precond0, update; the
   // stretched scatter with density stretching, the step redo with backtracking
-  o->kernels_per_iter = 2 + 4 + wa + 3 + (d.Ms ? 1 : 0) + (d.up ? 1 : 0);
+  // the steady graph (the first iteration after a reset adds k_precond0)
+  o->kernels_per_iter = 2 + 4 + wa + 2 + (d.Ms ? 1 : 0) + (d.up ? 1 : 0);
   o->dct_mode = d.tc ? PLACE_DCT_BF16X3 : PLACE_DCT_FP32;
   for (int s = 0; s < 4; ++s) {
     o->gemm_bn[s] = d.tc ? d.tc_bn[s] : 0;
@@ -1275,7 +1303,7 @@ int place_step(place_t *h, int32_t n_iters, int32_t *converged) {
   if (n_iters > 0) {
     int rc = ensure_graph(h);
     if (rc) return rc;
-    for (int i = 0; i < n_iters; ++i) CK(cudaGraphLaunch(h->exec, h->stream));
+    for (int i = 0; i < n_iters; ++i) CK(launch_iter(h));
   }
   if (converged) {
     std::vector<CopyState> cs(h->d.K);
@@ -1299,7 +1327,7 @@ int place_step_multi(place_t *const *hs, int32_t n, int32_t n_iters, int32_t *co
       if (rc) return rc;
     }
     for (int it = 0; it < n_iters; ++it)
-      for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(hs[i]->exec, hs[i]->stream));
+      for (int i = 0; i < n; ++i) CK(launch_iter(hs[i]));
   }
   if (converged) {
     int off = 0;
@@ -1607,6 +1635,7 @@ int place_checkpoint_load(place_t *h, int32_t copy, const void *buf, int64_t byt
     CK(cudaMemcpyAsync(a.dev, p, a.bytes, cudaMemcpyHostToDevice, h->stream));
     p += pad8(a.bytes);
   }
+  h->k0_pending = true;  // the loaded state may be at k = 0
   CK(cudaStreamSynchronize(h->stream));
   return check_dev_err(h);
 }
@@ -1992,7 +2021,7 @@ int step_async(place_t *h, int n, int *stopped_host, cudaEvent_t ev) {
   if (n > 0) {
     int rc = ensure_graph(h);
     if (rc) return rc;
-    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(h->exec, h->stream));
+    for (int i = 0; i < n; ++i) CK(launch_iter(h));
   }
   for (int c = 0; c < h->d.K; ++c)
     CK(cudaMemcpyAsync(stopped_host + c, &h->d.cs[c].stopped, sizeof(int), cudaMemcpyDeviceToHost,
