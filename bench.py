@@ -235,6 +235,9 @@ def run_ours(args):
     nprof = max(3, min(args.steps, 20))
     place.place_step_timed(h, nprof, stage_ms)
     stage_ms /= nprof
+    # the WA stage's gather-and-reduce floor on this netlist: only the pin
+    # streams, one position gather and one 64-bit reduction per pin
+    wa_floor_ms = place.place_measure_wa_floor(h, 10)
 
     # end to end through the C ABI with pinned host buffers: every step uploads
     # the movable positions (place_set_positions, which restarts the optimiser
@@ -316,6 +319,14 @@ def run_ours(args):
                 "algorithmic": alg[dn], "peak_source": peak_note, "stages": per,
                 "traffic_note": "DRAM bytes of one pass of the stage from the committed ncu "
                                 "capture (cold L2), null if the kernel source changed since"}
+    if dn == "wirelength" and wa_floor_ms > 0:
+        # random 32-byte sector accesses in L2, not HBM bytes, bound this
+        # index stream: the floor's rate is what the stage can approach
+        roofline["floor"] = {"ms": wa_floor_ms,
+                             "GB/s": alg[dn]["bytes"] / (wa_floor_ms / 1e3) / 1e9,
+                             "stage_frac_of_floor_rate": wa_floor_ms / float(stage_ms[dom]),
+                             "what": "place_measure_wa_floor: pin streams, one random position "
+                                     "gather and one random 64-bit reduction per pin"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(d, args)

@@ -186,6 +186,26 @@ def test_checkpoint_rejects_another_design_and_short_buffers():
         place.place_destroy(a)
 
 
+def test_wa_floor_measurement_leaves_the_placement_unchanged():
+    # The gather-and-reduce floor of the WA stage adds into the gradient sums
+    # and clears them again: a placement measured between two steps goes on
+    # bit for bit as one that was not.
+    d = synth.scaled(20000, 128, seed=2)
+    out = []
+    for measure in (False, True):
+        h = place.place_create(d, place.place_default_params(tau_stop=-1.0, max_iters=10 ** 6))
+        try:
+            place.place_step(h, 20)
+            if measure:
+                assert place.place_measure_wa_floor(h, 5) > 0
+            place.place_step(h, 20)
+            out.append(_positions(h, d.n_cells))
+        finally:
+            place.place_destroy(h)
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
 def test_scatter_floor_measurement_leaves_the_map_to_the_next_pass():
     d = synth.scaled(20000, 128, seed=2)
     h = place.place_create(d, place.place_default_params(tau_stop=-1.0, max_iters=10 ** 6))
