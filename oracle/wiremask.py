@@ -38,9 +38,12 @@ The reading used here:
   position before it moves.  With no such candidate the macro stays where it
   is.  Either way it becomes an obstacle for the macros after it.
 
-Every comparison is on float64 values produced by the same sequence of
-correctly rounded operations as in the CUDA library, so the chosen
-positions are bit-exact.
+Every comparison is on float64 values from a fixed sequence of correctly
+rounded operations (each axis's mask summed over the macro's nets in
+increasing net index, each extent and corner formed as written above), so
+any implementation that evaluates these expressions in this order chooses
+bit-identical positions; the brute-force pins in the tests check the choice
+against the Eq. 1 HPWL itself.
 """
 from __future__ import annotations
 
