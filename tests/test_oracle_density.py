@@ -165,3 +165,19 @@ def test_stretched_gradient_in_a_uniform_field_is_minus_area_times_field():
     area = (W * H).astype(np.float64) * 2.0 ** (-2 * g.F)
     np.testing.assert_allclose(wgt * gx, -0.75 * area, rtol=1e-12)
     np.testing.assert_allclose(wgt * gy, 2.0 * area, rtol=1e-12)
+
+
+def test_scaled_term_is_the_exact_floored_product():
+    # floor(ov R / 2^31) against Python's unbounded integers, at the edges
+    # of its range and on random values
+    rng = np.random.default_rng(5)
+    ov = [0, 1, (1 << 31) - 1, 1 << 31, (1 << 62) - 1, (1 << 40) + 12345]
+    R = [0, 1, (1 << 31) - 1, 1 << 31, 1 << 30, 3]
+    ov += [int(v) for v in rng.integers(0, 1 << 62, 200, dtype=np.int64)]
+    R += [int(v) for v in rng.integers(0, (1 << 31) + 1, 200, dtype=np.int64)]
+    for a in ov:
+        for r in (R[:6] if a not in ov[:6] else R):
+            assert int(dens.scaled_term(a, r)) == (a * r) >> 31, (a, r)
+    # R = 2^31 leaves every term whole, R = 0 removes it
+    assert int(dens.scaled_term((1 << 62) - 1, 1 << 31)) == (1 << 62) - 1
+    assert int(dens.scaled_term((1 << 62) - 1, 0)) == 0

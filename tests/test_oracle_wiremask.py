@@ -202,3 +202,30 @@ def test_weighted_mask_is_weighted_total_hpwl_up_to_a_constant():
             tot = hpwl(d.net_ptr, d.pin_cell, d.pin_dx, d.pin_dy, xx, yy, net_w=net_w)
             diffs.append(tot - (fx[i] + fy[j]))
     assert np.ptp(diffs) <= 1e-9 * abs(max(diffs, key=abs))
+
+
+def test_nets_of_lists_each_net_of_a_cell_once_in_order():
+    # nets: 0 = {0, 1}, 1 = {2, 3}, 2 = {1, 1, 4} (cell 1 twice), 3 = {1}
+    net_ptr = [0, 2, 4, 7, 8]
+    pin_cell = [0, 1, 2, 3, 1, 1, 4, 1]
+    assert wm.nets_of(net_ptr, pin_cell, 1) == [0, 2, 3]
+    assert wm.nets_of(net_ptr, pin_cell, 2) == [1]
+    assert wm.nets_of(net_ptr, pin_cell, 5) == []
+
+
+def test_axis_mask_is_each_nets_extent_with_the_macro_at_the_corner():
+    # one axis, macro m = 0 with pins at offsets 1 and 3; net 0 joins it to
+    # cells at 10 and 4 (offsets 0.5, 0); net 1 to nothing else; net 2 is
+    # another cell's only (weight 2 for net 0 checks the weighting)
+    net_ptr = [0, 4, 5]
+    pin_cell = [0, 1, 0, 2, 0]
+    pin_d = np.array([1.0, 0.5, 3.0, 0.0, 2.0])
+    pos = np.array([0.0, 10.0, 4.0])
+    corners = np.array([0.0, 2.0, 8.0, 20.0])
+    got = wm.axis_mask(corners, [0, 1], net_ptr, pin_cell, pin_d, pos, 0, np.array([2.0, 1.0]))
+    want = []
+    for c in corners:
+        # net 0: points c+1, c+3 (macro), 10.5, 4; net 1: the single point c+2
+        pts = [c + 1, c + 3, 10.5, 4.0]
+        want.append(2.0 * (max(pts) - min(pts)) + 0.0)
+    np.testing.assert_array_equal(got, np.array(want))
